@@ -1,0 +1,160 @@
+"""Plain FP64 CPU oracle for Gaussian belief propagation on Ax = b.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the package's ``smoke()``
+check and the benchmark's CPU-baseline leg may import this package.  It
+shares no code with the CUDA library (``paper_0810_1119_gb300``) and never
+imports it; the CUDA library never imports this package.
+
+Contents
+--------
+* ``gabp``          -- synchronous GaBP from zero messages in one of three
+                       variants: the broadcast form (Algorithm 2), the naive
+                       form (Algorithm 1) and the Jacobi reduction (GaBP/Jacobi
+                       proposition, Section VI-C).  C code in ``gabp_oracle.c``.
+* ``residual_inf``  -- ||b - A x||_inf (Section II, residual definition).
+* ``augment_lsq``   -- the symmetric augmented system of Section VII
+                       (``augment.py``).
+
+Every function is pinned by CPU tests (``tests/test_oracle_*.py``) to values
+the paper prints, closed forms and brute force -- not to itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+from .augment import augment_lsq  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gabp_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BROADCAST, NAIVE, JACOBI = 0, 1, 2
+STOP_FIXED, STOP_MSG, STOP_RES_ABS, STOP_RES_REL = 0, 1, 2, 3
+STATUS = {0: "ok", 1: "bad_input", 2: "breakdown", 3: "not_converged"}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``gabp_oracle.c`` with gcc into ``_build/liboracle.so``.
+
+    IEEE semantics are kept: no fast-math and no FMA contraction, so the
+    oracle rounds the same way on every host.
+    """
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _bind(lib):
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    f64p = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_gabp.restype = ctypes.c_int
+    lib.oracle_gabp.argtypes = [ctypes.c_int, ctypes.c_int64, i64p, i32p, f64p, f64p,
+                                ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                f64p, f64p, f64p, f64p, ctypes.POINTER(ctypes.c_int)]
+    lib.oracle_residual_inf.restype = ctypes.c_double
+    lib.oracle_residual_inf.argtypes = [ctypes.c_int64, i64p, i32p, f64p, f64p, f64p, f64p]
+    lib.oracle_num_threads.restype = ctypes.c_int
+    lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def compile_variant(source: str, out_path: str):
+    """Compile an edited copy of the oracle source (used by the tests that
+    plant a mistake in the oracle and check that its pins catch it)."""
+    src = out_path + ".c"
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", src, "-o", out_path, "-lm"], check=True)
+    return _bind(ctypes.CDLL(out_path))
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype)) if a is not None else None
+
+
+def _csr_arrays(row_ptr, col, val):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    return row_ptr, col, val
+
+
+def gabp(row_ptr, col, val, b, *, variant=BROADCAST, stop=STOP_FIXED, max_rounds=1,
+         tol=0.0, want_messages=False, lib=None):
+    """Synchronous GaBP from zero messages on the CSR matrix (row_ptr, col, val).
+
+    The CSR holds the full symmetric matrix with its diagonal and sorted
+    columns.  Returns a dict with ``x`` (tentative means after the last
+    round), ``Pi`` (marginal precisions), ``rounds``, ``status`` and, if
+    ``want_messages``, ``P`` and ``mu``: the last round's message i -> j at
+    the CSR position of entry (i, j) (zero on the diagonal).  In the Jacobi
+    variant ``mu`` holds the product P_ij mu_ij, as the proposition carries it.
+    """
+    row_ptr, col, val = _csr_arrays(row_ptr, col, val)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = row_ptr.shape[0] - 1
+    nnz = int(row_ptr[-1])
+    x = np.empty(n)
+    Pi = np.empty(n)
+    P = np.empty(nnz) if want_messages else None
+    mu = np.empty(nnz) if want_messages else None
+    rounds = ctypes.c_int(0)
+    st = (lib or _load()).oracle_gabp(variant, n, _ptr(row_ptr, ctypes.c_int64), _ptr(col, ctypes.c_int32),
+                             _ptr(val, ctypes.c_double), _ptr(b, ctypes.c_double), stop,
+                             int(max_rounds), float(tol), _ptr(x, ctypes.c_double),
+                             _ptr(Pi, ctypes.c_double), _ptr(P, ctypes.c_double),
+                             _ptr(mu, ctypes.c_double), ctypes.byref(rounds))
+    out = {"x": x, "Pi": Pi, "rounds": rounds.value, "status": STATUS[st]}
+    if want_messages:
+        out["P"], out["mu"] = P, mu
+    return out
+
+
+def residual_inf(row_ptr, col, val, b, x):
+    """||b - A x||_inf computed row by row in FP64."""
+    row_ptr, col, val = _csr_arrays(row_ptr, col, val)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = row_ptr.shape[0] - 1
+    return float(_load().oracle_residual_inf(n, _ptr(row_ptr, ctypes.c_int64),
+                                             _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double),
+                                             _ptr(b, ctypes.c_double), _ptr(x, ctypes.c_double),
+                                             None))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    _load().oracle_set_num_threads(int(k))

@@ -1,0 +1,72 @@
+"""Plant plausible mistakes in a copy of the oracle and check that its pins
+catch every one.
+
+Each mutant is the oracle's C source with one edit (a sign, a dropped term, a
+transposed operand, a wrong divisor), compiled to a temporary library on the
+CPU.  The pins are the same kinds of facts as in test_oracle_pins.py: the
+paper's toy-tree tables, exact tree convergence and dense LU on loopy graphs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1119_gb300 import workloads as W
+from golden_io import toy_tree
+
+MUTANTS = {
+    "precision_sign": ("Pn[e] = -Aij * Aij / denom;", "Pn[e] = Aij * Aij / denom;"),
+    "denominator_adds_reverse": ("const double denom = Pt - Pji;", "const double denom = Pt + Pji;"),
+    "mean_drops_reverse_term": ("Mn[e] = (Pt * mut - Pji * muji) / Aij;", "Mn[e] = (Pt * mut) / Aij;"),
+    "precision_total_reads_outgoing": ("Psum += Po[twin[e]];                   /* P_ki, k = col[e] */",
+                                       "Psum += Po[e];"),
+    "mean_total_drops_precision": ("hsum += Po[twin[e]] * Mo[twin[e]];     /* P_ki mu_ki */",
+                                   "hsum += Mo[twin[e]];"),
+    "self_mean_not_divided": ("const double muii = b[i] / Pii;        /* mu_ii = b_i / A_ii */",
+                              "const double muii = b[i];"),
+    "marginal_divides_by_self_precision": ("    x[i] = hsum / Psum;\n    if (Pi) Pi[i] = Psum;",
+                                           "    x[i] = hsum / Pii;\n    if (Pi) Pi[i] = Psum;"),
+    "mean_message_sign": ("Mn[e] = (Pt * mut - Pji * muji) / Aij;", "Mn[e] = -(Pt * mut - Pji * muji) / Aij;"),
+}
+
+
+def _pins_hold(lib) -> bool:
+    g = toy_tree()
+    A = np.array([[float(v) for v in row] for row in g["A"]])
+    m = W.csr_from_dense(A)
+    b = np.array([float(v) for v in g["rhs"]])
+    pos = {(i, j): e for i in range(3) for e in range(m.row_ptr[i], m.row_ptr[i + 1])
+           for j in [int(m.col[e])]}
+    names = {"x": 0, "y": 1, "z": 2}
+    for t in (1, 2, 3):
+        r = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=t, want_messages=True, lib=lib)
+        for key, series in g.items():
+            kind, _, pair = key.partition("_")
+            if kind in ("P", "mu") and len(pair) == 2:
+                got = r["P" if kind == "P" else "mu"][pos[(names[pair[0]], names[pair[1]])]]
+                if abs(got - float(series[t])) > 1e-12:
+                    return False
+            if kind == "mu" and len(pair) == 1:
+                if abs(r["x"][names[pair]] - float(series[t])) > 1e-12:
+                    return False
+    for mm in (W.poisson2d(5), W.er_sdd(60, 6, 1.1, 5)):
+        rhs = W.uniform_rhs(mm.n, 1)
+        r = oracle.gabp(mm.row_ptr, mm.col, mm.val, rhs, stop=oracle.STOP_RES_REL, max_rounds=3000,
+                        tol=1e-12, lib=lib)
+        x_true = np.linalg.solve(mm.to_dense(), rhs)
+        if r["status"] != "ok" or not np.allclose(r["x"], x_true, rtol=1e-9, atol=1e-9):
+            return False
+    return True
+
+
+def test_unmodified_source_passes(tmp_path):
+    lib = oracle.compile_variant(oracle.source(), str(tmp_path / "orig.so"))
+    assert _pins_hold(lib)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = oracle.source()
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    lib = oracle.compile_variant(src.replace(old, new, 1), str(tmp_path / f"{name}.so"))
+    assert not _pins_hold(lib)

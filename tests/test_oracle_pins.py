@@ -1,0 +1,283 @@
+"""CPU pins of the FP64 oracle against what the paper and mathematics fix.
+
+Nothing here compares the oracle with itself: every expected value is either
+printed in the paper (tests/golden/), a closed form, a textbook method written
+out in the test, or a LAPACK solve of a small dense system.
+"""
+from collections import deque
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1119_gb300 import workloads as W
+from golden_io import paper_systems, toy_tree
+
+TOY_NAMES = {"x": 0, "y": 1, "z": 2}
+
+
+def _csr(A):
+    return W.csr_from_dense(np.asarray(A, dtype=float))
+
+
+def _pos(m, i, j):
+    for e in range(m.row_ptr[i], m.row_ptr[i + 1]):
+        if m.col[e] == j:
+            return e
+    raise KeyError((i, j))
+
+
+def _run(m, b, rounds, **kw):
+    return oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=rounds, want_messages=True, **kw)
+
+
+def _diameter(m):
+    """Graph diameter of a tree by two breadth-first searches."""
+    def bfs(src):
+        dist = {src: 0}
+        q = deque([src])
+        while q:
+            u = q.popleft()
+            for e in range(m.row_ptr[u], m.row_ptr[u + 1]):
+                v = int(m.col[e])
+                if v != u and v not in dist:
+                    dist[v] = dist[u] + 1
+                    q.append(v)
+        far = max(dist, key=dist.get)
+        return far, dist[far]
+    far, _ = bfs(0)
+    return bfs(far)[1]
+
+
+# --------------------------------------------------------------------------
+# Section VIII-A: the toy 3x3 tree, every printed message and mean.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("t", [0, 1, 2, 3])
+def test_toy_tree_message_table(t):
+    g = toy_tree()
+    m = _csr([[float(v) for v in row] for row in g["A"]])
+    b = np.array([float(v) for v in g["rhs"]])
+    r = _run(m, b, t)
+    assert r["status"] == "ok"
+    for key, series in g.items():
+        kind, _, pair = key.partition("_")
+        if kind in ("P", "mu") and len(pair) == 2:
+            i, j = TOY_NAMES[pair[0]], TOY_NAMES[pair[1]]
+            got = r["P" if kind == "P" else "mu"][_pos(m, i, j)]
+            assert got == pytest.approx(float(series[t]), abs=1e-14), (key, t)
+
+
+@pytest.mark.parametrize("t", [0, 1, 2, 3])
+def test_toy_tree_tentative_means(t):
+    g = toy_tree()
+    m = _csr([[float(v) for v in row] for row in g["A"]])
+    b = np.array([float(v) for v in g["rhs"]])
+    x = _run(m, b, t)["x"]
+    for name, idx in TOY_NAMES.items():
+        assert x[idx] == pytest.approx(float(g["mu_" + name][t]), abs=1e-14)
+
+
+def test_toy_tree_precisions_equal_inverse_diagonal():
+    g = toy_tree()
+    A = np.array([[float(v) for v in row] for row in g["A"]])
+    m = _csr(A)
+    r = _run(m, np.array([float(v) for v in g["rhs"]]), 3)
+    for name, idx in TOY_NAMES.items():
+        assert r["Pi"][idx] == pytest.approx(float(g["Pfinal_" + name][0]), abs=1e-14)
+    np.testing.assert_allclose(1.0 / r["Pi"], np.diag(np.linalg.inv(A)), rtol=1e-14)
+    np.testing.assert_allclose(r["x"], [float(v) for v in g["solution"]], atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Section IV: on a tree GaBP is exact, and it gets there in diameter rounds.
+# --------------------------------------------------------------------------
+TREES = [("path", W.path_graph(13, 1)),
+         ("recursive", W.random_tree(40, 2, diag_scale=1.0)),
+         ("recursive_indefinite", W.random_tree(25, 3, diag_scale=1.0, indefinite=True)),
+         ("recursive_big", W.random_tree(200, 4, diag_scale=0.7))]
+
+
+@pytest.mark.parametrize("name,m", TREES, ids=[t[0] for t in TREES])
+def test_tree_exact_within_diameter_rounds(name, m):
+    A = m.to_dense()
+    b = W.normal_rhs(m.n, 7)
+    D = _diameter(m)
+    x_true = np.linalg.solve(A, b)
+    var_true = np.diag(np.linalg.inv(A))
+    r = _run(m, b, D)
+    assert r["status"] == "ok"
+    scale = np.abs(x_true).max()
+    err = np.abs(r["x"] - x_true).max()
+    assert err <= 1e-10 * scale
+    np.testing.assert_allclose(1.0 / r["Pi"], var_true, rtol=1e-9)
+    # One round short of the diameter an endpoint of a longest path is not
+    # yet exact: its error is well above rounding level.
+    early = _run(m, b, D - 1)
+    early_err = np.abs(early["x"] - x_true).max()
+    assert early_err > 1e-11 * scale and early_err > 100 * err
+    # Further rounds do not move a converged tree.
+    later = _run(m, b, D + 3)
+    assert np.abs(later["x"] - r["x"]).max() <= 1e-12 * scale
+
+
+# --------------------------------------------------------------------------
+# Section III, Proposition (solution = marginal means): a converged GaBP mean
+# equals A^{-1} b on loopy graphs too.
+# --------------------------------------------------------------------------
+LOOPY = [("poisson2d_p6", W.poisson2d(6)),
+         ("er_n60", W.er_sdd(60, 6, 1.1, 5)),
+         ("er_n200", W.er_sdd(200, 8, 1.05, 6))]
+
+
+@pytest.mark.parametrize("name,m", LOOPY, ids=[t[0] for t in LOOPY])
+def test_converged_mean_equals_dense_solve(name, m):
+    A = m.to_dense()
+    b = W.uniform_rhs(m.n, 11)
+    r = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=5000,
+                    tol=1e-13)
+    assert r["status"] == "ok"
+    x_true = np.linalg.solve(A, b)
+    assert np.abs(r["x"] - x_true).max() <= 1e-10 * np.abs(x_true).max()
+
+
+# --------------------------------------------------------------------------
+# Section VI-C: zero precisions + "k in N(i)" instead of "N(i)\j" is Jacobi.
+# --------------------------------------------------------------------------
+def _textbook_jacobi(m, b, rounds):
+    """x^{t+1}_i = (b_i - sum_{k != i} A_ik x^t_k) / A_ii, x^0 = D^{-1} b."""
+    n = m.n
+    diag = np.array([m.val[_pos(m, i, i)] for i in range(n)])
+    x = b / diag
+    for _ in range(rounds):
+        new = np.empty(n)
+        for i in range(n):
+            s = b[i]
+            for e in range(m.row_ptr[i], m.row_ptr[i + 1]):
+                k = int(m.col[e])
+                if k != i:
+                    s -= m.val[e] * x[k]
+            new[i] = s / diag[i]
+        x = new
+    return x
+
+
+@pytest.mark.parametrize("m", [W.poisson2d(5), W.er_sdd(40, 5, 1.2, 9)])
+def test_jacobi_variant_is_textbook_jacobi(m):
+    b = W.uniform_rhs(m.n, 3)
+    for t in (0, 1, 2, 7, 20):
+        got = oracle.gabp(m.row_ptr, m.col, m.val, b, variant=oracle.JACOBI, max_rounds=t)["x"]
+        assert np.array_equal(got, _textbook_jacobi(m, b, t)), t
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 (naive) and Algorithm 2 (broadcast) send the same messages.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [W.poisson2d(4), W.er_sdd(50, 7, 1.1, 12), W.random_tree(30, 8)])
+def test_naive_equals_broadcast(m):
+    b = W.normal_rhs(m.n, 4)
+    for t in (1, 2, 5, 12):
+        a = _run(m, b, t, variant=oracle.BROADCAST)
+        c = _run(m, b, t, variant=oracle.NAIVE)
+        for key in ("P", "mu", "x", "Pi"):
+            ref = np.abs(c[key]).max()
+            assert np.abs(a[key] - c[key]).max() <= 1e-12 * max(ref, 1e-300), (key, t)
+
+
+# --------------------------------------------------------------------------
+# Section VIII-B/C and IX: the paper's small systems.
+# --------------------------------------------------------------------------
+def _spectral_radius_abs_jacobi(A):
+    D = np.diag(np.diag(A))
+    M = np.abs(np.eye(A.shape[0]) - np.linalg.solve(D, A))
+    return float(np.max(np.abs(np.linalg.eigvals(M))))
+
+
+@pytest.mark.parametrize("name", ["R3", "R4"])
+def test_cdma_spectral_radius_matches_paper(name):
+    s = paper_systems()[name]
+    assert _spectral_radius_abs_jacobi(s["A"]) == pytest.approx(s["spectral_radius"], abs=1e-4)
+
+
+@pytest.mark.parametrize("name", ["R3", "R4", "nonPSD", "poisson_p3"])
+def test_paper_systems_converge_to_solution(name):
+    s = paper_systems()[name]
+    m = _csr(s["A"])
+    r = oracle.gabp(m.row_ptr, m.col, m.val, s["b"], stop=oracle.STOP_RES_ABS, max_rounds=2000,
+                    tol=1e-14)
+    assert r["status"] == "ok"
+    x_true = np.linalg.solve(s["A"], s["b"])
+    np.testing.assert_allclose(r["x"], x_true, rtol=1e-12, atol=1e-13)
+    if "solution" in s:
+        np.testing.assert_allclose(r["x"], [float(v) for v in s["solution"]], rtol=1e-12)
+
+
+@pytest.mark.parametrize("name", ["R3", "R4", "nonPSD"])
+def test_paper_iteration_counts_same_order(name):
+    """Soft pin: message-change rule, threshold 1e-6 (Section VIII)."""
+    s = paper_systems()[name]
+    m = _csr(s["A"])
+    r = oracle.gabp(m.row_ptr, m.col, m.val, s["b"], stop=oracle.STOP_MSG, max_rounds=2000,
+                    tol=1e-6)
+    assert r["status"] == "ok"
+    paper = s["parallel_gabp_iterations"]
+    assert paper / 2 <= r["rounds"] <= paper * 2, (r["rounds"], paper)
+
+
+def test_poisson_iteration_count_same_order():
+    """The Poisson table (134 parallel rounds) is captioned p = 3 but the text
+    evaluates p = 10; at p = 10 with f = -1 the count is of that order."""
+    p = 10
+    m = W.poisson2d(p)
+    b = np.full(m.n, 1.0 / (p + 1) ** 2)
+    r = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_MSG, max_rounds=5000, tol=1e-6)
+    assert r["status"] == "ok"
+    paper = paper_systems()["poisson_p3"]["parallel_gabp_iterations"]
+    assert paper / 3 <= r["rounds"] <= paper * 3, r["rounds"]
+
+
+# --------------------------------------------------------------------------
+# Section VII: the augmented system yields (S^T S + sigma^2 I)^{-1} S^T y.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("K", [4, 9, 16])
+def test_augmented_system_closed_form(K):
+    sysd = W.detection_batch(1, K, K, 10.0, seed=K)[0]
+    row_ptr, col, val, rhs = oracle.augment_lsq(sysd.S, sysd.sigma2, sysd.y)
+    n = row_ptr.shape[0] - 1
+    m = W.CSR(n, row_ptr, col, val)
+    A_dense, b_dense = sysd.dense_system()
+    closed = np.linalg.solve(A_dense, b_dense)
+    # The augmented matrix itself, solved directly, gives the closed form ...
+    full = np.linalg.solve(m.to_dense(), rhs)
+    np.testing.assert_allclose(full[:K], closed, rtol=1e-11, atol=1e-12)
+    # ... and GaBP on it converges to the same vector.
+    r = oracle.gabp(row_ptr, col, val, rhs, stop=oracle.STOP_RES_ABS, max_rounds=3000, tol=1e-13)
+    assert r["status"] == "ok"
+    np.testing.assert_allclose(r["x"][:K], closed, rtol=1e-9, atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Residual helper, input validation and breakdown.
+# --------------------------------------------------------------------------
+def test_residual_inf_matches_dense():
+    m = W.er_sdd(80, 6, 1.1, 2)
+    b = W.normal_rhs(80, 1)
+    x = W.normal_rhs(80, 2)
+    ref = np.abs(b - m.to_dense() @ x).max()
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) == pytest.approx(ref, rel=1e-13)
+
+
+def test_bad_inputs_rejected():
+    b = np.ones(2)
+    asym = W.csr_from_dense(np.array([[2.0, 1.0], [0.5, 2.0]]))
+    assert oracle.gabp(asym.row_ptr, asym.col, asym.val, b)["status"] == "bad_input"
+    nodiag = W.csr_from_dense(np.array([[0.0, 1.0], [1.0, 2.0]]))
+    assert oracle.gabp(nodiag.row_ptr, nodiag.col, nodiag.val, b)["status"] == "bad_input"
+
+
+def test_breakdown_reported():
+    # Round 1 sends P_21 = P_31 = -1 into node 1, so at round 2 the message
+    # 1 -> 2 divides by P~_1 - P_21 = 1 - 1 - 1 + 1 = 0.
+    m = W.csr_from_dense(np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0]]))
+    b = np.ones(3)
+    assert _run(m, b, 1)["status"] == "ok"
+    assert _run(m, b, 2)["status"] == "breakdown"
