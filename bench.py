@@ -1,0 +1,341 @@
+"""Benchmark: GaBP edge-message updates/s and time to a 1e-10 relative residual.
+
+Workload: random sparse symmetric diagonally dominant system, Erdos-Renyi
+pattern with n = 1,000,000 and average degree 8, off-diagonals N(0,1),
+A_ii = 1.1 sum_j |A_ij|, b ~ N(0,1) (synthetic, seeded).
+
+One step = one complete solve to ||b - A x||_inf / ||b||_inf < 1e-10 with the
+mixed-precision path (FP32 messages, FP64 residual refinement), inputs
+already resident in HBM.  L2 is flushed (a 256 MiB write) before every step,
+outside the timed events.  The plain FP64 sweep solve of the same system is
+timed the same way for the comparison the metric asks for.
+
+value   = directed edges x sweeps / solve time (edge-message updates/s),
+          summed over ranks, divided by the slowest rank's time.
+e2e     = the same metric through gabp_solve_host (host b and x, the copies
+          inside the timed call), timed with the host clock.
+roofline: the kernel with the largest device time inside the timed region,
+          its algorithmic bytes per launch over its mean event-timed
+          duration, against the measured HBM copy bandwidth.
+
+Multi-GPU (torchrun): every rank solves its own system (same matrix, its own
+right-hand side); no data moves between ranks ("replicas", weak scaling).
+
+--impl reference times the CPU oracle (plain FP64 synchronous GaBP) on the
+host cores, on a bounded number of rounds of the same system per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_NODES = 1_000_000
+AVG_DEGREE = 8
+DOMINANCE = 1.1
+TOL = 1e-10
+METRIC = "GaBP edge-message updates/s (mixed FP32+FP64 refinement solve to 1e-10 rel. residual)"
+UNIT = "edge-updates/s"
+WORKLOAD = "ER n=1e6 avg-degree 8 SDD (dominance 1.1), b~N(0,1), solve to 1e-10 rel. residual"
+
+# Algorithmic bytes per launch of each kernel kind: values and indices the
+# method must move (per directed edge, per node).
+BYTES = {
+    "mean": (16, 12),      # c 4 + eta in 4 + rev 4 + eta out 4 | rhs 4 + 1/P 4 + d out 4
+    "full32": (24, 16),    # A 4 + (P,eta) in 8 + rev 4 + (P,eta) out 8 | diag 4 + rhs 4 + (P,d) out 8
+    "full64": (44, 24),    # A 8 + (P,eta) in 16 + rev 4 + (P,eta) out 16 | diag 8 + b 8 + x out 8
+    "residual": (20, 32),  # A 8 + col 4 + x[col] 8 | diag 8 + x 8 + b 8 + r 8
+}
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _workload(seed_rhs: int):
+    from paper_0810_1119_gb300 import workloads as W
+    m = W.er_sdd(N_NODES, AVG_DEGREE, DOMINANCE, 0)
+    b = W.normal_rhs(m.n, 1 + seed_rhs)
+    return m, b
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def _cpu_baseline(m, b, rounds: int):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_FIXED, max_rounds=rounds)
+    dt = time.perf_counter() - t0
+    E = m.n_directed_edges
+    return {"value": E * r["rounds"] / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{r['rounds']} synchronous FP64 rounds (Alg. 2) of the n=1e6 ER system, "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    m, b = _workload(0)
+    E = m.n_directed_edges
+    rounds = args.ref_rounds
+    for _ in range(args.warmup):
+        _cpu_baseline(m, b, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        import oracle
+        oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_FIXED, max_rounds=rounds)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = E * rounds * args.steps / tot
+    import oracle
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"{rounds} FP64 oracle rounds on host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{rounds} synchronous FP64 rounds per step, n=1e6 ER"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gabp(args):
+    import torch
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_0810_1119_gb300 import build_lib
+    build_lib.build()
+    from paper_0810_1119_gb300 import gabp
+
+    m, b = _workload(rank)
+    E = m.n_directed_edges
+    bt = torch.tensor(b, device=dev)
+    xt = torch.empty_like(bt)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    mixed = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32,
+                                 profile=True)
+    fp64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64, profile=True)
+    stream = torch.cuda.current_stream()
+
+    def timed_solves(solver, steps):
+        evs = []
+        stats = []
+        for _ in range(steps):
+            flush.zero_()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            it = gabp.gabp_solve(solver.handle, bt, xt, TOL, 5000)
+            z.record(stream)
+            evs.append((a, z))
+            st = solver.stats()
+            st["iters"] = it
+            stats.append(st)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(z) for a, z in evs], stats
+
+    for _ in range(args.warmup):
+        timed_solves(mixed, 1)
+        timed_solves(fp64, 1)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier()
+    ms_mixed, st_mixed = timed_solves(mixed, args.steps)
+    barrier()
+    ms_fp64, st_fp64 = timed_solves(fp64, max(1, min(args.steps, args.fp64_steps)))
+    barrier()
+    clocks = sampler.stop() if sampler else None
+
+    # end to end through the host-buffer entry point
+    b_host = torch.tensor(b, dtype=torch.float64).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    bh, xh = b_host.numpy(), x_host.numpy()
+    gabp.gabp_solve_host(mixed.handle, bh, TOL, 5000, x=xh)
+    barrier()
+    e2e_t, e2e_sweeps = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it = gabp.gabp_solve_host(mixed.handle, bh, TOL, 5000, x=xh)
+        e2e_t.append(time.perf_counter() - t0)
+        e2e_sweeps.append(it)
+    barrier()
+
+    tot_ms = sum(ms_mixed)
+    updates = sum(E * s["iters"] for s in st_mixed)
+    launches = sum(s["kernel_launches"] for s in st_mixed)
+    e2e_updates = sum(E * it for it in e2e_sweeps)
+    e2e_s = sum(e2e_t)
+    if dist is not None:
+        t = torch.tensor([tot_ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([updates, e2e_updates, launches], dtype=torch.float64, device=dev)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        tot_ms, e2e_s = float(t[0]), float(t[1])
+        updates, e2e_updates, launches = float(u[0]), float(u[1]), int(u[2])
+
+    if rank == 0:
+        hbm, peak_kind = _peaks()
+        # roofline of the dominant kernel kind inside the timed mixed solves
+        kinds = {
+            "mean": (sum(s["ms_mean"] for s in st_mixed), sum(s["sweeps_mean"] for s in st_mixed)),
+            "full32": (sum(s["ms_full"] for s in st_mixed), sum(s["sweeps_full"] for s in st_mixed)),
+            "residual": (sum(s["ms_residual"] for s in st_mixed),
+                         sum(s["residual_checks"] for s in st_mixed)),
+        }
+        dom = max(kinds, key=lambda k: kinds[k][0])
+        ms_k, n_k = kinds[dom]
+        per_edge, per_node = BYTES[dom]
+        bytes_launch = per_edge * E + per_node * m.n
+        achieved = bytes_launch * n_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None
+        kernel_names = {"mean": "mean32_kernel (FP32 mean-only sweep)",
+                        "full32": "sweep32_kernel (FP32 full sweep)",
+                        "residual": "residual64_kernel (FP64 residual)"}
+        fp64_ms = statistics.mean(ms_fp64)
+        mixed_ms = tot_ms / args.steps
+        line = {
+            "metric": METRIC, "value": updates / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": m.n, "directed_edges": E,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "flushed (256 MiB write) before every step",
+                       "precision": "FP32 messages, FP64 residual refinement"},
+            "time_to_solution_ms": {"mixed_fp32": mixed_ms, "fp64_sweep": fp64_ms,
+                                    "speedup_vs_fp64": fp64_ms / mixed_ms},
+            "sweeps": {"mixed_total": st_mixed[-1]["sweeps_total"],
+                       "mixed_full": st_mixed[-1]["sweeps_full"],
+                       "mixed_mean": st_mixed[-1]["sweeps_mean"],
+                       "mixed_outer": st_mixed[-1]["outer_steps"],
+                       "fp64": st_fp64[-1]["sweeps_total"]},
+            "fp64_edge_updates_per_s": E * st_fp64[-1]["sweeps_total"] / (fp64_ms * 1e-3),
+            "final_rel_residual": st_mixed[-1]["residual"] / st_mixed[-1]["rhs_norm"],
+            "roofline": {"bound": "hbm", "kernel": kernel_names[dom],
+                         "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": (achieved / hbm) if achieved else None,
+                         "peak_source": peak_kind, "traffic": None,
+                         "bytes_per_launch": bytes_launch, "launches": n_k,
+                         "mean_launch_us": 1e3 * ms_k / max(n_k, 1)},
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+            "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * m.n, "d2h_bytes_per_step": 8 * m.n,
+                    "ms_per_step": 1e3 * e2e_s / args.steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = _cpu_baseline(m, b, args.cpu_rounds)
+        print(json.dumps(line), flush=True)
+    mixed.close()
+    fp64.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gabp", choices=["gabp", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--cpu-rounds", type=int, default=10)
+    ap.add_argument("--ref-rounds", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gabp(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,201 @@
+/*
+ * gabp.h -- C ABI of the GB300 (sm_103a) Gaussian belief propagation solver.
+ *
+ * The library solves A x = b for a square symmetric A by synchronous
+ * ("parallel", flooding) Gaussian belief propagation in the broadcast form of
+ * Algorithm 2 of Shental, Bickson, Siegel, Wolf and Dolev, "Gaussian Belief
+ * Propagation for Solving Systems of Linear Equations: Theory and
+ * Application":
+ *
+ *   node totals     P~_i = A_ii + sum_{k in N(i)} P_ki
+ *                   h~_i = b_i  + sum_{k in N(i)} P_ki mu_ki   (h~_i = P~_i mu~_i)
+ *   edge messages   P_ij = -A_ij^2 / (P~_i - P_ji)
+ *                   mu_ij = (h~_i - P_ji mu_ji) / A_ij
+ *   solution        x_i = h~_i / P~_i                          (Alg. 2, steps 2 and 4)
+ *
+ * where every round reads only the previous round's messages (Section III-C,
+ * parallel scheduling) and the graph has one node per row of A and one edge
+ * per off-diagonal non-zero (Section II-B).  All messages start at zero
+ * (Alg. 2, step 1).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are passed as a full symmetric CSR (diagonal included, column
+ *     indices strictly increasing in each row), 0-based.  Explicit zeros
+ *     off the diagonal are dropped (they are not edges).  The number of
+ *     off-diagonal entries must be below 2^31 - 64.
+ *   - Arrays named *_host are host memory; arrays named *_dev are device
+ *     memory of the current CUDA device.  Device work is issued on the
+ *     handle's stream (gabp_options.stream, NULL = the legacy default stream).
+ *   - Functions return a gabp_status and never abort; gabp_last_error()
+ *     gives a message for the last failure on a handle.
+ *   - A handle runs one operation at a time (no concurrent calls on the same
+ *     handle); different handles are independent.
+ */
+#ifndef GABP_H
+#define GABP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gabp_s *gabp_handle;
+
+typedef enum {
+  GABP_OK = 0,
+  GABP_ERR_INVALID_ARG = 1,    /* null pointer, bad size, malformed CSR */
+  GABP_ERR_NOT_SYMMETRIC = 2,  /* pattern or values of A not symmetric, or rev inconsistent */
+  GABP_ERR_ZERO_DIAG = 3,      /* a missing or zero diagonal entry (P_ii = A_ii must be != 0) */
+  GABP_ERR_BREAKDOWN = 4,      /* some P~_i - P_ji was zero or not finite */
+  GABP_ERR_DIVERGED = 5,       /* the residual became non-finite or grew by > 1e30 */
+  GABP_ERR_NOT_CONVERGED = 6,  /* stop rule not met within max_iter sweeps */
+  GABP_ERR_CUDA = 7,           /* a CUDA runtime call failed */
+  GABP_ERR_OOM = 8,            /* device allocation failed */
+  GABP_ERR_TIMEOUT = 9         /* a bounded device wait gave up */
+} gabp_status;
+
+typedef enum {
+  GABP_PREC_FP64 = 0,        /* plain FP64 messages, every sweep updates P and mu */
+  GABP_PREC_MIXED_FP32 = 1,  /* FP32 messages inside FP64 residual refinement */
+  GABP_PREC_MIXED_BF16 = 2   /* as MIXED_FP32 with BF16 storage of the mean messages */
+} gabp_precision;
+
+typedef enum {
+  GABP_RESIDUAL_ABS = 0,     /* stop when ||b - A x||_inf < tol */
+  GABP_RESIDUAL_REL = 1      /* stop when ||b - A x||_inf / ||b||_inf < tol */
+} gabp_residual_kind;
+
+typedef struct {
+  int32_t precision;      /* gabp_precision */
+  int32_t residual_kind;  /* gabp_residual_kind */
+  int32_t check_every;    /* sweeps between convergence checks; 0 = automatic */
+  int32_t group_lanes;    /* lanes per row in the sweep kernels (1..32, power of 2); 0 = automatic */
+  int32_t autotune;       /* 1 = time the candidate launch shapes once at create and keep the fastest */
+  int32_t profile;        /* 1 = bracket every kernel with CUDA events and report the times in gabp_stats */
+  int32_t reserved_i[2];
+  double inner_tol;       /* mixed modes: relative accuracy asked of each inner FP32 solve; 0 = 1e-6 */
+  void *stream;           /* cudaStream_t used by every call on the handle; NULL = legacy default */
+  double reserved_d[4];
+} gabp_options;
+
+/* Statistics of the last solve on a handle. */
+typedef struct {
+  int32_t sweeps_total;     /* all message sweeps (full and mean-only) */
+  int32_t sweeps_full;      /* sweeps that updated precisions and means */
+  int32_t sweeps_mean;      /* mean-only sweeps with frozen precisions */
+  int32_t outer_steps;      /* FP64 refinement steps (mixed modes; 1 for FP64) */
+  int32_t residual_checks;  /* FP64 residual evaluations */
+  int32_t status;           /* gabp_status of the solve */
+  double residual;          /* final ||b - A x||_inf (absolute) */
+  double rhs_norm;          /* ||b||_inf */
+  int64_t n;                /* unknowns */
+  int64_t edges;            /* directed edges = off-diagonal non-zeros */
+  int64_t kernel_launches;  /* kernels launched by the solve */
+  /* With gabp_options.profile: summed device time (ms) of the kernels of
+   * each kind, measured with CUDA events on the handle's stream. */
+  double ms_full;           /* full sweeps (FP64 or FP32) */
+  double ms_mean;           /* mean-only sweeps */
+  double ms_residual;       /* FP64 residual evaluations */
+  double ms_other;          /* norms, scaling, refinement updates */
+  double reserved[2];
+} gabp_stats;
+
+/* Fills *opt with the defaults: FP64, relative residual, automatic check
+ * interval and launch shape, no autotuning, inner_tol 1e-6, NULL stream. */
+void gabp_default_options(gabp_options *opt);
+
+/*
+ * Builds a solver for the n x n symmetric matrix given as a full CSR in host
+ * memory: row_ptr_host[n+1], col_host[nnz], val_host[nnz] (Section II-B: one
+ * graph node per row, one edge per off-diagonal non-zero).
+ *
+ * rev_host (optional, may be NULL): the reverse-edge permutation over the
+ * CSR entries, rev[e] = position of entry (j, i) for e = (i, j) (rev of a
+ * diagonal entry is itself).  It is validated when given and computed when
+ * NULL.
+ *
+ * Ownership: the library copies what it needs into device memory it owns;
+ * the caller may free the inputs on return.  opt may be NULL (defaults).
+ * Errors: GABP_ERR_INVALID_ARG (n < 1, malformed CSR, unsorted columns,
+ * too many edges), GABP_ERR_NOT_SYMMETRIC (|A_ij - A_ji| > 1e-14 max|A_ij|,
+ * asymmetric pattern or a wrong rev), GABP_ERR_ZERO_DIAG, GABP_ERR_OOM,
+ * GABP_ERR_CUDA.  On error *out is NULL.
+ */
+gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t *row_ptr_host,
+                        const int32_t *col_host, const double *val_host, const int64_t *rev_host,
+                        const gabp_options *opt);
+
+/* Releases the handle and all device memory it owns.  NULL is accepted. */
+gabp_status gabp_destroy(gabp_handle h);
+
+/* Replaces the stream used by later calls on the handle. */
+gabp_status gabp_set_stream(gabp_handle h, void *stream);
+
+/*
+ * Solves A x = b (b_dev[n], x_dev[n], FP64 device arrays, caller-owned) with
+ * the handle's precision mode, starting from zero messages (Alg. 2, step 1;
+ * the initial content of x_dev is ignored).  Stops when the FP64 residual
+ * ||b - A x||_inf (absolute or relative to ||b||_inf, per residual_kind)
+ * falls below tol, or after max_iter sweeps.
+ *
+ * *iters (may be NULL) receives the number of message sweeps executed.
+ * The call returns when x_dev holds the result (the stream is synchronised).
+ * Errors: GABP_ERR_NOT_CONVERGED (x_dev holds the last iterate),
+ * GABP_ERR_BREAKDOWN (a zero or non-finite P~_i - P_ji), GABP_ERR_DIVERGED,
+ * GABP_ERR_INVALID_ARG, GABP_ERR_CUDA.
+ */
+gabp_status gabp_solve(gabp_handle h, const double *b_dev, double *x_dev, double tol,
+                       int32_t max_iter, int32_t *iters);
+
+/* As gabp_solve with b and x in host memory: the library copies b to the
+ * device, solves, and copies x back, all on the handle's stream. */
+gabp_status gabp_solve_host(gabp_handle h, const double *b_host, double *x_host, double tol,
+                            int32_t max_iter, int32_t *iters);
+
+/*
+ * Solves A X = B for nrhs right-hand sides at once.  B_dev and X_dev are
+ * n x nrhs FP64 device arrays, row-major ("column-interleaved": element
+ * (i, k) at i * nrhs + k).  The precision messages do not depend on b
+ * (Alg. 2: P_ij involves only A and other precisions), so they are iterated
+ * once and shared; the mean messages of all right-hand sides then advance
+ * together.  Stops when every column meets the residual rule.  In FP64 mode
+ * the columns are solved one after another with gabp_solve's path.
+ * *iters receives the sweeps executed.  Errors as gabp_solve.
+ */
+gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, int32_t nrhs,
+                             double tol, int32_t max_iter, int32_t *iters);
+
+/* Statistics of the last solve on the handle. */
+gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats);
+
+/*
+ * Instrumentation for parity tests.  Runs exactly `rounds` synchronous FP64
+ * rounds of Alg. 2 from zero messages on b_dev and writes the tentative
+ * means after the last round to x_dev (rounds = 0 gives x_i = b_i / A_ii).
+ * The messages of the last round stay in the handle for gabp_get_messages.
+ */
+gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, double *x_dev);
+
+/*
+ * Copies the messages left by gabp_run_rounds into host arrays of length
+ * nnz laid out like the CSR given to gabp_create: the message from i to j
+ * (precision P_ij and mean mu_ij) at the position of entry (i, j); diagonal
+ * positions receive 0.
+ */
+gabp_status gabp_get_messages(gabp_handle h, double *P_host, double *mu_host);
+
+/* Message of the last failure on the handle (never NULL; "" when none). */
+const char *gabp_last_error(gabp_handle h);
+
+/* Name of a status code. */
+const char *gabp_status_string(gabp_status s);
+
+/* Library version string. */
+const char *gabp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GABP_H */

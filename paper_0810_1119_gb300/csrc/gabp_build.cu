@@ -1,0 +1,197 @@
+// gabp_build.cu -- graph builder: validates the CSR of A, splits off the
+// diagonal, drops explicit zeros, derives the reverse-edge index in slot
+// numbering, bins rows by degree and uploads the device arrays.
+//
+// Graph of Section II-B: node i per row, an edge per off-diagonal non-zero;
+// P_ii = A_ii must be non-zero (Alg. 2 step 1 divides by it).
+#include "gabp_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace gabp {
+
+namespace {
+
+template <class T>
+cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t st) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
+  if (e != cudaSuccess) return e;
+  if (count) e = cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
+  return e;
+}
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+// Returns GABP_OK or an error with *msg set.
+gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                        const int32_t *col, const double *val, const int64_t *rev,
+                        const gabp_options &opt, cudaStream_t st, std::string *msg) {
+  if (n < 1 || n > (int64_t{1} << 31) - 2) { *msg = "n out of range"; return GABP_ERR_INVALID_ARG; }
+  if (!row_ptr || !col || !val) { *msg = "null CSR pointer"; return GABP_ERR_INVALID_ARG; }
+  if (row_ptr[0] != 0 || row_ptr[n] != nnz || nnz < n) {
+    *msg = "row_ptr must start at 0, end at nnz, and nnz >= n";
+    return GABP_ERR_INVALID_ARG;
+  }
+  double amax = 0.0;
+  std::vector<int64_t> diag_pos(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) { *msg = "row_ptr not monotone"; return GABP_ERR_INVALID_ARG; }
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      if (col[e] < 0 || col[e] >= n) { *msg = "column index out of range"; return GABP_ERR_INVALID_ARG; }
+      if (e > row_ptr[i] && col[e] <= col[e - 1]) {
+        *msg = "columns of a row must be strictly increasing";
+        return GABP_ERR_INVALID_ARG;
+      }
+      if (!std::isfinite(val[e])) { *msg = "non-finite matrix value"; return GABP_ERR_INVALID_ARG; }
+      amax = std::max(amax, std::fabs(val[e]));
+      if (col[e] == i) diag_pos[i] = e;
+    }
+    if (diag_pos[i] < 0 || val[diag_pos[i]] == 0.0) {
+      *msg = "missing or zero diagonal entry at row " + std::to_string(i);
+      return GABP_ERR_ZERO_DIAG;
+    }
+  }
+  // Twin (entry (j, i)) of every off-diagonal entry, from rev or by search.
+  std::vector<int64_t> twin(nnz);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      if (j == i) { twin[e] = e; continue; }
+      int64_t t;
+      if (rev) {
+        t = rev[e];
+        if (t < row_ptr[j] || t >= row_ptr[j + 1] || col[t] != i) {
+          *msg = "rev is not the reverse-edge permutation of the CSR";
+          return GABP_ERR_NOT_SYMMETRIC;
+        }
+      } else {
+        const int32_t *b = col + row_ptr[j], *en = col + row_ptr[j + 1];
+        const int32_t *p = std::lower_bound(b, en, static_cast<int32_t>(i));
+        if (p == en || *p != i) { *msg = "pattern of A is not symmetric"; return GABP_ERR_NOT_SYMMETRIC; }
+        t = row_ptr[j] + (p - b);
+      }
+      if (std::fabs(val[t] - val[e]) > 1e-14 * amax) {
+        *msg = "values of A are not symmetric";
+        return GABP_ERR_NOT_SYMMETRIC;
+      }
+      twin[e] = t;
+    }
+  }
+  // Slots: off-diagonal entries in CSR order.  A pair (i,j)/(j,i) whose
+  // values are both zero is not an edge and gets no slot; otherwise both
+  // directions get one (so every slot has a reverse slot).
+  std::vector<int64_t> slot_of(nnz, -1);
+  int64_t E = 0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+      if (col[e] != i && (val[e] != 0.0 || val[twin[e]] != 0.0)) slot_of[e] = E++;
+  if (E > (int64_t{1} << 31) - 64) { *msg = "too many off-diagonal entries"; return GABP_ERR_INVALID_ARG; }
+
+  g.n = static_cast<int32_t>(n);
+  g.E = E;
+  g.h_rp.assign(n + 1, 0);
+  g.h_col.resize(E);
+  g.h_rev.resize(E);
+  g.h_user_pos.resize(E);
+  std::vector<double> a64(E), d64(n);
+  std::vector<float> a32(E), d32(n);
+  int max_deg = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    d64[i] = val[diag_pos[i]];
+    d32[i] = static_cast<float>(d64[i]);
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int64_t s = slot_of[e];
+      if (s < 0) continue;
+      g.h_col[s] = col[e];
+      g.h_rev[s] = static_cast<int32_t>(slot_of[twin[e]]);
+      g.h_user_pos[s] = e;
+      a64[s] = val[e];
+      a32[s] = static_cast<float>(val[e]);
+    }
+  }
+  // row pointers over slots
+  {
+    int64_t s = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      g.h_rp[i] = static_cast<int32_t>(s);
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+        if (slot_of[e] >= 0) ++s;
+      max_deg = std::max<int>(max_deg, static_cast<int>(s - g.h_rp[i]));
+    }
+    g.h_rp[n] = static_cast<int32_t>(s);
+  }
+  g.max_degree = max_deg;
+
+  // Degree bins: rows of degree <= kCacheSlots * G run with G lanes per row;
+  // longer rows run warp-per-row.
+  int G = opt.group_lanes;
+  if (G <= 0) {
+    const double avg = static_cast<double>(E) / static_cast<double>(n);
+    G = std::min(32, std::max(2, next_pow2(static_cast<int>(std::ceil(avg)))));
+  }
+  G = std::min(32, std::max(1, next_pow2(G)));
+  std::vector<int32_t> short_rows, long_rows;
+  const int long_threshold = kCacheSlots * G;
+  for (int64_t i = 0; i < n; ++i) {
+    const int deg = g.h_rp[i + 1] - g.h_rp[i];
+    if (G < 32 && deg > long_threshold) long_rows.push_back(static_cast<int32_t>(i));
+  }
+  g.bins.clear();
+  cudaError_t ce = cudaSuccess;
+  if (long_rows.empty()) {
+    RowBin b;
+    b.rows = nullptr;
+    b.nrows = g.n;
+    b.group = G;
+    g.bins.push_back(b);
+  } else {
+    for (int64_t i = 0, k = 0; i < n; ++i) {
+      if (k < static_cast<int64_t>(long_rows.size()) && long_rows[k] == i) { ++k; continue; }
+      short_rows.push_back(static_cast<int32_t>(i));
+    }
+    RowBin b0, b1;
+    b0.group = G;
+    b0.nrows = static_cast<int32_t>(short_rows.size());
+    b1.group = 32;
+    b1.nrows = static_cast<int32_t>(long_rows.size());
+    ce = upload(&b0.rows, short_rows.data(), short_rows.size(), st);
+    if (ce == cudaSuccess) ce = upload(&b1.rows, long_rows.data(), long_rows.size(), st);
+    g.bins.push_back(b0);
+    g.bins.push_back(b1);
+  }
+  if (ce == cudaSuccess) ce = upload(&g.rp, g.h_rp.data(), g.h_rp.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.col, g.h_col.data(), g.h_col.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.rev, g.h_rev.data(), g.h_rev.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.a64, a64.data(), a64.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.a32, a32.data(), a32.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.diag64, d64.data(), d64.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.diag32, d32.data(), d32.size(), st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    *msg = std::string("device upload failed: ") + cudaGetErrorString(ce);
+    return ce == cudaErrorMemoryAllocation ? GABP_ERR_OOM : GABP_ERR_CUDA;
+  }
+  return GABP_OK;
+}
+
+void free_graph(Graph &g) {
+  for (RowBin &b : g.bins) cudaFree(b.rows);
+  g.bins.clear();
+  cudaFree(g.rp); cudaFree(g.col); cudaFree(g.rev);
+  cudaFree(g.a64); cudaFree(g.a32); cudaFree(g.diag64); cudaFree(g.diag32);
+  g.rp = g.col = g.rev = nullptr;
+  g.a64 = g.diag64 = nullptr;
+  g.a32 = g.diag32 = nullptr;
+}
+
+}  // namespace gabp

@@ -1,0 +1,293 @@
+"""GPU parity of the CUDA library against the FP64 CPU oracle, through the C ABI.
+
+Tolerances (written here, derived from the arithmetic):
+  * FP64 sweeps, per round: 1e-12 relative (infinity norm over each array of
+    P_ij, mu_ij and x).  Both sides compute the same IEEE operations except
+    for summation order and the eta = P mu storage form, i.e. a few ulps per
+    round; 1e-12 leaves room for the growth of that over tens of rounds.
+  * Solves: the FP64 residual ||b - A x||_inf, recomputed by the oracle, below
+    tol (1e-10 relative, or absolute where the workload says so), and the
+    error against the oracle's converged solution within the residual times
+    the conditioning of the small test systems (1e-8 relative).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1119_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_0810_1119_gb300 import build_lib
+    build_lib.build()
+    from paper_0810_1119_gb300 import gabp
+    gabp.load()
+    return gabp
+
+
+def _rel(a, ref):
+    return float(np.abs(a - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def _star_with_ring(n_leaves, seed):
+    """A hub joined to every other node plus a ring: one row of degree
+    n_leaves (runs warp-per-row) next to rows of degree 3."""
+    rng = np.random.default_rng(seed)
+    n = n_leaves + 1
+    rows, cols, vals = [], [], []
+    for k in range(1, n):
+        w = rng.standard_normal() * 0.1
+        rows += [0, k]; cols += [k, 0]; vals += [w, w]
+        nxt = 1 + (k % n_leaves)
+        if nxt != k:
+            w2 = rng.standard_normal() * 0.3
+            rows += [k, nxt]; cols += [nxt, k]; vals += [w2, w2]
+    A = np.zeros((n, n))
+    for r, c, v in zip(rows, cols, vals):
+        A[r, c] += v
+    A = (A + A.T) / 2
+    np.fill_diagonal(A, 1.5 * np.abs(A).sum(1) + 0.5)
+    return W.csr_from_dense(A)
+
+
+PARITY_CASES = {
+    "single_node": W.csr_from_dense(np.array([[3.0]])),
+    "toy_tree": W.csr_from_dense(np.array([[1.0, -2.0, 3.0], [-2.0, 1.0, 0.0], [3.0, 0.0, 1.0]])),
+    "poisson2d_p9": W.poisson2d(9),
+    "poisson2d_p33": W.poisson2d(33),
+    "poisson3d_p12": W.poisson3d(12),
+    "er_4000": W.er_sdd(4000, 8, 1.1, 1),
+    "er_ragged_isolated": W.er_sdd(3001, 3, 1.05, 2),
+    "tree_400": W.random_tree(400, 5, diag_scale=1.0),
+    "star_300_long_row": _star_with_ring(300, 3),
+}
+
+
+def _solver(G, m, **kw):
+    return G.Solver.from_csr(m.row_ptr, m.col, m.val, **kw)
+
+
+def _round_parity(G, m, b, rounds, **kw):
+    s = _solver(G, m, **kw)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    worst = {}
+    for r in rounds:
+        ref = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=r, want_messages=True)
+        assert ref["status"] == "ok"
+        G.gabp_run_rounds(s.handle, bt, r, xt)
+        P, mu = G.gabp_get_messages(s.handle, m.nnz)
+        for key, got, want in (("x", xt.cpu().numpy(), ref["x"]), ("P", P, ref["P"]),
+                               ("mu", mu, ref["mu"])):
+            e = _rel(got, want) if np.abs(want).max() > 0 else float(np.abs(got).max())
+            worst[(key, r)] = e
+    s.close()
+    return worst
+
+
+@pytest.mark.parametrize("name", sorted(PARITY_CASES))
+def test_fp64_messages_match_oracle_every_round(G, name):
+    m = PARITY_CASES[name]
+    b = W.normal_rhs(m.n, 17)
+    worst = _round_parity(G, m, b, (0, 1, 2, 3, 7, 15))
+    bad = {k: v for k, v in worst.items() if v > 1e-12}
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_fp64_parity_for_every_group_width(G, lanes):
+    m = W.er_sdd(2500, 9, 1.1, 4)
+    b = W.uniform_rhs(m.n, 5)
+    worst = _round_parity(G, m, b, (1, 4, 9), group_lanes=lanes)
+    bad = {k: v for k, v in worst.items() if v > 1e-12}
+    assert not bad, bad
+
+
+def test_rev_given_equals_rev_computed(G):
+    m = W.er_sdd(3000, 7, 1.1, 8)
+    b = W.normal_rhs(m.n, 1)
+    rev = W.reverse_index(m)
+    s1 = _solver(G, m)
+    s2 = G.Solver(G.gabp_create(m.row_ptr, m.col, m.val, rev), m.n, m.nnz)
+    bt = torch.tensor(b, device="cuda")
+    x1, x2 = torch.empty_like(bt), torch.empty_like(bt)
+    G.gabp_run_rounds(s1.handle, bt, 6, x1)
+    G.gabp_run_rounds(s2.handle, bt, 6, x2)
+    assert torch.equal(x1, x2)
+
+
+def _oracle_solution(m, b):
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=100000,
+                      tol=1e-13)
+    assert ref["status"] == "ok"
+    return ref["x"]
+
+
+SOLVE_CASES = {
+    "er_20000": (W.er_sdd(20000, 8, 1.1, 11), "normal"),
+    "poisson3d_p16": (W.poisson3d(16), "uniform"),
+    "er_dom105_deg10": (W.er_sdd(20000, 10, 1.05, 12), "normal"),
+}
+
+
+def _rhs(m, kind, seed):
+    return W.normal_rhs(m.n, seed) if kind == "normal" else W.uniform_rhs(m.n, seed)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", sorted(SOLVE_CASES))
+def test_solve_reaches_relative_residual(G, name, precision):
+    m, kind = SOLVE_CASES[name]
+    b = _rhs(m, kind, 21)
+    s = _solver(G, m, precision=precision)
+    bt = torch.tensor(b, device="cuda")
+    xt, iters = s.solve(bt, tol=1e-10, max_iter=20000)
+    x = xt.cpu().numpy()
+    res = oracle.residual_inf(m.row_ptr, m.col, m.val, b, x)
+    assert res < 1e-10 * np.abs(b).max()
+    assert _rel(x, _oracle_solution(m, b)) < 1e-8
+    st = s.stats()
+    assert st["sweeps_total"] == iters and st["status"] == 0
+    if precision == 1:
+        assert st["sweeps_mean"] > 0 and st["outer_steps"] >= 2
+    s.close()
+
+
+def test_config1_poisson2d_p32_absolute_residual(G):
+    """2-D Poisson 32x32, b ~ U[-1,1], plain FP64 sweeps until
+    ||Ax - b||_inf < 1e-10 (absolute)."""
+    m = W.poisson2d(32)
+    b = W.uniform_rhs(m.n, 0)
+    s = _solver(G, m, precision=0, residual_kind=0)
+    xt, iters = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=20000)
+    x = xt.cpu().numpy()
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_ABS, max_rounds=20000, tol=1e-10)
+    # The GPU checks every few sweeps, so it stops at most check_every - 1
+    # rounds after the oracle's first round that meets the rule.
+    assert ref["rounds"] <= iters <= ref["rounds"] + 8
+    s.close()
+
+
+def test_mixed_precision_matches_fp64_oracle_poisson2d(G):
+    m = W.poisson2d(32)
+    b = W.uniform_rhs(m.n, 0)
+    s = _solver(G, m, precision=1, residual_kind=0)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=50000)
+    x = xt.cpu().numpy()
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10
+    assert _rel(x, _oracle_solution(m, b)) < 1e-8
+    s.close()
+
+
+def test_solve_host_matches_device(G):
+    m = W.er_sdd(5000, 8, 1.1, 3)
+    b = W.normal_rhs(m.n, 4)
+    s = _solver(G, m, precision=1)
+    xd, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10)
+    xh, _ = G.gabp_solve_host(s.handle, b, 1e-10, 10000)
+    assert np.array_equal(xd.cpu().numpy(), xh)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_rhs_matches_single_solves(G, precision):
+    m = W.er_sdd(4000, 10, 1.05, 6)
+    B = W.normal_rhs(m.n, 7, k=5)
+    s = _solver(G, m, precision=precision)
+    Bt = torch.tensor(B, device="cuda")
+    Xt = torch.empty_like(Bt)
+    G.gabp_solve_multi(s.handle, Bt, Xt, 1e-10, 10000)
+    X = Xt.cpu().numpy()
+    for k in range(B.shape[1]):
+        res = oracle.residual_inf(m.row_ptr, m.col, m.val, B[:, k], X[:, k])
+        assert res < 1e-10 * np.abs(B[:, k]).max()
+    s.close()
+
+
+def test_breakdown_is_reported(G):
+    m = W.csr_from_dense(np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0]]))
+    s = _solver(G, m, precision=0, check_every=1)
+    with pytest.raises(G.GabpError) as ei:
+        s.solve(torch.ones(3, dtype=torch.float64, device="cuda"), tol=1e-12, max_iter=50)
+    assert ei.value.name == "GABP_ERR_BREAKDOWN"
+    s.close()
+
+
+def test_not_converged_keeps_last_iterate(G):
+    m = W.poisson2d(20)
+    b = W.uniform_rhs(m.n, 1)
+    s = _solver(G, m, precision=0, check_every=1)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.zeros_like(bt)
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_solve(s.handle, bt, xt, 1e-10, 5)
+    assert ei.value.name == "GABP_ERR_NOT_CONVERGED"
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=4)   # x of round 4 after 5 sweeps
+    assert _rel(xt.cpu().numpy(), ref["x"]) < 1e-12
+    s.close()
+
+
+def test_dense_detection_system_diverges(G):
+    """Dense A = S^T S + sigma^2 I of the detection workload: plain GaBP
+    diverges (rho(|I - D^-1 A|) > 1); the solver says so instead of
+    returning garbage."""
+    sysd = W.detection_batch(1, 48, 48, 10.0, seed=3)[0]
+    A, bb = sysd.dense_system()
+    m = W.csr_from_dense(A)
+    s = _solver(G, m, precision=0, check_every=1)
+    with pytest.raises(G.GabpError) as ei:
+        s.solve(torch.tensor(bb, device="cuda"), tol=1e-10, max_iter=2000)
+    assert ei.value.name in ("GABP_ERR_DIVERGED", "GABP_ERR_BREAKDOWN")
+    s.close()
+
+
+def test_nondefault_stream(G):
+    m = W.er_sdd(3000, 8, 1.1, 9)
+    b = W.normal_rhs(m.n, 2)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        s = _solver(G, m, precision=1)
+        bt = torch.tensor(b, device="cuda")
+        xt, _ = s.solve(bt, tol=1e-10)
+    side.synchronize()
+    x = xt.cpu().numpy()
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    s.close()
+
+
+# ---------------------------------------------------------------------------
+# The benchmark's workload at full size: Erdos-Renyi n = 1,000,000, average
+# degree 8, dominance 1.1, b ~ N(0,1), with the launch configuration the
+# benchmark uses (automatic group width, mixed FP32 + FP64 refinement).
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def er_full():
+    m = W.er_sdd(1_000_000, 8, 1.1, 0)
+    b = W.normal_rhs(m.n, 1)
+    return m, b
+
+
+def test_full_size_rounds_match_oracle(G, er_full):
+    m, b = er_full
+    worst = _round_parity(G, m, b, (3,))
+    assert max(worst.values()) <= 1e-12, worst
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_solve(G, er_full, precision):
+    m, b = er_full
+    s = _solver(G, m, precision=precision)
+    xt, iters = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=2000)
+    x = xt.cpu().numpy()
+    res = oracle.residual_inf(m.row_ptr, m.col, m.val, b, x)
+    assert res < 1e-10 * np.abs(b).max()
+    assert _rel(x, _oracle_solution(m, b)) < 1e-9
+    s.close()

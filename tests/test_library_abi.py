@@ -1,0 +1,97 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+symbol include/gabp.h declares, and its host-side validation rejects bad
+matrices before any device work (no GPU needed for any of this)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_0810_1119_gb300 import build_lib
+from paper_0810_1119_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gabp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build_lib.build()
+    from paper_0810_1119_gb300 import gabp
+    return gabp.load(path)
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gabp_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_names():
+    from paper_0810_1119_gb300 import gabp
+    assert _declared_functions() == sorted(gabp.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", build_lib.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (gabp_\w+)", out))
+    for name in _declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_default_options_and_strings(lib):
+    from paper_0810_1119_gb300 import gabp
+    o = gabp.gabp_default_options()
+    assert o.precision == gabp.PREC_FP64 and o.residual_kind == gabp.RESIDUAL_REL
+    assert o.inner_tol == pytest.approx(1e-6)
+    assert lib.gabp_status_string(4) == b"GABP_ERR_BREAKDOWN"
+    assert b"sm_103a" in lib.gabp_version()
+
+
+def _create_status(m, rev=None):
+    from paper_0810_1119_gb300 import gabp
+    try:
+        gabp.gabp_create(m.row_ptr, m.col, m.val, rev)
+    except gabp.GabpError as e:
+        return e.name, str(e)
+    return "GABP_OK", ""
+
+
+@pytest.mark.parametrize("A,expect", [
+    (np.array([[2.0, 1.0], [0.5, 2.0]]), "GABP_ERR_NOT_SYMMETRIC"),
+    (np.array([[2.0, 1.0], [0.0, 2.0]]), "GABP_ERR_NOT_SYMMETRIC"),
+    (np.array([[0.0, 1.0], [1.0, 2.0]]), "GABP_ERR_ZERO_DIAG"),
+])
+def test_create_rejects_bad_matrices_on_the_host(lib, A, expect):
+    status, msg = _create_status(W.csr_from_dense(A))
+    assert status == expect, msg
+
+
+def test_create_rejects_malformed_csr(lib):
+    m = W.poisson2d(3)
+    bad = W.CSR(m.n, m.row_ptr.copy(), m.col.copy(), m.val.copy())
+    bad.col[1], bad.col[2] = bad.col[2], bad.col[1]     # unsorted row
+    assert _create_status(bad)[0] == "GABP_ERR_INVALID_ARG"
+    bad = W.CSR(m.n, m.row_ptr.copy(), m.col.copy(), m.val.copy())
+    bad.col[0] = m.n + 5                                # out of range
+    assert _create_status(bad)[0] == "GABP_ERR_INVALID_ARG"
+
+
+def test_create_rejects_wrong_rev(lib):
+    m = W.poisson2d(4)
+    rev = W.reverse_index(m)
+    off = np.flatnonzero(np.repeat(np.arange(m.n), np.diff(m.row_ptr)) != m.col)
+    rev[off[0]], rev[off[1]] = rev[off[1]], rev[off[0]]
+    assert _create_status(m, rev)[0] == "GABP_ERR_NOT_SYMMETRIC"
+
+
+def test_reverse_index_is_an_involution():
+    m = W.er_sdd(500, 6, 1.1, 3)
+    rev = W.reverse_index(m)
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    assert np.array_equal(rev[rev], np.arange(m.nnz))
+    assert np.array_equal(m.col[rev], rows)
