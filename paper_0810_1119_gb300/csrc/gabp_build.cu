@@ -1,6 +1,7 @@
 // gabp_build.cu -- graph builder: validates the CSR of A, splits off the
 // diagonal, drops explicit zeros, derives the reverse-edge index in slot
-// numbering, bins rows by degree and uploads the device arrays.
+// numbering, cuts the rows into tiles for the staged sweep kernels, picks the
+// lanes-per-row from the mean degree and uploads the device arrays.
 //
 // Graph of Section II-B: node i per row, an edge per off-diagonal non-zero;
 // P_ii = A_ii must be non-zero (Alg. 2 step 1 divides by it).
@@ -15,13 +16,35 @@ namespace gabp {
 
 namespace {
 
+// Device copy with kPad elements of zeroed slack past the end (the staged
+// kernels round their bulk copies up to 16 bytes).
 template <class T>
 cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t st) {
-  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  const size_t bytes = (count + kPad) * sizeof(T);
   cudaError_t e = cudaMalloc(reinterpret_cast<void **>(dst), bytes);
   if (e != cudaSuccess) return e;
-  if (count) e = cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
+  e = cudaMemsetAsync(*dst, 0, bytes, st);
+  if (e == cudaSuccess && count)
+    e = cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
   return e;
+}
+
+// Greedy row tiles: consecutive rows while the tile keeps <= max_slots slots
+// and <= max_rows rows; a row with more than max_slots slots is alone.
+std::vector<int2> make_tiles(const std::vector<int32_t> &rp, int64_t n, int max_slots,
+                             int max_rows) {
+  std::vector<int2> t;
+  int64_t r = 0;
+  while (r < n) {
+    const int32_t s0 = rp[r];
+    int64_t end = r + 1;
+    if (rp[r + 1] - s0 <= max_slots)
+      while (end < n && end - r < max_rows && rp[end + 1] - s0 <= max_slots) ++end;
+    t.push_back(make_int2(static_cast<int>(r), s0));
+    r = end;
+  }
+  t.push_back(make_int2(static_cast<int>(n), rp[n]));
+  return t;
 }
 
 int next_pow2(int v) {
@@ -132,43 +155,21 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
   }
   g.max_degree = max_deg;
 
-  // Degree bins: rows of degree <= kCacheSlots * G run with G lanes per row;
-  // longer rows run warp-per-row.
+  // Lanes per row: the next power of two at or above the mean degree.
   int G = opt.group_lanes;
   if (G <= 0) {
     const double avg = static_cast<double>(E) / static_cast<double>(n);
-    G = std::min(32, std::max(2, next_pow2(static_cast<int>(std::ceil(avg)))));
+    G = next_pow2(static_cast<int>(std::ceil(avg)));
   }
-  G = std::min(32, std::max(1, next_pow2(G)));
-  std::vector<int32_t> short_rows, long_rows;
-  const int long_threshold = kCacheSlots * G;
-  for (int64_t i = 0; i < n; ++i) {
-    const int deg = g.h_rp[i + 1] - g.h_rp[i];
-    if (G < 32 && deg > long_threshold) long_rows.push_back(static_cast<int32_t>(i));
-  }
-  g.bins.clear();
-  cudaError_t ce = cudaSuccess;
-  if (long_rows.empty()) {
-    RowBin b;
-    b.rows = nullptr;
-    b.nrows = g.n;
-    b.group = G;
-    g.bins.push_back(b);
-  } else {
-    for (int64_t i = 0, k = 0; i < n; ++i) {
-      if (k < static_cast<int64_t>(long_rows.size()) && long_rows[k] == i) { ++k; continue; }
-      short_rows.push_back(static_cast<int32_t>(i));
-    }
-    RowBin b0, b1;
-    b0.group = G;
-    b0.nrows = static_cast<int32_t>(short_rows.size());
-    b1.group = 32;
-    b1.nrows = static_cast<int32_t>(long_rows.size());
-    ce = upload(&b0.rows, short_rows.data(), short_rows.size(), st);
-    if (ce == cudaSuccess) ce = upload(&b1.rows, long_rows.data(), long_rows.size(), st);
-    g.bins.push_back(b0);
-    g.bins.push_back(b1);
-  }
+  g.group = std::min(32, std::max(2, next_pow2(G)));
+  int big_s, big_r, small_s, small_r;
+  tile_sizes(&big_s, &big_r, &small_s, &small_r);
+  const std::vector<int2> tb = make_tiles(g.h_rp, n, big_s, big_r);
+  const std::vector<int2> ts = make_tiles(g.h_rp, n, small_s, small_r);
+  g.ntiles_big = static_cast<int32_t>(tb.size() - 1);
+  g.ntiles_small = static_cast<int32_t>(ts.size() - 1);
+  cudaError_t ce = upload(&g.tiles_big, tb.data(), tb.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.tiles_small, ts.data(), ts.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.rp, g.h_rp.data(), g.h_rp.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.col, g.h_col.data(), g.h_col.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.rev, g.h_rev.data(), g.h_rev.size(), st);
@@ -177,6 +178,10 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
   if (ce == cudaSuccess) ce = upload(&g.diag64, d64.data(), d64.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.diag32, d32.data(), d32.size(), st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce == cudaSuccess) {
+    prepare_kernels(g.group, opt.precision == GABP_PREC_MIXED_BF16);
+    ce = cudaGetLastError();
+  }
   if (ce != cudaSuccess) {
     *msg = std::string("device upload failed: ") + cudaGetErrorString(ce);
     return ce == cudaErrorMemoryAllocation ? GABP_ERR_OOM : GABP_ERR_CUDA;
@@ -185,8 +190,8 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
 }
 
 void free_graph(Graph &g) {
-  for (RowBin &b : g.bins) cudaFree(b.rows);
-  g.bins.clear();
+  cudaFree(g.tiles_big); cudaFree(g.tiles_small);
+  g.tiles_big = g.tiles_small = nullptr;
   cudaFree(g.rp); cudaFree(g.col); cudaFree(g.rev);
   cudaFree(g.a64); cudaFree(g.a32); cudaFree(g.diag64); cudaFree(g.diag32);
   g.rp = g.col = g.rev = nullptr;

@@ -9,6 +9,13 @@
 //   sends m_{i->j} by writing slot rev[s] (the slot of entry (j, i) in row j).
 //   Each message is the pair (P, eta) with eta = P * mu (information form:
 //   no division by A_ij is needed and eta sums directly into h~).
+//
+// Control: every solve is driven by a small control block (Ctl) in device
+// memory.  Kernels read their buffer parities and flags from it, and the last
+// block of each controlling launch runs the decision logic (convergence,
+// precision freeze, refinement, stop) and writes the next phase back, so a
+// whole solve can run as one CUDA graph (a WHILE node around a SWITCH on the
+// phase) with a single host synchronisation at the end.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,10 +32,10 @@ namespace gabp {
 constexpr int kBlock = 256;          // threads per block of the row kernels
 constexpr int kCacheSlots = 4;       // slots per lane kept in registers
 
-// Device-side reduction slots, zeroed before use.  Maxima of non-negative
-// doubles are accumulated with 64-bit atomicMax on their bit patterns
-// (IEEE order and unsigned order agree for non-negative values; NaN compares
-// above +inf and so surfaces as "not finite").
+// Device-side reduction slots.  Maxima of non-negative doubles are kept with
+// 64-bit atomicMax on their bit patterns (IEEE order and unsigned order agree
+// for non-negative values; NaN compares above +inf and so reads as "not
+// finite").  The controller zeroes what it consumed.
 struct DevScalars {
   unsigned long long max_dx;      // max_i |x_i^t - x_i^{t-1}|   (or |d| change)
   unsigned long long max_x;       // max_i |x_i^t|
@@ -37,14 +44,71 @@ struct DevScalars {
   unsigned long long max_r;       // max_i |r_i|
   unsigned long long max_b;       // max_i |b_i|
   int breakdown;                  // set when P~_i - P_ji is zero or not finite
-  int pad[3];
+  int timeout;                    // set when a bounded wait gave up
+  int pad[2];
 };
 
-// One row bin: the rows a launch covers and its lanes-per-row.
-struct RowBin {
-  int32_t *rows = nullptr;  // device list of row ids; nullptr = rows 0..nrows-1
-  int32_t nrows = 0;
-  int group = 8;            // lanes per row (power of two, 1..32)
+// Solve phases (the SWITCH index of the solve graph).
+enum Phase : int {
+  PH_FULL64 = 0,    // FP64 full sweep
+  PH_CHECK64 = 1,   // FP64 residual check
+  PH_FULL32 = 2,    // FP32 full sweep (freezes when pending_freeze is set)
+  PH_MEAN = 3,      // mean-only sweep with frozen precisions
+  PH_REFINE = 4,    // x += ||r|| d, r = b - A x
+  PH_COUNT = 5,
+  PH_DONE = 7
+};
+
+enum CtlMode : int { CTL_ROUNDS = 0, CTL_FP64 = 1, CTL_MIXED = 2 };
+
+struct Ctl {
+  // ---- set by the host before a solve ----
+  const double *b;          // right-hand side (device)
+  double *x;                // solution (device)
+  double tol;
+  int rel;                  // 1 = relative residual
+  int mode;                 // CtlMode
+  int max_iter;
+  int check_every;
+  double inner_tol;
+  int in_graph;             // 1 = set the graph's conditional handles
+  int rounds_target;        // CTL_ROUNDS: sweeps before the infer-only pass
+  unsigned long long h_while, h_phase;
+  // ---- state ----
+  int phase;
+  int par_m, par_e, par_mon;    // buffer parities: in = buf[par], out = buf[par ^ 1]
+  int first;                    // first sweep of an inner solve: incoming messages are zero
+  int write_x;                  // FP64: this sweep writes the tentative means
+  int frozen, pending_freeze;
+  int k, stall, sweeps, sweeps_full, sweeps_mean, outer, checks, steps;
+  double prev_dd, prev_dP;
+  double bnorm, thr, rn, inv_rn, residual;
+  int status, done;
+  unsigned int blocks_done;     // last-block detection counter
+  int pad;
+};
+
+// Device buffers of a handle, passed to the kernels by value.
+struct Buffers {
+  double2 *m64[2];
+  float2 *m32[2];
+  void *e[2];               // mean messages: float or bf16 (per precision mode)
+  float *c32;               // frozen coefficients c_ij (slot s of row i)
+  float *invP32;            // frozen 1/P~_i
+  float2 *mon32[2];         // (P~_i, d_i) of the last two sweeps
+  double *r64;              // FP64 residual
+};
+
+// Row tiles: tiles[t] = (first row, first slot) of tile t, tiles[ntiles] =
+// (n, E).  A tile holds at most a fixed number of slots and rows, except a
+// single row with more slots, which is a tile of its own.
+struct GraphView {
+  const int32_t *rp, *rev, *col;
+  const double *a64, *diag64;
+  const float *a32, *diag32;
+  const int2 *tiles_big, *tiles_small;
+  int32_t ntiles_big, ntiles_small;
+  int32_t n;
 };
 
 struct Graph {
@@ -57,9 +121,39 @@ struct Graph {
   int32_t *rp = nullptr, *col = nullptr, *rev = nullptr;
   double *a64 = nullptr, *diag64 = nullptr;
   float *a32 = nullptr, *diag32 = nullptr;
-  std::vector<RowBin> bins;      // a partition of the rows
+  int2 *tiles_big = nullptr, *tiles_small = nullptr;
+  int32_t ntiles_big = 0, ntiles_small = 0;
+  int group = 8;                 // lanes per row in the sweep kernels
   int max_degree = 0;
+
+  GraphView view() const {
+    return GraphView{rp,       rev,       col,        a64,         diag64,      a32,
+                     diag32,   tiles_big, tiles_small, ntiles_big, ntiles_small, n};
+  }
 };
+
+// Kernel launchers (gabp_kernels.cu).  Each returns the number of kernels it
+// launched; the last kernel of every launcher runs the controller in its
+// last block.
+int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
+int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
+int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+void prepare_kernels(int group, bool bf16);
+void tile_sizes(int *big_slots, int *big_rows, int *small_slots, int *small_rows);
+double bits_to_double(unsigned long long u);
+
+// Extra elements allocated past the end of every array the kernels stage
+// into shared memory: the bulk copies round their ends up to 16 bytes.
+constexpr size_t kPad = 32;
+
+// ---- graph builder (gabp_build.cu) ----
+gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr,
+                        const int32_t *col, const double *val, const int64_t *rev,
+                        const gabp_options &opt, cudaStream_t st, std::string *msg);
+void free_graph(Graph &g);
 
 }  // namespace gabp
 
@@ -71,52 +165,22 @@ struct gabp_s {
   gabp_stats stats{};
   int64_t user_nnz = 0;            // nnz of the CSR given to gabp_create
 
-  // FP64 full sweep state
-  double2 *m64[2] = {nullptr, nullptr};
-  int m64_cur = 0;                 // buffer holding the latest messages
-  double *x_prev = nullptr;        // [n] previous tentative means (monitor)
-  // FP32 state
-  float2 *m32[2] = {nullptr, nullptr};
-  float *e32[2] = {nullptr, nullptr};
-  float *c32 = nullptr;            // [E] frozen mean coefficients
-  float *invP32 = nullptr;         // [n] frozen 1/P~_i
-  float *rhs32 = nullptr;          // [n] scaled right-hand side of the inner solve
-  float2 *mon32[2] = {nullptr, nullptr};  // [n] (P~_i, d_i) of the last two sweeps
-  // FP64 refinement state
-  double *xw = nullptr, *r64 = nullptr;
-  gabp::DevScalars *red = nullptr;        // device
-  gabp::DevScalars *red_host = nullptr;   // pinned host mirror
+  gabp::Buffers buf{};
+  bool have64 = false, have32 = false;
+  int m64_cur = 0;                 // buffer holding the messages left by gabp_run_rounds
+  gabp::Ctl *ctl = nullptr;        // device control block
+  gabp::Ctl *ctl_host = nullptr;   // pinned mirror
+  gabp::DevScalars *red = nullptr; // device reductions
   double *bbuf = nullptr, *xbuf = nullptr;  // device staging for gabp_solve_host
+
+  // one instantiated solve graph per control mode
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphConditionalHandle cond[3][2] = {};   // (WHILE, SWITCH) handles per mode
+  cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
+
   // profiling (gabp_options.profile): pairs of events around kernels
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_kind;
   int ev_used = 0;
 };
-
-namespace gabp {
-
-// ---- kernels (gabp_kernels.cu) ----
-int launch_sweep64(const Graph &g, cudaStream_t st, const double2 *min, double2 *mout,
-                    const double *b, double *x_out, const double *x_prev, DevScalars *red,
-                    bool write_msgs);
-int launch_sweep32(const Graph &g, cudaStream_t st, const float2 *min, float2 *mout,
-                    const float *rhs, const float2 *mon_prev, float2 *mon_out,
-                    float *c_out, float *invP_out, float *eta_out, DevScalars *red);
-int launch_mean32(const Graph &g, cudaStream_t st, const float *ein, float *eout,
-                   const float *c, const float *invP, const float *rhs, const float2 *mon_prev,
-                   float2 *mon_out, DevScalars *red);
-int launch_residual64(const Graph &g, cudaStream_t st, const double *b, const double *x,
-                       double *r_out, DevScalars *red);
-int launch_max_abs(cudaStream_t st, const double *v, int64_t n, unsigned long long *slot);
-int launch_scale_to_f32(cudaStream_t st, const double *v, int64_t n, double scale, float *out);
-int launch_refine_update(cudaStream_t st, int64_t n, double *x, const float2 *mon, double inv_scale);
-void launch_fill_zero(cudaStream_t st, void *p, size_t bytes);
-double bits_to_double(unsigned long long u);
-
-// ---- graph builder (gabp_build.cu) ----
-gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr,
-                        const int32_t *col, const double *val, const int64_t *rev,
-                        const gabp_options &opt, cudaStream_t st, std::string *msg);
-void free_graph(Graph &g);
-
-}  // namespace gabp

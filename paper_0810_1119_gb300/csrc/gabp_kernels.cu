@@ -1,12 +1,13 @@
-// gabp_kernels.cu -- sm_103a kernels of the synchronous broadcast GaBP sweep.
+// gabp_kernels.cu -- sm_103a kernels of the synchronous broadcast GaBP sweep
+// and the device-side solve controller.
 //
 // Every sweep kernel implements one round of Alg. 2 (broadcast GaBP) with the
 // parallel schedule of Section III-C: it reads only the previous round's
 // messages (buffer "in") and writes the new round (buffer "out").
 //
-// Work mapping: a group of G lanes (G a power of two, G <= 32) owns one row i.
-// The lanes stride over the row's slots, which hold the incoming messages
-// m_{j->i}; the row totals
+// Work mapping: a group of G lanes (G a power of two, 2 <= G <= 32) owns one
+// row i.  The lanes stride over the row's slots, which hold the incoming
+// messages m_{j->i}; the row totals
 //     P~_i = A_ii + sum_k P_ki,        h~_i = b_i + sum_k eta_ki
 // are formed with a shuffle reduction inside the group, and each lane then
 // sends the messages of its own slots (the reverse message m_{j->i} needed by
@@ -16,16 +17,29 @@
 // written to slot rev[s] of row j.  Reads are contiguous; only the message
 // store is a scatter.  Up to kCacheSlots slots per lane stay in registers
 // between the two passes; longer rows re-read the tail.
+//
+// Control: kernels take their buffer parities and flags from the control
+// block (Ctl).  The last block to finish a controlling launch (detected with
+// an atomic counter, no waiting) runs `control`, which reads the reductions,
+// decides the next phase, and -- inside a solve graph -- sets the graph's
+// WHILE and SWITCH conditions.
 #include "gabp_internal.h"
 
 #include <algorithm>
+#include <cfloat>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 namespace gabp {
 namespace {
 
 __device__ __forceinline__ unsigned long long bits(double v) {
   return static_cast<unsigned long long>(__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double dv(unsigned long long u) {
+  return __longlong_as_double(static_cast<long long>(u));
 }
 
 __device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) {
@@ -39,8 +53,8 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 }
 
 // Block-wide maximum of up to four non-negative values (as bit patterns),
-// committed with one atomicMax per value and block.  Every thread of the
-// block must call it.
+// committed with one atomicMax per value and block by thread 0.  Every thread
+// of the block must call it.
 __device__ void block_max4(unsigned long long v0, unsigned long long v1, unsigned long long v2,
                            unsigned long long v3, unsigned long long *d0, unsigned long long *d1,
                            unsigned long long *d2, unsigned long long *d3) {
@@ -70,303 +84,784 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// Storage type of the mean messages: FP32, or BF16 with FP32 arithmetic.
+__device__ __forceinline__ float ld_eta(const float *p) { return *p; }
+__device__ __forceinline__ float ld_eta(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st_eta(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_eta(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
-// Row owned by this lane's group in the current warp step.
-struct RowSlot {
-  bool valid;
-  int32_t i, rs, re;
-};
+// ---------------------------------------------------------------------------
+// Controller (one thread of the last block of a controlling launch).
+// ---------------------------------------------------------------------------
+enum CtrlKind { CK_INIT = 1, CK_SWEEP64, CK_CHECK64, CK_SWEEP32, CK_MEAN, CK_REFINE };
 
-__device__ __forceinline__ RowSlot row_at(const int32_t *__restrict__ rp,
-                                          const int32_t *__restrict__ rows, int32_t nrows,
-                                          int64_t ri) {
-  RowSlot r;
-  r.valid = ri < nrows;
-  r.i = r.valid ? (rows ? rows[ri] : static_cast<int32_t>(ri)) : 0;
-  r.rs = r.valid ? rp[r.i] : 0;
-  r.re = r.valid ? rp[r.i + 1] : 0;
-  return r;
+__device__ void finish(Ctl &c, int status) {
+  c.status = status;
+  c.done = 1;
+  c.phase = PH_DONE;
 }
 
-// ---------------------------------------------------------------------------
-// FP64 full sweep: new (P, eta) for every directed edge, plus optionally the
-// tentative means x_i = h~_i / P~_i of the messages read (Alg. 2 step 4).
-// ---------------------------------------------------------------------------
-template <int G>
-__global__ void __launch_bounds__(kBlock)
-sweep64_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ rev,
-               const int32_t *__restrict__ rows, int32_t nrows, const double *__restrict__ a,
-               const double *__restrict__ diag, const double *__restrict__ b,
-               const double2 *__restrict__ min, double2 *__restrict__ mout,
-               double *__restrict__ x_out, const double *__restrict__ x_prev, DevScalars *red,
-               int write_msgs) {
-  constexpr int R = kCacheSlots;
-  constexpr int RPW = 32 / G;
-  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  unsigned long long mdx = 0, mx = 0;
-  bool brk = false;
+__device__ bool diverged(double rn, double bnorm) {
+  return !isfinite(rn) || rn > 1e30 * fmax(bnorm, DBL_MIN);
+}
 
-  for (int64_t base = warp * RPW; base < nrows; base += nwarps * RPW) {
-    const RowSlot row = row_at(rp, rows, nrows, base + sub);
-    double2 mc[R];
-    double ac[R];
-    int32_t rc[R];
-    double sP = 0.0, sH = 0.0;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int32_t s = row.rs + gl + k * G;
-      if (s < row.re) {
-        mc[k] = min[s];
-        sP += mc[k].x;
-        sH += mc[k].y;
-        if (write_msgs) { ac[k] = a[s]; rc[k] = rev[s]; }
+// Reductions are read through volatile loads (they were committed by other
+// blocks' atomics) and zeroed once consumed.
+__device__ void control(Ctl &c, DevScalars *red, int kind) {
+  volatile DevScalars *r = red;
+  c.steps++;
+  if (r->timeout) {
+    finish(c, GABP_ERR_TIMEOUT);
+    kind = 0;
+  }
+  switch (kind) {
+    case CK_INIT: {
+      c.bnorm = dv(r->max_b);
+      r->max_b = 0;
+      c.thr = c.rel ? c.tol * c.bnorm : c.tol;
+      c.residual = c.bnorm;
+      if (!isfinite(c.bnorm)) { finish(c, GABP_ERR_INVALID_ARG); break; }
+      if (c.mode == CTL_FP64) {
+        c.phase = PH_FULL64;
+        c.write_x = (c.check_every <= 1) || (c.max_iter <= 1);
+      } else {
+        c.rn = c.bnorm;
+        if (c.rn < c.thr || c.bnorm == 0.0) { finish(c, GABP_OK); break; }
+        c.inv_rn = 1.0 / c.rn;
+        c.outer = 1;
+        c.phase = c.frozen ? PH_MEAN : PH_FULL32;
       }
+      break;
     }
-    for (int32_t s = row.rs + gl + R * G; s < row.re; s += G) {
-      const double2 m = min[s];
-      sP += m.x;
-      sH += m.y;
-    }
-    sP = group_sum<G>(sP);
-    sH = group_sum<G>(sH);
-    if (!row.valid) continue;
-    const double TP = diag[row.i] + sP;   // P~_i
-    const double Th = b[row.i] + sH;      // h~_i = P~_i mu~_i
-    if (x_out && gl == 0) {
-      const double xi = Th / TP;
-      x_out[row.i] = xi;
-      if (x_prev) {
-        mdx = umax(mdx, bits(fabs(xi - x_prev[row.i])));
-        mx = umax(mx, bits(fabs(xi)));
+    case CK_SWEEP64: {
+      if (c.mode == CTL_ROUNDS) {
+        // the pass after `rounds_target` sweeps only infers and leaves the
+        // state alone, so the last round's messages stay in m64[par_m]
+        if (c.sweeps < c.rounds_target) { c.sweeps++; c.par_m ^= 1; c.first = 0; }
+        break;
       }
+      c.sweeps++;
+      c.sweeps_full++;
+      c.par_m ^= 1;
+      c.first = 0;
+      if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
+      if (c.write_x) c.phase = PH_CHECK64;
+      const int next = c.sweeps + 1;
+      c.write_x = (next % c.check_every == 0) || next >= c.max_iter;
+      break;
     }
-    if (!write_msgs) continue;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int32_t s = row.rs + gl + k * G;
-      if (s < row.re) {
-        const double d = TP - mc[k].x;    // P_{i\j} = P~_i - P_ji
-        brk |= !(d != 0.0) || !isfinite(d);
-        const double inv = 1.0 / d;
-        mout[rc[k]] = make_double2(-(ac[k] * ac[k]) * inv, -ac[k] * (Th - mc[k].y) * inv);
+    case CK_CHECK64:
+    case CK_REFINE: {
+      c.checks++;
+      const double rn = dv(r->max_r);
+      r->max_r = 0;
+      c.residual = rn;
+      if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
+      if (rn < c.thr) { finish(c, GABP_OK); break; }
+      if (diverged(rn, c.bnorm)) { finish(c, GABP_ERR_DIVERGED); break; }
+      if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
+      if (kind == CK_CHECK64) { c.phase = PH_FULL64; break; }
+      // next refinement step: solve A d = r / ||r|| from zero mean messages
+      c.outer++;
+      c.rn = rn;
+      c.inv_rn = 1.0 / rn;
+      c.k = 0;
+      c.stall = 0;
+      c.prev_dd = INFINITY;
+      c.prev_dP = INFINITY;
+      c.first = 1;
+      c.phase = c.frozen ? PH_MEAN : PH_FULL32;
+      break;
+    }
+    case CK_SWEEP32:
+    case CK_MEAN: {
+      if (kind == CK_SWEEP32) {
+        c.sweeps_full++;
+        if (c.pending_freeze) { c.frozen = 1; c.pending_freeze = 0; c.par_e ^= 1; }
+        else c.par_m ^= 1;
+      } else {
+        c.sweeps_mean++;
+        c.par_e ^= 1;
       }
-    }
-    for (int32_t s = row.rs + gl + R * G; s < row.re; s += G) {
-      const double2 m = min[s];
-      const double av = a[s];
-      const double d = TP - m.x;
-      brk |= !(d != 0.0) || !isfinite(d);
-      const double inv = 1.0 / d;
-      mout[rev[s]] = make_double2(-(av * av) * inv, -av * (Th - m.y) * inv);
+      c.par_mon ^= 1;
+      c.first = 0;
+      c.sweeps++;
+      c.k++;
+      const double mx = dv(r->max_x), mdx = dv(r->max_dx);
+      const double mP = dv(r->max_P), mdP = dv(r->max_dP);
+      r->max_x = 0; r->max_dx = 0; r->max_P = 0; r->max_dP = 0;
+      if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
+      const double dd = mdx / fmax(mx, DBL_MIN);
+      if (!isfinite(dd)) { finish(c, GABP_ERR_DIVERGED); break; }
+      if (kind == CK_SWEEP32 && !c.frozen && !c.pending_freeze) {
+        // Precision convergence: relative change of the node precisions,
+        // remaining error extrapolated with the observed contraction rate.
+        const double dP = mdP / fmax(mP, DBL_MIN);
+        const double rho = dP / c.prev_dP;
+        const double errP = dP == 0.0 ? 0.0 : (rho < 1.0 ? dP * rho / (1.0 - rho) : INFINITY);
+        if (c.k >= 3 && (errP < 1e-6 || dP < 1e-7 || (rho >= 1.0 && dP < 1e-5))) c.pending_freeze = 1;
+        c.prev_dP = dP;
+      }
+      const double rho_d = dd / c.prev_dd;
+      const double err_d = dd == 0.0 ? 0.0 : (rho_d < 1.0 ? dd * rho_d / (1.0 - rho_d) : INFINITY);
+      c.stall = rho_d >= 1.0 ? c.stall + 1 : 0;
+      c.prev_dd = dd;
+      const bool inner_done =
+          c.frozen && c.k >= 3 && (err_d < c.inner_tol || (c.stall >= 2 && dd < 1e-4));
+      if (inner_done || c.sweeps >= c.max_iter) c.phase = PH_REFINE;
+      else c.phase = c.frozen ? PH_MEAN : PH_FULL32;
+      break;
     }
   }
-  if (brk) atomicOr(&red->breakdown, 1);
-  if (x_prev) block_max4(mdx, mx, 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
+  // Hard bound on controller steps: the loop ends even if a rule misfires.
+  if (!c.done && c.mode != CTL_ROUNDS && c.steps > 4 * c.max_iter + 64)
+    finish(c, GABP_ERR_NOT_CONVERGED);
+  if (c.in_graph) {
+    cudaGraphSetConditional(c.h_phase, c.done ? 0u : static_cast<unsigned>(c.phase));
+    cudaGraphSetConditional(c.h_while, c.done ? 0u : 1u);
+  }
+}
+
+// Called by every thread at the end of a controlling launch.  No waiting:
+// each block bumps a counter after its atomics; the block that brings it to
+// gridDim.x runs the controller.
+__device__ void last_block_control(Ctl *ctl, DevScalars *red, int kind) {
+  __shared__ int is_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (is_last && threadIdx.x == 0) {
+    __threadfence();
+    ctl->blocks_done = 0;
+    control(*ctl, red, kind);
+    __threadfence();
+  }
 }
 
 // ---------------------------------------------------------------------------
-// FP32 full sweep (mixed modes, precision phase).  Messages (P, eta) in FP32,
-// totals in FP32.  Always records (P~_i, d_i = h~_i / P~_i) per node and the
-// change against the previous sweep.  With c_out != nullptr it is the
-// freezing sweep: instead of new (P, eta) it stores the frozen coefficient
-// c_ij = -A_ij / (P~_i - P_ji) at slot s of row i, 1/P~_i, and the first
-// mean-only messages eta_ij = c_ij (h~_i - eta_ji) into eta_out.
+// Solve set-up: ||b||_inf; in the mixed modes also x = 0 and r = b.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) init_kernel(int32_t n, double *__restrict__ r64,
+                                                      Ctl *ctl, DevScalars *red) {
+  const double *b = ctl->b;
+  double *x = ctl->x;
+  const bool mixed = ctl->mode == CTL_MIXED;
+  unsigned long long m = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double bi = b[i];
+    m = umax(m, bits(fabs(bi)));
+    if (mixed) { x[i] = 0.0; r64[i] = bi; }
+  }
+  block_max4(m, 0, 0, 0, &red->max_b, nullptr, nullptr, nullptr);
+  last_block_control(ctl, red, CK_INIT);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory staging of row tiles.
+//
+// A tile is a run of consecutive rows [r0, r1) whose slots [s0, s1) number
+// at most TS (and rows at most TR); a row with more than TS slots is a tile
+// of its own ("long tile") that the whole CTA processes straight from global
+// memory.  Persistent CTAs walk the tiles with a two-stage pipeline: thread 0
+// stages the next tile's contiguous slot and node arrays into shared memory
+// with cp.async.bulk (one copy per array, completion counted on an
+// mbarrier) while the CTA computes the current tile from shared memory.
+// Every wait is bounded; a wait that gives up sets `timeout` in the
+// reductions (the controller then stops the solve with GABP_ERR_TIMEOUT).
+// ---------------------------------------------------------------------------
+constexpr int kTileSlotsBig = 2048, kTileRowsBig = 512;     // FP32 sweeps, residual
+constexpr int kTileSlotsSmall = 1024, kTileRowsSmall = 256; // FP64 sweep
+constexpr int kWaitLimit = 1 << 22;                         // try_wait polls before giving up
+
+__host__ __device__ constexpr uint32_t r128(uint64_t b) {
+  return static_cast<uint32_t>((b + 127) & ~uint64_t{127});
+}
+// Bytes of a staged array of `count` elements of size `es` (plus slack for
+// the 16-byte rounding of the copy's start and end).
+__host__ __device__ constexpr uint32_t region(int count, int es) {
+  return r128(static_cast<uint64_t>(count + 32) * es);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One staged array: elements [first, first + count) of `base`, copied from
+// the 16-byte boundary at or below `first` to the one at or above the end.
+template <class E>
+struct Seg {
+  static constexpr int64_t kPer = 16 / static_cast<int64_t>(sizeof(E));
+  __device__ static uint32_t bytes(int64_t first, int64_t count) {
+    const int64_t a0 = first - first % kPer;
+    const int64_t a1 = (first + count + kPer - 1) / kPer * kPer;
+    return static_cast<uint32_t>((a1 - a0) * static_cast<int64_t>(sizeof(E)));
+  }
+  __device__ static void copy(uint32_t dst, const E *base, int64_t first, int64_t count,
+                              uint32_t bar) {
+    const uint32_t b = bytes(first, count);
+    if (b) bulk_g2s(dst, base + (first - first % kPer), b, bar);
+  }
+  // Shared-memory pointer to element `first` of a staged run.
+  __device__ static const E *at(const unsigned char *region_ptr, int64_t first) {
+    return reinterpret_cast<const E *>(region_ptr) + first % kPer;
+  }
+};
+
+struct TileBounds {
+  int32_t r0, r1, s0, s1;
+};
+__device__ __forceinline__ TileBounds tile_at(const int2 *__restrict__ tiles, int32_t t) {
+  const int2 a = tiles[t], b = tiles[t + 1];
+  return TileBounds{a.x, b.x, a.y, b.y};
+}
+
+// Persistent two-stage loop over the tiles.  `issue(t, stage_ptr, bar)` is
+// called by thread 0 and must arrive once on `bar` with the bytes it copies;
+// `work(t, stage_ptr)` is called by all threads once the stage has landed.
+// Returns false if a wait gave up (after draining the copy in flight).
+template <class Issue, class Work>
+__device__ bool run_tiles(int32_t ntiles, unsigned char *smem, uint32_t stage_bytes,
+                          uint64_t *bars, Issue issue, Work work) {
+  const uint32_t bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  if (threadIdx.x == 0) {
+    mbar_init(bar[0], 1);
+    mbar_init(bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int32_t t = blockIdx.x;
+  if (t < ntiles && threadIdx.x == 0) issue(t, smem, bar[0]);
+  bool ok = true;
+  for (int j = 0; t < ntiles; ++j, t += gridDim.x) {
+    const int st = j & 1;
+    const int32_t tn = t + gridDim.x;
+    if (tn < ntiles && threadIdx.x == 0) {
+      fence_proxy_async();   // stage st^1 was last read by generic loads
+      issue(tn, smem + (st ^ 1) * stage_bytes, bar[st ^ 1]);
+    }
+    const bool got = mbar_wait(bar[st], (j >> 1) & 1);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+      if (tn < ntiles) mbar_wait(bar[st ^ 1], ((j + 1) >> 1) & 1);
+      __syncthreads();
+      break;
+    }
+    work(t, smem + st * stage_bytes);
+    __syncthreads();
+  }
+  return ok;
+}
+
+// Block-wide sum (all threads call it; every thread gets the result).
+template <class T>
+__device__ T block_sum(T v) {
+  __shared__ T part[kBlock / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  T tot = T(0);
+#pragma unroll
+  for (int k = 0; k < kBlock / 32; ++k) tot += part[k];
+  return tot;
+}
+
+// 1/d in FP64: an FP32 reciprocal seed (relative error e0 < 2^-22), then the
+// cubic Newton-Raphson step y (1 + e + e^2) with e = 1 - d y, whose error is
+// e0^3 < 2^-66 before rounding.  Outside the FP32 normal range (or for
+// zero / non-finite d) the IEEE division is used.
+__device__ __forceinline__ double recip64(double d) {
+  const double ad = fabs(d);
+  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  const double y = static_cast<double>(__frcp_rn(static_cast<float>(d)));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 full sweep: new (P, eta) for every directed edge, plus (when asked)
+// the tentative means x_i = h~_i / P~_i of the messages read (Alg. 2 step 4).
+// Staged per tile: (P, eta) in, A_ij, rev, row pointers, A_ii.
+// ---------------------------------------------------------------------------
+struct Layout64 {
+  static constexpr int TS = kTileSlotsSmall, TR = kTileRowsSmall;
+  static constexpr uint32_t m = 0, a = m + region(TS, 16), rev = a + region(TS, 8),
+                            rp = rev + region(TS, 4), dg = rp + region(TR + 1, 4),
+                            bytes = dg + region(TR, 8);
+};
+
 template <int G>
 __global__ void __launch_bounds__(kBlock)
-sweep32_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ rev,
-               const int32_t *__restrict__ rows, int32_t nrows, const float *__restrict__ a,
-               const float *__restrict__ diag, const float *__restrict__ rhs,
-               const float2 *__restrict__ min, float2 *__restrict__ mout,
-               const float2 *__restrict__ mon_prev, float2 *__restrict__ mon_out,
-               float *__restrict__ c_out, float *__restrict__ invP_out,
-               float *__restrict__ eta_out, DevScalars *red) {
-  constexpr int R = kCacheSlots;
-  constexpr int RPW = 32 / G;
-  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  const bool freeze = c_out != nullptr;
+sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
+  using L = Layout64;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  const int par = ctl->par_m;
+  const bool first = ctl->first != 0;
+  bool write_x, write_msgs;
+  if (ctl->mode == CTL_ROUNDS) {
+    const bool infer_only = ctl->sweeps >= ctl->rounds_target;
+    write_x = infer_only;
+    write_msgs = !infer_only;
+  } else {
+    write_x = ctl->write_x != 0;
+    write_msgs = true;
+  }
+  const double *__restrict__ b = ctl->b;
+  double *__restrict__ x = ctl->x;
+  const double2 *__restrict__ min = B.m64[par];
+  double2 *__restrict__ mout = B.m64[par ^ 1];
+  const int gl = threadIdx.x % G;
+  bool brk = false;
+
+  auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
+    const TileBounds tb = tile_at(g.tiles_small, t);
+    const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
+    const bool msgs = !first;
+    const uint32_t tx = (msgs ? Seg<double2>::bytes(tb.s0, ns) : 0) +
+                        Seg<double>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
+                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr);
+    mbar_expect_tx(bar, tx);
+    const uint32_t base = smem_u32(stage);
+    if (msgs) Seg<double2>::copy(base + L::m, min, tb.s0, ns, bar);
+    Seg<double>::copy(base + L::a, g.a64, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
+    Seg<double>::copy(base + L::dg, g.diag64, tb.r0, nr, bar);
+  };
+
+  auto emit = [&](double a, double2 m, int32_t dst, double TP, double Th) {
+    const double d = TP - m.x;   // P_{i\j} = P~_i - P_ji
+    brk |= !(d != 0.0) || !isfinite(d);
+    const double inv = recip64(d);
+    mout[dst] = make_double2(-(a * a) * inv, -a * (Th - m.y) * inv);
+  };
+
+  auto work = [&](int32_t t, unsigned char *stage) {
+    const TileBounds tb = tile_at(g.tiles_small, t);
+    const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) {
+      // one long row, straight from global memory, the whole CTA on it
+      const int32_t i = tb.r0;
+      double sP = 0.0, sH = 0.0;
+      if (!first)
+        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) {
+          const double2 m = min[s];
+          sP += m.x;
+          sH += m.y;
+        }
+      sP = block_sum(sP);
+      sH = block_sum(sH);
+      const double TP = g.diag64[i] + sP, Th = b[i] + sH;
+      if (write_x && threadIdx.x == 0) x[i] = Th / TP;
+      if (write_msgs)
+        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock)
+          emit(g.a64[s], first ? make_double2(0.0, 0.0) : min[s], g.rev[s], TP, Th);
+      return;
+    }
+    const double2 *ms = Seg<double2>::at(stage + L::m, tb.s0);
+    const double *as = Seg<double>::at(stage + L::a, tb.s0);
+    const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
+    const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+    const double *dg = Seg<double>::at(stage + L::dg, tb.r0);
+    for (int32_t base_r = 0; base_r < nr; base_r += kBlock / G) {
+      const int32_t lr = base_r + static_cast<int32_t>(threadIdx.x) / G;
+      const bool valid = lr < nr;
+      const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
+      double sP = 0.0, sH = 0.0;
+      if (!first)
+        for (int32_t s = rs + gl; s < re; s += G) {
+          sP += ms[s].x;
+          sH += ms[s].y;
+        }
+      sP = group_sum<G>(sP);
+      sH = group_sum<G>(sH);
+      if (!valid) continue;
+      const int32_t i = tb.r0 + lr;
+      const double TP = dg[lr] + sP, Th = b[i] + sH;
+      if (write_x && gl == 0) x[i] = Th / TP;
+      if (!write_msgs) continue;
+      for (int32_t s = rs + gl; s < re; s += G)
+        emit(as[s], first ? make_double2(0.0, 0.0) : ms[s], rv[s], TP, Th);
+    }
+  };
+
+  const bool ok = run_tiles(g.ntiles_small, smem, L::bytes, bars, issue, work);
+  if (brk) atomicOr(&red->breakdown, 1);
+  if (!ok) atomicOr(&red->timeout, 1);
+  last_block_control(ctl, red, CK_SWEEP64);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 full sweep (mixed modes, precision phase).  Messages (P, eta) and
+// totals in FP32; rhs_i = r_i / ||r||.  Records (P~_i, d_i = h~_i / P~_i) per
+// node and the change against the previous sweep.  When the controller has
+// set pending_freeze, the sweep freezes instead: it stores the coefficient
+// c_ij = -A_ij / (P~_i - P_ji) at slot s of row i, 1/P~_i, and the first
+// mean-only messages eta_ij = c_ij (h~_i - eta_ji).
+// Staged per tile: (P, eta) in, A_ij, rev, row pointers, A_ii, r, monitors.
+// ---------------------------------------------------------------------------
+struct Layout32 {
+  static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
+  static constexpr uint32_t m = 0, a = m + region(TS, 8), rev = a + region(TS, 4),
+                            rp = rev + region(TS, 4), dg = rp + region(TR + 1, 4),
+                            r = dg + region(TR, 4), mon = r + region(TR, 8),
+                            bytes = mon + region(TR, 8);
+};
+
+template <int G, class T>
+__global__ void __launch_bounds__(kBlock)
+sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
+  using L = Layout32;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  const int pm = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
+  const bool first = ctl->first != 0;
+  const bool freeze = ctl->pending_freeze != 0;
+  const double inv_rn = ctl->inv_rn;
+  const float2 *__restrict__ min = B.m32[pm];
+  float2 *__restrict__ mout = B.m32[pm ^ 1];
+  T *__restrict__ eta_out = static_cast<T *>(B.e[pe ^ 1]);
+  const float2 *__restrict__ mon_prev = B.mon32[pmon];
+  float2 *__restrict__ mon_out = B.mon32[pmon ^ 1];
+  const int gl = threadIdx.x % G;
   unsigned long long mdd = 0, md = 0, mdP = 0, mP = 0;
   bool brk = false;
 
-  for (int64_t base = warp * RPW; base < nrows; base += nwarps * RPW) {
-    const RowSlot row = row_at(rp, rows, nrows, base + sub);
-    float2 mc[R];
-    float ac[R];
-    int32_t rc[R];
-    float sP = 0.f, sH = 0.f;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int32_t s = row.rs + gl + k * G;
-      if (s < row.re) {
-        mc[k] = min[s];
-        ac[k] = a[s];
-        rc[k] = rev[s];
-        sP += mc[k].x;
-        sH += mc[k].y;
-      }
+  auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
+    const TileBounds tb = tile_at(g.tiles_big, t);
+    const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
+    const uint32_t tx = (first ? 0 : Seg<float2>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr)) +
+                        Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
+                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<float>::bytes(tb.r0, nr) +
+                        Seg<double>::bytes(tb.r0, nr);
+    mbar_expect_tx(bar, tx);
+    const uint32_t base = smem_u32(stage);
+    if (!first) {
+      Seg<float2>::copy(base + L::m, min, tb.s0, ns, bar);
+      Seg<float2>::copy(base + L::mon, mon_prev, tb.r0, nr, bar);
     }
-    for (int32_t s = row.rs + gl + R * G; s < row.re; s += G) {
-      const float2 m = min[s];
-      sP += m.x;
-      sH += m.y;
+    Seg<float>::copy(base + L::a, g.a32, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
+    Seg<float>::copy(base + L::dg, g.diag32, tb.r0, nr, bar);
+    Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
+  };
+
+  // node part: monitors (and 1/P~ when freezing) by one lane per row
+  auto node = [&](int32_t i, float TP, float Th, float2 prev) {
+    const float di = Th / TP;
+    mon_out[i] = make_float2(TP, di);
+    mdd = umax(mdd, bits(fabs(static_cast<double>(di) - prev.y)));
+    md = umax(md, bits(fabs(static_cast<double>(di))));
+    mdP = umax(mdP, bits(fabs(static_cast<double>(TP) - prev.x)));
+    mP = umax(mP, bits(fabs(static_cast<double>(TP))));
+    if (freeze) B.invP32[i] = 1.0f / TP;
+  };
+  auto emit = [&](int32_t s, float a, float2 m, int32_t dst, float TP, float Th) {
+    const float d = TP - m.x;
+    brk |= !(d != 0.0f) || !isfinite(d);
+    const float inv = 1.0f / d;
+    if (freeze) {
+      const float c = -a * inv;
+      B.c32[s] = c;
+      st_eta(eta_out + dst, c * (Th - m.y));
+    } else {
+      mout[dst] = make_float2(-(a * a) * inv, -a * (Th - m.y) * inv);
     }
-    sP = group_sum<G>(sP);
-    sH = group_sum<G>(sH);
-    if (!row.valid) continue;
-    const float TP = diag[row.i] + sP;
-    const float Th = rhs[row.i] + sH;
-    if (gl == 0) {
-      const float di = Th / TP;
-      const float2 prev = mon_prev[row.i];
-      mon_out[row.i] = make_float2(TP, di);
-      mdd = umax(mdd, bits(fabs(static_cast<double>(di) - prev.y)));
-      md = umax(md, bits(fabs(static_cast<double>(di))));
-      mdP = umax(mdP, bits(fabs(static_cast<double>(TP) - prev.x)));
-      mP = umax(mP, bits(fabs(static_cast<double>(TP))));
-      if (freeze) invP_out[row.i] = 1.0f / TP;
-    }
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int32_t s = row.rs + gl + k * G;
-      if (s < row.re) {
-        const float d = TP - mc[k].x;
-        brk |= !(d != 0.0f) || !isfinite(d);
-        const float inv = 1.0f / d;
-        if (freeze) {
-          const float c = -ac[k] * inv;
-          c_out[s] = c;
-          eta_out[rc[k]] = c * (Th - mc[k].y);
-        } else {
-          mout[rc[k]] = make_float2(-(ac[k] * ac[k]) * inv, -ac[k] * (Th - mc[k].y) * inv);
+  };
+
+  auto work = [&](int32_t t, unsigned char *stage) {
+    const TileBounds tb = tile_at(g.tiles_big, t);
+    const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) {
+      const int32_t i = tb.r0;
+      float sP = 0.f, sH = 0.f;
+      if (!first)
+        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) {
+          const float2 m = min[s];
+          sP += m.x;
+          sH += m.y;
         }
-      }
+      sP = block_sum(sP);
+      sH = block_sum(sH);
+      const float TP = g.diag32[i] + sP;
+      const float Th = static_cast<float>(B.r64[i] * inv_rn) + sH;
+      if (threadIdx.x == 0) node(i, TP, Th, first ? make_float2(0.f, 0.f) : mon_prev[i]);
+      for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock)
+        emit(s, g.a32[s], first ? make_float2(0.f, 0.f) : min[s], g.rev[s], TP, Th);
+      return;
     }
-    for (int32_t s = row.rs + gl + R * G; s < row.re; s += G) {
-      const float2 m = min[s];
-      const float av = a[s];
-      const float d = TP - m.x;
-      brk |= !(d != 0.0f) || !isfinite(d);
-      const float inv = 1.0f / d;
-      if (freeze) {
-        const float c = -av * inv;
-        c_out[s] = c;
-        eta_out[rev[s]] = c * (Th - m.y);
-      } else {
-        mout[rev[s]] = make_float2(-(av * av) * inv, -av * (Th - m.y) * inv);
-      }
+    const float2 *ms = Seg<float2>::at(stage + L::m, tb.s0);
+    const float *as = Seg<float>::at(stage + L::a, tb.s0);
+    const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
+    const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+    const float *dg = Seg<float>::at(stage + L::dg, tb.r0);
+    const double *rr = Seg<double>::at(stage + L::r, tb.r0);
+    const float2 *mp = Seg<float2>::at(stage + L::mon, tb.r0);
+    for (int32_t base_r = 0; base_r < nr; base_r += kBlock / G) {
+      const int32_t lr = base_r + static_cast<int32_t>(threadIdx.x) / G;
+      const bool valid = lr < nr;
+      const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
+      float sP = 0.f, sH = 0.f;
+      if (!first)
+        for (int32_t s = rs + gl; s < re; s += G) {
+          sP += ms[s].x;
+          sH += ms[s].y;
+        }
+      sP = group_sum<G>(sP);
+      sH = group_sum<G>(sH);
+      if (!valid) continue;
+      const int32_t i = tb.r0 + lr;
+      const float TP = dg[lr] + sP;
+      const float Th = static_cast<float>(rr[lr] * inv_rn) + sH;
+      if (gl == 0) node(i, TP, Th, first ? make_float2(0.f, 0.f) : mp[lr]);
+      for (int32_t s = rs + gl; s < re; s += G)
+        emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], TP, Th);
     }
-  }
+  };
+
+  const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
   if (brk) atomicOr(&red->breakdown, 1);
+  if (!ok) atomicOr(&red->timeout, 1);
   block_max4(mdd, md, mdP, mP, &red->max_dx, &red->max_x, &red->max_dP, &red->max_P);
+  last_block_control(ctl, red, CK_SWEEP32);
 }
 
 // ---------------------------------------------------------------------------
-// FP32 mean-only sweep with frozen precisions: eta_ij = c_ij (h~_i - eta_ji),
-// h~_i = rhs_i + sum_k eta_ki, d_i = h~_i / P~_i.  Records d_i and its change.
+// Mean-only sweep with frozen precisions (storage T = float or bf16, FP32
+// arithmetic): eta_ij = c_ij (h~_i - eta_ji), h~_i = r_i/||r|| + sum_k eta_ki,
+// d_i = h~_i / P~_i.  Records d_i and its change.
+// Staged per tile: eta in, c, rev, row pointers, r, 1/P~, monitors.
 // ---------------------------------------------------------------------------
-template <int G>
+template <class T>
+struct LayoutMean {
+  static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
+  static constexpr uint32_t e = 0, c = e + region(TS, sizeof(T)), rev = c + region(TS, 4),
+                            rp = rev + region(TS, 4), r = rp + region(TR + 1, 4),
+                            ip = r + region(TR, 8), mon = ip + region(TR, 4),
+                            bytes = mon + region(TR, 8);
+};
+
+template <int G, class T>
 __global__ void __launch_bounds__(kBlock)
-mean32_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ rev,
-              const int32_t *__restrict__ rows, int32_t nrows, const float *__restrict__ c,
-              const float *__restrict__ invP, const float *__restrict__ rhs,
-              const float *__restrict__ ein, float *__restrict__ eout,
-              const float2 *__restrict__ mon_prev, float2 *__restrict__ mon_out,
-              DevScalars *red) {
-  constexpr int R = kCacheSlots;
-  constexpr int RPW = 32 / G;
-  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
+  using L = LayoutMean<T>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  const int pe = ctl->par_e, pmon = ctl->par_mon;
+  const bool first = ctl->first != 0;
+  const double inv_rn = ctl->inv_rn;
+  const T *__restrict__ ein = static_cast<const T *>(B.e[pe]);
+  T *__restrict__ eout = static_cast<T *>(B.e[pe ^ 1]);
+  const float2 *__restrict__ mon_prev = B.mon32[pmon];
+  float2 *__restrict__ mon_out = B.mon32[pmon ^ 1];
+  const int gl = threadIdx.x % G;
   unsigned long long mdd = 0, md = 0;
 
-  for (int64_t base = warp * RPW; base < nrows; base += nwarps * RPW) {
-    const RowSlot row = row_at(rp, rows, nrows, base + sub);
-    float ec[R], cc[R];
-    int32_t rc[R];
-    float sH = 0.f;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int32_t s = row.rs + gl + k * G;
-      if (s < row.re) {
-        ec[k] = ein[s];
-        cc[k] = c[s];
-        rc[k] = rev[s];
-        sH += ec[k];
+  auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
+    const TileBounds tb = tile_at(g.tiles_big, t);
+    const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
+    const uint32_t tx = (first ? 0 : Seg<T>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr)) +
+                        Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
+                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr) +
+                        Seg<float>::bytes(tb.r0, nr);
+    mbar_expect_tx(bar, tx);
+    const uint32_t base = smem_u32(stage);
+    if (!first) {
+      Seg<T>::copy(base + L::e, ein, tb.s0, ns, bar);
+      Seg<float2>::copy(base + L::mon, mon_prev, tb.r0, nr, bar);
+    }
+    Seg<float>::copy(base + L::c, B.c32, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
+    Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
+    Seg<float>::copy(base + L::ip, B.invP32, tb.r0, nr, bar);
+  };
+
+  auto node = [&](int32_t i, float Th, float invP, float prev) {
+    const float di = Th * invP;
+    mon_out[i] = make_float2(0.f, di);
+    mdd = umax(mdd, bits(fabs(static_cast<double>(di) - prev)));
+    md = umax(md, bits(fabs(static_cast<double>(di))));
+  };
+
+  auto work = [&](int32_t t, unsigned char *stage) {
+    const TileBounds tb = tile_at(g.tiles_big, t);
+    const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) {
+      const int32_t i = tb.r0;
+      float sH = 0.f;
+      if (!first)
+        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) sH += ld_eta(ein + s);
+      sH = block_sum(sH);
+      const float Th = static_cast<float>(B.r64[i] * inv_rn) + sH;
+      if (threadIdx.x == 0) node(i, Th, B.invP32[i], first ? 0.f : mon_prev[i].y);
+      for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) {
+        const float e = first ? 0.f : ld_eta(ein + s);
+        st_eta(eout + g.rev[s], B.c32[s] * (Th - e));
+      }
+      return;
+    }
+    const T *es = Seg<T>::at(stage + L::e, tb.s0);
+    const float *cs = Seg<float>::at(stage + L::c, tb.s0);
+    const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
+    const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+    const double *rr = Seg<double>::at(stage + L::r, tb.r0);
+    const float *ip = Seg<float>::at(stage + L::ip, tb.r0);
+    const float2 *mp = Seg<float2>::at(stage + L::mon, tb.r0);
+    for (int32_t base_r = 0; base_r < nr; base_r += kBlock / G) {
+      const int32_t lr = base_r + static_cast<int32_t>(threadIdx.x) / G;
+      const bool valid = lr < nr;
+      const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
+      float sH = 0.f;
+      if (!first)
+        for (int32_t s = rs + gl; s < re; s += G) sH += ld_eta(es + s);
+      sH = group_sum<G>(sH);
+      if (!valid) continue;
+      const int32_t i = tb.r0 + lr;
+      const float Th = static_cast<float>(rr[lr] * inv_rn) + sH;
+      if (gl == 0) node(i, Th, ip[lr], first ? 0.f : mp[lr].y);
+      for (int32_t s = rs + gl; s < re; s += G) {
+        const float e = first ? 0.f : ld_eta(es + s);
+        st_eta(eout + rv[s], cs[s] * (Th - e));
       }
     }
-    for (int32_t s = row.rs + gl + R * G; s < row.re; s += G) sH += ein[s];
-    sH = group_sum<G>(sH);
-    if (!row.valid) continue;
-    const float Th = rhs[row.i] + sH;
-    if (gl == 0) {
-      const float di = Th * invP[row.i];
-      const float2 prev = mon_prev[row.i];
-      mon_out[row.i] = make_float2(0.f, di);
-      mdd = umax(mdd, bits(fabs(static_cast<double>(di) - prev.y)));
-      md = umax(md, bits(fabs(static_cast<double>(di))));
-    }
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int32_t s = row.rs + gl + k * G;
-      if (s < row.re) eout[rc[k]] = cc[k] * (Th - ec[k]);
-    }
-    for (int32_t s = row.rs + gl + R * G; s < row.re; s += G) eout[rev[s]] = c[s] * (Th - ein[s]);
-  }
+  };
+
+  const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
+  if (!ok) atomicOr(&red->timeout, 1);
   block_max4(mdd, md, 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
+  last_block_control(ctl, red, CK_MEAN);
+}
+
+// x_i += ||r|| d_i (FP64), d_i from the latest monitor.
+__global__ void __launch_bounds__(kBlock) refine_update_kernel(int32_t n, Buffers B, Ctl *ctl) {
+  double *x = ctl->x;
+  const double rn = ctl->rn;
+  const float2 *mon = B.mon32[ctl->par_mon];
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    x[i] += static_cast<double>(mon[i].y) * rn;
 }
 
 // ---------------------------------------------------------------------------
-// FP64 residual r = b - A x with its infinity norm (a CSR SpMV over the same
-// row groups).
+// FP64 residual r = b - A x with its infinity norm (a CSR SpMV).  Staged per
+// tile: A_ij, col, row pointers, A_ii; x[col] is gathered from global memory.
 // ---------------------------------------------------------------------------
+struct LayoutRes {
+  static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
+  static constexpr uint32_t a = 0, col = a + region(TS, 8), rp = col + region(TS, 4),
+                            dg = rp + region(TR + 1, 4), bytes = dg + region(TR, 8);
+};
+
 template <int G>
 __global__ void __launch_bounds__(kBlock)
-residual64_kernel(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-                  const int32_t *__restrict__ rows, int32_t nrows, const double *__restrict__ a,
-                  const double *__restrict__ diag, const double *__restrict__ b,
-                  const double *__restrict__ x, double *__restrict__ r_out, DevScalars *red) {
-  constexpr int RPW = 32 / G;
-  const int lane = threadIdx.x & 31, sub = lane / G, gl = lane % G;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars *red, int kind) {
+  using L = LayoutRes;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  const double *__restrict__ b = ctl->b;
+  const double *__restrict__ x = ctl->x;
+  const int gl = threadIdx.x % G;
   unsigned long long mr = 0;
-  for (int64_t base = warp * RPW; base < nrows; base += nwarps * RPW) {
-    const RowSlot row = row_at(rp, rows, nrows, base + sub);
-    double acc = 0.0;
-    for (int32_t s = row.rs + gl; s < row.re; s += G) acc += a[s] * x[col[s]];
-    acc = group_sum<G>(acc);
-    if (!row.valid || gl != 0) continue;
-    const double ri = b[row.i] - (diag[row.i] * x[row.i] + acc);
-    if (r_out) r_out[row.i] = ri;
+
+  auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
+    const TileBounds tb = tile_at(g.tiles_big, t);
+    const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
+    const uint32_t tx = Seg<double>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
+                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr);
+    mbar_expect_tx(bar, tx);
+    const uint32_t base = smem_u32(stage);
+    Seg<double>::copy(base + L::a, g.a64, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::col, g.col, tb.s0, ns, bar);
+    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
+    Seg<double>::copy(base + L::dg, g.diag64, tb.r0, nr, bar);
+  };
+
+  auto node = [&](int32_t i, double dgi, double acc) {
+    const double ri = b[i] - (dgi * x[i] + acc);
+    if (r_out) r_out[i] = ri;
     mr = umax(mr, bits(fabs(ri)));
-  }
+  };
+
+  auto work = [&](int32_t t, unsigned char *stage) {
+    const TileBounds tb = tile_at(g.tiles_big, t);
+    const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    if (ns > L::TS) {
+      double acc = 0.0;
+      for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) acc += g.a64[s] * x[g.col[s]];
+      acc = block_sum(acc);
+      if (threadIdx.x == 0) node(tb.r0, g.diag64[tb.r0], acc);
+      return;
+    }
+    const double *as = Seg<double>::at(stage + L::a, tb.s0);
+    const int32_t *cs = Seg<int32_t>::at(stage + L::col, tb.s0);
+    const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+    const double *dg = Seg<double>::at(stage + L::dg, tb.r0);
+    for (int32_t base_r = 0; base_r < nr; base_r += kBlock / G) {
+      const int32_t lr = base_r + static_cast<int32_t>(threadIdx.x) / G;
+      const bool valid = lr < nr;
+      const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
+      double acc = 0.0;
+      for (int32_t s = rs + gl; s < re; s += G) acc += as[s] * x[cs[s]];
+      acc = group_sum<G>(acc);
+      if (valid && gl == 0) node(tb.r0 + lr, dg[lr], acc);
+    }
+  };
+
+  const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
+  if (!ok) atomicOr(&red->timeout, 1);
   block_max4(mr, 0, 0, 0, &red->max_r, nullptr, nullptr, nullptr);
-}
-
-__global__ void max_abs_kernel(const double *__restrict__ v, int64_t n, unsigned long long *slot) {
-  unsigned long long m = 0;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    m = umax(m, bits(fabs(v[i])));
-  block_max4(m, 0, 0, 0, slot, nullptr, nullptr, nullptr);
-}
-
-__global__ void scale_to_f32_kernel(const double *__restrict__ v, int64_t n, double scale,
-                                    float *__restrict__ out) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    out[i] = static_cast<float>(v[i] * scale);
-}
-
-__global__ void refine_update_kernel(int64_t n, double *__restrict__ x,
-                                     const float2 *__restrict__ mon, double inv_scale) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    x[i] += static_cast<double>(mon[i].y) * inv_scale;
+  last_block_control(ctl, red, kind);
 }
 
 int g_num_sms = 0;
@@ -381,110 +876,141 @@ int num_sms() {
   return g_num_sms;
 }
 
-// Blocks for a row launch: enough to give every row its group, capped at a
-// whole number of waves over the SMs (the kernels are grid-stride).
-int row_grid(int32_t nrows, int group) {
-  const int64_t need = (static_cast<int64_t>(nrows) * group + kBlock - 1) / kBlock;
-  const int64_t cap = static_cast<int64_t>(num_sms()) * 8;
-  return static_cast<int>(std::max<int64_t>(1, std::min(need, cap)));
-}
-
 int flat_grid(int64_t n) {
   const int64_t need = (n + kBlock - 1) / kBlock;
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, num_sms() * 8)));
 }
 
-#define GABP_DISPATCH_G(group, KERNEL, ...)                               \
-  switch (group) {                                                        \
-    case 1: KERNEL<1><<<grid, kBlock, 0, st>>>(__VA_ARGS__); break;       \
-    case 2: KERNEL<2><<<grid, kBlock, 0, st>>>(__VA_ARGS__); break;       \
-    case 4: KERNEL<4><<<grid, kBlock, 0, st>>>(__VA_ARGS__); break;       \
-    case 8: KERNEL<8><<<grid, kBlock, 0, st>>>(__VA_ARGS__); break;       \
-    case 16: KERNEL<16><<<grid, kBlock, 0, st>>>(__VA_ARGS__); break;     \
-    default: KERNEL<32><<<grid, kBlock, 0, st>>>(__VA_ARGS__); break;     \
-  }
+// Blocks per SM of a tiled kernel with its two-stage shared memory; the
+// dynamic shared-memory limit is raised once per kernel.
+std::mutex g_occ_mu;
+std::unordered_map<const void *, int> g_occ;
+
+template <class K>
+int resident_blocks(K kernel, size_t smem) {
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  auto it = g_occ.find(reinterpret_cast<const void *>(kernel));
+  if (it != g_occ.end()) return it->second;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kBlock, smem);
+  bps = std::max(bps, 1);
+  g_occ[reinterpret_cast<const void *>(kernel)] = bps;
+  return bps;
+}
+
+// Persistent grid: one wave of resident CTAs (a multiple of the SM count),
+// or fewer when there are fewer tiles.
+template <class K>
+int tile_grid(K kernel, size_t smem, int32_t ntiles) {
+  const int64_t cap = static_cast<int64_t>(num_sms()) * resident_blocks(kernel, smem);
+  return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ntiles, cap)));
+}
+
+#define GABP_TILED(group, KERNEL_T, SMEM, NT, ...)                                  \
+  do {                                                                              \
+    switch (group) {                                                                \
+      case 2: { auto k = KERNEL_T(2); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break;   \
+      case 4: { auto k = KERNEL_T(4); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break;   \
+      case 8: { auto k = KERNEL_T(8); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break;   \
+      case 16: { auto k = KERNEL_T(16); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break; \
+      default: { auto k = KERNEL_T(32); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break; \
+    }                                                                               \
+  } while (0)
+
+#define K64(G) sweep64_kernel<G>
+#define K32F(G) sweep32_kernel<G, float>
+#define K32H(G) sweep32_kernel<G, __nv_bfloat16>
+#define KMF(G) mean_kernel<G, float>
+#define KMH(G) mean_kernel<G, __nv_bfloat16>
+#define KRES(G) residual64_kernel<G>
 
 }  // namespace
 
-int launch_sweep64(const Graph &g, cudaStream_t st, const double2 *min, double2 *mout,
-                    const double *b, double *x_out, const double *x_prev, DevScalars *red,
-                    bool write_msgs) {
-  int launched = 0;
-  for (const RowBin &bin : g.bins) {
-    if (bin.nrows == 0) continue;
-    ++launched;
-    const int grid = row_grid(bin.nrows, bin.group);
-    GABP_DISPATCH_G(bin.group, sweep64_kernel, g.rp, g.rev, bin.rows, bin.nrows, g.a64, g.diag64,
-                    b, min, mout, x_out, x_prev, red, write_msgs ? 1 : 0);
-  }
-  return launched;
-}
-
-int launch_sweep32(const Graph &g, cudaStream_t st, const float2 *min, float2 *mout,
-                    const float *rhs, const float2 *mon_prev, float2 *mon_out, float *c_out,
-                    float *invP_out, float *eta_out, DevScalars *red) {
-  int launched = 0;
-  for (const RowBin &bin : g.bins) {
-    if (bin.nrows == 0) continue;
-    ++launched;
-    const int grid = row_grid(bin.nrows, bin.group);
-    GABP_DISPATCH_G(bin.group, sweep32_kernel, g.rp, g.rev, bin.rows, bin.nrows, g.a32, g.diag32,
-                    rhs, min, mout, mon_prev, mon_out, c_out, invP_out, eta_out, red);
-  }
-  return launched;
-}
-
-int launch_mean32(const Graph &g, cudaStream_t st, const float *ein, float *eout, const float *c,
-                   const float *invP, const float *rhs, const float2 *mon_prev, float2 *mon_out,
-                   DevScalars *red) {
-  int launched = 0;
-  for (const RowBin &bin : g.bins) {
-    if (bin.nrows == 0) continue;
-    ++launched;
-    const int grid = row_grid(bin.nrows, bin.group);
-    GABP_DISPATCH_G(bin.group, mean32_kernel, g.rp, g.rev, bin.rows, bin.nrows, c, invP, rhs,
-                    ein, eout, mon_prev, mon_out, red);
-  }
-  return launched;
-}
-
-int launch_residual64(const Graph &g, cudaStream_t st, const double *b, const double *x,
-                       double *r_out, DevScalars *red) {
-  int launched = 0;
-  for (const RowBin &bin : g.bins) {
-    if (bin.nrows == 0) continue;
-    ++launched;
-    const int grid = row_grid(bin.nrows, bin.group);
-    GABP_DISPATCH_G(bin.group, residual64_kernel, g.rp, g.col, bin.rows, bin.nrows, g.a64,
-                    g.diag64, b, x, r_out, red);
-  }
-  return launched;
-}
-
-int launch_max_abs(cudaStream_t st, const double *v, int64_t n, unsigned long long *slot) {
-  max_abs_kernel<<<flat_grid(n), kBlock, 0, st>>>(v, n, slot);
+int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  init_kernel<<<flat_grid(g.n), kBlock, 0, st>>>(g.n, B.r64, ctl, red);
   return 1;
 }
 
-int launch_scale_to_f32(cudaStream_t st, const double *v, int64_t n, double scale, float *out) {
-  scale_to_f32_kernel<<<flat_grid(n), kBlock, 0, st>>>(v, n, scale, out);
+int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  const size_t smem = 2 * Layout64::bytes;
+  GABP_TILED(g.group, K64, smem, g.ntiles_small, g.view(), B, ctl, red);
   return 1;
 }
 
-int launch_refine_update(cudaStream_t st, int64_t n, double *x, const float2 *mon,
-                         double inv_scale) {
-  refine_update_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, x, mon, inv_scale);
+int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                   bool bf16) {
+  const size_t smem = 2 * Layout32::bytes;
+  if (bf16) GABP_TILED(g.group, K32H, smem, g.ntiles_big, g.view(), B, ctl, red);
+  else GABP_TILED(g.group, K32F, smem, g.ntiles_big, g.view(), B, ctl, red);
   return 1;
 }
 
-void launch_fill_zero(cudaStream_t st, void *p, size_t bytes) {
-  if (bytes) cudaMemsetAsync(p, 0, bytes, st);
+int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16) {
+  if (bf16) {
+    const size_t smem = 2 * LayoutMean<__nv_bfloat16>::bytes;
+    GABP_TILED(g.group, KMH, smem, g.ntiles_big, g.view(), B, ctl, red);
+  } else {
+    const size_t smem = 2 * LayoutMean<float>::bytes;
+    GABP_TILED(g.group, KMF, smem, g.ntiles_big, g.view(), B, ctl, red);
+  }
+  return 1;
+}
+
+static int launch_residual(const Graph &g, cudaStream_t st, double *r_out, Ctl *ctl,
+                           DevScalars *red, int kind) {
+  const size_t smem = 2 * LayoutRes::bytes;
+  GABP_TILED(g.group, KRES, smem, g.ntiles_big, g.view(), r_out, ctl, red, kind);
+  return 1;
+}
+
+int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  (void)B;
+  return launch_residual(g, st, nullptr, ctl, red, CK_CHECK64);
+}
+
+int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  refine_update_kernel<<<flat_grid(g.n), kBlock, 0, st>>>(g.n, B, ctl);
+  return 1 + launch_residual(g, st, B.r64, ctl, red, CK_REFINE);
+}
+
+// Sets the shared-memory limits and caches the occupancy of every kernel
+// the handle can launch (done at create time, before any graph is recorded).
+template <int G>
+void prepare_group(bool bf16) {
+  resident_blocks(sweep64_kernel<G>, 2 * Layout64::bytes);
+  resident_blocks(residual64_kernel<G>, 2 * LayoutRes::bytes);
+  if (bf16) {
+    resident_blocks(sweep32_kernel<G, __nv_bfloat16>, 2 * Layout32::bytes);
+    resident_blocks(mean_kernel<G, __nv_bfloat16>, 2 * LayoutMean<__nv_bfloat16>::bytes);
+  } else {
+    resident_blocks(sweep32_kernel<G, float>, 2 * Layout32::bytes);
+    resident_blocks(mean_kernel<G, float>, 2 * LayoutMean<float>::bytes);
+  }
+}
+
+void prepare_kernels(int group, bool bf16) {
+  num_sms();
+  switch (group) {
+    case 2: prepare_group<2>(bf16); break;
+    case 4: prepare_group<4>(bf16); break;
+    case 8: prepare_group<8>(bf16); break;
+    case 16: prepare_group<16>(bf16); break;
+    default: prepare_group<32>(bf16); break;
+  }
+}
+
+void tile_sizes(int *big_slots, int *big_rows, int *small_slots, int *small_rows) {
+  *big_slots = kTileSlotsBig;
+  *big_rows = kTileRowsBig;
+  *small_slots = kTileSlotsSmall;
+  *small_rows = kTileRowsSmall;
 }
 
 double bits_to_double(unsigned long long u) {
   double d;
   static_assert(sizeof(d) == sizeof(u), "size");
-  memcpy(&d, &u, sizeof(d));
+  std::memcpy(&d, &u, sizeof(d));
   return d;
 }
 

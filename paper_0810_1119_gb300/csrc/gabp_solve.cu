@@ -12,6 +12,15 @@
 //   full FP32 sweeps until the node precisions P~_i settle, then freezes them
 //   into c_ij = -A_ij / (P~_i - P_ji) and 1/P~_i; every later sweep is the
 //   linear mean-only map eta_ij = c_ij (h~_i - eta_ji).
+//
+// All decisions are taken on the device (the controller in gabp_kernels.cu).
+// Two drivers run the same kernels:
+//   * graph driver (default): one CUDA graph per handle and mode -- an init
+//     kernel, then a WHILE node around a SWITCH on the phase; the controller
+//     sets both conditions.  One launch and one synchronisation per solve.
+//   * host driver (gabp_options.profile = 1): the host reads the control
+//     block after every phase and launches the next one, bracketing each
+//     kernel with CUDA events to report per-kind device times.
 #include "gabp_internal.h"
 
 #include <algorithm>
@@ -37,9 +46,14 @@ struct CudaFail {
 
 thread_local std::string g_create_error;
 
+// Device buffer with kPad elements of slack (the staged kernels round their
+// bulk copies up to 16 bytes).
 template <class T>
 void ensure(T **p, size_t count) {
-  if (!*p) CK(cudaMalloc(reinterpret_cast<void **>(p), std::max<size_t>(count, 1) * sizeof(T)));
+  if (!*p) {
+    CK(cudaMalloc(reinterpret_cast<void **>(p), (count + kPad) * sizeof(T)));
+    CK(cudaMemset(*p, 0, (count + kPad) * sizeof(T)));
+  }
 }
 
 gabp_status fail(gabp_handle h, gabp_status s, const std::string &msg) {
@@ -59,37 +73,45 @@ gabp_status guarded(gabp_handle h, F &&f) {
   }
 }
 
-constexpr double kTiny = std::numeric_limits<double>::min();
-
-double dval(unsigned long long u) { return bits_to_double(u); }
+bool is_bf16(gabp_handle h) { return h->opt.precision == GABP_PREC_MIXED_BF16; }
 
 void ensure_common(gabp_handle h) {
   ensure(&h->red, 1);
-  if (!h->red_host) CK(cudaMallocHost(reinterpret_cast<void **>(&h->red_host), sizeof(DevScalars)));
+  ensure(&h->ctl, 1);
+  if (!h->ctl_host) CK(cudaMallocHost(reinterpret_cast<void **>(&h->ctl_host), sizeof(Ctl)));
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 }
 
 void ensure64(gabp_handle h) {
   ensure_common(h);
-  ensure(&h->m64[0], h->g.E);
-  ensure(&h->m64[1], h->g.E);
+  if (h->have64) return;
+  ensure(&h->buf.m64[0], h->g.E);
+  ensure(&h->buf.m64[1], h->g.E);
+  h->have64 = true;
 }
 
 void ensure32(gabp_handle h) {
   ensure_common(h);
+  if (h->have32) return;
   const size_t n = h->g.n, E = h->g.E;
-  ensure(&h->m32[0], E); ensure(&h->m32[1], E);
-  ensure(&h->e32[0], E); ensure(&h->e32[1], E);
-  ensure(&h->c32, E);
-  ensure(&h->invP32, n); ensure(&h->rhs32, n);
-  ensure(&h->mon32[0], n); ensure(&h->mon32[1], n);
-  ensure(&h->r64, n);
+  Buffers &B = h->buf;
+  ensure(&B.m32[0], E); ensure(&B.m32[1], E);
+  const size_t eb = (E + kPad) * (is_bf16(h) ? sizeof(__nv_bfloat16) : sizeof(float));
+  CK(cudaMalloc(&B.e[0], eb));
+  CK(cudaMalloc(&B.e[1], eb));
+  CK(cudaMemset(B.e[0], 0, eb));
+  CK(cudaMemset(B.e[1], 0, eb));
+  ensure(&B.c32, E);
+  ensure(&B.invP32, n);
+  ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
+  ensure(&B.r64, n);
+  h->have32 = true;
 }
 
+// ---- profiling (host driver) ----
 enum { K_FULL = 0, K_MEAN = 1, K_RES = 2, K_OTHER = 3 };
 constexpr int kEventPairs = 64;
 
-// Adds the device time of the recorded kernels to the stats (the stream has
-// been synchronised by the caller).
 void prof_flush(gabp_handle h) {
   for (int p = 0; p < h->ev_used; ++p) {
     float ms = 0.f;
@@ -126,201 +148,183 @@ void run(gabp_handle h, int kind, F &&f) {
   if (pair >= 0) CK(cudaEventRecord(h->ev[2 * pair + 1], h->stream));
 }
 
-void zero_scalars(gabp_handle h) { CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), h->stream)); }
-
-void read_scalars(gabp_handle h) {
-  CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(h->red_host, h->red, sizeof(DevScalars), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  prof_flush(h);
+// Kernels of one phase on stream st (used by both drivers).
+int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
+  const Graph &g = h->g;
+  switch (phase) {
+    case PH_FULL64: return launch_sweep64(g, st, h->buf, h->ctl, h->red);
+    case PH_CHECK64: return launch_check64(g, st, h->buf, h->ctl, h->red);
+    case PH_FULL32: return launch_sweep32(g, st, h->buf, h->ctl, h->red, is_bf16(h));
+    case PH_MEAN: return launch_mean(g, st, h->buf, h->ctl, h->red, is_bf16(h));
+    case PH_REFINE: return launch_refine(g, st, h->buf, h->ctl, h->red);
+  }
+  return 0;
 }
 
-// ||b||_inf on the device.
-double rhs_norm(gabp_handle h, const double *b) {
-  zero_scalars(h);
-  run(h, K_OTHER, [&] { return launch_max_abs(h->stream, b, h->g.n, &h->red->max_b); });
-  read_scalars(h);
-  return dval(h->red_host->max_b);
+int phase_kind(int phase) {
+  switch (phase) {
+    case PH_FULL64: case PH_FULL32: return K_FULL;
+    case PH_MEAN: return K_MEAN;
+    case PH_CHECK64: case PH_REFINE: return K_RES;
+  }
+  return K_OTHER;
 }
 
-bool diverged(double rn, double bnorm) {
-  return !std::isfinite(rn) || rn > 1e30 * std::max(bnorm, kTiny);
+// Records the solve graph of one control mode:
+//   init -> WHILE(h_while) { SWITCH(h_phase) { phase bodies } }
+void build_solve_graph(gabp_handle h, int mode) {
+  cudaGraph_t graph;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle hw, hp;
+  CK(cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault));
+  CK(cudaGraphConditionalHandleCreate(&hp, graph, 0, cudaGraphCondAssignDefault));
+  cudaStream_t cs = h->cap_stream;
+
+  CK(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  launch_init(h->g, cs, h->buf, h->ctl, h->red);
+  cudaGraph_t captured;
+  CK(cudaStreamEndCapture(cs, &captured));
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> roots(nn);
+  CK(cudaGraphGetNodes(graph, roots.data(), &nn));
+
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, graph, roots.data(), nullptr, nn, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+
+  cudaGraphNodeParams sp{};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = hp;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = PH_COUNT;
+  cudaGraphNode_t snode;
+  CK(cudaGraphAddNode(&snode, body, nullptr, nullptr, 0, &sp));
+  for (int p = 0; p < PH_COUNT; ++p) {
+    cudaGraph_t pb = sp.conditional.phGraph_out[p];
+    const bool used = mode == CTL_FP64 ? (p == PH_FULL64 || p == PH_CHECK64)
+                                       : (p == PH_FULL32 || p == PH_MEAN || p == PH_REFINE);
+    if (!used) {
+      cudaGraphNode_t e;
+      CK(cudaGraphAddEmptyNode(&e, pb, nullptr, 0));
+      continue;
+    }
+    CK(cudaStreamBeginCaptureToGraph(cs, pb, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch_phase(h, cs, p);
+    cudaGraph_t out;
+    CK(cudaStreamEndCapture(cs, &out));
+  }
+  CK(cudaGraphInstantiate(&h->exec[mode], graph, 0));
+  h->graph[mode] = graph;
+  h->cond[mode][0] = hw;
+  h->cond[mode][1] = hp;
 }
 
-gabp_status solve_fp64(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+// Control block of a solve, in the pinned host mirror.
+void init_ctl(gabp_handle h, int mode, const double *b, double *x, double tol, int32_t max_iter,
+              bool in_graph) {
+  Ctl &c = *h->ctl_host;
+  std::memset(&c, 0, sizeof(Ctl));
+  c.b = b;
+  c.x = x;
+  c.tol = tol;
+  c.rel = h->opt.residual_kind == GABP_RESIDUAL_REL;
+  c.mode = mode;
+  c.max_iter = max_iter;
+  c.check_every = h->opt.check_every > 0 ? h->opt.check_every : 4;
+  c.inner_tol = h->opt.inner_tol > 0 ? h->opt.inner_tol : 1e-6;
+  c.in_graph = in_graph ? 1 : 0;
+  if (in_graph) {
+    c.h_while = h->cond[mode][0];
+    c.h_phase = h->cond[mode][1];
+  }
+  c.first = 1;
+  c.prev_dd = std::numeric_limits<double>::infinity();
+  c.prev_dP = std::numeric_limits<double>::infinity();
+  c.status = GABP_ERR_NOT_CONVERGED;
+}
+
+void finish_stats(gabp_handle h) {
+  const Ctl &c = *h->ctl_host;
+  gabp_stats &S = h->stats;
+  S.sweeps_total = c.sweeps;
+  S.sweeps_full = c.sweeps_full;
+  S.sweeps_mean = c.sweeps_mean;
+  S.outer_steps = c.mode == CTL_MIXED ? c.outer : 1;
+  S.residual_checks = c.checks;
+  S.status = c.status;
+  S.residual = c.residual;
+  S.rhs_norm = c.bnorm;
+  S.n = h->g.n;
+  S.edges = h->g.E;
+}
+
+gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                        int32_t *iters) {
-  Graph &g = h->g;
+  const bool mixed = h->opt.precision != GABP_PREC_FP64;
+  const int mode = mixed ? CTL_MIXED : CTL_FP64;
+  if (mixed) ensure32(h); else ensure64(h);
   cudaStream_t st = h->stream;
-  ensure64(h);
-  gabp_stats &S = h->stats;
-  S = gabp_stats{};
-  S.n = g.n;
-  S.edges = g.E;
-  const double bnorm = rhs_norm(h, b);
-  S.rhs_norm = bnorm;
-  if (!std::isfinite(bnorm)) return fail(h, GABP_ERR_INVALID_ARG, "b has non-finite entries");
-  const double thr = h->opt.residual_kind == GABP_RESIDUAL_REL ? tol * bnorm : tol;
-  const int check = h->opt.check_every > 0 ? h->opt.check_every : 4;
-  CK(cudaMemsetAsync(h->m64[0], 0, sizeof(double2) * std::max<int64_t>(g.E, 1), st));
-  int cur = 0, t = 0;
-  gabp_status status = GABP_ERR_NOT_CONVERGED;
-  double rn = std::numeric_limits<double>::infinity();
-  zero_scalars(h);
-  if (max_iter <= 0) {
-    // Round 0: all messages zero, x_i = b_i / A_ii.
-    run(h, K_FULL, [&] { return launch_sweep64(g, st, h->m64[cur], h->m64[cur ^ 1], b, x, nullptr, h->red, false); });
-    run(h, K_RES, [&] { return launch_residual64(g, st, b, x, nullptr, h->red); });
-    read_scalars(h);
-    S.residual_checks = 1;
-    rn = dval(h->red_host->max_r);
-    status = rn < thr ? GABP_OK : GABP_ERR_NOT_CONVERGED;
-  }
-  while (t < max_iter) {
-    ++t;
-    const bool chk = (t % check == 0) || t == max_iter;
-    // Sweep t reads round t-1, writes round t and (on check sweeps) the
-    // tentative means of round t-1.
-    run(h, K_FULL, [&] { return launch_sweep64(g, st, h->m64[cur], h->m64[cur ^ 1], b, chk ? x : nullptr, nullptr, h->red, true); });
-    cur ^= 1;
-    if (!chk) continue;
-    CK(cudaMemsetAsync(&h->red->max_r, 0, sizeof(unsigned long long), st));
-    run(h, K_RES, [&] { return launch_residual64(g, st, b, x, nullptr, h->red); });
-    read_scalars(h);
-    ++S.residual_checks;
-    if (h->red_host->breakdown) { status = GABP_ERR_BREAKDOWN; break; }
-    rn = dval(h->red_host->max_r);
-    if (rn < thr) { status = GABP_OK; break; }
-    if (diverged(rn, bnorm)) { status = GABP_ERR_DIVERGED; break; }
-  }
-  h->m64_cur = cur;
-  S.sweeps_total = S.sweeps_full = t;
-  S.outer_steps = 1;
-  S.residual = rn;
-  S.status = status;
-  if (iters) *iters = t;
-  if (status != GABP_OK)
-    return fail(h, status, std::string("FP64 solve: ") + gabp_status_string(status) +
-                               ", residual " + std::to_string(rn));
-  return GABP_OK;
-}
-
-gabp_status solve_mixed(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
-                        int32_t *iters) {
-  Graph &g = h->g;
-  cudaStream_t st = h->stream;
-  ensure32(h);
-  const int64_t n = g.n, E = std::max<int64_t>(g.E, 1);
-  gabp_stats &S = h->stats;
-  S = gabp_stats{};
-  S.n = g.n;
-  S.edges = g.E;
-  const double bnorm = rhs_norm(h, b);
-  S.rhs_norm = bnorm;
-  if (!std::isfinite(bnorm)) return fail(h, GABP_ERR_INVALID_ARG, "b has non-finite entries");
-  const double thr = h->opt.residual_kind == GABP_RESIDUAL_REL ? tol * bnorm : tol;
-  const double inner_tol = h->opt.inner_tol > 0 ? h->opt.inner_tol : 1e-6;
-  CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-  CK(cudaMemcpyAsync(h->r64, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-  double rn = bnorm;
-  gabp_status status = GABP_ERR_NOT_CONVERGED;
-  int sweeps = 0;
-  if (rn < thr) status = GABP_OK;
-  bool frozen = false;
-  int mc = 0, ec = 0, pc = 0;
-  while (status == GABP_ERR_NOT_CONVERGED) {
-    ++S.outer_steps;
-    run(h, K_OTHER, [&] { return launch_scale_to_f32(st, h->r64, n, 1.0 / rn, h->rhs32); });
-    if (!frozen) {
-      mc = 0;
-      CK(cudaMemsetAsync(h->m32[mc], 0, sizeof(float2) * E, st));
-    } else {
-      CK(cudaMemsetAsync(h->e32[ec], 0, sizeof(float) * E, st));
+  h->stats = gabp_stats{};
+  const bool host_driver = h->opt.profile != 0;
+  if (!host_driver && !h->exec[mode]) build_solve_graph(h, mode);
+  init_ctl(h, mode, b, x, tol, max_iter, !host_driver);
+  CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
+  if (!host_driver) {
+    CK(cudaGraphLaunch(h->exec[mode], st));
+    CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const Ctl &c = *h->ctl_host;
+    h->stats.kernel_launches = 1 + static_cast<int64_t>(c.sweeps) +
+                               static_cast<int64_t>(c.checks) * (mixed ? 2 : 1);
+  } else {
+    run(h, K_OTHER, [&] { return launch_init(h->g, st, h->buf, h->ctl, h->red); });
+    const int64_t cap = 4 * static_cast<int64_t>(max_iter) + 128;
+    for (int64_t it = 0; it < cap; ++it) {
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      prof_flush(h);
+      if (h->ctl_host->done) break;
+      const int phase = h->ctl_host->phase;
+      run(h, phase_kind(phase), [&] { return launch_phase(h, st, phase); });
     }
-    CK(cudaMemsetAsync(h->mon32[pc], 0, sizeof(float2) * n, st));
-    bool pending_freeze = false, inner_done = false;
-    double prev_dd = std::numeric_limits<double>::infinity();
-    double prev_dP = prev_dd;
-    int k = 0, stall = 0;
-    while (!inner_done && sweeps < max_iter) {
-      zero_scalars(h);
-      const int po = pc ^ 1;
-      if (!frozen) {
-        if (pending_freeze) {
-          run(h, K_FULL, [&] { return launch_sweep32(g, st, h->m32[mc], nullptr, h->rhs32, h->mon32[pc], h->mon32[po], h->c32,
-                         h->invP32, h->e32[ec], h->red); });
-          frozen = true;
-        } else {
-          run(h, K_FULL, [&] { return launch_sweep32(g, st, h->m32[mc], h->m32[mc ^ 1], h->rhs32, h->mon32[pc], h->mon32[po],
-                         nullptr, nullptr, nullptr, h->red); });
-          mc ^= 1;
-        }
-        ++S.sweeps_full;
-      } else {
-        run(h, K_MEAN, [&] { return launch_mean32(g, st, h->e32[ec], h->e32[ec ^ 1], h->c32, h->invP32, h->rhs32, h->mon32[pc],
-                      h->mon32[po], h->red); });
-        ec ^= 1;
-        ++S.sweeps_mean;
-      }
-      pc = po;
-      ++sweeps;
-      ++k;
-      read_scalars(h);
-      const DevScalars &R = *h->red_host;
-      if (R.breakdown) { status = GABP_ERR_BREAKDOWN; break; }
-      const double dd = dval(R.max_dx) / std::max(dval(R.max_x), kTiny);
-      if (!std::isfinite(dd)) { status = GABP_ERR_DIVERGED; break; }
-      if (!frozen && !pending_freeze) {
-        // Precision convergence: relative change of the node precisions,
-        // with the remaining error estimated from the contraction rate.
-        const double dP = dval(R.max_dP) / std::max(dval(R.max_P), kTiny);
-        const double rho = dP / prev_dP;
-        const double errP = rho < 1.0 ? dP * rho / (1.0 - rho) : std::numeric_limits<double>::infinity();
-        if (k >= 3 && (errP < 1e-6 || dP < 1e-7 || (rho >= 1.0 && dP < 1e-5))) pending_freeze = true;
-        prev_dP = dP;
-      }
-      const double rho_d = dd / prev_dd;
-      const double err_d = rho_d < 1.0 ? dd * rho_d / (1.0 - rho_d) : std::numeric_limits<double>::infinity();
-      stall = rho_d >= 1.0 ? stall + 1 : 0;
-      prev_dd = dd;
-      if (frozen && k >= 3 && (err_d < inner_tol || (stall >= 2 && dd < 1e-4))) inner_done = true;
-    }
-    if (status != GABP_ERR_NOT_CONVERGED) break;
-    // x += ||r|| d, then the FP64 residual.
-    run(h, K_OTHER, [&] { return launch_refine_update(st, n, x, h->mon32[pc], rn); });
-    CK(cudaMemsetAsync(&h->red->max_r, 0, sizeof(unsigned long long), st));
-    run(h, K_RES, [&] { return launch_residual64(g, st, b, x, h->r64, h->red); });
-    read_scalars(h);
-    ++S.residual_checks;
-    rn = dval(h->red_host->max_r);
-    if (rn < thr) { status = GABP_OK; break; }
-    if (diverged(rn, bnorm)) { status = GABP_ERR_DIVERGED; break; }
-    if (sweeps >= max_iter) break;
   }
-  S.sweeps_total = sweeps;
-  S.residual = rn;
-  S.status = status;
-  if (iters) *iters = sweeps;
+  CK(cudaGetLastError());
+  finish_stats(h);
+  const Ctl &c = *h->ctl_host;
+  if (iters) *iters = c.sweeps;
+  if (!c.done) return fail(h, GABP_ERR_NOT_CONVERGED, "controller did not finish");
+  const gabp_status status = static_cast<gabp_status>(c.status);
   if (status != GABP_OK)
-    return fail(h, status, std::string("mixed solve: ") + gabp_status_string(status) +
-                               ", residual " + std::to_string(rn));
+    return fail(h, status, std::string(mixed ? "mixed" : "FP64") + " solve: " +
+                               gabp_status_string(status) + ", residual " +
+                               std::to_string(c.residual) + " after " + std::to_string(c.sweeps) +
+                               " sweeps");
   return GABP_OK;
-}
-
-gabp_status solve_dispatch(gabp_handle h, const double *b, double *x, double tol,
-                           int32_t max_iter, int32_t *iters) {
-  if (h->opt.precision == GABP_PREC_FP64) return solve_fp64(h, b, x, tol, max_iter, iters);
-  return solve_mixed(h, b, x, tol, max_iter, iters);
 }
 
 void release(gabp_handle h) {
+  for (int m = 0; m < 3; ++m) {
+    if (h->exec[m]) cudaGraphExecDestroy(h->exec[m]);
+    if (h->graph[m]) cudaGraphDestroy(h->graph[m]);
+  }
   free_graph(h->g);
-  cudaFree(h->m64[0]); cudaFree(h->m64[1]); cudaFree(h->x_prev);
-  cudaFree(h->m32[0]); cudaFree(h->m32[1]); cudaFree(h->e32[0]); cudaFree(h->e32[1]);
-  cudaFree(h->c32); cudaFree(h->invP32); cudaFree(h->rhs32);
-  cudaFree(h->mon32[0]); cudaFree(h->mon32[1]);
-  cudaFree(h->xw); cudaFree(h->r64); cudaFree(h->red);
+  Buffers &B = h->buf;
+  cudaFree(B.m64[0]); cudaFree(B.m64[1]);
+  cudaFree(B.m32[0]); cudaFree(B.m32[1]); cudaFree(B.e[0]); cudaFree(B.e[1]);
+  cudaFree(B.c32); cudaFree(B.invP32); cudaFree(B.mon32[0]); cudaFree(B.mon32[1]);
+  cudaFree(B.r64);
+  cudaFree(h->red); cudaFree(h->ctl);
   cudaFree(h->bbuf); cudaFree(h->xbuf);
-  if (h->red_host) cudaFreeHost(h->red_host);
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
 }
@@ -334,11 +338,7 @@ void gabp_default_options(gabp_options *opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->precision = GABP_PREC_FP64;
   opt->residual_kind = GABP_RESIDUAL_REL;
-  opt->check_every = 0;
-  opt->group_lanes = 0;
-  opt->autotune = 0;
   opt->inner_tol = 1e-6;
-  opt->stream = nullptr;
 }
 
 gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t *row_ptr_host,
@@ -392,22 +392,22 @@ gabp_status gabp_set_stream(gabp_handle h, void *stream) {
 gabp_status gabp_solve(gabp_handle h, const double *b_dev, double *x_dev, double tol,
                        int32_t max_iter, int32_t *iters) {
   if (!h) return GABP_ERR_INVALID_ARG;
-  if (!b_dev || !x_dev || !(tol >= 0.0) || !std::isfinite(tol))
-    return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve: null pointer or invalid tol");
-  return guarded(h, [&] { return solve_dispatch(h, b_dev, x_dev, tol, max_iter, iters); });
+  if (!b_dev || !x_dev || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
+    return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve: null pointer, invalid tol or max_iter < 1");
+  return guarded(h, [&] { return solve_impl(h, b_dev, x_dev, tol, max_iter, iters); });
 }
 
 gabp_status gabp_solve_host(gabp_handle h, const double *b_host, double *x_host, double tol,
                             int32_t max_iter, int32_t *iters) {
   if (!h) return GABP_ERR_INVALID_ARG;
-  if (!b_host || !x_host || !(tol >= 0.0) || !std::isfinite(tol))
-    return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_host: null pointer or invalid tol");
+  if (!b_host || !x_host || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
+    return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_host: null pointer, invalid tol or max_iter < 1");
   return guarded(h, [&] {
     const size_t bytes = sizeof(double) * h->g.n;
     ensure(&h->bbuf, h->g.n);
     ensure(&h->xbuf, h->g.n);
     CK(cudaMemcpyAsync(h->bbuf, b_host, bytes, cudaMemcpyHostToDevice, h->stream));
-    const gabp_status s = solve_dispatch(h, h->bbuf, h->xbuf, tol, max_iter, iters);
+    const gabp_status s = solve_impl(h, h->bbuf, h->xbuf, tol, max_iter, iters);
     CK(cudaMemcpyAsync(x_host, h->xbuf, bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return s;
@@ -417,7 +417,7 @@ gabp_status gabp_solve_host(gabp_handle h, const double *b_host, double *x_host,
 gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, int32_t nrhs,
                              double tol, int32_t max_iter, int32_t *iters) {
   if (!h) return GABP_ERR_INVALID_ARG;
-  if (!B_dev || !X_dev || nrhs < 1 || !(tol >= 0.0) || !std::isfinite(tol))
+  if (!B_dev || !X_dev || nrhs < 1 || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: invalid argument");
   return guarded(h, [&] {
     const int64_t n = h->g.n;
@@ -425,18 +425,20 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
     ensure(&h->xbuf, n);
     int32_t total = 0;
     gabp_status worst = GABP_OK;
+    std::string msg;
     for (int32_t k = 0; k < nrhs; ++k) {
       CK(cudaMemcpy2DAsync(h->bbuf, sizeof(double), B_dev + k, sizeof(double) * nrhs,
                            sizeof(double), n, cudaMemcpyDeviceToDevice, h->stream));
       int32_t it = 0;
-      const gabp_status s = solve_dispatch(h, h->bbuf, h->xbuf, tol, max_iter, &it);
+      const gabp_status s = solve_impl(h, h->bbuf, h->xbuf, tol, max_iter, &it);
       total += it;
       CK(cudaMemcpy2DAsync(X_dev + k, sizeof(double) * nrhs, h->xbuf, sizeof(double),
                            sizeof(double), n, cudaMemcpyDeviceToDevice, h->stream));
-      if (s != GABP_OK && worst == GABP_OK) worst = s;
+      if (s != GABP_OK && worst == GABP_OK) { worst = s; msg = h->last_error; }
     }
     CK(cudaStreamSynchronize(h->stream));
     if (iters) *iters = total;
+    if (worst != GABP_OK) h->last_error = msg;
     return worst;
   });
 }
@@ -452,21 +454,21 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
   if (!b_dev || !x_dev || rounds < 0)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_run_rounds: invalid argument");
   return guarded(h, [&] {
-    Graph &g = h->g;
     cudaStream_t st = h->stream;
     ensure64(h);
-    zero_scalars(h);
-    CK(cudaMemsetAsync(h->m64[0], 0, sizeof(double2) * std::max<int64_t>(g.E, 1), st));
-    int cur = 0;
-    for (int32_t t = 0; t < rounds; ++t) {
-      run(h, K_FULL, [&] { return launch_sweep64(g, st, h->m64[cur], h->m64[cur ^ 1], b_dev, nullptr, nullptr, h->red, true); });
-      cur ^= 1;
-    }
-    // Tentative means of the last round's messages (no messages written).
-    run(h, K_FULL, [&] { return launch_sweep64(g, st, h->m64[cur], h->m64[cur ^ 1], b_dev, x_dev, nullptr, h->red, false); });
-    h->m64_cur = cur;
-    read_scalars(h);
-    if (h->red_host->breakdown) return fail(h, GABP_ERR_BREAKDOWN, "breakdown during rounds");
+    init_ctl(h, CTL_ROUNDS, b_dev, x_dev, 0.0, rounds, false);
+    h->ctl_host->rounds_target = rounds;
+    CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
+    // `rounds` message sweeps, then one pass that only writes the means.
+    for (int32_t t = 0; t <= rounds; ++t) launch_sweep64(h->g, st, h->buf, h->ctl, h->red);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    DevScalars red{};
+    CK(cudaMemcpyAsync(&red, h->red, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->m64_cur = h->ctl_host->par_m;
+    if (red.breakdown) return fail(h, GABP_ERR_BREAKDOWN, "breakdown during rounds");
     return GABP_OK;
   });
 }
@@ -477,9 +479,9 @@ gabp_status gabp_get_messages(gabp_handle h, double *P_host, double *mu_host) {
     const Graph &g = h->g;
     std::memset(P_host, 0, sizeof(double) * h->user_nnz);
     std::memset(mu_host, 0, sizeof(double) * h->user_nnz);
-    if (g.E == 0 || !h->m64[h->m64_cur]) return GABP_OK;
+    if (g.E == 0 || !h->have64) return GABP_OK;
     std::vector<double2> m(g.E);
-    CK(cudaMemcpyAsync(m.data(), h->m64[h->m64_cur], sizeof(double2) * g.E,
+    CK(cudaMemcpyAsync(m.data(), h->buf.m64[h->m64_cur], sizeof(double2) * g.E,
                        cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     // Slot s of row i holds m_{j->i}; it belongs at the CSR entry (j, i),
@@ -514,6 +516,6 @@ const char *gabp_status_string(gabp_status s) {
   return "GABP_UNKNOWN_STATUS";
 }
 
-const char *gabp_version(void) { return "gabp-gb300 0.1 (sm_103a)"; }
+const char *gabp_version(void) { return "gabp-gb300 0.2 (sm_103a)"; }
 
 }  // extern "C"

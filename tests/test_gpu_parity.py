@@ -291,3 +291,55 @@ def test_full_size_solve(G, er_full, precision):
     assert res < 1e-10 * np.abs(b).max()
     assert _rel(x, _oracle_solution(m, b)) < 1e-9
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# Drivers and storage modes
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_and_host_drivers_agree(G, precision):
+    """The graph driver (one CUDA graph per solve) and the host driver
+    (profile mode) run the same kernels and the same device-side decisions,
+    so they give bit-identical solutions and sweep counts."""
+    m = W.er_sdd(6000, 8, 1.1, 14)
+    b = W.normal_rhs(m.n, 15)
+    bt = torch.tensor(b, device="cuda")
+    out = []
+    for profile in (False, True):
+        s = _solver(G, m, precision=precision, profile=profile)
+        xt, it = s.solve(bt, tol=1e-10, max_iter=5000)
+        st = s.stats()
+        out.append((xt.cpu().numpy(), it, st))
+        s.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    assert out[1][2]["ms_full"] > 0 and out[1][2]["ms_residual"] > 0
+
+
+def test_bf16_mean_storage_reaches_tolerance(G):
+    """BF16 storage of the mean messages (FP32 arithmetic) inside FP64
+    refinement still reaches 1e-10; it needs more refinement steps."""
+    m = W.er_sdd(20000, 8, 1.1, 16)
+    b = W.normal_rhs(m.n, 17)
+    s32 = _solver(G, m, precision=1)
+    s16 = _solver(G, m, precision=2)
+    bt = torch.tensor(b, device="cuda")
+    x32, _ = s32.solve(bt, tol=1e-10, max_iter=5000)
+    x16, _ = s16.solve(bt, tol=1e-10, max_iter=5000)
+    for xt in (x32, x16):
+        x = xt.cpu().numpy()
+        assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    assert s16.stats()["outer_steps"] >= s32.stats()["outer_steps"]
+    s32.close()
+    s16.close()
+
+
+def test_repeated_solves_reuse_the_graph(G):
+    m = W.er_sdd(5000, 8, 1.1, 18)
+    s = _solver(G, m, precision=1)
+    for seed in range(3):
+        b = W.normal_rhs(m.n, 30 + seed)
+        xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10)
+        x = xt.cpu().numpy()
+        assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    s.close()
