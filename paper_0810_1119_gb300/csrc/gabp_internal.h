@@ -97,6 +97,7 @@ struct Buffers {
   float *invP32;            // frozen 1/P~_i
   float2 *mon32[2];         // (P~_i, d_i) of the last two sweeps
   double *r64;              // FP64 residual
+  float *rhs32;             // r_i / ||r|| of the current inner solve
 };
 
 // Row tiles: tiles[t] = (first row, first slot) of tile t, tiles[ntiles] =
@@ -107,6 +108,7 @@ struct GraphView {
   const double *a64, *diag64;
   const float *a32, *diag32;
   const int2 *tiles_big, *tiles_small;
+  const uint16_t *lrow_big;     // tile-local row id of every slot (big tiles)
   int32_t ntiles_big, ntiles_small;
   int32_t n;
 };
@@ -122,13 +124,14 @@ struct Graph {
   double *a64 = nullptr, *diag64 = nullptr;
   float *a32 = nullptr, *diag32 = nullptr;
   int2 *tiles_big = nullptr, *tiles_small = nullptr;
+  uint16_t *lrow_big = nullptr;
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
   int max_degree = 0;
 
   GraphView view() const {
-    return GraphView{rp,       rev,       col,        a64,         diag64,      a32,
-                     diag32,   tiles_big, tiles_small, ntiles_big, ntiles_small, n};
+    return GraphView{rp,        rev,         col,      a64,        diag64,       a32, diag32,
+                     tiles_big, tiles_small, lrow_big, ntiles_big, ntiles_small, n};
   }
 };
 

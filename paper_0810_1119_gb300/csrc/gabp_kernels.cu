@@ -3,26 +3,34 @@
 //
 // Every sweep kernel implements one round of Alg. 2 (broadcast GaBP) with the
 // parallel schedule of Section III-C: it reads only the previous round's
-// messages (buffer "in") and writes the new round (buffer "out").
+// messages (buffer "in") and writes the new round (buffer "out").  Slot s of
+// row i holds the incoming message m_{j->i}; a row forms
+//     P~_i = A_ii + sum_k P_ki,        h~_i = b_i + sum_k eta_ki      (eta = P mu)
+// and sends, to slot rev[s] of row j,
+//     P_ij   = -A_ij^2 / (P~_i - P_ji),
+//     eta_ij = -A_ij (h~_i - eta_ji) / (P~_i - P_ji),
+// using the reverse message m_{j->i} it already holds.  Reads are contiguous;
+// only the message store is a scatter.
 //
-// Work mapping: a group of G lanes (G a power of two, 2 <= G <= 32) owns one
-// row i.  The lanes stride over the row's slots, which hold the incoming
-// messages m_{j->i}; the row totals
-//     P~_i = A_ii + sum_k P_ki,        h~_i = b_i + sum_k eta_ki
-// are formed with a shuffle reduction inside the group, and each lane then
-// sends the messages of its own slots (the reverse message m_{j->i} needed by
-// P~_i - P_ji is the value the lane already holds):
-//     P_ij   = -A_ij^2 / (P~_i - P_ji)
-//     eta_ij = -A_ij (h~_i - eta_ji) / (P~_i - P_ji)     (eta = P mu)
-// written to slot rev[s] of row j.  Reads are contiguous; only the message
-// store is a scatter.  Up to kCacheSlots slots per lane stay in registers
-// between the two passes; longer rows re-read the tail.
+// Memory pipeline: persistent CTAs walk row tiles (a few thousand slots of
+// consecutive rows).  Thread 0 stages the next tile's contiguous slot and node
+// arrays into shared memory with cp.async.bulk on an mbarrier while the CTA
+// computes the current tile from shared memory.
+//
+// Work mapping inside a tile (FP32 sweeps): slot-parallel.  Threads take slots
+// tid, tid + blockDim, ...; the tile-local row id of each slot (staged with the
+// slots) drives a warp-segmented sum whose run heads add into per-row totals
+// in shared memory; after one barrier every slot sends its message and one
+// thread per row does the node work.  Lanes stay busy whatever the degree
+// distribution.  The FP64 sweep keeps a G-lanes-per-row mapping (its row sums
+// cost one FP64 add per slot; a segmented scan would cost five on GB300's
+// 1/64-rate FP64 pipe).
 //
 // Control: kernels take their buffer parities and flags from the control
-// block (Ctl).  The last block to finish a controlling launch (detected with
-// an atomic counter, no waiting) runs `control`, which reads the reductions,
-// decides the next phase, and -- inside a solve graph -- sets the graph's
-// WHILE and SWITCH conditions.
+// block (Ctl).  The last block to finish a launch (detected with an atomic
+// counter, no waiting) runs `control`, which reads the reductions, decides the
+// next phase, and -- inside a solve graph -- sets the graph's WHILE and SWITCH
+// conditions.
 #include "gabp_internal.h"
 
 #include <algorithm>
@@ -46,6 +54,17 @@ __device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigne
   return a > b ? a : b;
 }
 
+// Running maximum of |v| for FP32 values, kept as the bit pattern of the
+// non-negative float (NaN compares above +inf); widened to the FP64 bit
+// pattern once per thread for the block reduction.
+__device__ __forceinline__ uint32_t fmax_bits(uint32_t m, float v) {
+  const uint32_t u = __float_as_uint(fabsf(v));
+  return u > m ? u : m;
+}
+__device__ __forceinline__ unsigned long long widen(uint32_t m) {
+  return bits(static_cast<double>(__uint_as_float(m)));
+}
+
 __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = umax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -58,7 +77,7 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 __device__ void block_max4(unsigned long long v0, unsigned long long v1, unsigned long long v2,
                            unsigned long long v3, unsigned long long *d0, unsigned long long *d1,
                            unsigned long long *d2, unsigned long long *d3) {
-  __shared__ unsigned long long sm[4][kBlock / 32];
+  __shared__ unsigned long long sm[4][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   v0 = warp_max(v0); v1 = warp_max(v1); v2 = warp_max(v2); v3 = warp_max(v3);
   if (lane == 0) { sm[0][w] = v0; sm[1][w] = v1; sm[2][w] = v2; sm[3][w] = v3; }
@@ -81,6 +100,48 @@ template <int G, class T>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (all threads call it; every thread gets the result).
+template <class T>
+__device__ T block_sum(T v) {
+  __shared__ T part[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  T tot = T(0);
+  for (int k = 0; k < nw; ++k) tot += part[k];
+  return tot;
+}
+
+// Warp sum by key over 32 consecutive slots whose keys (tile-local row ids)
+// do not decrease along the lanes: a doubling scan that only adds a partner
+// with the same key, so after five steps the first lane of every run of
+// equal keys holds the run's total.  Sets `head` in those lanes.
+__device__ __forceinline__ float shfl_down(float v, int off) {
+  return __shfl_down_sync(0xffffffffu, v, off);
+}
+__device__ __forceinline__ float2 shfl_down(float2 v, int off) {
+  return make_float2(__shfl_down_sync(0xffffffffu, v.x, off), __shfl_down_sync(0xffffffffu, v.y, off));
+}
+__device__ __forceinline__ void add_to(float &a, float b) { a += b; }
+__device__ __forceinline__ void add_to(float2 &a, float2 b) { a.x += b.x; a.y += b.y; }
+
+template <class V>
+__device__ __forceinline__ V seg_sum(V v, int key, bool &head) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const V w = shfl_down(v, off);
+    const int k = __shfl_down_sync(0xffffffffu, key, off);
+    if (lane + off < 32 && k == key) add_to(v, w);
+  }
+  const int kp = __shfl_up_sync(0xffffffffu, key, 1);
+  head = lane == 0 || kp != key;
   return v;
 }
 
@@ -267,15 +328,13 @@ __global__ void __launch_bounds__(kBlock) init_kernel(int32_t n, double *__restr
 // A tile is a run of consecutive rows [r0, r1) whose slots [s0, s1) number
 // at most TS (and rows at most TR); a row with more than TS slots is a tile
 // of its own ("long tile") that the whole CTA processes straight from global
-// memory.  Persistent CTAs walk the tiles with a two-stage pipeline: thread 0
-// stages the next tile's contiguous slot and node arrays into shared memory
-// with cp.async.bulk (one copy per array, completion counted on an
-// mbarrier) while the CTA computes the current tile from shared memory.
-// Every wait is bounded; a wait that gives up sets `timeout` in the
+// memory.  Every wait is bounded; a wait that gives up sets `timeout` in the
 // reductions (the controller then stops the solve with GABP_ERR_TIMEOUT).
 // ---------------------------------------------------------------------------
 constexpr int kTileSlotsBig = 2048, kTileRowsBig = 512;     // FP32 sweeps, residual
 constexpr int kTileSlotsSmall = 1024, kTileRowsSmall = 256; // FP64 sweep
+constexpr int kTileBlock = 512;                             // threads of the slot-parallel kernels
+constexpr int kNoRow = 0xFFFF;                              // key of lanes past the tile's end
 constexpr int kWaitLimit = 1 << 22;                         // try_wait polls before giving up
 
 __host__ __device__ constexpr uint32_t r128(uint64_t b) {
@@ -344,8 +403,8 @@ struct Seg {
     if (b) bulk_g2s(dst, base + (first - first % kPer), b, bar);
   }
   // Shared-memory pointer to element `first` of a staged run.
-  __device__ static const E *at(const unsigned char *region_ptr, int64_t first) {
-    return reinterpret_cast<const E *>(region_ptr) + first % kPer;
+  __device__ static E *at(unsigned char *region_ptr, int64_t first) {
+    return reinterpret_cast<E *>(region_ptr) + first % kPer;
   }
 };
 
@@ -357,57 +416,44 @@ __device__ __forceinline__ TileBounds tile_at(const int2 *__restrict__ tiles, in
   return TileBounds{a.x, b.x, a.y, b.y};
 }
 
-// Persistent two-stage loop over the tiles.  `issue(t, stage_ptr, bar)` is
-// called by thread 0 and must arrive once on `bar` with the bytes it copies;
-// `work(t, stage_ptr)` is called by all threads once the stage has landed.
-// Returns false if a wait gave up (after draining the copy in flight).
+// Persistent two-stage loop over the tiles.  `issue(t, stage, bar)` is called
+// by thread 0 and must arrive once on `bar` with the bytes it copies.
+// `work(t, stage, st, got)` is called by all threads once thread-local waits
+// returned (`got` = this thread saw the stage land); it must pass
+// __syncthreads_or(!got) before any side effect outside shared memory and
+// return that value (true = abort).  Returns false if a wait gave up (after
+// draining the copy in flight).
 template <class Issue, class Work>
 __device__ bool run_tiles(int32_t ntiles, unsigned char *smem, uint32_t stage_bytes,
                           uint64_t *bars, Issue issue, Work work) {
-  const uint32_t bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  const uint32_t bar0 = smem_u32(&bars[0]), bar1 = smem_u32(&bars[1]);
   if (threadIdx.x == 0) {
-    mbar_init(bar[0], 1);
-    mbar_init(bar[1], 1);
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
     fence_mbar_init();
   }
   __syncthreads();
   int32_t t = blockIdx.x;
-  if (t < ntiles && threadIdx.x == 0) issue(t, smem, bar[0]);
+  if (t < ntiles && threadIdx.x == 0) issue(t, smem, bar0);
   bool ok = true;
   for (int j = 0; t < ntiles; ++j, t += gridDim.x) {
     const int st = j & 1;
+    const uint32_t bar_cur = st ? bar1 : bar0, bar_next = st ? bar0 : bar1;
     const int32_t tn = t + gridDim.x;
     if (tn < ntiles && threadIdx.x == 0) {
       fence_proxy_async();   // stage st^1 was last read by generic loads
-      issue(tn, smem + (st ^ 1) * stage_bytes, bar[st ^ 1]);
+      issue(tn, smem + (st ^ 1) * stage_bytes, bar_next);
     }
-    const bool got = mbar_wait(bar[st], (j >> 1) & 1);
-    if (__syncthreads_or(!got)) {
+    const bool got = mbar_wait(bar_cur, (j >> 1) & 1);
+    if (work(t, smem + st * stage_bytes, st, got)) {
       ok = false;
-      if (tn < ntiles) mbar_wait(bar[st ^ 1], ((j + 1) >> 1) & 1);
+      if (tn < ntiles) mbar_wait(bar_next, ((j + 1) >> 1) & 1);
       __syncthreads();
       break;
     }
-    work(t, smem + st * stage_bytes);
     __syncthreads();
   }
   return ok;
-}
-
-// Block-wide sum (all threads call it; every thread gets the result).
-template <class T>
-__device__ T block_sum(T v) {
-  __shared__ T part[kBlock / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) part[w] = v;
-  __syncthreads();
-  T tot = T(0);
-#pragma unroll
-  for (int k = 0; k < kBlock / 32; ++k) tot += part[k];
-  return tot;
 }
 
 // 1/d in FP64: an FP32 reciprocal seed (relative error e0 < 2^-22), then the
@@ -425,7 +471,8 @@ __device__ __forceinline__ double recip64(double d) {
 // ---------------------------------------------------------------------------
 // FP64 full sweep: new (P, eta) for every directed edge, plus (when asked)
 // the tentative means x_i = h~_i / P~_i of the messages read (Alg. 2 step 4).
-// Staged per tile: (P, eta) in, A_ij, rev, row pointers, A_ii.
+// Staged per tile: (P, eta) in, A_ij, rev, row pointers, A_ii.  G lanes per
+// row.
 // ---------------------------------------------------------------------------
 struct Layout64 {
   static constexpr int TS = kTileSlotsSmall, TR = kTileRowsSmall;
@@ -453,8 +500,8 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   }
   const double *__restrict__ b = ctl->b;
   double *__restrict__ x = ctl->x;
-  const double2 *__restrict__ min = B.m64[par];
-  double2 *__restrict__ mout = B.m64[par ^ 1];
+  const double2 *__restrict__ min = (par ? B.m64[1] : B.m64[0]);
+  double2 *__restrict__ mout = (par ? B.m64[0] : B.m64[1]);
   const int gl = threadIdx.x % G;
   bool brk = false;
 
@@ -462,13 +509,12 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const TileBounds tb = tile_at(g.tiles_small, t);
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
-    const bool msgs = !first;
-    const uint32_t tx = (msgs ? Seg<double2>::bytes(tb.s0, ns) : 0) +
+    const uint32_t tx = (first ? 0 : Seg<double2>::bytes(tb.s0, ns)) +
                         Seg<double>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
                         Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (msgs) Seg<double2>::copy(base + L::m, min, tb.s0, ns, bar);
+    if (!first) Seg<double2>::copy(base + L::m, min, tb.s0, ns, bar);
     Seg<double>::copy(base + L::a, g.a64, tb.s0, ns, bar);
     Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
     Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
@@ -482,7 +528,8 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     mout[dst] = make_double2(-(a * a) * inv, -a * (Th - m.y) * inv);
   };
 
-  auto work = [&](int32_t t, unsigned char *stage) {
+  auto work = [&](int32_t t, unsigned char *stage, int, bool got) {
+    if (__syncthreads_or(!got)) return true;
     const TileBounds tb = tile_at(g.tiles_small, t);
     const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) {
@@ -490,7 +537,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       const int32_t i = tb.r0;
       double sP = 0.0, sH = 0.0;
       if (!first)
-        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) {
+        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += blockDim.x) {
           const double2 m = min[s];
           sP += m.x;
           sH += m.y;
@@ -500,9 +547,9 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       const double TP = g.diag64[i] + sP, Th = b[i] + sH;
       if (write_x && threadIdx.x == 0) x[i] = Th / TP;
       if (write_msgs)
-        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock)
+        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += blockDim.x)
           emit(g.a64[s], first ? make_double2(0.0, 0.0) : min[s], g.rev[s], TP, Th);
-      return;
+      return false;
     }
     const double2 *ms = Seg<double2>::at(stage + L::m, tb.s0);
     const double *as = Seg<double>::at(stage + L::a, tb.s0);
@@ -529,6 +576,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       for (int32_t s = rs + gl; s < re; s += G)
         emit(as[s], first ? make_double2(0.0, 0.0) : ms[s], rv[s], TP, Th);
     }
+    return false;
   };
 
   const bool ok = run_tiles(g.ntiles_small, smem, L::bytes, bars, issue, work);
@@ -539,73 +587,80 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 
 // ---------------------------------------------------------------------------
 // FP32 full sweep (mixed modes, precision phase).  Messages (P, eta) and
-// totals in FP32; rhs_i = r_i / ||r||.  Records (P~_i, d_i = h~_i / P~_i) per
+// totals in FP32; rhs_i = r_i / ||r|| (scaled in FP64 by the first sweep of
+// an inner solve, then kept in FP32).  Records (P~_i, d_i = h~_i / P~_i) per
 // node and the change against the previous sweep.  When the controller has
 // set pending_freeze, the sweep freezes instead: it stores the coefficient
 // c_ij = -A_ij / (P~_i - P_ji) at slot s of row i, 1/P~_i, and the first
 // mean-only messages eta_ij = c_ij (h~_i - eta_ji).
-// Staged per tile: (P, eta) in, A_ij, rev, row pointers, A_ii, r, monitors.
+// Staged per tile: (P, eta) in, A_ij, rev, local row ids, A_ii, rhs, monitors.
 // ---------------------------------------------------------------------------
 struct Layout32 {
   static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
   static constexpr uint32_t m = 0, a = m + region(TS, 8), rev = a + region(TS, 4),
-                            rp = rev + region(TS, 4), dg = rp + region(TR + 1, 4),
+                            lr = rev + region(TS, 4), dg = lr + region(TS, 2),
                             r = dg + region(TR, 4), mon = r + region(TR, 8),
                             bytes = mon + region(TR, 8);
 };
 
-template <int G, class T>
-__global__ void __launch_bounds__(kBlock)
+template <class T>
+__global__ void __launch_bounds__(kTileBlock)
 sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   using L = Layout32;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
+  __shared__ float2 tot[2][L::TR];   // per-row sums of incoming (P, eta), double-buffered
+  __shared__ float rhs_s[L::TR];
   const int pm = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
   const bool freeze = ctl->pending_freeze != 0;
   const double inv_rn = ctl->inv_rn;
-  const float2 *__restrict__ min = B.m32[pm];
-  float2 *__restrict__ mout = B.m32[pm ^ 1];
-  T *__restrict__ eta_out = static_cast<T *>(B.e[pe ^ 1]);
-  const float2 *__restrict__ mon_prev = B.mon32[pmon];
-  float2 *__restrict__ mon_out = B.mon32[pmon ^ 1];
-  const int gl = threadIdx.x % G;
-  unsigned long long mdd = 0, md = 0, mdP = 0, mP = 0;
+  const float2 *__restrict__ min = (pm ? B.m32[1] : B.m32[0]);
+  float2 *__restrict__ mout = (pm ? B.m32[0] : B.m32[1]);
+  T *__restrict__ eta_out = static_cast<T *>((pe ? B.e[0] : B.e[1]));
+  const float2 *__restrict__ mon_prev = (pmon ? B.mon32[1] : B.mon32[0]);
+  float2 *__restrict__ mon_out = (pmon ? B.mon32[0] : B.mon32[1]);
+  const int NT = blockDim.x, tid = threadIdx.x;
+  uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;
   bool brk = false;
+  for (int k = tid; k < 2 * L::TR; k += NT) (&tot[0][0])[k] = make_float2(0.f, 0.f);
 
   auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
-    const uint32_t tx = (first ? 0 : Seg<float2>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr)) +
+    const uint32_t tx = (first ? Seg<double>::bytes(tb.r0, nr)
+                               : Seg<float2>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr) +
+                                     Seg<float>::bytes(tb.r0, nr)) +
                         Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
-                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<float>::bytes(tb.r0, nr) +
-                        Seg<double>::bytes(tb.r0, nr);
+                        Seg<uint16_t>::bytes(tb.s0, ns) + Seg<float>::bytes(tb.r0, nr);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (!first) {
+    if (first) {
+      Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
+    } else {
       Seg<float2>::copy(base + L::m, min, tb.s0, ns, bar);
       Seg<float2>::copy(base + L::mon, mon_prev, tb.r0, nr, bar);
+      Seg<float>::copy(base + L::r, B.rhs32, tb.r0, nr, bar);
     }
     Seg<float>::copy(base + L::a, g.a32, tb.s0, ns, bar);
     Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
-    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
+    Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar);
     Seg<float>::copy(base + L::dg, g.diag32, tb.r0, nr, bar);
-    Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
   };
 
-  // node part: monitors (and 1/P~ when freezing) by one lane per row
-  auto node = [&](int32_t i, float TP, float Th, float2 prev) {
+  auto node = [&](int32_t i, float TP, float Th, float rhs, float2 prev) {
     const float di = Th / TP;
     mon_out[i] = make_float2(TP, di);
-    mdd = umax(mdd, bits(fabs(static_cast<double>(di) - prev.y)));
-    md = umax(md, bits(fabs(static_cast<double>(di))));
-    mdP = umax(mdP, bits(fabs(static_cast<double>(TP) - prev.x)));
-    mP = umax(mP, bits(fabs(static_cast<double>(TP))));
+    mdd = fmax_bits(mdd, di - prev.y);
+    md = fmax_bits(md, di);
+    mdP = fmax_bits(mdP, TP - prev.x);
+    mP = fmax_bits(mP, TP);
     if (freeze) B.invP32[i] = 1.0f / TP;
+    if (first) B.rhs32[i] = rhs;
   };
   auto emit = [&](int32_t s, float a, float2 m, int32_t dst, float TP, float Th) {
-    const float d = TP - m.x;
+    const float d = TP - m.x;   // P_{i\j} = P~_i - P_ji
     brk |= !(d != 0.0f) || !isfinite(d);
     const float inv = 1.0f / d;
     if (freeze) {
@@ -617,14 +672,15 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     }
   };
 
-  auto work = [&](int32_t t, unsigned char *stage) {
+  auto work = [&](int32_t t, unsigned char *stage, int st, bool got) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) {
+      if (__syncthreads_or(!got)) return true;
       const int32_t i = tb.r0;
       float sP = 0.f, sH = 0.f;
       if (!first)
-        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) {
+        for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) {
           const float2 m = min[s];
           sP += m.x;
           sH += m.y;
@@ -632,45 +688,59 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       sP = block_sum(sP);
       sH = block_sum(sH);
       const float TP = g.diag32[i] + sP;
-      const float Th = static_cast<float>(B.r64[i] * inv_rn) + sH;
-      if (threadIdx.x == 0) node(i, TP, Th, first ? make_float2(0.f, 0.f) : mon_prev[i]);
-      for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock)
+      const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+      const float Th = rhs + sH;
+      if (tid == 0) node(i, TP, Th, rhs, first ? make_float2(0.f, 0.f) : mon_prev[i]);
+      for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT)
         emit(s, g.a32[s], first ? make_float2(0.f, 0.f) : min[s], g.rev[s], TP, Th);
-      return;
+      return false;
     }
+    float2 *tc = tot[st], *tn = tot[st ^ 1];
     const float2 *ms = Seg<float2>::at(stage + L::m, tb.s0);
     const float *as = Seg<float>::at(stage + L::a, tb.s0);
     const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
-    const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+    const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
     const float *dg = Seg<float>::at(stage + L::dg, tb.r0);
-    const double *rr = Seg<double>::at(stage + L::r, tb.r0);
+    const double *r64s = Seg<double>::at(stage + L::r, tb.r0);
+    const float *r32s = Seg<float>::at(stage + L::r, tb.r0);
     const float2 *mp = Seg<float2>::at(stage + L::mon, tb.r0);
-    for (int32_t base_r = 0; base_r < nr; base_r += kBlock / G) {
-      const int32_t lr = base_r + static_cast<int32_t>(threadIdx.x) / G;
-      const bool valid = lr < nr;
-      const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
-      float sP = 0.f, sH = 0.f;
-      if (!first)
-        for (int32_t s = rs + gl; s < re; s += G) {
-          sP += ms[s].x;
-          sH += ms[s].y;
+    // phase 1: rhs per row, clear the next tile's sums, segmented sums
+    for (int32_t k = tid; k < nr; k += NT)
+      rhs_s[k] = first ? static_cast<float>(r64s[k] * inv_rn) : r32s[k];
+    for (int32_t k = tid; k < L::TR; k += NT) tn[k] = make_float2(0.f, 0.f);
+    if (!first) {
+      for (int32_t base = tid & ~31; base < ns; base += NT) {
+        const int32_t s = base + (tid & 31);
+        const bool v = s < ns;
+        const int key = v ? lrow[s] : kNoRow;
+        bool head;
+        const float2 sum = seg_sum(v ? ms[s] : make_float2(0.f, 0.f), key, head);
+        if (head && v) {
+          atomicAdd(&tc[key].x, sum.x);
+          atomicAdd(&tc[key].y, sum.y);
         }
-      sP = group_sum<G>(sP);
-      sH = group_sum<G>(sH);
-      if (!valid) continue;
-      const int32_t i = tb.r0 + lr;
-      const float TP = dg[lr] + sP;
-      const float Th = static_cast<float>(rr[lr] * inv_rn) + sH;
-      if (gl == 0) node(i, TP, Th, first ? make_float2(0.f, 0.f) : mp[lr]);
-      for (int32_t s = rs + gl; s < re; s += G)
-        emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], TP, Th);
+      }
     }
+    if (__syncthreads_or(!got)) return true;
+    // phase 2: node work per row, messages per slot
+    for (int32_t k = tid; k < nr; k += NT) {
+      const float TP = dg[k] + tc[k].x, Th = rhs_s[k] + tc[k].y;
+      node(tb.r0 + k, TP, Th, rhs_s[k], first ? make_float2(0.f, 0.f) : mp[k]);
+    }
+    for (int32_t s = tid; s < ns; s += NT) {
+      const int k = lrow[s];
+      const float2 tk = tc[k];
+      emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], dg[k] + tk.x,
+           rhs_s[k] + tk.y);
+    }
+    return false;
   };
 
   const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
   if (brk) atomicOr(&red->breakdown, 1);
   if (!ok) atomicOr(&red->timeout, 1);
-  block_max4(mdd, md, mdP, mP, &red->max_dx, &red->max_x, &red->max_dP, &red->max_P);
+  block_max4(widen(mdd), widen(md), widen(mdP), widen(mP), &red->max_dx, &red->max_x,
+             &red->max_dP, &red->max_P);
   last_block_control(ctl, red, CK_SWEEP32);
 }
 
@@ -678,107 +748,125 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 // Mean-only sweep with frozen precisions (storage T = float or bf16, FP32
 // arithmetic): eta_ij = c_ij (h~_i - eta_ji), h~_i = r_i/||r|| + sum_k eta_ki,
 // d_i = h~_i / P~_i.  Records d_i and its change.
-// Staged per tile: eta in, c, rev, row pointers, r, 1/P~, monitors.
+// Staged per tile: eta in, c, rev, local row ids, rhs, 1/P~, monitors.
 // ---------------------------------------------------------------------------
 template <class T>
 struct LayoutMean {
   static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
   static constexpr uint32_t e = 0, c = e + region(TS, sizeof(T)), rev = c + region(TS, 4),
-                            rp = rev + region(TS, 4), r = rp + region(TR + 1, 4),
+                            lr = rev + region(TS, 4), r = lr + region(TS, 2),
                             ip = r + region(TR, 8), mon = ip + region(TR, 4),
                             bytes = mon + region(TR, 8);
 };
 
-template <int G, class T>
-__global__ void __launch_bounds__(kBlock)
+template <class T>
+__global__ void __launch_bounds__(kTileBlock)
 mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   using L = LayoutMean<T>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
+  __shared__ float tot[2][L::TR];    // per-row sums of incoming eta, double-buffered
+  __shared__ float rhs_s[L::TR];
   const int pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
   const double inv_rn = ctl->inv_rn;
-  const T *__restrict__ ein = static_cast<const T *>(B.e[pe]);
-  T *__restrict__ eout = static_cast<T *>(B.e[pe ^ 1]);
-  const float2 *__restrict__ mon_prev = B.mon32[pmon];
-  float2 *__restrict__ mon_out = B.mon32[pmon ^ 1];
-  const int gl = threadIdx.x % G;
-  unsigned long long mdd = 0, md = 0;
+  const T *__restrict__ ein = static_cast<const T *>((pe ? B.e[1] : B.e[0]));
+  T *__restrict__ eout = static_cast<T *>((pe ? B.e[0] : B.e[1]));
+  const float2 *__restrict__ mon_prev = (pmon ? B.mon32[1] : B.mon32[0]);
+  float2 *__restrict__ mon_out = (pmon ? B.mon32[0] : B.mon32[1]);
+  const int NT = blockDim.x, tid = threadIdx.x;
+  uint32_t mdd = 0, md = 0;
+  for (int k = tid; k < 2 * L::TR; k += NT) (&tot[0][0])[k] = 0.f;
 
   auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
-    const uint32_t tx = (first ? 0 : Seg<T>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr)) +
+    const uint32_t tx = (first ? Seg<double>::bytes(tb.r0, nr)
+                               : Seg<T>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr) +
+                                     Seg<float>::bytes(tb.r0, nr)) +
                         Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
-                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr) +
-                        Seg<float>::bytes(tb.r0, nr);
+                        Seg<uint16_t>::bytes(tb.s0, ns) + Seg<float>::bytes(tb.r0, nr);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (!first) {
+    if (first) {
+      Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
+    } else {
       Seg<T>::copy(base + L::e, ein, tb.s0, ns, bar);
       Seg<float2>::copy(base + L::mon, mon_prev, tb.r0, nr, bar);
+      Seg<float>::copy(base + L::r, B.rhs32, tb.r0, nr, bar);
     }
     Seg<float>::copy(base + L::c, B.c32, tb.s0, ns, bar);
     Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
-    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
-    Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
+    Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar);
     Seg<float>::copy(base + L::ip, B.invP32, tb.r0, nr, bar);
   };
 
-  auto node = [&](int32_t i, float Th, float invP, float prev) {
+  auto node = [&](int32_t i, float Th, float invP, float rhs, float prev) {
     const float di = Th * invP;
     mon_out[i] = make_float2(0.f, di);
-    mdd = umax(mdd, bits(fabs(static_cast<double>(di) - prev)));
-    md = umax(md, bits(fabs(static_cast<double>(di))));
+    mdd = fmax_bits(mdd, di - prev);
+    md = fmax_bits(md, di);
+    if (first) B.rhs32[i] = rhs;
   };
 
-  auto work = [&](int32_t t, unsigned char *stage) {
+  auto work = [&](int32_t t, unsigned char *stage, int st, bool got) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) {
+      if (__syncthreads_or(!got)) return true;
       const int32_t i = tb.r0;
       float sH = 0.f;
       if (!first)
-        for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) sH += ld_eta(ein + s);
+        for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) sH += ld_eta(ein + s);
       sH = block_sum(sH);
-      const float Th = static_cast<float>(B.r64[i] * inv_rn) + sH;
-      if (threadIdx.x == 0) node(i, Th, B.invP32[i], first ? 0.f : mon_prev[i].y);
-      for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) {
+      const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+      const float Th = rhs + sH;
+      if (tid == 0) node(i, Th, B.invP32[i], rhs, first ? 0.f : mon_prev[i].y);
+      for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) {
         const float e = first ? 0.f : ld_eta(ein + s);
         st_eta(eout + g.rev[s], B.c32[s] * (Th - e));
       }
-      return;
+      return false;
     }
+    float *tc = tot[st], *tn = tot[st ^ 1];
     const T *es = Seg<T>::at(stage + L::e, tb.s0);
     const float *cs = Seg<float>::at(stage + L::c, tb.s0);
     const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
-    const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
-    const double *rr = Seg<double>::at(stage + L::r, tb.r0);
+    const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
+    const double *r64s = Seg<double>::at(stage + L::r, tb.r0);
+    const float *r32s = Seg<float>::at(stage + L::r, tb.r0);
     const float *ip = Seg<float>::at(stage + L::ip, tb.r0);
     const float2 *mp = Seg<float2>::at(stage + L::mon, tb.r0);
-    for (int32_t base_r = 0; base_r < nr; base_r += kBlock / G) {
-      const int32_t lr = base_r + static_cast<int32_t>(threadIdx.x) / G;
-      const bool valid = lr < nr;
-      const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
-      float sH = 0.f;
-      if (!first)
-        for (int32_t s = rs + gl; s < re; s += G) sH += ld_eta(es + s);
-      sH = group_sum<G>(sH);
-      if (!valid) continue;
-      const int32_t i = tb.r0 + lr;
-      const float Th = static_cast<float>(rr[lr] * inv_rn) + sH;
-      if (gl == 0) node(i, Th, ip[lr], first ? 0.f : mp[lr].y);
-      for (int32_t s = rs + gl; s < re; s += G) {
-        const float e = first ? 0.f : ld_eta(es + s);
-        st_eta(eout + rv[s], cs[s] * (Th - e));
+    // phase 1: rhs per row, clear the next tile's sums, segmented sums
+    for (int32_t k = tid; k < nr; k += NT)
+      rhs_s[k] = first ? static_cast<float>(r64s[k] * inv_rn) : r32s[k];
+    for (int32_t k = tid; k < L::TR; k += NT) tn[k] = 0.f;
+    if (!first) {
+      for (int32_t base = tid & ~31; base < ns; base += NT) {
+        const int32_t s = base + (tid & 31);
+        const bool v = s < ns;
+        const int key = v ? lrow[s] : kNoRow;
+        bool head;
+        const float sum = seg_sum(v ? ld_eta(es + s) : 0.f, key, head);
+        if (head && v) atomicAdd(&tc[key], sum);
       }
     }
+    if (__syncthreads_or(!got)) return true;
+    // phase 2: node work per row, messages per slot
+    for (int32_t k = tid; k < nr; k += NT)
+      node(tb.r0 + k, rhs_s[k] + tc[k], ip[k], rhs_s[k], first ? 0.f : mp[k].y);
+    for (int32_t s = tid; s < ns; s += NT) {
+      const int k = lrow[s];
+      const float e = first ? 0.f : ld_eta(es + s);
+      st_eta(eout + rv[s], cs[s] * (rhs_s[k] + tc[k] - e));
+    }
+    return false;
   };
 
   const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
   if (!ok) atomicOr(&red->timeout, 1);
-  block_max4(mdd, md, 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
+  block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
   last_block_control(ctl, red, CK_MEAN);
 }
 
@@ -786,7 +874,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 __global__ void __launch_bounds__(kBlock) refine_update_kernel(int32_t n, Buffers B, Ctl *ctl) {
   double *x = ctl->x;
   const double rn = ctl->rn;
-  const float2 *mon = B.mon32[ctl->par_mon];
+  const float2 *mon = (ctl->par_mon ? B.mon32[1] : B.mon32[0]);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
     x[i] += static_cast<double>(mon[i].y) * rn;
@@ -794,7 +882,10 @@ __global__ void __launch_bounds__(kBlock) refine_update_kernel(int32_t n, Buffer
 
 // ---------------------------------------------------------------------------
 // FP64 residual r = b - A x with its infinity norm (a CSR SpMV).  Staged per
-// tile: A_ij, col, row pointers, A_ii; x[col] is gathered from global memory.
+// tile: A_ij, col, row pointers, A_ii.  Phase 1 (slot-parallel): the products
+// A_ij x_j, with x_j gathered from global memory, overwrite A_ij in shared
+// memory.  Phase 2: one thread per row sums its products (one FP64 add per
+// slot) and forms r_i.
 // ---------------------------------------------------------------------------
 struct LayoutRes {
   static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
@@ -802,15 +893,14 @@ struct LayoutRes {
                             dg = rp + region(TR + 1, 4), bytes = dg + region(TR, 8);
 };
 
-template <int G>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kTileBlock)
 residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars *red, int kind) {
   using L = LayoutRes;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
   const double *__restrict__ b = ctl->b;
   const double *__restrict__ x = ctl->x;
-  const int gl = threadIdx.x % G;
+  const int NT = blockDim.x, tid = threadIdx.x;
   unsigned long long mr = 0;
 
   auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
@@ -833,29 +923,30 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
     mr = umax(mr, bits(fabs(ri)));
   };
 
-  auto work = [&](int32_t t, unsigned char *stage) {
+  auto work = [&](int32_t t, unsigned char *stage, int, bool got) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) {
+      if (__syncthreads_or(!got)) return true;
       double acc = 0.0;
-      for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += kBlock) acc += g.a64[s] * x[g.col[s]];
+      for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) acc += g.a64[s] * x[g.col[s]];
       acc = block_sum(acc);
-      if (threadIdx.x == 0) node(tb.r0, g.diag64[tb.r0], acc);
-      return;
+      if (tid == 0) node(tb.r0, g.diag64[tb.r0], acc);
+      return false;
     }
-    const double *as = Seg<double>::at(stage + L::a, tb.s0);
+    double *as = Seg<double>::at(stage + L::a, tb.s0);
     const int32_t *cs = Seg<int32_t>::at(stage + L::col, tb.s0);
     const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
     const double *dg = Seg<double>::at(stage + L::dg, tb.r0);
-    for (int32_t base_r = 0; base_r < nr; base_r += kBlock / G) {
-      const int32_t lr = base_r + static_cast<int32_t>(threadIdx.x) / G;
-      const bool valid = lr < nr;
-      const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
+    if (got)
+      for (int32_t s = tid; s < ns; s += NT) as[s] *= x[cs[s]];
+    if (__syncthreads_or(!got)) return true;
+    for (int32_t k = tid; k < nr; k += NT) {
       double acc = 0.0;
-      for (int32_t s = rs + gl; s < re; s += G) acc += as[s] * x[cs[s]];
-      acc = group_sum<G>(acc);
-      if (valid && gl == 0) node(tb.r0 + lr, dg[lr], acc);
+      for (int32_t s = rp[k] - tb.s0; s < rp[k + 1] - tb.s0; ++s) acc += as[s];
+      node(tb.r0 + k, dg[k], acc);
     }
+    return false;
   };
 
   const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
@@ -887,13 +978,13 @@ std::mutex g_occ_mu;
 std::unordered_map<const void *, int> g_occ;
 
 template <class K>
-int resident_blocks(K kernel, size_t smem) {
+int resident_blocks(K kernel, size_t smem, int threads) {
   std::lock_guard<std::mutex> lk(g_occ_mu);
   auto it = g_occ.find(reinterpret_cast<const void *>(kernel));
   if (it != g_occ.end()) return it->second;
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   int bps = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kBlock, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, threads, smem);
   bps = std::max(bps, 1);
   g_occ[reinterpret_cast<const void *>(kernel)] = bps;
   return bps;
@@ -902,28 +993,34 @@ int resident_blocks(K kernel, size_t smem) {
 // Persistent grid: one wave of resident CTAs (a multiple of the SM count),
 // or fewer when there are fewer tiles.
 template <class K>
-int tile_grid(K kernel, size_t smem, int32_t ntiles) {
-  const int64_t cap = static_cast<int64_t>(num_sms()) * resident_blocks(kernel, smem);
+int tile_grid(K kernel, size_t smem, int32_t ntiles, int threads) {
+  const int64_t cap = static_cast<int64_t>(num_sms()) * resident_blocks(kernel, smem, threads);
   return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ntiles, cap)));
 }
 
-#define GABP_TILED(group, KERNEL_T, SMEM, NT, ...)                                  \
-  do {                                                                              \
-    switch (group) {                                                                \
-      case 2: { auto k = KERNEL_T(2); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break;   \
-      case 4: { auto k = KERNEL_T(4); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break;   \
-      case 8: { auto k = KERNEL_T(8); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break;   \
-      case 16: { auto k = KERNEL_T(16); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break; \
-      default: { auto k = KERNEL_T(32); k<<<tile_grid(k, SMEM, NT), kBlock, SMEM, st>>>(__VA_ARGS__); } break; \
-    }                                                                               \
-  } while (0)
+template <class K, class... Args>
+void launch_tiled(K kernel, size_t smem, int32_t ntiles, int threads, cudaStream_t st,
+                  Args... args) {
+  kernel<<<tile_grid(kernel, smem, ntiles, threads), threads, smem, st>>>(args...);
+}
 
-#define K64(G) sweep64_kernel<G>
-#define K32F(G) sweep32_kernel<G, float>
-#define K32H(G) sweep32_kernel<G, __nv_bfloat16>
-#define KMF(G) mean_kernel<G, float>
-#define KMH(G) mean_kernel<G, __nv_bfloat16>
-#define KRES(G) residual64_kernel<G>
+template <int G>
+void launch64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  launch_tiled(sweep64_kernel<G>, 2 * Layout64::bytes, g.ntiles_small, kBlock, st, g.view(), B,
+               ctl, red);
+}
+
+int launch_residual(const Graph &g, cudaStream_t st, double *r_out, Ctl *ctl, DevScalars *red,
+                    int kind) {
+  launch_tiled(residual64_kernel, 2 * LayoutRes::bytes, g.ntiles_big, kTileBlock, st, g.view(),
+               r_out, ctl, red, kind);
+  return 1;
+}
+
+template <int G>
+void prepare_group() {
+  resident_blocks(sweep64_kernel<G>, 2 * Layout64::bytes, kBlock);
+}
 
 }  // namespace
 
@@ -933,34 +1030,34 @@ int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars
 }
 
 int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
-  const size_t smem = 2 * Layout64::bytes;
-  GABP_TILED(g.group, K64, smem, g.ntiles_small, g.view(), B, ctl, red);
+  switch (g.group) {
+    case 2: launch64<2>(g, st, B, ctl, red); break;
+    case 4: launch64<4>(g, st, B, ctl, red); break;
+    case 8: launch64<8>(g, st, B, ctl, red); break;
+    case 16: launch64<16>(g, st, B, ctl, red); break;
+    default: launch64<32>(g, st, B, ctl, red); break;
+  }
   return 1;
 }
 
 int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                    bool bf16) {
   const size_t smem = 2 * Layout32::bytes;
-  if (bf16) GABP_TILED(g.group, K32H, smem, g.ntiles_big, g.view(), B, ctl, red);
-  else GABP_TILED(g.group, K32F, smem, g.ntiles_big, g.view(), B, ctl, red);
+  if (bf16)
+    launch_tiled(sweep32_kernel<__nv_bfloat16>, smem, g.ntiles_big, kTileBlock, st, g.view(), B,
+                 ctl, red);
+  else
+    launch_tiled(sweep32_kernel<float>, smem, g.ntiles_big, kTileBlock, st, g.view(), B, ctl, red);
   return 1;
 }
 
 int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16) {
-  if (bf16) {
-    const size_t smem = 2 * LayoutMean<__nv_bfloat16>::bytes;
-    GABP_TILED(g.group, KMH, smem, g.ntiles_big, g.view(), B, ctl, red);
-  } else {
-    const size_t smem = 2 * LayoutMean<float>::bytes;
-    GABP_TILED(g.group, KMF, smem, g.ntiles_big, g.view(), B, ctl, red);
-  }
-  return 1;
-}
-
-static int launch_residual(const Graph &g, cudaStream_t st, double *r_out, Ctl *ctl,
-                           DevScalars *red, int kind) {
-  const size_t smem = 2 * LayoutRes::bytes;
-  GABP_TILED(g.group, KRES, smem, g.ntiles_big, g.view(), r_out, ctl, red, kind);
+  if (bf16)
+    launch_tiled(mean_kernel<__nv_bfloat16>, 2 * LayoutMean<__nv_bfloat16>::bytes, g.ntiles_big,
+                 kTileBlock, st, g.view(), B, ctl, red);
+  else
+    launch_tiled(mean_kernel<float>, 2 * LayoutMean<float>::bytes, g.ntiles_big, kTileBlock, st,
+                 g.view(), B, ctl, red);
   return 1;
 }
 
@@ -974,29 +1071,24 @@ int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScala
   return 1 + launch_residual(g, st, B.r64, ctl, red, CK_REFINE);
 }
 
-// Sets the shared-memory limits and caches the occupancy of every kernel
-// the handle can launch (done at create time, before any graph is recorded).
-template <int G>
-void prepare_group(bool bf16) {
-  resident_blocks(sweep64_kernel<G>, 2 * Layout64::bytes);
-  resident_blocks(residual64_kernel<G>, 2 * LayoutRes::bytes);
-  if (bf16) {
-    resident_blocks(sweep32_kernel<G, __nv_bfloat16>, 2 * Layout32::bytes);
-    resident_blocks(mean_kernel<G, __nv_bfloat16>, 2 * LayoutMean<__nv_bfloat16>::bytes);
-  } else {
-    resident_blocks(sweep32_kernel<G, float>, 2 * Layout32::bytes);
-    resident_blocks(mean_kernel<G, float>, 2 * LayoutMean<float>::bytes);
-  }
-}
-
+// Sets the shared-memory limits and caches the occupancy of every kernel the
+// handle can launch (done at create time, before any graph is recorded).
 void prepare_kernels(int group, bool bf16) {
   num_sms();
   switch (group) {
-    case 2: prepare_group<2>(bf16); break;
-    case 4: prepare_group<4>(bf16); break;
-    case 8: prepare_group<8>(bf16); break;
-    case 16: prepare_group<16>(bf16); break;
-    default: prepare_group<32>(bf16); break;
+    case 2: prepare_group<2>(); break;
+    case 4: prepare_group<4>(); break;
+    case 8: prepare_group<8>(); break;
+    case 16: prepare_group<16>(); break;
+    default: prepare_group<32>(); break;
+  }
+  resident_blocks(residual64_kernel, 2 * LayoutRes::bytes, kTileBlock);
+  if (bf16) {
+    resident_blocks(sweep32_kernel<__nv_bfloat16>, 2 * Layout32::bytes, kTileBlock);
+    resident_blocks(mean_kernel<__nv_bfloat16>, 2 * LayoutMean<__nv_bfloat16>::bytes, kTileBlock);
+  } else {
+    resident_blocks(sweep32_kernel<float>, 2 * Layout32::bytes, kTileBlock);
+    resident_blocks(mean_kernel<float>, 2 * LayoutMean<float>::bytes, kTileBlock);
   }
 }
 

@@ -105,6 +105,7 @@ void ensure32(gabp_handle h) {
   ensure(&B.invP32, n);
   ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
   ensure(&B.r64, n);
+  ensure(&B.rhs32, n);
   h->have32 = true;
 }
 
@@ -320,7 +321,7 @@ void release(gabp_handle h) {
   cudaFree(B.m64[0]); cudaFree(B.m64[1]);
   cudaFree(B.m32[0]); cudaFree(B.m32[1]); cudaFree(B.e[0]); cudaFree(B.e[1]);
   cudaFree(B.c32); cudaFree(B.invP32); cudaFree(B.mon32[0]); cudaFree(B.mon32[1]);
-  cudaFree(B.r64);
+  cudaFree(B.r64); cudaFree(B.rhs32);
   cudaFree(h->red); cudaFree(h->ctl);
   cudaFree(h->bbuf); cudaFree(h->xbuf);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
