@@ -174,9 +174,14 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
     for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
       for (int32_t sl = g.h_rp[r]; sl < g.h_rp[r + 1]; ++sl)
         lrow[sl] = static_cast<uint16_t>(r - tb[t].x);
+  std::vector<uint8_t> heavy(tb.size() - 1, 0);
+  for (size_t t = 0; t + 1 < tb.size(); ++t)
+    for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
+      if (g.h_rp[r + 1] - g.h_rp[r] > kHeavyDegree) heavy[t] = 1;
   cudaError_t ce = upload(&g.tiles_big, tb.data(), tb.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.tiles_small, ts.data(), ts.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.lrow_big, lrow.data(), lrow.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.heavy_big, heavy.data(), heavy.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.rp, g.h_rp.data(), g.h_rp.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.col, g.h_col.data(), g.h_col.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.rev, g.h_rev.data(), g.h_rev.size(), st);
@@ -197,9 +202,10 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
 }
 
 void free_graph(Graph &g) {
-  cudaFree(g.tiles_big); cudaFree(g.tiles_small); cudaFree(g.lrow_big);
+  cudaFree(g.tiles_big); cudaFree(g.tiles_small); cudaFree(g.lrow_big); cudaFree(g.heavy_big);
   g.tiles_big = g.tiles_small = nullptr;
   g.lrow_big = nullptr;
+  g.heavy_big = nullptr;
   cudaFree(g.rp); cudaFree(g.col); cudaFree(g.rev);
   cudaFree(g.a64); cudaFree(g.a32); cudaFree(g.diag64); cudaFree(g.diag32);
   g.rp = g.col = g.rev = nullptr;

@@ -109,6 +109,7 @@ struct GraphView {
   const float *a32, *diag32;
   const int2 *tiles_big, *tiles_small;
   const uint16_t *lrow_big;     // tile-local row id of every slot (big tiles)
+  const uint8_t *heavy_big;     // 1 if the big tile holds a row of degree > kHeavyDegree
   int32_t ntiles_big, ntiles_small;
   int32_t n;
 };
@@ -125,13 +126,14 @@ struct Graph {
   float *a32 = nullptr, *diag32 = nullptr;
   int2 *tiles_big = nullptr, *tiles_small = nullptr;
   uint16_t *lrow_big = nullptr;
+  uint8_t *heavy_big = nullptr;
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
   int max_degree = 0;
 
   GraphView view() const {
-    return GraphView{rp,        rev,         col,      a64,        diag64,       a32, diag32,
-                     tiles_big, tiles_small, lrow_big, ntiles_big, ntiles_small, n};
+    return GraphView{rp,          rev,      col,       a64,        diag64,       a32, diag32, tiles_big,
+                     tiles_small, lrow_big, heavy_big, ntiles_big, ntiles_small, n};
   }
 };
 
@@ -147,6 +149,11 @@ int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScala
 void prepare_kernels(int group, bool bf16);
 void tile_sizes(int *big_slots, int *big_rows, int *small_slots, int *small_rows);
 double bits_to_double(unsigned long long u);
+
+// Rows of degree above this make a tile "heavy": the FP32 sweeps and the
+// residual then spread the tile's slots over the threads instead of giving
+// each thread a row.
+constexpr int kHeavyDegree = 64;
 
 // Extra elements allocated past the end of every array the kernels stage
 // into shared memory: the bulk copies round their ends up to 16 bytes.

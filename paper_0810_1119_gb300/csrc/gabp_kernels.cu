@@ -331,9 +331,9 @@ __global__ void __launch_bounds__(kBlock) init_kernel(int32_t n, double *__restr
 // memory.  Every wait is bounded; a wait that gives up sets `timeout` in the
 // reductions (the controller then stops the solve with GABP_ERR_TIMEOUT).
 // ---------------------------------------------------------------------------
-constexpr int kTileSlotsBig = 2048, kTileRowsBig = 512;     // FP32 sweeps, residual
+constexpr int kTileSlotsBig = 1024, kTileRowsBig = 256;     // FP32 sweeps, residual
 constexpr int kTileSlotsSmall = 1024, kTileRowsSmall = 256; // FP64 sweep
-constexpr int kTileBlock = 512;                             // threads of the slot-parallel kernels
+constexpr int kTileBlock = 128;                             // threads of the FP32 / residual tile kernels
 constexpr int kNoRow = 0xFFFF;                              // key of lanes past the tile's end
 constexpr int kWaitLimit = 1 << 22;                         // try_wait polls before giving up
 
@@ -380,6 +380,42 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+// L2 eviction policies (createpolicy): the once-per-sweep streams (A, c, rev,
+// row pointers) are loaded evict-first so that the message buffers, which are
+// read back on the next sweep, stay resident in the 126 MB L2.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uint32_t bytes,
+                                              uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+      : "memory");
+}
+// Scattered message stores, kept in L2 (evict-last).
+__device__ __forceinline__ void st_keep(float *p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(__nv_bfloat16 *p, float v, uint64_t pol) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  const unsigned short u = *reinterpret_cast<const unsigned short *>(&h);
+  asm volatile("st.global.L2::cache_hint.b16 [%0], %1, %2;" ::"l"(p), "h"(u), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(float2 *p, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y),
+               "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -401,6 +437,11 @@ struct Seg {
                               uint32_t bar) {
     const uint32_t b = bytes(first, count);
     if (b) bulk_g2s(dst, base + (first - first % kPer), b, bar);
+  }
+  __device__ static void copy(uint32_t dst, const E *base, int64_t first, int64_t count,
+                              uint32_t bar, uint64_t policy) {
+    const uint32_t b = bytes(first, count);
+    if (b) bulk_g2s_hint(dst, base + (first - first % kPer), b, bar, policy);
   }
   // Shared-memory pointer to element `first` of a staged run.
   __device__ static E *at(unsigned char *region_ptr, int64_t first) {
@@ -593,14 +634,15 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 // set pending_freeze, the sweep freezes instead: it stores the coefficient
 // c_ij = -A_ij / (P~_i - P_ji) at slot s of row i, 1/P~_i, and the first
 // mean-only messages eta_ij = c_ij (h~_i - eta_ji).
-// Staged per tile: (P, eta) in, A_ij, rev, local row ids, A_ii, rhs, monitors.
+// Staged per tile: (P, eta) in, A_ij, rev, and row pointers (light tiles) or
+// local row ids (heavy tiles).  Per-row values are read straight from global
+// memory by the thread that owns the row (coalesced).
 // ---------------------------------------------------------------------------
 struct Layout32 {
   static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
   static constexpr uint32_t m = 0, a = m + region(TS, 8), rev = a + region(TS, 4),
-                            lr = rev + region(TS, 4), dg = lr + region(TS, 2),
-                            r = dg + region(TR, 4), mon = r + region(TR, 8),
-                            bytes = mon + region(TR, 8);
+                            lr = rev + region(TS, 4), rp = lr + region(TS, 2),
+                            bytes = rp + region(TR + 1, 4);
 };
 
 template <class T>
@@ -609,8 +651,8 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   using L = Layout32;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ float2 tot[2][L::TR];   // per-row sums of incoming (P, eta), double-buffered
-  __shared__ float rhs_s[L::TR];
+  __shared__ float2 tot[2][L::TR];   // heavy tiles: per-row sums, double-buffered
+  __shared__ float2 nd[L::TR];       // heavy tiles: (A_ii, rhs_i) of the tile's rows
   const int pm = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
   const bool freeze = ctl->pending_freeze != 0;
@@ -621,6 +663,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const float2 *__restrict__ mon_prev = (pmon ? B.mon32[1] : B.mon32[0]);
   float2 *__restrict__ mon_out = (pmon ? B.mon32[0] : B.mon32[1]);
   const int NT = blockDim.x, tid = threadIdx.x;
+  const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
   uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;
   bool brk = false;
   for (int k = tid; k < 2 * L::TR; k += NT) (&tot[0][0])[k] = make_float2(0.f, 0.f);
@@ -629,27 +672,26 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
-    const uint32_t tx = (first ? Seg<double>::bytes(tb.r0, nr)
-                               : Seg<float2>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr) +
-                                     Seg<float>::bytes(tb.r0, nr)) +
-                        Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
-                        Seg<uint16_t>::bytes(tb.s0, ns) + Seg<float>::bytes(tb.r0, nr);
+    const bool heavy = g.heavy_big[t] != 0;
+    const uint32_t tx = (first ? 0 : Seg<float2>::bytes(tb.s0, ns)) +
+                        (heavy ? Seg<uint16_t>::bytes(tb.s0, ns) : Seg<int32_t>::bytes(tb.r0, nr + 1)) +
+                        Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (first) {
-      Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
-    } else {
-      Seg<float2>::copy(base + L::m, min, tb.s0, ns, bar);
-      Seg<float2>::copy(base + L::mon, mon_prev, tb.r0, nr, bar);
-      Seg<float>::copy(base + L::r, B.rhs32, tb.r0, nr, bar);
-    }
-    Seg<float>::copy(base + L::a, g.a32, tb.s0, ns, bar);
-    Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
-    Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar);
-    Seg<float>::copy(base + L::dg, g.diag32, tb.r0, nr, bar);
+    if (!first) Seg<float2>::copy(base + L::m, min, tb.s0, ns, bar, pol_keep);
+    if (heavy) Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
+    else Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
+    Seg<float>::copy(base + L::a, g.a32, tb.s0, ns, bar, pol_stream);
+    Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar, pol_stream);
   };
 
-  auto node = [&](int32_t i, float TP, float Th, float rhs, float2 prev) {
+  // rhs_i = r_i / ||r||: scaled once (FP64) in the first sweep of an inner
+  // solve, kept in FP32 for the rest of it.
+  auto rhs_at = [&](int32_t i) {
+    return first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+  };
+  auto node = [&](int32_t i, float TP, float Th, float rhs) {
+    const float2 prev = first ? make_float2(0.f, 0.f) : mon_prev[i];
     const float di = Th / TP;
     mon_out[i] = make_float2(TP, di);
     mdd = fmax_bits(mdd, di - prev.y);
@@ -666,9 +708,9 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     if (freeze) {
       const float c = -a * inv;
       B.c32[s] = c;
-      st_eta(eta_out + dst, c * (Th - m.y));
+      st_keep(eta_out + dst, c * (Th - m.y), pol_keep);
     } else {
-      mout[dst] = make_float2(-(a * a) * inv, -a * (Th - m.y) * inv);
+      st_keep(mout + dst, make_float2(-(a * a) * inv, -a * (Th - m.y) * inv), pol_keep);
     }
   };
 
@@ -687,26 +729,41 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
         }
       sP = block_sum(sP);
       sH = block_sum(sH);
-      const float TP = g.diag32[i] + sP;
-      const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
-      const float Th = rhs + sH;
-      if (tid == 0) node(i, TP, Th, rhs, first ? make_float2(0.f, 0.f) : mon_prev[i]);
+      const float rhs = rhs_at(i);
+      const float TP = g.diag32[i] + sP, Th = rhs + sH;
+      if (tid == 0) node(i, TP, Th, rhs);
       for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT)
         emit(s, g.a32[s], first ? make_float2(0.f, 0.f) : min[s], g.rev[s], TP, Th);
       return false;
     }
-    float2 *tc = tot[st], *tn = tot[st ^ 1];
     const float2 *ms = Seg<float2>::at(stage + L::m, tb.s0);
     const float *as = Seg<float>::at(stage + L::a, tb.s0);
     const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
+    if (!g.heavy_big[t]) {
+      // light tile: one thread per row does the sums, the node and the sends
+      const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+      if (__syncthreads_or(!got)) return true;
+      for (int32_t k = tid; k < nr; k += NT) {
+        const int32_t i = tb.r0 + k;
+        const float dgi = g.diag32[i], rhs = rhs_at(i);
+        const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
+        float sP = 0.f, sH = 0.f;
+        if (!first)
+          for (int32_t s = rs; s < re; ++s) {
+            sP += ms[s].x;
+            sH += ms[s].y;
+          }
+        const float TP = dgi + sP, Th = rhs + sH;
+        node(i, TP, Th, rhs);
+        for (int32_t s = rs; s < re; ++s)
+          emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], TP, Th);
+      }
+      return false;
+    }
+    // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
+    float2 *tc = tot[st], *tn = tot[st ^ 1];
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
-    const float *dg = Seg<float>::at(stage + L::dg, tb.r0);
-    const double *r64s = Seg<double>::at(stage + L::r, tb.r0);
-    const float *r32s = Seg<float>::at(stage + L::r, tb.r0);
-    const float2 *mp = Seg<float2>::at(stage + L::mon, tb.r0);
-    // phase 1: rhs per row, clear the next tile's sums, segmented sums
-    for (int32_t k = tid; k < nr; k += NT)
-      rhs_s[k] = first ? static_cast<float>(r64s[k] * inv_rn) : r32s[k];
+    for (int32_t k = tid; k < nr; k += NT) nd[k] = make_float2(g.diag32[tb.r0 + k], rhs_at(tb.r0 + k));
     for (int32_t k = tid; k < L::TR; k += NT) tn[k] = make_float2(0.f, 0.f);
     if (!first) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
@@ -722,16 +779,12 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       }
     }
     if (__syncthreads_or(!got)) return true;
-    // phase 2: node work per row, messages per slot
-    for (int32_t k = tid; k < nr; k += NT) {
-      const float TP = dg[k] + tc[k].x, Th = rhs_s[k] + tc[k].y;
-      node(tb.r0 + k, TP, Th, rhs_s[k], first ? make_float2(0.f, 0.f) : mp[k]);
-    }
+    for (int32_t k = tid; k < nr; k += NT)
+      node(tb.r0 + k, nd[k].x + tc[k].x, nd[k].y + tc[k].y, nd[k].y);
     for (int32_t s = tid; s < ns; s += NT) {
       const int k = lrow[s];
-      const float2 tk = tc[k];
-      emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], dg[k] + tk.x,
-           rhs_s[k] + tk.y);
+      emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], nd[k].x + tc[k].x,
+           nd[k].y + tc[k].y);
     }
     return false;
   };
@@ -748,15 +801,14 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 // Mean-only sweep with frozen precisions (storage T = float or bf16, FP32
 // arithmetic): eta_ij = c_ij (h~_i - eta_ji), h~_i = r_i/||r|| + sum_k eta_ki,
 // d_i = h~_i / P~_i.  Records d_i and its change.
-// Staged per tile: eta in, c, rev, local row ids, rhs, 1/P~, monitors.
+// Staged per tile: eta in, c, rev, and row pointers or local row ids.
 // ---------------------------------------------------------------------------
 template <class T>
 struct LayoutMean {
   static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
   static constexpr uint32_t e = 0, c = e + region(TS, sizeof(T)), rev = c + region(TS, 4),
-                            lr = rev + region(TS, 4), r = lr + region(TS, 2),
-                            ip = r + region(TR, 8), mon = ip + region(TR, 4),
-                            bytes = mon + region(TR, 8);
+                            lr = rev + region(TS, 4), rp = lr + region(TS, 2),
+                            bytes = rp + region(TR + 1, 4);
 };
 
 template <class T>
@@ -765,8 +817,8 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   using L = LayoutMean<T>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
-  __shared__ float tot[2][L::TR];    // per-row sums of incoming eta, double-buffered
-  __shared__ float rhs_s[L::TR];
+  __shared__ float tot[2][L::TR];    // heavy tiles: per-row sums, double-buffered
+  __shared__ float rhs_s[L::TR];     // heavy tiles: rhs of the tile's rows
   const int pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
   const double inv_rn = ctl->inv_rn;
@@ -775,6 +827,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const float2 *__restrict__ mon_prev = (pmon ? B.mon32[1] : B.mon32[0]);
   float2 *__restrict__ mon_out = (pmon ? B.mon32[0] : B.mon32[1]);
   const int NT = blockDim.x, tid = threadIdx.x;
+  const uint64_t pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
   uint32_t mdd = 0, md = 0;
   for (int k = tid; k < 2 * L::TR; k += NT) (&tot[0][0])[k] = 0.f;
 
@@ -782,28 +835,25 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
-    const uint32_t tx = (first ? Seg<double>::bytes(tb.r0, nr)
-                               : Seg<T>::bytes(tb.s0, ns) + Seg<float2>::bytes(tb.r0, nr) +
-                                     Seg<float>::bytes(tb.r0, nr)) +
-                        Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
-                        Seg<uint16_t>::bytes(tb.s0, ns) + Seg<float>::bytes(tb.r0, nr);
+    const bool heavy = g.heavy_big[t] != 0;
+    const uint32_t tx = (first ? 0 : Seg<T>::bytes(tb.s0, ns)) +
+                        (heavy ? Seg<uint16_t>::bytes(tb.s0, ns) : Seg<int32_t>::bytes(tb.r0, nr + 1)) +
+                        Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (first) {
-      Seg<double>::copy(base + L::r, B.r64, tb.r0, nr, bar);
-    } else {
-      Seg<T>::copy(base + L::e, ein, tb.s0, ns, bar);
-      Seg<float2>::copy(base + L::mon, mon_prev, tb.r0, nr, bar);
-      Seg<float>::copy(base + L::r, B.rhs32, tb.r0, nr, bar);
-    }
-    Seg<float>::copy(base + L::c, B.c32, tb.s0, ns, bar);
-    Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
-    Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar);
-    Seg<float>::copy(base + L::ip, B.invP32, tb.r0, nr, bar);
+    if (!first) Seg<T>::copy(base + L::e, ein, tb.s0, ns, bar, pol_keep);
+    if (heavy) Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
+    else Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
+    Seg<float>::copy(base + L::c, B.c32, tb.s0, ns, bar, pol_stream);
+    Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar, pol_stream);
   };
 
-  auto node = [&](int32_t i, float Th, float invP, float rhs, float prev) {
-    const float di = Th * invP;
+  auto rhs_at = [&](int32_t i) {
+    return first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+  };
+  auto node = [&](int32_t i, float Th, float rhs) {
+    const float prev = first ? 0.f : mon_prev[i].y;
+    const float di = Th * B.invP32[i];
     mon_out[i] = make_float2(0.f, di);
     mdd = fmax_bits(mdd, di - prev);
     md = fmax_bits(md, di);
@@ -820,27 +870,42 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       if (!first)
         for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) sH += ld_eta(ein + s);
       sH = block_sum(sH);
-      const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
-      const float Th = rhs + sH;
-      if (tid == 0) node(i, Th, B.invP32[i], rhs, first ? 0.f : mon_prev[i].y);
+      const float rhs = rhs_at(i), Th = rhs + sH;
+      if (tid == 0) node(i, Th, rhs);
       for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) {
         const float e = first ? 0.f : ld_eta(ein + s);
-        st_eta(eout + g.rev[s], B.c32[s] * (Th - e));
+        st_keep(eout + g.rev[s], B.c32[s] * (Th - e), pol_keep);
       }
       return false;
     }
-    float *tc = tot[st], *tn = tot[st ^ 1];
     const T *es = Seg<T>::at(stage + L::e, tb.s0);
     const float *cs = Seg<float>::at(stage + L::c, tb.s0);
     const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
+    if (!g.heavy_big[t]) {
+      // light tile: one thread per row does the sum, the node and the sends
+      const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+      if (__syncthreads_or(!got)) return true;
+      for (int32_t k = tid; k < nr; k += NT) {
+        const int32_t i = tb.r0 + k;
+        const float rhs = rhs_at(i);
+        const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
+        float sH = 0.f;
+        if (!first)
+          for (int32_t s = rs; s < re; ++s) sH += ld_eta(es + s);
+        const float Th = rhs + sH;
+        node(i, Th, rhs);
+        if (first)
+          for (int32_t s = rs; s < re; ++s) st_keep(eout + rv[s], cs[s] * Th, pol_keep);
+        else
+          for (int32_t s = rs; s < re; ++s)
+            st_keep(eout + rv[s], cs[s] * (Th - ld_eta(es + s)), pol_keep);
+      }
+      return false;
+    }
+    // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
+    float *tc = tot[st], *tn = tot[st ^ 1];
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
-    const double *r64s = Seg<double>::at(stage + L::r, tb.r0);
-    const float *r32s = Seg<float>::at(stage + L::r, tb.r0);
-    const float *ip = Seg<float>::at(stage + L::ip, tb.r0);
-    const float2 *mp = Seg<float2>::at(stage + L::mon, tb.r0);
-    // phase 1: rhs per row, clear the next tile's sums, segmented sums
-    for (int32_t k = tid; k < nr; k += NT)
-      rhs_s[k] = first ? static_cast<float>(r64s[k] * inv_rn) : r32s[k];
+    for (int32_t k = tid; k < nr; k += NT) rhs_s[k] = rhs_at(tb.r0 + k);
     for (int32_t k = tid; k < L::TR; k += NT) tn[k] = 0.f;
     if (!first) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
@@ -853,13 +918,11 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       }
     }
     if (__syncthreads_or(!got)) return true;
-    // phase 2: node work per row, messages per slot
-    for (int32_t k = tid; k < nr; k += NT)
-      node(tb.r0 + k, rhs_s[k] + tc[k], ip[k], rhs_s[k], first ? 0.f : mp[k].y);
+    for (int32_t k = tid; k < nr; k += NT) node(tb.r0 + k, rhs_s[k] + tc[k], rhs_s[k]);
     for (int32_t s = tid; s < ns; s += NT) {
       const int k = lrow[s];
       const float e = first ? 0.f : ld_eta(es + s);
-      st_eta(eout + rv[s], cs[s] * (rhs_s[k] + tc[k] - e));
+      st_keep(eout + rv[s], cs[s] * (rhs_s[k] + tc[k] - e), pol_keep);
     }
     return false;
   };
@@ -901,6 +964,7 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
   const double *__restrict__ b = ctl->b;
   const double *__restrict__ x = ctl->x;
   const int NT = blockDim.x, tid = threadIdx.x;
+  const uint64_t pol_stream = policy_evict_first();
   unsigned long long mr = 0;
 
   auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
@@ -911,10 +975,10 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
                         Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    Seg<double>::copy(base + L::a, g.a64, tb.s0, ns, bar);
-    Seg<int32_t>::copy(base + L::col, g.col, tb.s0, ns, bar);
-    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
-    Seg<double>::copy(base + L::dg, g.diag64, tb.r0, nr, bar);
+    Seg<double>::copy(base + L::a, g.a64, tb.s0, ns, bar, pol_stream);
+    Seg<int32_t>::copy(base + L::col, g.col, tb.s0, ns, bar, pol_stream);
+    Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
+    Seg<double>::copy(base + L::dg, g.diag64, tb.r0, nr, bar, pol_stream);
   };
 
   auto node = [&](int32_t i, double dgi, double acc) {
@@ -938,6 +1002,26 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
     const int32_t *cs = Seg<int32_t>::at(stage + L::col, tb.s0);
     const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
     const double *dg = Seg<double>::at(stage + L::dg, tb.r0);
+    if (!g.heavy_big[t]) {
+      // light tile: one thread per row, gathers unrolled for memory parallelism
+      if (__syncthreads_or(!got)) return true;
+      for (int32_t k = tid; k < nr; k += NT) {
+        const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
+        double acc = 0.0;
+        int32_t s = rs;
+        for (; s + 4 <= re; s += 4) {
+          const double x0 = x[cs[s]], x1 = x[cs[s + 1]], x2 = x[cs[s + 2]], x3 = x[cs[s + 3]];
+          acc += as[s] * x0;
+          acc += as[s + 1] * x1;
+          acc += as[s + 2] * x2;
+          acc += as[s + 3] * x3;
+        }
+        for (; s < re; ++s) acc += as[s] * x[cs[s]];
+        node(tb.r0 + k, dg[k], acc);
+      }
+      return false;
+    }
+    // heavy tile: slot-parallel products, then per-row sums
     if (got)
       for (int32_t s = tid; s < ns; s += NT) as[s] *= x[cs[s]];
     if (__syncthreads_or(!got)) return true;
