@@ -156,12 +156,21 @@ gabp_status gabp_solve_host(gabp_handle h, const double *b_host, double *x_host,
 /*
  * Solves A X = B for nrhs right-hand sides at once.  B_dev and X_dev are
  * n x nrhs FP64 device arrays, row-major ("column-interleaved": element
- * (i, k) at i * nrhs + k).  The precision messages do not depend on b
+ * (i, k) at i * nrhs + k).
+ *
+ * Mixed modes (nrhs <= 256): the precision messages do not depend on b
  * (Alg. 2: P_ij involves only A and other precisions), so they are iterated
- * once and shared; the mean messages of all right-hand sides then advance
- * together.  Stops when every column meets the residual rule.  In FP64 mode
- * the columns are solved one after another with gabp_solve's path.
- * *iters receives the sweeps executed.  Errors as gabp_solve.
+ * once (FP32 sweeps on a zero right-hand side) and frozen; then the FP32
+ * mean messages of all columns advance together, stored column-interleaved
+ * (message k of slot s at s * nrhs + k), inside FP64 refinement with a
+ * residual norm and scale per column.  Stops when every column meets the
+ * residual rule (absolute, or relative to that column's ||b_k||_inf).  The
+ * mean messages are FP32 in both mixed modes.
+ * FP64 mode: the columns are solved one after another with gabp_solve's path.
+ *
+ * *iters receives the sweeps executed (precision sweeps plus K-column mean
+ * sweeps in the mixed modes).  Errors as gabp_solve; GABP_ERR_INVALID_ARG
+ * for nrhs < 1, or nrhs > 256 in a mixed mode.
  */
 gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, int32_t nrhs,
                              double tol, int32_t max_iter, int32_t *iters);

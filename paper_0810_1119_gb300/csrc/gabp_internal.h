@@ -55,11 +55,22 @@ enum Phase : int {
   PH_FULL32 = 2,    // FP32 full sweep (freezes when pending_freeze is set)
   PH_MEAN = 3,      // mean-only sweep with frozen precisions
   PH_REFINE = 4,    // x += ||r|| d, r = b - A x
-  PH_COUNT = 5,
-  PH_DONE = 7
+  PH_MEANK = 5,     // mean-only sweep of K right-hand sides at once
+  PH_REFINEK = 6,   // X += ||r_k|| D, R = B - A X for K columns
+  PH_COUNT = 7,
+  PH_DONE = 15
 };
 
-enum CtlMode : int { CTL_ROUNDS = 0, CTL_FP64 = 1, CTL_MIXED = 2 };
+// CTL_PREC converges and freezes the precisions only (zero right-hand
+// side); CTL_MULTI then solves K right-hand sides with them.
+enum CtlMode : int { CTL_ROUNDS = 0, CTL_FP64 = 1, CTL_MIXED = 2, CTL_PREC = 3, CTL_MULTI = 4,
+                     CTL_MODES = 5 };
+
+// Per-column state of a multi right-hand-side solve (device arrays of K).
+struct MultiCols {
+  double *bnorm, *thr, *rn, *inv_rn;
+  unsigned long long *bmax, *rmax;   // reductions (bit patterns of maxima)
+};
 
 struct Ctl {
   // ---- set by the host before a solve ----
@@ -85,7 +96,10 @@ struct Ctl {
   double bnorm, thr, rn, inv_rn, residual;
   int status, done;
   unsigned int blocks_done;     // last-block detection counter
-  int pad;
+  int K;                        // CTL_MULTI: right-hand sides
+  const double *Bm;             // CTL_MULTI: n x K right-hand sides (row-major)
+  double *Xm;                   // CTL_MULTI: n x K solutions (row-major)
+  MultiCols cols;               // CTL_MULTI: per-column state
 };
 
 // Device buffers of a handle, passed to the kernels by value.
@@ -98,6 +112,11 @@ struct Buffers {
   float2 *mon32[2];         // (P~_i, d_i) of the last two sweeps
   double *r64;              // FP64 residual
   float *rhs32;             // r_i / ||r|| of the current inner solve
+  // multi right-hand sides (K columns, row-major n x K / E x K)
+  float *eK[2];             // mean messages of all columns
+  float *dK;                // d of the last sweep
+  float *rhsK;              // scaled right-hand sides of the inner solve
+  double *rK;               // FP64 residuals
 };
 
 // Row tiles: tiles[t] = (first row, first slot) of tile t, tiles[ntiles] =
@@ -146,6 +165,9 @@ int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScal
 int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
 int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
 int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_init_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
+int launch_mean_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
+int launch_refine_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
 void prepare_kernels(int group, bool bf16);
 void tile_sizes(int *big_slots, int *big_rows, int *small_slots, int *small_rows);
 double bits_to_double(unsigned long long u);
@@ -184,9 +206,12 @@ struct gabp_s {
   double *bbuf = nullptr, *xbuf = nullptr;  // device staging for gabp_solve_host
 
   // one instantiated solve graph per control mode
-  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
-  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-  cudaGraphConditionalHandle cond[3][2] = {};   // (WHILE, SWITCH) handles per mode
+  cudaGraphExec_t exec[gabp::CTL_MODES] = {};
+  cudaGraph_t graph[gabp::CTL_MODES] = {};
+  cudaGraphConditionalHandle cond[gabp::CTL_MODES][2] = {};   // (WHILE, SWITCH) per mode
+  int graph_K = 0;                     // K the CTL_MULTI graph was recorded for
+  size_t capK = 0;                     // columns the multi buffers hold
+  gabp::MultiCols cols{};              // device per-column arrays (capK each)
   cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
 
   // profiling (gabp_options.profile): pairs of events around kernels

@@ -154,7 +154,8 @@ __device__ __forceinline__ void st_eta(__nv_bfloat16 *p, float v) { *p = __float
 // ---------------------------------------------------------------------------
 // Controller (one thread of the last block of a controlling launch).
 // ---------------------------------------------------------------------------
-enum CtrlKind { CK_INIT = 1, CK_SWEEP64, CK_CHECK64, CK_SWEEP32, CK_MEAN, CK_REFINE };
+enum CtrlKind { CK_INIT = 1, CK_SWEEP64, CK_CHECK64, CK_SWEEP32, CK_MEAN, CK_REFINE, CK_INITK,
+                CK_MEANK, CK_REFINEK };
 
 __device__ void finish(Ctl &c, int status) {
   c.status = status;
@@ -185,6 +186,12 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (c.mode == CTL_FP64) {
         c.phase = PH_FULL64;
         c.write_x = (c.check_every <= 1) || (c.max_iter <= 1);
+      } else if (c.mode == CTL_PREC) {
+        // precisions only: zero right-hand side, unit scale
+        c.rn = 1.0;
+        c.inv_rn = 1.0;
+        c.outer = 1;
+        c.phase = PH_FULL32;
       } else {
         c.rn = c.bnorm;
         if (c.rn < c.thr || c.bnorm == 0.0) { finish(c, GABP_OK); break; }
@@ -244,6 +251,12 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
         c.sweeps_mean++;
         c.par_e ^= 1;
       }
+      if (c.mode == CTL_PREC && c.frozen) {
+        c.sweeps++;
+        if (r->breakdown) finish(c, GABP_ERR_BREAKDOWN);
+        else finish(c, GABP_OK);
+        break;
+      }
       c.par_mon ^= 1;
       c.first = 0;
       c.sweeps++;
@@ -271,6 +284,73 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
           c.frozen && c.k >= 3 && (err_d < c.inner_tol || (c.stall >= 2 && dd < 1e-4));
       if (inner_done || c.sweeps >= c.max_iter) c.phase = PH_REFINE;
       else c.phase = c.frozen ? PH_MEAN : PH_FULL32;
+      break;
+    }
+    case CK_INITK: {
+      // per-column ||b_k||, thresholds and scales
+      double worst = 0.0;
+      bool all_done = true, bad = false;
+      for (int k = 0; k < c.K; ++k) {
+        const double bn = dv(c.cols.bmax[k]);
+        c.cols.bmax[k] = 0;
+        c.cols.bnorm[k] = bn;
+        c.cols.thr[k] = c.rel ? c.tol * bn : c.tol;
+        c.cols.rn[k] = bn;
+        c.cols.inv_rn[k] = bn > 0.0 ? 1.0 / bn : 0.0;
+        bad |= !isfinite(bn);
+        all_done &= bn < c.cols.thr[k] || bn == 0.0;
+        worst = fmax(worst, bn);
+      }
+      c.bnorm = worst;
+      c.residual = worst;
+      if (bad) { finish(c, GABP_ERR_INVALID_ARG); break; }
+      if (all_done) { finish(c, GABP_OK); break; }
+      c.outer = 1;
+      c.first = 1;
+      c.phase = PH_MEANK;
+      break;
+    }
+    case CK_MEANK: {
+      c.sweeps_mean++;
+      c.par_e ^= 1;
+      c.first = 0;
+      c.sweeps++;
+      c.k++;
+      const double mx = dv(r->max_x), mdx = dv(r->max_dx);
+      r->max_x = 0; r->max_dx = 0;
+      const double dd = mdx / fmax(mx, DBL_MIN);
+      if (!isfinite(dd)) { finish(c, GABP_ERR_DIVERGED); break; }
+      const double rho_d = dd / c.prev_dd;
+      const double err_d = dd == 0.0 ? 0.0 : (rho_d < 1.0 ? dd * rho_d / (1.0 - rho_d) : INFINITY);
+      c.stall = rho_d >= 1.0 ? c.stall + 1 : 0;
+      c.prev_dd = dd;
+      const bool inner_done = c.k >= 3 && (err_d < c.inner_tol || (c.stall >= 2 && dd < 1e-4));
+      c.phase = (inner_done || c.sweeps >= c.max_iter) ? PH_REFINEK : PH_MEANK;
+      break;
+    }
+    case CK_REFINEK: {
+      c.checks++;
+      double worst = 0.0;
+      bool all_done = true, bad = false;
+      for (int k = 0; k < c.K; ++k) {
+        const double rn = dv(c.cols.rmax[k]);
+        c.cols.rmax[k] = 0;
+        c.cols.rn[k] = rn;
+        c.cols.inv_rn[k] = rn > 0.0 ? 1.0 / rn : 0.0;
+        all_done &= rn < c.cols.thr[k];
+        bad |= diverged(rn, c.cols.bnorm[k]);
+        worst = fmax(worst, rn);
+      }
+      c.residual = worst;
+      if (all_done) { finish(c, GABP_OK); break; }
+      if (bad) { finish(c, GABP_ERR_DIVERGED); break; }
+      if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
+      c.outer++;
+      c.k = 0;
+      c.stall = 0;
+      c.prev_dd = INFINITY;
+      c.first = 1;
+      c.phase = PH_MEANK;
       break;
     }
   }
@@ -310,10 +390,11 @@ __global__ void __launch_bounds__(kBlock) init_kernel(int32_t n, double *__restr
                                                       Ctl *ctl, DevScalars *red) {
   const double *b = ctl->b;
   double *x = ctl->x;
-  const bool mixed = ctl->mode == CTL_MIXED;
+  const bool mixed = ctl->mode == CTL_MIXED, prec = ctl->mode == CTL_PREC;
   unsigned long long m = 0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (prec) { r64[i] = 0.0; continue; }
     const double bi = b[i];
     m = umax(m, bits(fabs(bi)));
     if (mixed) { x[i] = 0.0; r64[i] = bi; }
@@ -1039,6 +1120,181 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
   last_block_control(ctl, red, kind);
 }
 
+// ---------------------------------------------------------------------------
+// K right-hand sides at once (frozen precisions, FP32 mean messages, FP64
+// refinement).  Mean messages are stored column-interleaved: message k of
+// slot s at s * K + k, so the K messages of a slot are one contiguous run.
+// One warp per row; lane l handles columns l, l + 32, ... (NC per lane), so
+// every message read and every reverse-slot write moves K contiguous values.
+// ---------------------------------------------------------------------------
+// Per-column maxima of a block, then one atomicMax per column and block.
+template <int NC>
+__device__ void column_max_commit(const unsigned long long (&m)[NC], unsigned long long *dst,
+                                  int K, unsigned long long *sm) {
+  const int lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) sm[k] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int c = lane + 32 * j;
+    if (c < K && m[j]) atomicMax(&sm[c], m[j]);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x)
+    if (sm[k]) atomicMax(&dst[k], sm[k]);
+}
+
+// X = 0, R = B and the per-column max |B|.
+template <int NC>
+__global__ void __launch_bounds__(kBlock)
+init_multi_kernel(int32_t n, Buffers B, Ctl *ctl, DevScalars *red, int K) {
+  __shared__ unsigned long long sm[32 * NC];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const double *Bm = ctl->Bm;
+  double *X = ctl->Xm;
+  unsigned long long m[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) m[j] = 0;
+  for (int64_t i = warp; i < n; i += nwarps) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int c = lane + 32 * j;
+      if (c >= K) continue;
+      const int64_t idx = i * K + c;
+      const double bv = Bm[idx];
+      X[idx] = 0.0;
+      B.rK[idx] = bv;
+      m[j] = umax(m[j], bits(fabs(bv)));
+    }
+  }
+  column_max_commit<NC>(m, ctl->cols.bmax, K, sm);
+  last_block_control(ctl, red, CK_INITK);
+}
+
+// eta_ij^(k) = c_ij (h~_i^(k) - eta_ji^(k)),  h~_i^(k) = r_i^(k)/||r^(k)|| + sum eta_ki^(k)
+template <int NC>
+__global__ void __launch_bounds__(kBlock)
+mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const int pe = ctl->par_e;
+  const bool first = ctl->first != 0;
+  const float *__restrict__ ein = pe ? B.eK[1] : B.eK[0];
+  float *__restrict__ eout = pe ? B.eK[0] : B.eK[1];
+  double irn[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) {
+    const int c = lane + 32 * j;
+    irn[j] = (first && c < K) ? ctl->cols.inv_rn[c] : 0.0;
+  }
+  uint32_t mdd = 0, md = 0;
+  for (int64_t i = warp; i < g.n; i += nwarps) {
+    const int32_t rs = g.rp[i], re = g.rp[i + 1];
+    float th[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int c = lane + 32 * j;
+      th[j] = 0.f;
+      if (c >= K) continue;
+      const int64_t idx = i * K + c;
+      if (first) {
+        th[j] = static_cast<float>(B.rK[idx] * irn[j]);
+        B.rhsK[idx] = th[j];
+      } else {
+        th[j] = B.rhsK[idx];
+      }
+    }
+    if (!first)
+      for (int32_t s = rs; s < re; ++s) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          const int c = lane + 32 * j;
+          if (c < K) th[j] += ein[static_cast<int64_t>(s) * K + c];
+        }
+      }
+    const float ip = B.invP32[i];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int c = lane + 32 * j;
+      if (c >= K) continue;
+      const int64_t idx = i * K + c;
+      const float d = th[j] * ip;
+      const float prev = first ? 0.f : B.dK[idx];
+      B.dK[idx] = d;
+      mdd = fmax_bits(mdd, d - prev);
+      md = fmax_bits(md, d);
+    }
+    for (int32_t s = rs; s < re; ++s) {
+      const float cs = B.c32[s];
+      const int64_t dst = static_cast<int64_t>(g.rev[s]) * K;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int c = lane + 32 * j;
+        if (c >= K) continue;
+        const float e = first ? 0.f : ein[static_cast<int64_t>(s) * K + c];
+        eout[dst + c] = cs * (th[j] - e);
+      }
+    }
+  }
+  block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
+  last_block_control(ctl, red, CK_MEANK);
+}
+
+// X += ||r_k|| D (FP64).
+__global__ void __launch_bounds__(kBlock) refine_multi_update_kernel(int64_t total, Buffers B,
+                                                                     Ctl *ctl, int K) {
+  double *X = ctl->Xm;
+  const double *rn = ctl->cols.rn;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    X[idx] += static_cast<double>(B.dK[idx]) * rn[idx % K];
+}
+
+// R = B - A X (FP64) with per-column max |R|.
+template <int NC>
+__global__ void __launch_bounds__(kBlock)
+residual_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
+  __shared__ unsigned long long sm[32 * NC];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const double *__restrict__ Bm = ctl->Bm;
+  const double *__restrict__ X = ctl->Xm;
+  unsigned long long m[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) m[j] = 0;
+  for (int64_t i = warp; i < g.n; i += nwarps) {
+    const int32_t rs = g.rp[i], re = g.rp[i + 1];
+    double acc[NC];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = 0.0;
+    for (int32_t s = rs; s < re; ++s) {
+      const double a = g.a64[s];
+      const int64_t xc = static_cast<int64_t>(g.col[s]) * K;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int c = lane + 32 * j;
+        if (c < K) acc[j] = fma(a, X[xc + c], acc[j]);
+      }
+    }
+    const double dg = g.diag64[i];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      const int c = lane + 32 * j;
+      if (c >= K) continue;
+      const int64_t idx = i * K + c;
+      const double r = Bm[idx] - (dg * X[idx] + acc[j]);
+      B.rK[idx] = r;
+      m[j] = umax(m[j], bits(fabs(r)));
+    }
+  }
+  column_max_commit<NC>(m, ctl->cols.rmax, K, sm);
+  last_block_control(ctl, red, CK_REFINEK);
+}
+
 int g_num_sms = 0;
 
 int num_sms() {
@@ -1153,6 +1409,40 @@ int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScal
 int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
   refine_update_kernel<<<flat_grid(g.n), kBlock, 0, st>>>(g.n, B, ctl);
   return 1 + launch_residual(g, st, B.r64, ctl, red, CK_REFINE);
+}
+
+// Columns per lane of the multi right-hand-side kernels: ceil(K / 32) rounded
+// up to 1, 2, 4 or 8 (K <= 256).
+#define GABP_NC_DISPATCH(K, CALL)                  \
+  do {                                             \
+    const int nc_ = ((K) + 31) / 32;               \
+    if (nc_ <= 1) { constexpr int NC = 1; CALL; }  \
+    else if (nc_ <= 2) { constexpr int NC = 2; CALL; } \
+    else if (nc_ <= 4) { constexpr int NC = 4; CALL; } \
+    else { constexpr int NC = 8; CALL; }           \
+  } while (0)
+
+int launch_init_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K) {
+  const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(g.n) * 32 + kBlock - 1) / kBlock,
+                                                      static_cast<int64_t>(num_sms()) * 8));
+  GABP_NC_DISPATCH(K, (init_multi_kernel<NC><<<std::max(grid, 1), kBlock, 0, st>>>(g.n, B, ctl, red, K)));
+  return 1;
+}
+
+int launch_mean_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K) {
+  const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(g.n) * 32 + kBlock - 1) / kBlock,
+                                                      static_cast<int64_t>(num_sms()) * 8));
+  GABP_NC_DISPATCH(K, (mean_multi_kernel<NC><<<std::max(grid, 1), kBlock, 0, st>>>(g.view(), B, ctl, red, K)));
+  return 1;
+}
+
+int launch_refine_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K) {
+  const int64_t total = static_cast<int64_t>(g.n) * K;
+  refine_multi_update_kernel<<<flat_grid(total), kBlock, 0, st>>>(total, B, ctl, K);
+  const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(g.n) * 32 + kBlock - 1) / kBlock,
+                                                      static_cast<int64_t>(num_sms()) * 8));
+  GABP_NC_DISPATCH(K, (residual_multi_kernel<NC><<<std::max(grid, 1), kBlock, 0, st>>>(g.view(), B, ctl, red, K)));
+  return 2;
 }
 
 // Sets the shared-memory limits and caches the occupancy of every kernel the

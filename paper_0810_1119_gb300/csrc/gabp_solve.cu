@@ -158,15 +158,32 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     case PH_FULL32: return launch_sweep32(g, st, h->buf, h->ctl, h->red, is_bf16(h));
     case PH_MEAN: return launch_mean(g, st, h->buf, h->ctl, h->red, is_bf16(h));
     case PH_REFINE: return launch_refine(g, st, h->buf, h->ctl, h->red);
+    case PH_MEANK: return launch_mean_multi(g, st, h->buf, h->ctl, h->red, h->graph_K);
+    case PH_REFINEK: return launch_refine_multi(g, st, h->buf, h->ctl, h->red, h->graph_K);
   }
   return 0;
+}
+
+int launch_mode_init(gabp_handle h, cudaStream_t st, int mode) {
+  if (mode == CTL_MULTI) return launch_init_multi(h->g, st, h->buf, h->ctl, h->red, h->graph_K);
+  return launch_init(h->g, st, h->buf, h->ctl, h->red);
+}
+
+bool phase_used(int mode, int p) {
+  switch (mode) {
+    case CTL_FP64: return p == PH_FULL64 || p == PH_CHECK64;
+    case CTL_MIXED: return p == PH_FULL32 || p == PH_MEAN || p == PH_REFINE;
+    case CTL_PREC: return p == PH_FULL32;
+    case CTL_MULTI: return p == PH_MEANK || p == PH_REFINEK;
+  }
+  return false;
 }
 
 int phase_kind(int phase) {
   switch (phase) {
     case PH_FULL64: case PH_FULL32: return K_FULL;
-    case PH_MEAN: return K_MEAN;
-    case PH_CHECK64: case PH_REFINE: return K_RES;
+    case PH_MEAN: case PH_MEANK: return K_MEAN;
+    case PH_CHECK64: case PH_REFINE: case PH_REFINEK: return K_RES;
   }
   return K_OTHER;
 }
@@ -182,7 +199,7 @@ void build_solve_graph(gabp_handle h, int mode) {
   cudaStream_t cs = h->cap_stream;
 
   CK(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  launch_init(h->g, cs, h->buf, h->ctl, h->red);
+  launch_mode_init(h, cs, mode);
   cudaGraph_t captured;
   CK(cudaStreamEndCapture(cs, &captured));
   size_t nn = 0;
@@ -208,9 +225,7 @@ void build_solve_graph(gabp_handle h, int mode) {
   CK(cudaGraphAddNode(&snode, body, nullptr, nullptr, 0, &sp));
   for (int p = 0; p < PH_COUNT; ++p) {
     cudaGraph_t pb = sp.conditional.phGraph_out[p];
-    const bool used = mode == CTL_FP64 ? (p == PH_FULL64 || p == PH_CHECK64)
-                                       : (p == PH_FULL32 || p == PH_MEAN || p == PH_REFINE);
-    if (!used) {
+    if (!phase_used(mode, p)) {
       cudaGraphNode_t e;
       CK(cudaGraphAddEmptyNode(&e, pb, nullptr, 0));
       continue;
@@ -256,7 +271,7 @@ void finish_stats(gabp_handle h) {
   S.sweeps_total = c.sweeps;
   S.sweeps_full = c.sweeps_full;
   S.sweeps_mean = c.sweeps_mean;
-  S.outer_steps = c.mode == CTL_MIXED ? c.outer : 1;
+  S.outer_steps = (c.mode == CTL_MIXED || c.mode == CTL_MULTI) ? c.outer : 1;
   S.residual_checks = c.checks;
   S.status = c.status;
   S.residual = c.residual;
@@ -265,16 +280,28 @@ void finish_stats(gabp_handle h) {
   S.edges = h->g.E;
 }
 
-gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
-                       int32_t *iters) {
-  const bool mixed = h->opt.precision != GABP_PREC_FP64;
-  const int mode = mixed ? CTL_MIXED : CTL_FP64;
-  if (mixed) ensure32(h); else ensure64(h);
+// Runs one control mode whose control block has been filled in the pinned
+// mirror (init_ctl + mode fields): graph driver or, with profiling, host
+// driver.  Leaves the final control block in the mirror.
+void run_mode(gabp_handle h, int mode, int32_t max_iter) {
   cudaStream_t st = h->stream;
-  h->stats = gabp_stats{};
   const bool host_driver = h->opt.profile != 0;
-  if (!host_driver && !h->exec[mode]) build_solve_graph(h, mode);
-  init_ctl(h, mode, b, x, tol, max_iter, !host_driver);
+  if (!host_driver) {
+    if (mode == CTL_MULTI && h->exec[mode] && h->graph_K != h->ctl_host->K) {
+      cudaGraphExecDestroy(h->exec[mode]);
+      cudaGraphDestroy(h->graph[mode]);
+      h->exec[mode] = nullptr;
+      h->graph[mode] = nullptr;
+    }
+    if (mode == CTL_MULTI) h->graph_K = h->ctl_host->K;
+    if (!h->exec[mode]) build_solve_graph(h, mode);
+    h->ctl_host->in_graph = 1;
+    h->ctl_host->h_while = h->cond[mode][0];
+    h->ctl_host->h_phase = h->cond[mode][1];
+  } else {
+    if (mode == CTL_MULTI) h->graph_K = h->ctl_host->K;
+    h->ctl_host->in_graph = 0;
+  }
   CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
   if (!host_driver) {
@@ -282,10 +309,11 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
     CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const Ctl &c = *h->ctl_host;
-    h->stats.kernel_launches = 1 + static_cast<int64_t>(c.sweeps) +
-                               static_cast<int64_t>(c.checks) * (mixed ? 2 : 1);
+    const int per_check = (mode == CTL_MIXED || mode == CTL_MULTI) ? 2 : 1;
+    h->stats.kernel_launches +=
+        1 + static_cast<int64_t>(c.sweeps) + static_cast<int64_t>(c.checks) * per_check;
   } else {
-    run(h, K_OTHER, [&] { return launch_init(h->g, st, h->buf, h->ctl, h->red); });
+    run(h, K_OTHER, [&] { return launch_mode_init(h, st, mode); });
     const int64_t cap = 4 * static_cast<int64_t>(max_iter) + 128;
     for (int64_t it = 0; it < cap; ++it) {
       CK(cudaGetLastError());
@@ -298,24 +326,91 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
     }
   }
   CK(cudaGetLastError());
-  finish_stats(h);
+}
+
+gabp_status report(gabp_handle h, const char *what) {
   const Ctl &c = *h->ctl_host;
-  if (iters) *iters = c.sweeps;
-  if (!c.done) return fail(h, GABP_ERR_NOT_CONVERGED, "controller did not finish");
+  if (!c.done) return fail(h, GABP_ERR_NOT_CONVERGED, std::string(what) + ": controller did not finish");
   const gabp_status status = static_cast<gabp_status>(c.status);
   if (status != GABP_OK)
-    return fail(h, status, std::string(mixed ? "mixed" : "FP64") + " solve: " +
-                               gabp_status_string(status) + ", residual " +
+    return fail(h, status, std::string(what) + ": " + gabp_status_string(status) + ", residual " +
                                std::to_string(c.residual) + " after " + std::to_string(c.sweeps) +
                                " sweeps");
   return GABP_OK;
 }
 
+gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                       int32_t *iters) {
+  const bool mixed = h->opt.precision != GABP_PREC_FP64;
+  const int mode = mixed ? CTL_MIXED : CTL_FP64;
+  if (mixed) ensure32(h); else ensure64(h);
+  h->stats = gabp_stats{};
+  init_ctl(h, mode, b, x, tol, max_iter, false);
+  run_mode(h, mode, max_iter);
+  finish_stats(h);
+  if (iters) *iters = h->ctl_host->sweeps;
+  return report(h, mixed ? "mixed solve" : "FP64 solve");
+}
+
+void ensure_multi(gabp_handle h, int K) {
+  if (h->capK >= static_cast<size_t>(K)) return;
+  Buffers &B = h->buf;
+  cudaFree(B.eK[0]); cudaFree(B.eK[1]); cudaFree(B.dK); cudaFree(B.rhsK); cudaFree(B.rK);
+  B.eK[0] = B.eK[1] = B.dK = B.rhsK = nullptr;
+  B.rK = nullptr;
+  MultiCols &C = h->cols;
+  cudaFree(C.bnorm); cudaFree(C.thr); cudaFree(C.rn); cudaFree(C.inv_rn);
+  cudaFree(C.bmax); cudaFree(C.rmax);
+  C = MultiCols{};
+  h->capK = 0;
+  const size_t n = h->g.n, E = h->g.E;
+  ensure(&B.eK[0], E * K); ensure(&B.eK[1], E * K);
+  ensure(&B.dK, n * K); ensure(&B.rhsK, n * K); ensure(&B.rK, n * K);
+  ensure(&C.bnorm, K); ensure(&C.thr, K); ensure(&C.rn, K); ensure(&C.inv_rn, K);
+  ensure(&C.bmax, K); ensure(&C.rmax, K);
+  h->capK = K;
+}
+
+// Mixed-mode multi right-hand-side solve: precisions once (CTL_PREC), then
+// all K columns together (CTL_MULTI).
+gabp_status solve_multi_mixed(gabp_handle h, const double *B, double *X, int32_t K, double tol,
+                              int32_t max_iter, int32_t *iters) {
+  ensure32(h);
+  ensure_multi(h, K);
+  h->stats = gabp_stats{};
+  init_ctl(h, CTL_PREC, nullptr, nullptr, tol, max_iter, false);
+  run_mode(h, CTL_PREC, max_iter);
+  const int prec_sweeps = h->ctl_host->sweeps;
+  gabp_status s = report(h, "precision phase");
+  if (s != GABP_OK) {
+    finish_stats(h);
+    if (iters) *iters = prec_sweeps;
+    return s;
+  }
+  init_ctl(h, CTL_MULTI, nullptr, nullptr, tol, std::max(1, max_iter - prec_sweeps), false);
+  Ctl &c = *h->ctl_host;
+  c.K = K;
+  c.Bm = B;
+  c.Xm = X;
+  c.cols = h->cols;
+  c.frozen = 1;
+  run_mode(h, CTL_MULTI, max_iter);
+  finish_stats(h);
+  h->stats.sweeps_full = prec_sweeps;
+  h->stats.sweeps_total = prec_sweeps + h->ctl_host->sweeps;
+  if (iters) *iters = prec_sweeps + h->ctl_host->sweeps;
+  return report(h, "multi right-hand-side solve");
+}
+
 void release(gabp_handle h) {
-  for (int m = 0; m < 3; ++m) {
+  for (int m = 0; m < CTL_MODES; ++m) {
     if (h->exec[m]) cudaGraphExecDestroy(h->exec[m]);
     if (h->graph[m]) cudaGraphDestroy(h->graph[m]);
   }
+  cudaFree(h->buf.eK[0]); cudaFree(h->buf.eK[1]); cudaFree(h->buf.dK);
+  cudaFree(h->buf.rhsK); cudaFree(h->buf.rK);
+  cudaFree(h->cols.bnorm); cudaFree(h->cols.thr); cudaFree(h->cols.rn);
+  cudaFree(h->cols.inv_rn); cudaFree(h->cols.bmax); cudaFree(h->cols.rmax);
   free_graph(h->g);
   Buffers &B = h->buf;
   cudaFree(B.m64[0]); cudaFree(B.m64[1]);
@@ -420,6 +515,10 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
   if (!h) return GABP_ERR_INVALID_ARG;
   if (!B_dev || !X_dev || nrhs < 1 || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: invalid argument");
+  if (h->opt.precision != GABP_PREC_FP64 && nrhs > 256)
+    return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: at most 256 right-hand sides per call");
+  if (h->opt.precision != GABP_PREC_FP64)
+    return guarded(h, [&] { return solve_multi_mixed(h, B_dev, X_dev, nrhs, tol, max_iter, iters); });
   return guarded(h, [&] {
     const int64_t n = h->g.n;
     ensure(&h->bbuf, n);

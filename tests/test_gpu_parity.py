@@ -343,3 +343,43 @@ def test_repeated_solves_reuse_the_graph(G):
         x = xt.cpu().numpy()
         assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# Multi right-hand sides: precisions once, all columns in one mean sweep
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("K", [1, 5, 40, 64, 100, 256])
+def test_multi_rhs_widths(G, K):
+    """K columns at once for every columns-per-lane width (1, 2, 4, 8 per lane);
+    every column meets its own relative residual and matches the oracle."""
+    m = W.er_sdd(3000, 10, 1.05, 40 + K)
+    B = W.normal_rhs(m.n, 41, k=K)
+    B[:, 0] *= 1e-3                      # columns of very different scale
+    s = _solver(G, m, precision=1)
+    Bt = torch.tensor(B, device="cuda")
+    Xt = torch.empty_like(Bt)
+    G.gabp_solve_multi(s.handle, Bt, Xt, 1e-10, 10000)
+    X = Xt.cpu().numpy()
+    st = s.stats()
+    assert st["sweeps_full"] > 0 and st["sweeps_mean"] > 0
+    for k in sorted({0, K // 2, K - 1}):
+        res = oracle.residual_inf(m.row_ptr, m.col, m.val, B[:, k], X[:, k])
+        assert res < 1e-10 * np.abs(B[:, k]).max(), (k, res)
+        assert _rel(X[:, k], _oracle_solution(m, B[:, k])) < 1e-8
+    s.close()
+
+
+def test_multi_rhs_64_columns_dominance_105(G):
+    """The multi right-hand-side workload's structure at reduced size: random
+    SDD matrix, average degree 10, dominance 1.05, 64 columns b ~ N(0,1)."""
+    m = W.er_sdd(50000, 10, 1.05, 3)
+    B = W.normal_rhs(m.n, 4, k=64)
+    s = _solver(G, m, precision=1)
+    Bt = torch.tensor(B, device="cuda")
+    Xt = torch.empty_like(Bt)
+    G.gabp_solve_multi(s.handle, Bt, Xt, 1e-10, 10000)
+    X = Xt.cpu().numpy()
+    worst = max(oracle.residual_inf(m.row_ptr, m.col, m.val, B[:, k], X[:, k]) / np.abs(B[:, k]).max()
+                for k in range(64))
+    assert worst < 1e-10
+    s.close()
