@@ -76,7 +76,10 @@ typedef struct {
   int32_t reserved_i[2];
   double inner_tol;       /* mixed modes: relative accuracy asked of each inner FP32 solve; 0 = 1e-6 */
   void *stream;           /* cudaStream_t used by every call on the handle; NULL = legacy default */
-  double reserved_d[4];
+  double damping;         /* gamma in [0, 1): each new message's information P_ij mu_ij becomes
+                             gamma * previous + (1 - gamma) * new (precisions undamped); a fixed
+                             point is unchanged.  0 = the plain rule of Alg. 2. */
+  double reserved_d[3];
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */
@@ -174,6 +177,45 @@ gabp_status gabp_solve_host(gabp_handle h, const double *b_host, double *x_host,
  */
 gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, int32_t nrhs,
                              double tol, int32_t max_iter, int32_t *iters);
+
+/*
+ * Batched independent systems.  The CSR (host arrays, as for gabp_create)
+ * holds nsys systems along the diagonal: rows sys_row_off_host[s] ..
+ * sys_row_off_host[s+1]-1 belong to system s, and no entry may couple two
+ * systems (GABP_ERR_INVALID_ARG otherwise).  GaBP on a block-diagonal matrix
+ * is GaBP on every block, so one sweep kernel advances all systems at once
+ * (one persistent launch per sweep, one CUDA graph per solve).
+ * gabp_solve on such a handle applies the stop rule to every system: with
+ * the relative rule, each system's ||b_s - A_s x_s||_inf must fall below
+ * tol ||b_s||_inf.  Errors as gabp_create.
+ */
+gabp_status gabp_create_batched(gabp_handle *out, int32_t nsys, const int64_t *sys_row_off_host,
+                                int64_t nnz, const int64_t *row_ptr_host, const int32_t *col_host,
+                                const double *val_host, const gabp_options *opt);
+
+/*
+ * Batched least squares through the symmetric augmented system of Section
+ * VII: for every s, with S_s of shape N_s x K_s (row-major, the matrices
+ * concatenated in S_host) and Psi_s = psi_s I,
+ *     [ I_K   S_s^T  ] [x^_s]   [ 0  ]
+ *     [ S_s  -Psi_s  ] [z_s ] = [ y_s],
+ * whose first K_s unknowns are x^_s = (S_s^T S_s + psi_s I)^{-1} S_s^T y_s
+ * (the MMSE detector of Section VIII-B when psi_s is the noise variance).
+ * The handle is a batched handle over the augmented systems (3 K_s rows
+ * when N_s = 2 K_s).  Requires K_s, N_s >= 1 and psi_s > 0.
+ */
+gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_t *K_host,
+                                    const int32_t *N_host, const double *S_host,
+                                    const double *psi_host, const gabp_options *opt);
+
+/*
+ * Solves every augmented system of a gabp_create_lsq_batched handle:
+ * y_dev = the y_s concatenated (sum N_s FP64 device values), xhat_dev = the
+ * x^_s concatenated (sum K_s values).  The stop rule (per system) is applied
+ * to the augmented systems.  *iters as gabp_solve.
+ */
+gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *xhat_dev, double tol,
+                                   int32_t max_iter, int32_t *iters);
 
 /* Statistics of the last solve on the handle. */
 gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats);

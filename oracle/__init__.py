@@ -67,7 +67,8 @@ def _bind(lib):
     lib.oracle_gabp.restype = ctypes.c_int
     lib.oracle_gabp.argtypes = [ctypes.c_int, ctypes.c_int64, i64p, i32p, f64p, f64p,
                                 ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                f64p, f64p, f64p, f64p, ctypes.POINTER(ctypes.c_int)]
+                                f64p, f64p, f64p, f64p, ctypes.POINTER(ctypes.c_int),
+                                ctypes.c_double]
     lib.oracle_residual_inf.restype = ctypes.c_double
     lib.oracle_residual_inf.argtypes = [ctypes.c_int64, i64p, i32p, f64p, f64p, f64p, f64p]
     lib.oracle_num_threads.restype = ctypes.c_int
@@ -110,7 +111,7 @@ def _csr_arrays(row_ptr, col, val):
 
 
 def gabp(row_ptr, col, val, b, *, variant=BROADCAST, stop=STOP_FIXED, max_rounds=1,
-         tol=0.0, want_messages=False, lib=None):
+         tol=0.0, want_messages=False, lib=None, damping=0.0):
     """Synchronous GaBP from zero messages on the CSR matrix (row_ptr, col, val).
 
     The CSR holds the full symmetric matrix with its diagonal and sorted
@@ -119,6 +120,8 @@ def gabp(row_ptr, col, val, b, *, variant=BROADCAST, stop=STOP_FIXED, max_rounds
     ``want_messages``, ``P`` and ``mu``: the last round's message i -> j at
     the CSR position of entry (i, j) (zero on the diagonal).  In the Jacobi
     variant ``mu`` holds the product P_ij mu_ij, as the proposition carries it.
+    ``damping`` (broadcast variant) blends each new message's P_ij mu_ij
+    with the previous round's: gamma old + (1 - gamma) new.
     """
     row_ptr, col, val = _csr_arrays(row_ptr, col, val)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -133,7 +136,7 @@ def gabp(row_ptr, col, val, b, *, variant=BROADCAST, stop=STOP_FIXED, max_rounds
                              _ptr(val, ctypes.c_double), _ptr(b, ctypes.c_double), stop,
                              int(max_rounds), float(tol), _ptr(x, ctypes.c_double),
                              _ptr(Pi, ctypes.c_double), _ptr(P, ctypes.c_double),
-                             _ptr(mu, ctypes.c_double), ctypes.byref(rounds))
+                             _ptr(mu, ctypes.c_double), ctypes.byref(rounds), float(damping))
     out = {"x": x, "Pi": Pi, "rounds": rounds.value, "status": STATUS[st]}
     if want_messages:
         out["P"], out["mu"] = P, mu

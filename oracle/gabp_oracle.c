@@ -118,7 +118,7 @@ double oracle_residual_inf(int64_t n, const int64_t *row_ptr, const int32_t *col
 static int one_round(int variant, int64_t n, const int64_t *row_ptr, const int32_t *col,
                      const double *val, const double *b, const int64_t *diag_pos,
                      const int64_t *twin, const double *Po, const double *Mo, double *Pn,
-                     double *Mn) {
+                     double *Mn, double gamma) {
   int status = OR_OK;
 #pragma omp parallel for schedule(dynamic, 256) reduction(max : status)
   for (int64_t i = 0; i < n; ++i) {
@@ -141,6 +141,14 @@ static int one_round(int variant, int64_t n, const int64_t *row_ptr, const int32
         if (denom == 0.0 || !isfinite(denom)) { status = OR_BREAKDOWN; }
         Pn[e] = -Aij * Aij / denom;
         Mn[e] = (Pt * mut - Pji * muji) / Aij;
+        if (gamma > 0.0) {
+          /* Damping (the heuristic Section VI-D cites for belief propagation):
+           * the information P_ij mu_ij of the new message is blended with the
+           * previous round's, the precision is not; a fixed point of the
+           * damped rule is a fixed point of the undamped one. */
+          const double eta = gamma * (Po[e] * Mo[e]) + (1.0 - gamma) * (Pn[e] * Mn[e]);
+          Mn[e] = eta / Pn[e];
+        }
       }
     } else if (variant == OR_NAIVE) {
       /* Algorithm 1: every message sums over N(i)\j directly. */
@@ -215,11 +223,12 @@ static void infer(int variant, int64_t n, const int64_t *row_ptr, const double *
  *   Pi[n]      marginal precisions P_i after the last round (may be NULL)
  *   msgP[nnz], msgMu[nnz]   messages of the last round, i->j at entry (i,j)
  *   rounds     rounds executed
+ *   gamma      damping in [0, 1) of the broadcast variant (0 = the plain rule)
  * Returns OR_OK, OR_BAD_INPUT, OR_BREAKDOWN or OR_NOT_CONVERGED.
  */
 int oracle_gabp(int variant, int64_t n, const int64_t *row_ptr, const int32_t *col,
                 const double *val, const double *b, int stop, int max_rounds, double tol,
-                double *x, double *Pi, double *msgP, double *msgMu, int *rounds) {
+                double *x, double *Pi, double *msgP, double *msgMu, int *rounds, double gamma) {
   const int64_t nnz = row_ptr[n];
   int64_t *diag_pos = malloc(sizeof(int64_t) * (size_t)n);
   int64_t *twin = malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
@@ -239,7 +248,7 @@ int oracle_gabp(int variant, int64_t n, const int64_t *row_ptr, const int32_t *c
   infer(variant, n, row_ptr, val, b, diag_pos, twin, P0, M0, x, Pi);
   status = (stop == OR_STOP_FIXED && max_rounds == 0) ? OR_OK : OR_NOT_CONVERGED;
   for (int t = 1; t <= max_rounds; ++t) {
-    int s = one_round(variant, n, row_ptr, col, val, b, diag_pos, twin, P0, M0, P1, M1);
+    int s = one_round(variant, n, row_ptr, col, val, b, diag_pos, twin, P0, M0, P1, M1, gamma);
     double *tp = P0; P0 = P1; P1 = tp;
     double *tm = M0; M0 = M1; M1 = tm;
     *rounds = t;

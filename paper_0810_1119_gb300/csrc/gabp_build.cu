@@ -201,7 +201,43 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
   return GABP_OK;
 }
 
+gabp_status build_systems(Graph &g, int32_t nsys, const int64_t *sys_row_off,
+                          const int64_t *row_ptr, const int32_t *col, cudaStream_t st,
+                          std::string *msg) {
+  if (nsys < 1 || !sys_row_off || sys_row_off[0] != 0 || sys_row_off[nsys] != g.n) {
+    *msg = "system offsets must start at 0 and end at n";
+    return GABP_ERR_INVALID_ARG;
+  }
+  std::vector<int32_t> sys(g.n);
+  for (int32_t s = 0; s < nsys; ++s) {
+    const int64_t r0 = sys_row_off[s], r1 = sys_row_off[s + 1];
+    if (r1 <= r0) { *msg = "every system needs at least one row"; return GABP_ERR_INVALID_ARG; }
+    for (int64_t i = r0; i < r1; ++i) {
+      sys[i] = s;
+      for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+        if (col[e] < r0 || col[e] >= r1) {
+          *msg = "an entry couples two systems (row " + std::to_string(i) + ")";
+          return GABP_ERR_INVALID_ARG;
+        }
+    }
+  }
+  g.nsys = nsys;
+  g.h_sys_row_off.assign(sys_row_off, sys_row_off + nsys + 1);
+  cudaError_t ce = upload(&g.sys_of_row, sys.data(), sys.size(), st);
+  if (ce == cudaSuccess) ce = cudaMalloc(reinterpret_cast<void **>(&g.sys_bmax), sizeof(unsigned long long) * nsys);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(g.sys_bmax, 0, sizeof(unsigned long long) * nsys, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    *msg = std::string("device upload failed: ") + cudaGetErrorString(ce);
+    return ce == cudaErrorMemoryAllocation ? GABP_ERR_OOM : GABP_ERR_CUDA;
+  }
+  return GABP_OK;
+}
+
 void free_graph(Graph &g) {
+  cudaFree(g.sys_of_row); cudaFree(g.sys_bmax);
+  g.sys_of_row = nullptr;
+  g.sys_bmax = nullptr;
   cudaFree(g.tiles_big); cudaFree(g.tiles_small); cudaFree(g.lrow_big); cudaFree(g.heavy_big);
   g.tiles_big = g.tiles_small = nullptr;
   g.lrow_big = nullptr;

@@ -43,6 +43,7 @@ struct DevScalars {
   unsigned long long max_P;       // max_i |P~_i^t|
   unsigned long long max_r;       // max_i |r_i|
   unsigned long long max_b;       // max_i |b_i|
+  unsigned long long max_rrel;    // batched: max_i |r_i| / ||b_sys(i)||_inf
   int breakdown;                  // set when P~_i - P_ji is zero or not finite
   int timeout;                    // set when a bounded wait gave up
   int pad[2];
@@ -83,6 +84,8 @@ struct Ctl {
   int check_every;
   double inner_tol;
   int in_graph;             // 1 = set the graph's conditional handles
+  int batched;              // 1 = independent systems, relative rule per system
+  double damping;           // gamma: eta <- gamma eta_old + (1 - gamma) eta_new
   int rounds_target;        // CTL_ROUNDS: sweeps before the infer-only pass
   unsigned long long h_while, h_phase;
   // ---- state ----
@@ -131,6 +134,9 @@ struct GraphView {
   const uint8_t *heavy_big;     // 1 if the big tile holds a row of degree > kHeavyDegree
   int32_t ntiles_big, ntiles_small;
   int32_t n;
+  // batched handles: system of every row, per-system max |b| (bit patterns)
+  const int32_t *sys_of_row;
+  unsigned long long *sys_bmax;
 };
 
 struct Graph {
@@ -149,10 +155,16 @@ struct Graph {
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
   int max_degree = 0;
+  // batched handles (independent systems along the diagonal)
+  int32_t nsys = 0;
+  int32_t *sys_of_row = nullptr;
+  unsigned long long *sys_bmax = nullptr;
+  std::vector<int64_t> h_sys_row_off;
 
   GraphView view() const {
     return GraphView{rp,          rev,      col,       a64,        diag64,       a32, diag32, tiles_big,
-                     tiles_small, lrow_big, heavy_big, ntiles_big, ntiles_small, n};
+                     tiles_small, lrow_big, heavy_big, ntiles_big, ntiles_small, n,   sys_of_row,
+                     sys_bmax};
   }
 };
 
@@ -185,6 +197,17 @@ constexpr size_t kPad = 32;
 gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr,
                         const int32_t *col, const double *val, const int64_t *rev,
                         const gabp_options &opt, cudaStream_t st, std::string *msg);
+// Marks the graph as `nsys` independent systems with row offsets
+// sys_row_off[0..nsys] (checks that no entry couples two systems).
+gabp_status build_systems(Graph &g, int32_t nsys, const int64_t *sys_row_off,
+                          const int64_t *row_ptr, const int32_t *col, cudaStream_t st,
+                          std::string *msg);
+int launch_lsq_rhs(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row,
+                   const int64_t *aug_off, const int32_t *K, const int64_t *y_off, const double *y,
+                   double *rhs);
+int launch_lsq_extract(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row,
+                       const int64_t *aug_off, const int32_t *K, const int64_t *x_off,
+                       const double *x_aug, double *xhat);
 void free_graph(Graph &g);
 
 }  // namespace gabp
@@ -209,6 +232,13 @@ struct gabp_s {
   cudaGraphExec_t exec[gabp::CTL_MODES] = {};
   cudaGraph_t graph[gabp::CTL_MODES] = {};
   cudaGraphConditionalHandle cond[gabp::CTL_MODES][2] = {};   // (WHILE, SWITCH) per mode
+  // least-squares batches (Section VII augmented systems)
+  int32_t *lsq_K = nullptr;            // device: K_s
+  int64_t *lsq_aug_off = nullptr;      // device: first augmented row of system s
+  int64_t *lsq_y_off = nullptr;        // device: offset of y_s in the concatenated y
+  int64_t *lsq_x_off = nullptr;        // device: offset of x^_s in the concatenated x^
+  int64_t lsq_ny = 0, lsq_nx = 0;      // total lengths of y and x^
+  double *lsq_rhs = nullptr, *lsq_x = nullptr;   // device: augmented rhs and solution
   int graph_K = 0;                     // K the CTL_MULTI graph was recorded for
   size_t capK = 0;                     // columns the multi buffers hold
   gabp::MultiCols cols{};              // device per-column arrays (capK each)

@@ -221,11 +221,14 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
     case CK_CHECK64:
     case CK_REFINE: {
       c.checks++;
-      const double rn = dv(r->max_r);
+      const double rn = dv(r->max_r), rrel = dv(r->max_rrel);
       r->max_r = 0;
+      r->max_rrel = 0;
       c.residual = rn;
       if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
-      if (rn < c.thr) { finish(c, GABP_OK); break; }
+      // batched handles: every system meets its own relative rule
+      const bool met = c.batched ? (c.rel ? rrel < c.tol : rn < c.tol) : rn < c.thr;
+      if (met) { finish(c, GABP_OK); break; }
       if (diverged(rn, c.bnorm)) { finish(c, GABP_ERR_DIVERGED); break; }
       if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
       if (kind == CK_CHECK64) { c.phase = PH_FULL64; break; }
@@ -387,7 +390,9 @@ __device__ void last_block_control(Ctl *ctl, DevScalars *red, int kind) {
 // Solve set-up: ||b||_inf; in the mixed modes also x = 0 and r = b.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) init_kernel(int32_t n, double *__restrict__ r64,
-                                                      Ctl *ctl, DevScalars *red) {
+                                                      Ctl *ctl, DevScalars *red,
+                                                      const int32_t *__restrict__ sys_of_row,
+                                                      unsigned long long *sys_bmax) {
   const double *b = ctl->b;
   double *x = ctl->x;
   const bool mixed = ctl->mode == CTL_MIXED, prec = ctl->mode == CTL_PREC;
@@ -398,6 +403,7 @@ __global__ void __launch_bounds__(kBlock) init_kernel(int32_t n, double *__restr
     const double bi = b[i];
     m = umax(m, bits(fabs(bi)));
     if (mixed) { x[i] = 0.0; r64[i] = bi; }
+    if (sys_bmax) atomicMax(&sys_bmax[sys_of_row[i]], bits(fabs(bi)));
   }
   block_max4(m, 0, 0, 0, &red->max_b, nullptr, nullptr, nullptr);
   last_block_control(ctl, red, CK_INIT);
@@ -643,11 +649,15 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     Seg<double>::copy(base + L::dg, g.diag64, tb.r0, nr, bar);
   };
 
+  const double gam = ctl->damping;
   auto emit = [&](double a, double2 m, int32_t dst, double TP, double Th) {
     const double d = TP - m.x;   // P_{i\j} = P~_i - P_ji
     brk |= !(d != 0.0) || !isfinite(d);
     const double inv = recip64(d);
-    mout[dst] = make_double2(-(a * a) * inv, -a * (Th - m.y) * inv);
+    double eta = -a * (Th - m.y) * inv;
+    // damping: blend with this message's previous value (slot dst of "in")
+    if (gam > 0.0) eta = gam * (first ? 0.0 : min[dst].y) + (1.0 - gam) * eta;
+    mout[dst] = make_double2(-(a * a) * inv, eta);
   };
 
   auto work = [&](int32_t t, unsigned char *stage, int, bool got) {
@@ -782,22 +792,32 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     if (freeze) B.invP32[i] = 1.0f / TP;
     if (first) B.rhs32[i] = rhs;
   };
+  const float gam = static_cast<float>(ctl->damping);
   auto emit = [&](int32_t s, float a, float2 m, int32_t dst, float TP, float Th) {
     const float d = TP - m.x;   // P_{i\j} = P~_i - P_ji
     brk |= !(d != 0.0f) || !isfinite(d);
     const float inv = 1.0f / d;
+    // damping: blend the information with this message's previous value
+    const float old_eta = (gam > 0.f && !first) ? min[dst].y : 0.f;
     if (freeze) {
       const float c = -a * inv;
       B.c32[s] = c;
-      st_keep(eta_out + dst, c * (Th - m.y), pol_keep);
+      float eta = c * (Th - m.y);
+      if (gam > 0.f) eta = gam * old_eta + (1.f - gam) * eta;
+      st_keep(eta_out + dst, eta, pol_keep);
     } else {
-      st_keep(mout + dst, make_float2(-(a * a) * inv, -a * (Th - m.y) * inv), pol_keep);
+      float eta = -a * (Th - m.y) * inv;
+      if (gam > 0.f) eta = gam * old_eta + (1.f - gam) * eta;
+      st_keep(mout + dst, make_float2(-(a * a) * inv, eta), pol_keep);
     }
   };
 
   auto work = [&](int32_t t, unsigned char *stage, int st, bool got) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    // clear the other totals buffer for the next tile, whatever this tile's kind
+    float2 *tc = tot[st], *tn = tot[st ^ 1];
+    for (int32_t k = tid; k < L::TR; k += NT) tn[k] = make_float2(0.f, 0.f);
     if (ns > L::TS) {
       if (__syncthreads_or(!got)) return true;
       const int32_t i = tb.r0;
@@ -842,10 +862,8 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       return false;
     }
     // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
-    float2 *tc = tot[st], *tn = tot[st ^ 1];
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
     for (int32_t k = tid; k < nr; k += NT) nd[k] = make_float2(g.diag32[tb.r0 + k], rhs_at(tb.r0 + k));
-    for (int32_t k = tid; k < L::TR; k += NT) tn[k] = make_float2(0.f, 0.f);
     if (!first) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
         const int32_t s = base + (tid & 31);
@@ -932,6 +950,12 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   auto rhs_at = [&](int32_t i) {
     return first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
   };
+  const float gam = static_cast<float>(ctl->damping);
+  // eta_ij sent to slot dst: damped with its previous value when gamma > 0
+  auto send = [&](int32_t dst, float v) {
+    if (gam > 0.f) v = gam * (first ? 0.f : ld_eta(ein + dst)) + (1.f - gam) * v;
+    st_keep(eout + dst, v, pol_keep);
+  };
   auto node = [&](int32_t i, float Th, float rhs) {
     const float prev = first ? 0.f : mon_prev[i].y;
     const float di = Th * B.invP32[i];
@@ -944,6 +968,9 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   auto work = [&](int32_t t, unsigned char *stage, int st, bool got) {
     const TileBounds tb = tile_at(g.tiles_big, t);
     const int32_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
+    // clear the other totals buffer for the next tile, whatever this tile's kind
+    float *tc = tot[st], *tn = tot[st ^ 1];
+    for (int32_t k = tid; k < L::TR; k += NT) tn[k] = 0.f;
     if (ns > L::TS) {
       if (__syncthreads_or(!got)) return true;
       const int32_t i = tb.r0;
@@ -955,7 +982,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       if (tid == 0) node(i, Th, rhs);
       for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) {
         const float e = first ? 0.f : ld_eta(ein + s);
-        st_keep(eout + g.rev[s], B.c32[s] * (Th - e), pol_keep);
+        send(g.rev[s], B.c32[s] * (Th - e));
       }
       return false;
     }
@@ -976,18 +1003,16 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
         const float Th = rhs + sH;
         node(i, Th, rhs);
         if (first)
-          for (int32_t s = rs; s < re; ++s) st_keep(eout + rv[s], cs[s] * Th, pol_keep);
+          for (int32_t s = rs; s < re; ++s) send(rv[s], cs[s] * Th);
         else
           for (int32_t s = rs; s < re; ++s)
-            st_keep(eout + rv[s], cs[s] * (Th - ld_eta(es + s)), pol_keep);
+            send(rv[s], cs[s] * (Th - ld_eta(es + s)));
       }
       return false;
     }
     // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
-    float *tc = tot[st], *tn = tot[st ^ 1];
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
     for (int32_t k = tid; k < nr; k += NT) rhs_s[k] = rhs_at(tb.r0 + k);
-    for (int32_t k = tid; k < L::TR; k += NT) tn[k] = 0.f;
     if (!first) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
         const int32_t s = base + (tid & 31);
@@ -1003,7 +1028,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     for (int32_t s = tid; s < ns; s += NT) {
       const int k = lrow[s];
       const float e = first ? 0.f : ld_eta(es + s);
-      st_keep(eout + rv[s], cs[s] * (rhs_s[k] + tc[k] - e), pol_keep);
+      send(rv[s], cs[s] * (rhs_s[k] + tc[k] - e));
     }
     return false;
   };
@@ -1046,7 +1071,7 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
   const double *__restrict__ x = ctl->x;
   const int NT = blockDim.x, tid = threadIdx.x;
   const uint64_t pol_stream = policy_evict_first();
-  unsigned long long mr = 0;
+  unsigned long long mr = 0, mrel = 0;
 
   auto issue = [&](int32_t t, unsigned char *stage, uint32_t bar) {
     const TileBounds tb = tile_at(g.tiles_big, t);
@@ -1066,6 +1091,11 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
     const double ri = b[i] - (dgi * x[i] + acc);
     if (r_out) r_out[i] = ri;
     mr = umax(mr, bits(fabs(ri)));
+    if (g.sys_bmax) {
+      // batched: residual relative to this row's own system
+      const double bs = dv(g.sys_bmax[g.sys_of_row[i]]);
+      mrel = umax(mrel, bits(bs > 0.0 ? fabs(ri) / bs : (ri == 0.0 ? 0.0 : INFINITY)));
+    }
   };
 
   auto work = [&](int32_t t, unsigned char *stage, int, bool got) {
@@ -1102,21 +1132,23 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
       }
       return false;
     }
-    // heavy tile: slot-parallel products, then per-row sums
+    // heavy tile: slot-parallel products, then one warp per row sums them
     if (got)
       for (int32_t s = tid; s < ns; s += NT) as[s] *= x[cs[s]];
     if (__syncthreads_or(!got)) return true;
-    for (int32_t k = tid; k < nr; k += NT) {
+    const int lane = tid & 31, nw = NT >> 5;
+    for (int32_t k = tid >> 5; k < nr; k += nw) {
       double acc = 0.0;
-      for (int32_t s = rp[k] - tb.s0; s < rp[k + 1] - tb.s0; ++s) acc += as[s];
-      node(tb.r0 + k, dg[k], acc);
+      for (int32_t s = rp[k] - tb.s0 + lane; s < rp[k + 1] - tb.s0; s += 32) acc += as[s];
+      acc = group_sum<32>(acc);
+      if (lane == 0) node(tb.r0 + k, dg[k], acc);
     }
     return false;
   };
 
   const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
   if (!ok) atomicOr(&red->timeout, 1);
-  block_max4(mr, 0, 0, 0, &red->max_r, nullptr, nullptr, nullptr);
+  block_max4(mr, mrel, 0, 0, &red->max_r, &red->max_rrel, nullptr, nullptr);
   last_block_control(ctl, red, kind);
 }
 
@@ -1184,6 +1216,7 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
   const bool first = ctl->first != 0;
   const float *__restrict__ ein = pe ? B.eK[1] : B.eK[0];
   float *__restrict__ eout = pe ? B.eK[0] : B.eK[1];
+  const float gam = static_cast<float>(ctl->damping);
   double irn[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
@@ -1207,14 +1240,31 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
         th[j] = B.rhsK[idx];
       }
     }
-    if (!first)
-      for (int32_t s = rs; s < re; ++s) {
+    if (!first) {
+      // four slots' messages in flight per lane before they are added
+      int32_t s = rs;
+      for (; s + 4 <= re; s += 4) {
+        float v[4][NC];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int j = 0; j < NC; ++j) {
+            const int c = lane + 32 * j;
+            v[u][j] = c < K ? ein[static_cast<int64_t>(s + u) * K + c] : 0.f;
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int j = 0; j < NC; ++j) th[j] += v[u][j];
+      }
+      for (; s < re; ++s) {
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
           const int c = lane + 32 * j;
           if (c < K) th[j] += ein[static_cast<int64_t>(s) * K + c];
         }
       }
+    }
     const float ip = B.invP32[i];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
@@ -1227,7 +1277,32 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
       mdd = fmax_bits(mdd, d - prev);
       md = fmax_bits(md, d);
     }
-    for (int32_t s = rs; s < re; ++s) {
+    int32_t s = rs;
+    for (; s + 4 <= re; s += 4) {
+      float cs[4], v[4][NC];
+      int64_t dst[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        cs[u] = B.c32[s + u];
+        dst[u] = static_cast<int64_t>(g.rev[s + u]) * K;
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          const int c = lane + 32 * j;
+          v[u][j] = (first || c >= K) ? 0.f : ein[static_cast<int64_t>(s + u) * K + c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          const int c = lane + 32 * j;
+          if (c >= K) continue;
+          float out = cs[u] * (th[j] - v[u][j]);
+          if (gam > 0.f) out = gam * (first ? 0.f : ein[dst[u] + c]) + (1.f - gam) * out;
+          eout[dst[u] + c] = out;
+        }
+    }
+    for (; s < re; ++s) {
       const float cs = B.c32[s];
       const int64_t dst = static_cast<int64_t>(g.rev[s]) * K;
 #pragma unroll
@@ -1235,7 +1310,9 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
         const int c = lane + 32 * j;
         if (c >= K) continue;
         const float e = first ? 0.f : ein[static_cast<int64_t>(s) * K + c];
-        eout[dst + c] = cs * (th[j] - e);
+        float out = cs * (th[j] - e);
+        if (gam > 0.f) out = gam * (first ? 0.f : ein[dst + c]) + (1.f - gam) * out;
+        eout[dst + c] = out;
       }
     }
   }
@@ -1271,7 +1348,21 @@ residual_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) 
     double acc[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) acc[j] = 0.0;
-    for (int32_t s = rs; s < re; ++s) {
+    int32_t s = rs;
+    for (; s + 2 <= re; s += 2) {
+      const double a0 = g.a64[s], a1 = g.a64[s + 1];
+      const int64_t x0 = static_cast<int64_t>(g.col[s]) * K, x1 = static_cast<int64_t>(g.col[s + 1]) * K;
+      double v0[NC], v1[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const int c = lane + 32 * j;
+        v0[j] = c < K ? X[x0 + c] : 0.0;
+        v1[j] = c < K ? X[x1 + c] : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[j] = fma(a1, v1[j], fma(a0, v0[j], acc[j]));
+    }
+    for (; s < re; ++s) {
       const double a = g.a64[s];
       const int64_t xc = static_cast<int64_t>(g.col[s]) * K;
 #pragma unroll
@@ -1293,6 +1384,34 @@ residual_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) 
   }
   column_max_commit<NC>(m, ctl->cols.rmax, K, sm);
   last_block_control(ctl, red, CK_REFINEK);
+}
+
+// ---------------------------------------------------------------------------
+// Section VII least-squares batches: right-hand side [0_K; y_s] of every
+// augmented system, and extraction of x^_s (the first K_s unknowns).
+// ---------------------------------------------------------------------------
+__global__ void lsq_rhs_kernel(int64_t n_aug, const int32_t *__restrict__ sys_of_row,
+                               const int64_t *__restrict__ aug_off, const int32_t *__restrict__ K,
+                               const int64_t *__restrict__ y_off, const double *__restrict__ y,
+                               double *__restrict__ rhs) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_aug;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t sy = sys_of_row[i];
+    const int64_t local = i - aug_off[sy];
+    rhs[i] = local < K[sy] ? 0.0 : y[y_off[sy] + (local - K[sy])];
+  }
+}
+
+__global__ void lsq_extract_kernel(int64_t n_aug, const int32_t *__restrict__ sys_of_row,
+                                   const int64_t *__restrict__ aug_off,
+                                   const int32_t *__restrict__ K, const int64_t *__restrict__ x_off,
+                                   const double *__restrict__ x_aug, double *__restrict__ xhat) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_aug;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t sy = sys_of_row[i];
+    const int64_t local = i - aug_off[sy];
+    if (local < K[sy]) xhat[x_off[sy] + local] = x_aug[i];
+  }
 }
 
 int g_num_sms = 0;
@@ -1365,7 +1484,7 @@ void prepare_group() {
 }  // namespace
 
 int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
-  init_kernel<<<flat_grid(g.n), kBlock, 0, st>>>(g.n, B.r64, ctl, red);
+  init_kernel<<<flat_grid(g.n), kBlock, 0, st>>>(g.n, B.r64, ctl, red, g.sys_of_row, g.sys_bmax);
   return 1;
 }
 
@@ -1471,6 +1590,21 @@ void tile_sizes(int *big_slots, int *big_rows, int *small_slots, int *small_rows
   *big_rows = kTileRowsBig;
   *small_slots = kTileSlotsSmall;
   *small_rows = kTileRowsSmall;
+}
+
+int launch_lsq_rhs(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row,
+                   const int64_t *aug_off, const int32_t *K, const int64_t *y_off, const double *y,
+                   double *rhs) {
+  lsq_rhs_kernel<<<flat_grid(n_aug), kBlock, 0, st>>>(n_aug, sys_of_row, aug_off, K, y_off, y, rhs);
+  return 1;
+}
+
+int launch_lsq_extract(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row,
+                       const int64_t *aug_off, const int32_t *K, const int64_t *x_off,
+                       const double *x_aug, double *xhat) {
+  lsq_extract_kernel<<<flat_grid(n_aug), kBlock, 0, st>>>(n_aug, sys_of_row, aug_off, K, x_off,
+                                                          x_aug, xhat);
+  return 1;
 }
 
 double bits_to_double(unsigned long long u) {

@@ -254,6 +254,7 @@ void init_ctl(gabp_handle h, int mode, const double *b, double *x, double tol, i
   c.max_iter = max_iter;
   c.check_every = h->opt.check_every > 0 ? h->opt.check_every : 4;
   c.inner_tol = h->opt.inner_tol > 0 ? h->opt.inner_tol : 1e-6;
+  c.damping = h->opt.damping;
   c.in_graph = in_graph ? 1 : 0;
   if (in_graph) {
     c.h_while = h->cond[mode][0];
@@ -346,6 +347,10 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
   if (mixed) ensure32(h); else ensure64(h);
   h->stats = gabp_stats{};
   init_ctl(h, mode, b, x, tol, max_iter, false);
+  if (h->g.nsys > 0) {
+    h->ctl_host->batched = 1;
+    CK(cudaMemsetAsync(h->g.sys_bmax, 0, sizeof(unsigned long long) * h->g.nsys, h->stream));
+  }
   run_mode(h, mode, max_iter);
   finish_stats(h);
   if (iters) *iters = h->ctl_host->sweeps;
@@ -402,6 +407,44 @@ gabp_status solve_multi_mixed(gabp_handle h, const double *B, double *X, int32_t
   return report(h, "multi right-hand-side solve");
 }
 
+// Section VII: the symmetric augmented system of every S_s (N_s x K_s,
+// row-major at S + sum of earlier N_t K_t):
+//   [ I_K   S^T  ] [x^]   [0]
+//   [ S    -psi I] [z ] = [y]
+// stored as one block-diagonal CSR, rows of x^ first in every block.
+void build_lsq_csr(int32_t nsys, const int32_t *K, const int32_t *N, const double *S,
+                   const double *psi, std::vector<int64_t> &row_ptr, std::vector<int32_t> &col,
+                   std::vector<double> &val, std::vector<int64_t> &sys_off) {
+  row_ptr.assign(1, 0);
+  sys_off.assign(1, 0);
+  int64_t soff = 0, base = 0;
+  for (int32_t s = 0; s < nsys; ++s) {
+    const int32_t k = K[s], m = N[s];
+    const double *Ss = S + soff;
+    for (int32_t r = 0; r < k; ++r) {   // x^_r: 1 on the diagonal, S_{j r} towards z_j
+      col.push_back(static_cast<int32_t>(base + r));
+      val.push_back(1.0);
+      for (int32_t j = 0; j < m; ++j) {
+        const double v = Ss[static_cast<int64_t>(j) * k + r];
+        if (v != 0.0) { col.push_back(static_cast<int32_t>(base + k + j)); val.push_back(v); }
+      }
+      row_ptr.push_back(static_cast<int64_t>(col.size()));
+    }
+    for (int32_t j = 0; j < m; ++j) {   // z_j: S_{j r} towards x^_r, -psi on the diagonal
+      for (int32_t r = 0; r < k; ++r) {
+        const double v = Ss[static_cast<int64_t>(j) * k + r];
+        if (v != 0.0) { col.push_back(static_cast<int32_t>(base + r)); val.push_back(v); }
+      }
+      col.push_back(static_cast<int32_t>(base + k + j));
+      val.push_back(-psi[s]);
+      row_ptr.push_back(static_cast<int64_t>(col.size()));
+    }
+    soff += static_cast<int64_t>(k) * m;
+    base += k + m;
+    sys_off.push_back(base);
+  }
+}
+
 void release(gabp_handle h) {
   for (int m = 0; m < CTL_MODES; ++m) {
     if (h->exec[m]) cudaGraphExecDestroy(h->exec[m]);
@@ -420,6 +463,8 @@ void release(gabp_handle h) {
   cudaFree(h->red); cudaFree(h->ctl);
   cudaFree(h->bbuf); cudaFree(h->xbuf);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  cudaFree(h->lsq_K); cudaFree(h->lsq_aug_off); cudaFree(h->lsq_y_off); cudaFree(h->lsq_x_off);
+  cudaFree(h->lsq_rhs); cudaFree(h->lsq_x);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
@@ -451,6 +496,11 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
     g_create_error = "unknown precision mode";
     return GABP_ERR_INVALID_ARG;
   }
+  if (!(h->opt.damping >= 0.0 && h->opt.damping < 1.0)) {
+    delete h;
+    g_create_error = "damping must lie in [0, 1)";
+    return GABP_ERR_INVALID_ARG;
+  }
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   h->user_nnz = nnz;
   gabp_status s = guarded(h, [&] {
@@ -468,6 +518,133 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
   }
   *out = h;
   return GABP_OK;
+}
+
+gabp_status gabp_create_batched(gabp_handle *out, int32_t nsys, const int64_t *sys_row_off_host,
+                                int64_t nnz, const int64_t *row_ptr_host, const int32_t *col_host,
+                                const double *val_host, const gabp_options *opt) {
+  if (!out) return GABP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nsys < 1 || !sys_row_off_host) {
+    g_create_error = "gabp_create_batched: nsys < 1 or null offsets";
+    return GABP_ERR_INVALID_ARG;
+  }
+  // block-diagonal structure is checked on the host before any device work
+  const int64_t n = sys_row_off_host[nsys];
+  if (sys_row_off_host[0] != 0 || n < 1 || !row_ptr_host || !col_host || row_ptr_host[n] != nnz) {
+    g_create_error = "gabp_create_batched: offsets must run from 0 to n and row_ptr[n] == nnz";
+    return GABP_ERR_INVALID_ARG;
+  }
+  for (int32_t sy = 0; sy < nsys; ++sy) {
+    const int64_t r0 = sys_row_off_host[sy], r1 = sys_row_off_host[sy + 1];
+    if (r1 <= r0) {
+      g_create_error = "gabp_create_batched: every system needs at least one row";
+      return GABP_ERR_INVALID_ARG;
+    }
+    for (int64_t i = r0; i < r1; ++i) {
+      if (row_ptr_host[i] < 0 || row_ptr_host[i + 1] < row_ptr_host[i] || row_ptr_host[i + 1] > nnz) {
+        g_create_error = "gabp_create_batched: row_ptr not monotone within [0, nnz]";
+        return GABP_ERR_INVALID_ARG;
+      }
+      for (int64_t e = row_ptr_host[i]; e < row_ptr_host[i + 1]; ++e)
+        if (col_host[e] < r0 || col_host[e] >= r1) {
+          g_create_error = "gabp_create_batched: an entry couples two systems";
+          return GABP_ERR_INVALID_ARG;
+        }
+    }
+  }
+  gabp_handle h = nullptr;
+  gabp_status s = gabp_create(&h, n, nnz, row_ptr_host, col_host, val_host, nullptr, opt);
+  if (s != GABP_OK) return s;
+  s = guarded(h, [&] {
+    std::string msg;
+    gabp_status r = build_systems(h->g, nsys, sys_row_off_host, row_ptr_host, col_host, h->stream, &msg);
+    if (r != GABP_OK) h->last_error = msg;
+    return r;
+  });
+  if (s != GABP_OK) {
+    g_create_error = h->last_error;
+    gabp_destroy(h);
+    return s;
+  }
+  *out = h;
+  return GABP_OK;
+}
+
+gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_t *K_host,
+                                    const int32_t *N_host, const double *S_host,
+                                    const double *psi_host, const gabp_options *opt) {
+  if (!out) return GABP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nsys < 1 || !K_host || !N_host || !S_host || !psi_host) {
+    g_create_error = "gabp_create_lsq_batched: invalid argument";
+    return GABP_ERR_INVALID_ARG;
+  }
+  for (int32_t s = 0; s < nsys; ++s)
+    if (K_host[s] < 1 || N_host[s] < 1 || !(psi_host[s] > 0.0) || !std::isfinite(psi_host[s])) {
+      g_create_error = "gabp_create_lsq_batched: K_s, N_s >= 1 and psi_s > 0 required";
+      return GABP_ERR_INVALID_ARG;
+    }
+  std::vector<int64_t> row_ptr, sys_off;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  try {
+    build_lsq_csr(nsys, K_host, N_host, S_host, psi_host, row_ptr, col, val, sys_off);
+  } catch (const std::bad_alloc &) {
+    return GABP_ERR_OOM;
+  }
+  gabp_handle h = nullptr;
+  gabp_status s = gabp_create_batched(&h, nsys, sys_off.data(), static_cast<int64_t>(col.size()),
+                                      row_ptr.data(), col.data(), val.data(), opt);
+  if (s != GABP_OK) return s;
+  s = guarded(h, [&] {
+    std::vector<int64_t> y_off(nsys + 1, 0), x_off(nsys + 1, 0);
+    for (int32_t k = 0; k < nsys; ++k) {
+      y_off[k + 1] = y_off[k] + N_host[k];
+      x_off[k + 1] = x_off[k] + K_host[k];
+    }
+    h->lsq_ny = y_off[nsys];
+    h->lsq_nx = x_off[nsys];
+    ensure(&h->lsq_K, nsys);
+    ensure(&h->lsq_aug_off, nsys + 1);
+    ensure(&h->lsq_y_off, nsys + 1);
+    ensure(&h->lsq_x_off, nsys + 1);
+    ensure(&h->lsq_rhs, h->g.n);
+    ensure(&h->lsq_x, h->g.n);
+    CK(cudaMemcpyAsync(h->lsq_K, K_host, sizeof(int32_t) * nsys, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->lsq_aug_off, sys_off.data(), sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->lsq_y_off, y_off.data(), sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->lsq_x_off, x_off.data(), sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return GABP_OK;
+  });
+  if (s != GABP_OK) {
+    g_create_error = h->last_error;
+    gabp_destroy(h);
+    return s;
+  }
+  *out = h;
+  return GABP_OK;
+}
+
+gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *xhat_dev, double tol,
+                                   int32_t max_iter, int32_t *iters) {
+  if (!h) return GABP_ERR_INVALID_ARG;
+  if (!h->lsq_K) return fail(h, GABP_ERR_INVALID_ARG, "handle was not made by gabp_create_lsq_batched");
+  if (!y_dev || !xhat_dev || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
+    return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_lsq_batched: invalid argument");
+  return guarded(h, [&] {
+    cudaStream_t st = h->stream;
+    launch_lsq_rhs(st, h->g.n, h->g.sys_of_row, h->lsq_aug_off, h->lsq_K, h->lsq_y_off, y_dev,
+                   h->lsq_rhs);
+    const gabp_status s = solve_impl(h, h->lsq_rhs, h->lsq_x, tol, max_iter, iters);
+    launch_lsq_extract(st, h->g.n, h->g.sys_of_row, h->lsq_aug_off, h->lsq_K, h->lsq_x_off,
+                       h->lsq_x, xhat_dev);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    h->stats.kernel_launches += 2;
+    return s;
+  });
 }
 
 gabp_status gabp_destroy(gabp_handle h) {

@@ -34,7 +34,8 @@ RESIDUAL_ABS, RESIDUAL_REL = 0, 1
 EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_stream",
             "gabp_solve", "gabp_solve_host", "gabp_solve_multi", "gabp_get_stats",
             "gabp_run_rounds", "gabp_get_messages", "gabp_last_error", "gabp_status_string",
-            "gabp_version")
+            "gabp_version", "gabp_create_batched", "gabp_create_lsq_batched",
+            "gabp_solve_lsq_batched")
 
 
 class GabpOptions(ctypes.Structure):
@@ -43,7 +44,7 @@ class GabpOptions(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("reserved_i", ctypes.c_int32 * 2),
                 ("inner_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("reserved_d", ctypes.c_double * 4)]
+                ("damping", ctypes.c_double), ("reserved_d", ctypes.c_double * 3)]
 
 
 class GabpStats(ctypes.Structure):
@@ -99,6 +100,11 @@ def load(path: str = LIB_PATH):
         "gabp_last_error": (ctypes.c_char_p, [H]),
         "gabp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "gabp_version": (ctypes.c_char_p, []),
+        "gabp_create_batched": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int32, i64p, ctypes.c_int64,
+                                               i64p, i32p, f64p, ctypes.POINTER(GabpOptions)]),
+        "gabp_create_lsq_batched": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int32, i32p, i32p, f64p,
+                                                   f64p, ctypes.POINTER(GabpOptions)]),
+        "gabp_solve_lsq_batched": (ctypes.c_int, [H, vp, vp, ctypes.c_double, ctypes.c_int32, i32p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -160,6 +166,52 @@ def gabp_create(row_ptr, col, val, rev=None, options: GabpOptions | None = None)
                          ctypes.byref(options))
     _check(None, st)
     return h
+
+
+def gabp_create_batched(sys_row_off, row_ptr, col, val, options: GabpOptions | None = None):
+    """Create a handle over independent systems along the diagonal of one CSR
+    (host arrays); sys_row_off[s]..sys_row_off[s+1] are the rows of system s."""
+    lib = load()
+    sys_row_off = np.ascontiguousarray(sys_row_off, dtype=np.int64)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    if options is None:
+        options = gabp_default_options()
+    h = ctypes.c_void_p()
+    st = lib.gabp_create_batched(ctypes.byref(h), len(sys_row_off) - 1, _ptr(sys_row_off, ctypes.c_int64),
+                                 int(row_ptr[-1]), _ptr(row_ptr, ctypes.c_int64),
+                                 _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double),
+                                 ctypes.byref(options))
+    _check(None, st)
+    return h
+
+
+def gabp_create_lsq_batched(S_list, psi, options: GabpOptions | None = None):
+    """Create a least-squares batch (Section VII augmented systems) from a list
+    of dense S_s (N_s x K_s) and noise variances psi_s (scalar or list)."""
+    lib = load()
+    K = np.ascontiguousarray([S.shape[1] for S in S_list], dtype=np.int32)
+    N = np.ascontiguousarray([S.shape[0] for S in S_list], dtype=np.int32)
+    Scat = np.ascontiguousarray(np.concatenate([np.asarray(S, dtype=np.float64).ravel() for S in S_list]))
+    psi = np.ascontiguousarray(np.broadcast_to(np.asarray(psi, dtype=np.float64), (len(S_list),)))
+    if options is None:
+        options = gabp_default_options()
+    h = ctypes.c_void_p()
+    st = lib.gabp_create_lsq_batched(ctypes.byref(h), len(S_list), _ptr(K, ctypes.c_int32),
+                                     _ptr(N, ctypes.c_int32), _ptr(Scat, ctypes.c_double),
+                                     _ptr(psi, ctypes.c_double), ctypes.byref(options))
+    _check(None, st)
+    return h
+
+
+def gabp_solve_lsq_batched(h, y, xhat, tol: float, max_iter: int) -> int:
+    """y: concatenated y_s (device float64), xhat: concatenated x^_s (output)."""
+    it = ctypes.c_int32(0)
+    st = load().gabp_solve_lsq_batched(h, _dev_ptr(y, "torch.float64"), _dev_ptr(xhat, "torch.float64"),
+                                       float(tol), int(max_iter), ctypes.byref(it))
+    _check(h, st)
+    return it.value
 
 
 def gabp_destroy(h):
@@ -234,7 +286,7 @@ class Solver:
     @classmethod
     def from_csr(cls, row_ptr, col, val, rev=None, *, precision=PREC_FP64,
                  residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=1e-6,
-                 profile=False, stream: int | None = None):
+                 profile=False, damping=0.0, stream: int | None = None):
         o = gabp_default_options()
         o.precision = precision
         o.residual_kind = residual_kind
@@ -242,6 +294,7 @@ class Solver:
         o.group_lanes = group_lanes
         o.inner_tol = inner_tol
         o.profile = 1 if profile else 0
+        o.damping = damping
         o.stream = current_stream_handle() if stream is None else stream
         h = gabp_create(row_ptr, col, val, rev, o)
         return cls(h, len(row_ptr) - 1, int(row_ptr[-1]))

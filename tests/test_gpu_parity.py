@@ -383,3 +383,151 @@ def test_multi_rhs_64_columns_dominance_105(G):
                 for k in range(64))
     assert worst < 1e-10
     s.close()
+
+
+# ---------------------------------------------------------------------------
+# Batched independent systems and Section VII least-squares batches
+# ---------------------------------------------------------------------------
+def _block_diag(mats):
+    rows, cols, vals, off = [], [], [], [0]
+    for m in mats:
+        r = np.repeat(np.arange(m.n), np.diff(m.row_ptr)) + off[-1]
+        rows.append(r); cols.append(m.col.astype(np.int64) + off[-1]); vals.append(m.val)
+        off.append(off[-1] + m.n)
+    big = W.csr_from_coo(off[-1], np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    return big, np.array(off)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_systems_each_meet_their_rule(G, precision):
+    mats = [W.er_sdd(800, 8, 1.1, 1), W.poisson2d(12), W.random_tree(300, 2, diag_scale=2.0),
+            W.er_sdd(1500, 5, 1.2, 3), W.poisson3d(6)]
+    big, off = _block_diag(mats)
+    scales = [1.0, 1e-6, 1e3, 1.0, 1e-2]    # very different magnitudes per system
+    b = np.concatenate([sc * W.normal_rhs(m.n, 10 + k) for k, (m, sc) in enumerate(zip(mats, scales))])
+    o = G.gabp_default_options()
+    o.precision = precision
+    o.stream = G.current_stream_handle()
+    h = G.gabp_create_batched(off, big.row_ptr, big.col, big.val, o)
+    s = G.Solver(h, big.n, big.nnz)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=20000)
+    x = xt.cpu().numpy()
+    for k, m in enumerate(mats):
+        bs, xs = b[off[k]:off[k + 1]], x[off[k]:off[k + 1]]
+        res = oracle.residual_inf(m.row_ptr, m.col, m.val, bs, xs)
+        assert res < 1e-10 * np.abs(bs).max(), (k, res)
+    s.close()
+
+
+def test_lsq_batch_matches_closed_form_and_oracle(G):
+    systems = W.detection_batch(24, 16, 64, 10.0, seed=7)
+    o = G.gabp_default_options()
+    o.precision = 1
+    o.stream = G.current_stream_handle()
+    h = G.gabp_create_lsq_batched([d.S for d in systems], [d.sigma2 for d in systems], o)
+    y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
+    xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
+    it = G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 20000)
+    got = xh.cpu().numpy()
+    off = 0
+    for d in systems:
+        A, bb = d.dense_system()
+        closed = np.linalg.solve(A, bb)
+        assert _rel(got[off:off + d.K], closed) < 1e-8
+        # the oracle's own augmentation and GaBP agree with the library
+        rp, cl, vl, rhs = oracle.augment_lsq(d.S, d.sigma2, d.y)
+        ref = oracle.gabp(rp, cl, vl, rhs, stop=oracle.STOP_RES_REL, max_rounds=20000, tol=1e-12)
+        assert ref["status"] == "ok"
+        assert _rel(got[off:off + d.K], ref["x"][:d.K]) < 1e-8
+        off += d.K
+    assert it > 0
+    G.gabp_destroy(h)
+
+
+def test_lsq_batch_many_tiles_per_cta(G):
+    """Enough systems that every CTA walks many tiles of both kinds (rows of
+    degree 2K > 64 make heavy tiles next to light ones): each system still
+    matches its closed form.  Two systems of this batch make plain GaBP
+    diverge (the oracle shows it), so the batch runs damped."""
+    systems = W.detection_batch(300, 16, 80, 10.0, seed=11)
+    o = G.gabp_default_options()
+    o.precision = 1
+    o.damping = 0.3
+    o.stream = G.current_stream_handle()
+    h = G.gabp_create_lsq_batched([d.S for d in systems], [d.sigma2 for d in systems], o)
+    y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
+    xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
+    G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 20000)
+    got = xh.cpu().numpy()
+    off = 0
+    for d in systems:
+        A, bb = d.dense_system()
+        assert _rel(got[off:off + d.K], np.linalg.solve(A, bb)) < 1e-8
+        off += d.K
+    G.gabp_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_heavy_and_light_tiles_mixed(G, precision):
+    """A graph with hub rows (degree 300) scattered among low-degree rows:
+    heavy and light tiles interleave across every CTA's tile sequence."""
+    rng = np.random.default_rng(5)
+    n = 40000
+    base = W.er_sdd(n, 4, 1.1, 6)
+    rows = np.repeat(np.arange(n), np.diff(base.row_ptr))
+    keep = rows != base.col
+    r, c, v = list(rows[keep]), list(base.col[keep].astype(np.int64)), list(base.val[keep])
+    hubs = rng.choice(n, 60, replace=False)
+    existing = set(zip(r, c))
+    for hbi in hubs:
+        for j in rng.choice(n, 300, replace=False):
+            if j != hbi and (hbi, j) not in existing:
+                w = 0.05 * rng.standard_normal()
+                r += [hbi, j]; c += [j, hbi]; v += [w, w]
+                existing.add((hbi, j)); existing.add((j, hbi))
+    r, c, v = np.array(r), np.array(c), np.array(v)
+    diag = 1.2 * np.bincount(r, np.abs(v), minlength=n) + 0.1
+    m = W.csr_from_coo(n, np.concatenate([r, np.arange(n)]), np.concatenate([c, np.arange(n)]),
+                       np.concatenate([v, diag]))
+    b = W.normal_rhs(n, 7)
+    s = _solver(G, m, precision=precision)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=20000)
+    x = xt.cpu().numpy()
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    assert _rel(x, _oracle_solution(m, b)) < 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["er_4000", "poisson2d_p33", "star_300_long_row"])
+def test_fp64_damped_rounds_match_damped_oracle(G, name):
+    m = PARITY_CASES[name]
+    b = W.normal_rhs(m.n, 23)
+    s = _solver(G, m, damping=0.4)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    for r in (1, 2, 6, 13):
+        ref = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=r, want_messages=True, damping=0.4)
+        G.gabp_run_rounds(s.handle, bt, r, xt)
+        P, mu = G.gabp_get_messages(s.handle, m.nnz)
+        assert _rel(xt.cpu().numpy(), ref["x"]) <= 1e-12
+        assert _rel(P, ref["P"]) <= 1e-12
+        assert _rel(mu, ref["mu"]) <= 1e-12
+    s.close()
+
+
+def test_damped_solve_rescues_diverging_system(G):
+    """Plain GaBP diverges on this augmented detection system; with damping
+    the mixed solve reaches 1e-10 and the closed form."""
+    sysd = W.detection_batch(300, 16, 80, 10.0, seed=11)[270]
+    rp, cl, vl, rhs = oracle.augment_lsq(sysd.S, sysd.sigma2, sysd.y)
+    m = W.CSR(len(rp) - 1, rp, cl, vl)
+    plain = _solver(G, m, precision=1)
+    with pytest.raises(G.GabpError):
+        plain.solve(torch.tensor(rhs, device="cuda"), tol=1e-10, max_iter=3000)
+    plain.close()
+    for precision in (0, 1):
+        s = _solver(G, m, precision=precision, damping=0.3)
+        xt, _ = s.solve(torch.tensor(rhs, device="cuda"), tol=1e-10, max_iter=20000)
+        A, bb = sysd.dense_system()
+        assert _rel(xt.cpu().numpy()[:sysd.K], np.linalg.solve(A, bb)) < 1e-8
+        s.close()

@@ -95,3 +95,20 @@ def test_reverse_index_is_an_involution():
     rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
     assert np.array_equal(rev[rev], np.arange(m.nnz))
     assert np.array_equal(m.col[rev], rows)
+
+
+def test_create_batched_rejects_coupled_systems(lib):
+    from paper_0810_1119_gb300 import gabp
+    A = np.array([[4.0, 1.0, 0.0], [1.0, 4.0, 1.0], [0.0, 1.0, 4.0]])
+    m = W.csr_from_dense(A)
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.gabp_create_batched([0, 1, 3], m.row_ptr, m.col, m.val)   # (0,1) couples the systems
+    assert ei.value.name == "GABP_ERR_INVALID_ARG"
+
+
+def test_create_lsq_batched_rejects_bad_noise(lib):
+    from paper_0810_1119_gb300 import gabp
+    S = np.ones((4, 2)) / 2.0
+    with pytest.raises(gabp.GabpError) as ei:
+        gabp.gabp_create_lsq_batched([S], 0.0)
+    assert ei.value.name == "GABP_ERR_INVALID_ARG"

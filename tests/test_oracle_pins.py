@@ -281,3 +281,34 @@ def test_breakdown_reported():
     b = np.ones(3)
     assert _run(m, b, 1)["status"] == "ok"
     assert _run(m, b, 2)["status"] == "breakdown"
+
+
+# --------------------------------------------------------------------------
+# Damping (the heuristic Section VI-D cites): same fixed point, and it
+# rescues a Section VII detection system on which plain GaBP diverges.
+# --------------------------------------------------------------------------
+def test_zero_damping_is_the_plain_rule():
+    m = W.er_sdd(120, 6, 1.1, 3)
+    b = W.normal_rhs(m.n, 4)
+    a = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=9, want_messages=True)
+    c = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=9, want_messages=True, damping=0.0)
+    for key in ("x", "P", "mu"):
+        assert np.array_equal(a[key], c[key])
+
+
+def test_damping_keeps_the_solution_and_rescues_divergence():
+    # System 270 of this batch: plain synchronous GaBP diverges on its
+    # augmented form (checked below), damped GaBP reaches the closed form.
+    sysd = W.detection_batch(300, 16, 80, 10.0, seed=11)[270]
+    rp, cl, vl, rhs = oracle.augment_lsq(sysd.S, sysd.sigma2, sysd.y)
+    plain = oracle.gabp(rp, cl, vl, rhs, stop=oracle.STOP_RES_REL, max_rounds=600, tol=1e-10)
+    assert plain["status"] == "not_converged"
+    assert oracle.residual_inf(rp, cl, vl, rhs, plain["x"]) > 1.0
+    damped = oracle.gabp(rp, cl, vl, rhs, stop=oracle.STOP_RES_REL, max_rounds=3000, tol=1e-12,
+                         damping=0.3)
+    assert damped["status"] == "ok"
+    A, bb = sysd.dense_system()
+    np.testing.assert_allclose(damped["x"][:sysd.K], np.linalg.solve(A, bb), rtol=1e-9, atol=1e-11)
+    # precisions are not damped: identical to the plain run's
+    np.testing.assert_allclose(damped["Pi"], oracle.gabp(rp, cl, vl, rhs, max_rounds=damped["rounds"])["Pi"],
+                               rtol=1e-13)
