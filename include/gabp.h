@@ -236,7 +236,45 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
  */
 gabp_status gabp_get_messages(gabp_handle h, double *P_host, double *mu_host);
 
-/* Message of the last failure on the handle (never NULL; "" when none). */
+/*
+ * gabp_run_rounds without any device allocation.  (The paper has no
+ * counterpart: this is an interface for callers that cannot allocate device
+ * memory when they call -- e.g. while another component records a CUDA
+ * stream capture, or in applications that reserve all device memory up
+ * front, or in loops that must never enter the allocator.)
+ *
+ * Runs exactly `rounds` synchronous FP64 rounds of Alg. 2 from zero messages
+ * on a matrix the caller already holds in device memory and writes the
+ * tentative means after the last round to x_dev, like gabp_run_rounds:
+ *   row_ptr_dev[n+1], col_dev[nnz], val_dev[nnz]: full symmetric CSR with
+ *     the diagonal stored (columns in any order within a row; the caller
+ *     guarantees symmetry, non-zero diagonal and in-range indices -- nothing
+ *     is validated on the device);
+ *   rev_dev[nnz]: reverse-entry permutation, rev[e] = position of (j, i) for
+ *     e = (i, j) (rev of a diagonal entry is itself);
+ *   b_dev[n] in, x_dev[n] out; all FP64 / int device arrays owned by the
+ *   caller; work is issued on `stream` (cudaStream_t, NULL = legacy default)
+ *   and the call returns after synchronising it.
+ * Working space: one fixed array of 2 x 2^18 message pairs (8 MiB) in the
+ * library's static device memory, present on every GPU that loads the
+ * library until the process exits.  nnz above 2^18 = 262144 is rejected
+ * with GABP_ERR_INVALID_ARG (message via gabp_last_error(NULL)).  The call
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ * The first call on each device looks up the array's device address; make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (nothing in it needs to start at zero
+ * except a status word the call clears itself); calls that overlap on the
+ * GPU -- on different streams or host threads -- race on it.
+ * Errors: GABP_ERR_INVALID_ARG, GABP_ERR_BREAKDOWN, GABP_ERR_CUDA.
+ */
+gabp_status gabp_run_rounds_noalloc(int64_t n, int64_t nnz, const int64_t *row_ptr_dev,
+                                    const int32_t *col_dev, const double *val_dev,
+                                    const int64_t *rev_dev, const double *b_dev, int32_t rounds,
+                                    double *x_dev, void *stream);
+
+/* Message of the last failure on the handle (never NULL; "" when none).
+ * With h == NULL: the last failure of gabp_create* or of an entry point
+ * without a handle on this thread. */
 const char *gabp_last_error(gabp_handle h);
 
 /* Name of a status code. */

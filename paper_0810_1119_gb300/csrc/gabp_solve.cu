@@ -46,6 +46,15 @@ struct CudaFail {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+namespace gabp {
+// Message for gabp_last_error(NULL) from entry points that have no handle.
+void set_thread_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace gabp
+
+namespace {
+
 // Device buffer with kPad elements of slack (the staged kernels round their
 // bulk copies up to 16 bytes).
 template <class T>

@@ -35,7 +35,7 @@ EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_str
             "gabp_solve", "gabp_solve_host", "gabp_solve_multi", "gabp_get_stats",
             "gabp_run_rounds", "gabp_get_messages", "gabp_last_error", "gabp_status_string",
             "gabp_version", "gabp_create_batched", "gabp_create_lsq_batched",
-            "gabp_solve_lsq_batched")
+            "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc")
 
 
 class GabpOptions(ctypes.Structure):
@@ -105,6 +105,8 @@ def load(path: str = LIB_PATH):
         "gabp_create_lsq_batched": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int32, i32p, i32p, f64p,
                                                    f64p, ctypes.POINTER(GabpOptions)]),
         "gabp_solve_lsq_batched": (ctypes.c_int, [H, vp, vp, ctypes.c_double, ctypes.c_int32, i32p]),
+        "gabp_run_rounds_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp,
+                                                   ctypes.c_int32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -270,6 +272,19 @@ def gabp_get_messages(h, nnz: int):
     mu = np.empty(nnz)
     _check(h, load().gabp_get_messages(h, _ptr(P, ctypes.c_double), _ptr(mu, ctypes.c_double)))
     return P, mu
+
+
+def gabp_run_rounds_noalloc(row_ptr, col, val, rev, b, rounds: int, x, stream: int | None = None):
+    """FP64 rounds without any device allocation by the library (for callers
+    that cannot allocate): every argument is a device tensor the caller owns
+    (row_ptr int64, col int32, val float64, rev int64, b / x float64)."""
+    n, nnz = b.numel(), val.numel()
+    st = load().gabp_run_rounds_noalloc(
+        n, nnz, _dev_ptr(row_ptr, "torch.int64", n + 1), _dev_ptr(col, "torch.int32", nnz),
+        _dev_ptr(val, "torch.float64"), _dev_ptr(rev, "torch.int64", nnz),
+        _dev_ptr(b, "torch.float64"), int(rounds), _dev_ptr(x, "torch.float64", n),
+        ctypes.c_void_p(current_stream_handle() if stream is None else stream))
+    _check(None, st)
 
 
 def gabp_version() -> str:
