@@ -73,7 +73,10 @@ typedef struct {
   int32_t group_lanes;    /* lanes per row in the sweep kernels (1..32, power of 2); 0 = automatic */
   int32_t autotune;       /* 1 = time the candidate launch shapes once at create and keep the fastest */
   int32_t profile;        /* 1 = bracket every kernel with CUDA events and report the times in gabp_stats */
-  int32_t reserved_i[2];
+  int32_t lsq_form;       /* gabp_create_lsq_batched: 0 = dense bipartite kernels when every
+                             K_s <= 256 and N_s <= 1024, else the general CSR path;
+                             1 = always the general CSR path */
+  int32_t reserved_i;
   double inner_tol;       /* mixed modes: relative accuracy asked of each inner FP32 solve; 0 = 1e-6 */
   void *stream;           /* cudaStream_t used by every call on the handle; NULL = legacy default */
   double damping;         /* gamma in [0, 1): each new message's information P_ij mu_ij becomes

@@ -1,0 +1,573 @@
+// gabp_dense.cu -- Section VII batches in dense bipartite form.
+//
+// The augmented system of Section VII,
+//     [ I_K   S^T ] [x^]   [0]
+//     [ S    -Psi ] [z ] = [y],        S of size N x K,
+// has a complete bipartite graph: every unknown x^_r (r < K) is joined to
+// every z_j (j < N) by the weight S_jr, and no two nodes of the same kind are
+// joined.  Both directed messages of edge (z_j, x^_r) therefore live at the
+// same position (j, r) of an N x K grid laid out like S:
+//     Mz(j, r) = message x^_r -> z_j,      Mx(j, r) = message z_j -> x^_r.
+// One synchronous round of Alg. 2 is then an elementwise map over the grid,
+//     Mz'(j, r) from S_jr, the totals of x^_r and Mx(j, r)   (its reverse),
+//     Mx'(j, r) from S_jr, the totals of z_j  and Mz(j, r),
+// and the totals of the next round are the row sums (z_j) and column sums
+// (x^_r) of the new grid.  There are no index arrays and no scatter: every
+// access is a coalesced run and a sweep streams the grid once.
+//
+// Work mapping: persistent CTAs of 8 warps claim whole systems, largest
+// first, from an atomic counter.  Inside a system, the K columns are cut into
+// chunks of 32 (one lane per column) and the 8 warps split into
+// (chunks, row groups); a warp walks the rows of its group, keeps the column
+// sums of its lanes in registers and adds each row's warp sum into the row
+// total in shared memory.  The node work of a round (totals, tentative means,
+// monitors) runs before the grid pass, from the sums the previous sweep left.
+#include "gabp_internal.h"
+#include "gabp_device.cuh"
+
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
+namespace gabp {
+namespace {
+
+constexpr int kDenseBlock = 256;   // 8 warps
+constexpr int kDenseWarps = kDenseBlock / 32;
+
+template <class T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+template <class T> using T2 = typename V2<T>::t;
+
+template <class T>
+__device__ __forceinline__ T2<T> mk2(T a, T b) {
+  T2<T> v;
+  v.x = a;
+  v.y = b;
+  return v;
+}
+
+__device__ __forceinline__ float rcp(float d) { return 1.0f / d; }
+__device__ __forceinline__ double rcp(double d) { return recip64(d); }
+
+template <class T>
+__device__ __forceinline__ bool bad(T d) {
+  return !(d != T(0)) || !isfinite(d);
+}
+
+// Both directed messages of one grid position.
+template <class T>
+struct Quad {
+  T pz, ez, px, ex;
+};
+
+template <class T> struct FullIO;
+template <> struct FullIO<float> {
+  const float4 *__restrict__ in;
+  float4 *__restrict__ out;
+  __device__ Quad<float> ld(int64_t p) const {
+    const float4 v = __ldcs(in + p);
+    return Quad<float>{v.x, v.y, v.z, v.w};
+  }
+  __device__ void st(int64_t p, const Quad<float> &q) const {
+    __stcs(out + p, make_float4(q.pz, q.ez, q.px, q.ex));
+  }
+};
+template <> struct FullIO<double> {
+  const double2 *__restrict__ inz, *__restrict__ inx;
+  double2 *__restrict__ outz, *__restrict__ outx;
+  __device__ Quad<double> ld(int64_t p) const {
+    const double2 z = __ldcs(inz + p), x = __ldcs(inx + p);
+    return Quad<double>{z.x, z.y, x.x, x.y};
+  }
+  __device__ void st(int64_t p, const Quad<double> &q) const {
+    __stcs(outz + p, make_double2(q.pz, q.ez));
+    __stcs(outx + p, make_double2(q.px, q.ex));
+  }
+};
+
+__device__ __forceinline__ float2 ld_h(const float2 *p) { return __ldcs(p); }
+__device__ __forceinline__ float2 ld_h(const __nv_bfloat162 *p) {
+  return __bfloat1622float2(__ldcs(p));
+}
+__device__ __forceinline__ void st_h(float2 *p, float2 v) { __stcs(p, v); }
+__device__ __forceinline__ void st_h(__nv_bfloat162 *p, float2 v) {
+  __stcs(p, __float22bfloat162_rn(v));
+}
+
+// Column sums run down up to 1024 rows in one lane.  In FP32 they are
+// compensated (Kahan): a plain running sum carries a rounding floor near
+// 1e-5 relative on 512-term columns, which the precision iteration turns into
+// a two-sweep cycle of that size; compensated, the floor is the rounding of
+// the messages themselves (about 2e-7).  FP64 sums need no compensation.
+template <class T>
+struct ColSum {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    if constexpr (sizeof(T) == 8) {
+      s += v;
+    } else {
+      const T y = v - c;
+      const T t = s + y;
+      c = (t - s) - y;
+      s = t;
+    }
+  }
+  __device__ __forceinline__ T value() const { return s - c; }
+};
+
+// Claims the next system (thread 0) and hands its index to the whole CTA.
+__device__ __forceinline__ int32_t claim(Ctl *ctl, int32_t *slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *slot = static_cast<int32_t>(atomicAdd(&ctl->work_next, 1u));
+  __syncthreads();
+  return *slot;
+}
+
+// Warp-to-work split of one system: chunk c of 32 columns and row group g.
+struct Split {
+  int kc, rg, c, g, r;
+  bool warp_on, lane_on;
+};
+__device__ __forceinline__ Split split_of(int K) {
+  Split s;
+  s.kc = (K + 31) >> 5;
+  const int kp = s.kc <= 1 ? 1 : s.kc <= 2 ? 2 : s.kc <= 4 ? 4 : 8;
+  const int w = threadIdx.x >> 5;
+  s.rg = kDenseWarps / kp;
+  s.c = w % kp;
+  s.g = w / kp;
+  s.r = s.c * 32 + (threadIdx.x & 31);
+  s.warp_on = s.c < s.kc;
+  s.lane_on = s.r < K;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Full sweep, T = double (FP64 solves and gabp_run_rounds) or float (mixed
+// modes, with the precision freeze).  Node i of the round: P~_i = A_ii +
+// sumP_i, h~_i = b_i + sumEta_i (A_ii = 1 for x^, -psi for z); the messages
+// of Alg. 2,
+//     P_ij = -S^2 / (P~_i - P_ji),   eta_ij = -S (h~_i - eta_ji) / (P~_i - P_ji).
+// FP32 freeze: c = -S / (P~_i - P_ji) is stored and the first mean-only
+// messages eta_ij = c (h~_i - eta_ji) are written (storage E) instead of full
+// messages.
+// ---------------------------------------------------------------------------
+template <class T, class E>
+__global__ void __launch_bounds__(kDenseBlock)
+dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
+  using V = T2<T>;
+  constexpr bool kF64 = sizeof(T) == 8;
+  __shared__ V tx[kDenseMaxK], tz[kDenseMaxN];   // (P~, h~) of this round
+  __shared__ V ax[kDenseMaxK], az[kDenseMaxN];   // sums of the new messages
+  __shared__ int32_t cur;
+  const int par = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
+  const bool first = ctl->first != 0;
+  bool write_x = false, write_msgs = true, freeze = false;
+  if (kF64) {
+    if (ctl->mode == CTL_ROUNDS) {
+      write_x = ctl->sweeps >= ctl->rounds_target;   // the infer-only pass
+      write_msgs = !write_x;
+    } else {
+      write_x = ctl->write_x != 0;
+    }
+  } else {
+    freeze = ctl->pending_freeze != 0;
+  }
+  const double inv_rn = ctl->inv_rn;
+  const double *__restrict__ b = ctl->b;
+  double *__restrict__ x = ctl->x;
+  const T gam = static_cast<T>(ctl->damping);
+  const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
+                                  : reinterpret_cast<const T *>(d.S32);
+  FullIO<T> io;
+  const V *__restrict__ sum_in;
+  V *__restrict__ sum_out;
+  if constexpr (kF64) {
+    io.inz = par ? d.Mz64[1] : d.Mz64[0];
+    io.inx = par ? d.Mx64[1] : d.Mx64[0];
+    io.outz = par ? d.Mz64[0] : d.Mz64[1];
+    io.outx = par ? d.Mx64[0] : d.Mx64[1];
+    sum_in = par ? d.sum64[1] : d.sum64[0];
+    sum_out = par ? d.sum64[0] : d.sum64[1];
+  } else {
+    io.in = par ? d.M32[1] : d.M32[0];
+    io.out = par ? d.M32[0] : d.M32[1];
+    sum_in = par ? d.sum32[1] : d.sum32[0];
+    sum_out = par ? d.sum32[0] : d.sum32[1];
+  }
+  // freeze outputs: mean messages and their sums go to the other mean buffer
+  E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
+  float *__restrict__ sumE_out = pe ? d.sumE[0] : d.sumE[1];
+  const float2 *__restrict__ mon_prev = pmon ? B.mon32[1] : B.mon32[0];
+  float2 *__restrict__ mon_out = pmon ? B.mon32[0] : B.mon32[1];
+  uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;
+  bool brk = false;
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  for (;;) {
+    const int32_t s = claim(ctl, &cur);
+    if (s >= d.nsys) break;
+    const DenseSys sy = d.sys[s];
+    const int K = sy.K, N = sy.N;
+    // ---- node work of the round ----
+    for (int k = tid; k < K + N; k += kDenseBlock) {
+      const int64_t i = sy.node0 + k;
+      const T aii = k < K ? T(1) : static_cast<T>(-sy.psi);
+      const V sm = first ? mk2<T>(T(0), T(0)) : sum_in[i];
+      T TP, Th;
+      if constexpr (kF64) {
+        TP = aii + sm.x;
+        Th = b[i] + sm.y;
+        if (write_x) x[i] = Th / TP;
+      } else {
+        const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+        TP = aii + sm.x;
+        Th = rhs + sm.y;
+        const float2 prev = first ? make_float2(0.f, 0.f) : mon_prev[i];
+        const float di = Th / TP;
+        mon_out[i] = make_float2(TP, di);
+        mdd = fmax_bits(mdd, di - prev.y);
+        md = fmax_bits(md, di);
+        mdP = fmax_bits(mdP, TP - prev.x);
+        mP = fmax_bits(mP, TP);
+        if (freeze) B.invP32[i] = 1.0f / TP;
+        if (first) B.rhs32[i] = rhs;
+      }
+      if (k < K) { tx[k] = mk2<T>(TP, Th); ax[k] = mk2<T>(T(0), T(0)); }
+      else { tz[k - K] = mk2<T>(TP, Th); az[k - K] = mk2<T>(T(0), T(0)); }
+    }
+    __syncthreads();
+    if (!write_msgs) continue;
+    // ---- grid pass ----
+    const Split w = split_of(K);
+    if (w.warp_on) {
+      const V xr = w.lane_on ? tx[w.r] : mk2<T>(T(1), T(0));
+      ColSum<T> cP, cE;
+      const int64_t base = sy.pair0 + w.r;
+      auto one = [&](int j, T a, const Quad<T> &m) {
+        T rz = T(0), re = T(0);
+        if (w.lane_on) {
+          const int64_t p = base + static_cast<int64_t>(j) * K;
+          const V zj = tz[j];
+          Quad<T> q{T(0), T(0), T(0), T(0)};
+          if (a != T(0)) {
+            const T dz = xr.x - m.px;   // P~_r - P_{z_j -> x_r}: towards z_j
+            const T dx = zj.x - m.pz;   // P~_j - P_{x_r -> z_j}: towards x_r
+            brk |= bad(dz) || bad(dx);
+            const T iz = rcp(dz), ix = rcp(dx);
+            if (!kF64 && freeze) {
+              const T cz = -a * iz, cx = -a * ix;
+              d.C32[p] = make_float2(static_cast<float>(cz), static_cast<float>(cx));
+              q.ez = cz * (xr.y - m.ex);
+              q.ex = cx * (zj.y - m.ez);
+            } else {
+              q.pz = -(a * a) * iz;
+              q.px = -(a * a) * ix;
+              q.ez = -a * (xr.y - m.ex) * iz;
+              q.ex = -a * (zj.y - m.ez) * ix;
+            }
+            if (gam > T(0)) {   // blend the information with its previous value
+              q.ez = gam * m.ez + (T(1) - gam) * q.ez;
+              q.ex = gam * m.ex + (T(1) - gam) * q.ex;
+            }
+          } else if (!kF64 && freeze) {
+            d.C32[p] = make_float2(0.f, 0.f);
+          }
+          if (!kF64 && freeze) {
+            st_h(h_out + p, make_float2(static_cast<float>(q.ez), static_cast<float>(q.ex)));
+          } else {
+            io.st(p, q);
+          }
+          rz = q.pz;
+          re = q.ez;
+          cP.add(q.px);
+          cE.add(q.ex);
+        }
+        rz = group_sum<32>(rz);
+        re = group_sum<32>(re);
+        if (lane == 0) {
+          atomicAdd(&az[j].x, rz);
+          atomicAdd(&az[j].y, re);
+        }
+      };
+      const Quad<T> zero{T(0), T(0), T(0), T(0)};
+      for (int j = w.g; j < N; j += 2 * w.rg) {
+        const int j2 = j + w.rg;
+        T a0 = T(0), a1 = T(0);
+        Quad<T> m0 = zero, m1 = zero;
+        if (w.lane_on) {
+          const int64_t p0 = base + static_cast<int64_t>(j) * K;
+          a0 = __ldcs(Sg + p0);
+          if (!first) m0 = io.ld(p0);
+          if (j2 < N) {
+            const int64_t p1 = p0 + static_cast<int64_t>(w.rg) * K;
+            a1 = __ldcs(Sg + p1);
+            if (!first) m1 = io.ld(p1);
+          }
+        }
+        one(j, a0, m0);
+        if (j2 < N) one(j2, a1, m1);
+      }
+      if (w.lane_on) {
+        atomicAdd(&ax[w.r].x, cP.value());
+        atomicAdd(&ax[w.r].y, cE.value());
+      }
+    }
+    __syncthreads();
+    // ---- sums of the new round ----
+    for (int k = tid; k < K + N; k += kDenseBlock) {
+      const V v = k < K ? ax[k] : az[k - K];
+      if (!kF64 && freeze) sumE_out[sy.node0 + k] = static_cast<float>(v.y);
+      else sum_out[sy.node0 + k] = v;
+    }
+  }
+  if (brk) atomicOr(&red->breakdown, 1);
+  if constexpr (kF64) {
+    last_block_control(ctl, red, CK_SWEEP64);
+  } else {
+    block_max4(widen(mdd), widen(md), widen(mdP), widen(mP), &red->max_dx, &red->max_x,
+               &red->max_dP, &red->max_P);
+    last_block_control(ctl, red, CK_SWEEP32);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mean-only sweep with frozen precisions (FP32 arithmetic; storage E = float2
+// or __nv_bfloat162 per grid position):
+//     eta_z' = c_z (h~_r - eta_x),   eta_x' = c_x (h~_j - eta_z),
+// h~_i = r_i / ||r|| + sumEta_i, d_i = h~_i / P~_i (frozen 1/P~_i).
+// ---------------------------------------------------------------------------
+template <class E>
+__global__ void __launch_bounds__(kDenseBlock)
+dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
+  __shared__ float tx[kDenseMaxK], tz[kDenseMaxN];   // h~ of this round
+  __shared__ float ax[kDenseMaxK], az[kDenseMaxN];   // sums of the new messages
+  __shared__ int32_t cur;
+  const int pe = ctl->par_e, pmon = ctl->par_mon;
+  const bool first = ctl->first != 0;
+  const double inv_rn = ctl->inv_rn;
+  const float gam = static_cast<float>(ctl->damping);
+  const E *__restrict__ h_in = static_cast<const E *>(pe ? d.H[1] : d.H[0]);
+  E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
+  const float *__restrict__ sum_in = pe ? d.sumE[1] : d.sumE[0];
+  float *__restrict__ sum_out = pe ? d.sumE[0] : d.sumE[1];
+  const float2 *__restrict__ mon_prev = pmon ? B.mon32[1] : B.mon32[0];
+  float2 *__restrict__ mon_out = pmon ? B.mon32[0] : B.mon32[1];
+  const float2 *__restrict__ C = d.C32;
+  uint32_t mdd = 0, md = 0;
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  for (;;) {
+    const int32_t s = claim(ctl, &cur);
+    if (s >= d.nsys) break;
+    const DenseSys sy = d.sys[s];
+    const int K = sy.K, N = sy.N;
+    for (int k = tid; k < K + N; k += kDenseBlock) {
+      const int64_t i = sy.node0 + k;
+      const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+      const float Th = rhs + (first ? 0.f : sum_in[i]);
+      const float prev = first ? 0.f : mon_prev[i].y;
+      const float di = Th * B.invP32[i];
+      mon_out[i] = make_float2(0.f, di);
+      mdd = fmax_bits(mdd, di - prev);
+      md = fmax_bits(md, di);
+      if (first) B.rhs32[i] = rhs;
+      if (k < K) { tx[k] = Th; ax[k] = 0.f; }
+      else { tz[k - K] = Th; az[k - K] = 0.f; }
+    }
+    __syncthreads();
+    const Split w = split_of(K);
+    if (w.warp_on) {
+      const float hr = w.lane_on ? tx[w.r] : 0.f;
+      ColSum<float> cE;
+      const int64_t base = sy.pair0 + w.r;
+      auto one = [&](int j, float2 c, float2 h) {
+        float re = 0.f;
+        if (w.lane_on) {
+          const int64_t p = base + static_cast<int64_t>(j) * K;
+          float ez = c.x * (hr - h.y), ex = c.y * (tz[j] - h.x);
+          if (gam > 0.f) {
+            ez = gam * h.x + (1.f - gam) * ez;
+            ex = gam * h.y + (1.f - gam) * ex;
+          }
+          st_h(h_out + p, make_float2(ez, ex));
+          re = ez;
+          cE.add(ex);
+        }
+        re = group_sum<32>(re);
+        if (lane == 0) atomicAdd(&az[j], re);
+      };
+      for (int j = w.g; j < N; j += 2 * w.rg) {
+        const int j2 = j + w.rg;
+        float2 c0 = make_float2(0.f, 0.f), c1 = c0, h0 = c0, h1 = c0;
+        if (w.lane_on) {
+          const int64_t p0 = base + static_cast<int64_t>(j) * K;
+          c0 = __ldcs(C + p0);
+          if (!first) h0 = ld_h(h_in + p0);
+          if (j2 < N) {
+            const int64_t p1 = p0 + static_cast<int64_t>(w.rg) * K;
+            c1 = __ldcs(C + p1);
+            if (!first) h1 = ld_h(h_in + p1);
+          }
+        }
+        one(j, c0, h0);
+        if (j2 < N) one(j2, c1, h1);
+      }
+      if (w.lane_on) atomicAdd(&ax[w.r], cE.value());
+    }
+    __syncthreads();
+    for (int k = tid; k < K + N; k += kDenseBlock)
+      sum_out[sy.node0 + k] = k < K ? ax[k] : az[k - K];
+  }
+  block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
+  last_block_control(ctl, red, CK_MEAN);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual of the augmented systems, r = b - R~ x:
+//     x^ rows:  r_r = b_r - (x_r + sum_j S_jr z_j),
+//     z rows:   r_j = b_j - (sum_r S_jr x_r - psi z_j),
+// with max |r| and, per system, max |r| / ||b_s||_inf.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kDenseBlock)
+dense_residual_kernel(DenseView d, double *__restrict__ r_out, Ctl *ctl, DevScalars *red,
+                      int kind) {
+  __shared__ double vx[kDenseMaxK], vz[kDenseMaxN];
+  __shared__ double ax[kDenseMaxK], az[kDenseMaxN];
+  __shared__ int32_t cur;
+  const double *__restrict__ b = ctl->b;
+  const double *__restrict__ x = ctl->x;
+  unsigned long long mr = 0, mrel = 0;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (;;) {
+    const int32_t s = claim(ctl, &cur);
+    if (s >= d.nsys) break;
+    const DenseSys sy = d.sys[s];
+    const int K = sy.K, N = sy.N;
+    for (int k = tid; k < K + N; k += kDenseBlock) {
+      const double v = x[sy.node0 + k];
+      if (k < K) { vx[k] = v; ax[k] = 0.0; }
+      else { vz[k - K] = v; az[k - K] = 0.0; }
+    }
+    __syncthreads();
+    const Split w = split_of(K);
+    if (w.warp_on) {
+      const double xr = w.lane_on ? vx[w.r] : 0.0;
+      double col = 0.0;
+      const int64_t base = sy.pair0 + w.r;
+      for (int j = w.g; j < N; j += w.rg) {
+        double row = 0.0;
+        if (w.lane_on) {
+          const double a = __ldcs(d.S64 + base + static_cast<int64_t>(j) * K);
+          row = a * xr;
+          col += a * vz[j];
+        }
+        row = group_sum<32>(row);
+        if (lane == 0) atomicAdd(&az[j], row);
+      }
+      if (w.lane_on) atomicAdd(&ax[w.r], col);
+    }
+    __syncthreads();
+    const double bs = dv(d.sys_bmax[sy.orig]);
+    for (int k = tid; k < K + N; k += kDenseBlock) {
+      const int64_t i = sy.node0 + k;
+      const double Ax = k < K ? vx[k] + ax[k] : az[k - K] - sy.psi * vz[k - K];
+      const double ri = b[i] - Ax;
+      if (r_out) r_out[i] = ri;
+      mr = umax(mr, bits(fabs(ri)));
+      mrel = umax(mrel, bits(bs > 0.0 ? fabs(ri) / bs : (ri == 0.0 ? 0.0 : INFINITY)));
+    }
+  }
+  block_max4(mr, mrel, 0, 0, &red->max_r, &red->max_rrel, nullptr, nullptr);
+  last_block_control(ctl, red, kind);
+}
+
+int g_sms = 0;
+std::mutex g_mu;
+std::unordered_map<const void *, int> g_res;
+
+int sms() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+// Persistent grid: every resident CTA slot, but no more CTAs than systems.
+template <class Kern>
+int dense_grid(Kern kernel, int32_t nsys) {
+  int bps = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_res.find(reinterpret_cast<const void *>(kernel));
+    if (it == g_res.end()) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kDenseBlock, 0);
+      bps = std::max(bps, 1);
+      g_res[reinterpret_cast<const void *>(kernel)] = bps;
+    } else {
+      bps = it->second;
+    }
+  }
+  return static_cast<int>(std::max<int64_t>(
+      1, std::min<int64_t>(nsys, static_cast<int64_t>(sms()) * bps)));
+}
+
+}  // namespace
+
+int launch_dense_full64(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  auto k = dense_full_kernel<double, float2>;
+  k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+  return 1;
+}
+
+int launch_dense_full32(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                        bool bf16) {
+  if (bf16) {
+    auto k = dense_full_kernel<float, __nv_bfloat162>;
+    k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+  } else {
+    auto k = dense_full_kernel<float, float2>;
+    k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+  }
+  return 1;
+}
+
+int launch_dense_mean(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                      bool bf16) {
+  if (bf16)
+    dense_mean_kernel<__nv_bfloat162>
+        <<<dense_grid(dense_mean_kernel<__nv_bfloat162>, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl,
+                                                                                        red);
+  else
+    dense_mean_kernel<float2><<<dense_grid(dense_mean_kernel<float2>, d.nsys), kDenseBlock, 0, st>>>(
+        d.v, B, ctl, red);
+  return 1;
+}
+
+int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *ctl,
+                          DevScalars *red, bool refine) {
+  dense_residual_kernel<<<dense_grid(dense_residual_kernel, d.nsys), kDenseBlock, 0, st>>>(
+      d.v, r_out, ctl, red, refine ? CK_REFINE : CK_CHECK64);
+  return 1;
+}
+
+// Caches the occupancy of every dense kernel (done at create time, before
+// any graph is recorded).
+void prepare_dense_kernels(bool bf16) {
+  dense_grid(dense_full_kernel<double, float2>, 1);
+  dense_grid(dense_residual_kernel, 1);
+  if (bf16) {
+    dense_grid(dense_full_kernel<float, __nv_bfloat162>, 1);
+    dense_grid(dense_mean_kernel<__nv_bfloat162>, 1);
+  } else {
+    dense_grid(dense_full_kernel<float, float2>, 1);
+    dense_grid(dense_mean_kernel<float2>, 1);
+  }
+}
+
+}  // namespace gabp

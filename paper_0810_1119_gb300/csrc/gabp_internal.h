@@ -96,9 +96,14 @@ struct Ctl {
   int frozen, pending_freeze;
   int k, stall, sweeps, sweeps_full, sweeps_mean, outer, checks, steps;
   double prev_dd, prev_dP;
+  double best_dd;               // smallest relative change of d in this inner solve
+  int since_best;               // sweeps since best_dd last shrank by 10 %
+  int plateau;                  // > 0: an inner solve also ends after this many such sweeps
+  double floor_dd;              // relative change below which a stall ends an inner solve
   double bnorm, thr, rn, inv_rn, residual;
   int status, done;
   unsigned int blocks_done;     // last-block detection counter
+  unsigned int work_next;       // dense batches: next system to claim (reset by the last block)
   int K;                        // CTL_MULTI: right-hand sides
   const double *Bm;             // CTL_MULTI: n x K right-hand sides (row-major)
   double *Xm;                   // CTL_MULTI: n x K solutions (row-major)
@@ -193,6 +198,62 @@ constexpr int kHeavyDegree = 64;
 // into shared memory: the bulk copies round their ends up to 16 bytes.
 constexpr size_t kPad = 32;
 
+// ---- Section VII batches in dense bipartite form (gabp_dense.cu) ----
+// System s of a batch: K unknowns x^_r, N observations z_j, its N x K grid of
+// edge weights S_jr (row-major, like the S given by the caller) at pairs
+// [pair0, pair0 + N K), its K + N augmented nodes at [node0, node0 + K + N)
+// (x^ first), and its index in the caller's order.
+struct DenseSys {
+  int32_t K, N, orig, pad;
+  int64_t pair0, node0;
+  double psi;
+};
+
+constexpr int kDenseMaxK = 256;    // largest K_s (and N_s) the dense kernels take
+constexpr int kDenseMaxN = 1024;
+
+// Device arrays of the dense form.  Grid position p = pair0 + j K + r holds
+// both directed messages of the edge (z_j, x^_r):
+//   full sweeps:  (Pz, eta_z, Px, eta_x), Pz/eta_z = message x^_r -> z_j and
+//                 Px/eta_x = message z_j -> x^_r;
+//   mean sweeps:  (eta_z, eta_x) with frozen coefficients (c_z, c_x).
+// Per node: the sums over its incoming messages of the round held in the
+// buffer of the same parity (sumP, sum eta).
+struct DenseView {
+  const DenseSys *sys;
+  int32_t nsys;
+  const float *S32;
+  const double *S64;
+  float4 *M32[2];
+  double2 *Mz64[2], *Mx64[2];
+  float2 *C32;
+  void *H[2];                   // float2 or __nv_bfloat162 (eta_z, eta_x)
+  float2 *sum32[2];
+  double2 *sum64[2];
+  float *sumE[2];
+  const int32_t *sys_of_row;
+  unsigned long long *sys_bmax;
+};
+
+struct Dense {
+  int32_t nsys = 0;
+  int64_t pairs = 0, nodes = 0;
+  int32_t maxK = 0, maxN = 0;
+  DenseView v{};
+  DenseSys *sys = nullptr;      // device, largest systems first
+  bool have64 = false, have32 = false;
+};
+
+int launch_dense_full64(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_dense_full32(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                        bool bf16);
+int launch_dense_mean(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                      bool bf16);
+int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *ctl,
+                          DevScalars *red, bool refine);
+int launch_refine_update(int32_t n, cudaStream_t st, Buffers B, Ctl *ctl);
+void prepare_dense_kernels(bool bf16);
+
 // ---- graph builder (gabp_build.cu) ----
 gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr,
                         const int32_t *col, const double *val, const int64_t *rev,
@@ -242,6 +303,7 @@ struct gabp_s {
   int graph_K = 0;                     // K the CTL_MULTI graph was recorded for
   size_t capK = 0;                     // columns the multi buffers hold
   gabp::MultiCols cols{};              // device per-column arrays (capK each)
+  gabp::Dense *dense = nullptr;        // Section VII batches in dense bipartite form
   cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
 
   // profiling (gabp_options.profile): pairs of events around kernels

@@ -32,6 +32,7 @@
 // next phase, and -- inside a solve graph -- sets the graph's WHILE and SWITCH
 // conditions.
 #include "gabp_internal.h"
+#include "gabp_device.cuh"
 
 #include <algorithm>
 #include <cfloat>
@@ -41,82 +42,6 @@
 
 namespace gabp {
 namespace {
-
-__device__ __forceinline__ unsigned long long bits(double v) {
-  return static_cast<unsigned long long>(__double_as_longlong(v));
-}
-
-__device__ __forceinline__ double dv(unsigned long long u) {
-  return __longlong_as_double(static_cast<long long>(u));
-}
-
-__device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) {
-  return a > b ? a : b;
-}
-
-// Running maximum of |v| for FP32 values, kept as the bit pattern of the
-// non-negative float (NaN compares above +inf); widened to the FP64 bit
-// pattern once per thread for the block reduction.
-__device__ __forceinline__ uint32_t fmax_bits(uint32_t m, float v) {
-  const uint32_t u = __float_as_uint(fabsf(v));
-  return u > m ? u : m;
-}
-__device__ __forceinline__ unsigned long long widen(uint32_t m) {
-  return bits(static_cast<double>(__uint_as_float(m)));
-}
-
-__device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = umax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Block-wide maximum of up to four non-negative values (as bit patterns),
-// committed with one atomicMax per value and block by thread 0.  Every thread
-// of the block must call it.
-__device__ void block_max4(unsigned long long v0, unsigned long long v1, unsigned long long v2,
-                           unsigned long long v3, unsigned long long *d0, unsigned long long *d1,
-                           unsigned long long *d2, unsigned long long *d3) {
-  __shared__ unsigned long long sm[4][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  v0 = warp_max(v0); v1 = warp_max(v1); v2 = warp_max(v2); v3 = warp_max(v3);
-  if (lane == 0) { sm[0][w] = v0; sm[1][w] = v1; sm[2][w] = v2; sm[3][w] = v3; }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    unsigned long long u[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) u[k] = warp_max(lane < nw ? sm[k][lane] : 0ull);
-    if (lane == 0) {
-      if (d0 && u[0]) atomicMax(d0, u[0]);
-      if (d1 && u[1]) atomicMax(d1, u[1]);
-      if (d2 && u[2]) atomicMax(d2, u[2]);
-      if (d3 && u[3]) atomicMax(d3, u[3]);
-    }
-  }
-}
-
-template <int G, class T>
-__device__ __forceinline__ T group_sum(T v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Block-wide sum (all threads call it; every thread gets the result).
-template <class T>
-__device__ T block_sum(T v) {
-  __shared__ T part[32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) part[w] = v;
-  __syncthreads();
-  T tot = T(0);
-  for (int k = 0; k < nw; ++k) tot += part[k];
-  return tot;
-}
 
 // Warp sum by key over 32 consecutive slots whose keys (tile-local row ids)
 // do not decrease along the lanes: a doubling scan that only adds a partner
@@ -151,240 +76,6 @@ __device__ __forceinline__ float ld_eta(const __nv_bfloat16 *p) { return __bfloa
 __device__ __forceinline__ void st_eta(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_eta(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
-// ---------------------------------------------------------------------------
-// Controller (one thread of the last block of a controlling launch).
-// ---------------------------------------------------------------------------
-enum CtrlKind { CK_INIT = 1, CK_SWEEP64, CK_CHECK64, CK_SWEEP32, CK_MEAN, CK_REFINE, CK_INITK,
-                CK_MEANK, CK_REFINEK };
-
-__device__ void finish(Ctl &c, int status) {
-  c.status = status;
-  c.done = 1;
-  c.phase = PH_DONE;
-}
-
-__device__ bool diverged(double rn, double bnorm) {
-  return !isfinite(rn) || rn > 1e30 * fmax(bnorm, DBL_MIN);
-}
-
-// Reductions are read through volatile loads (they were committed by other
-// blocks' atomics) and zeroed once consumed.
-__device__ void control(Ctl &c, DevScalars *red, int kind) {
-  volatile DevScalars *r = red;
-  c.steps++;
-  if (r->timeout) {
-    finish(c, GABP_ERR_TIMEOUT);
-    kind = 0;
-  }
-  switch (kind) {
-    case CK_INIT: {
-      c.bnorm = dv(r->max_b);
-      r->max_b = 0;
-      c.thr = c.rel ? c.tol * c.bnorm : c.tol;
-      c.residual = c.bnorm;
-      if (!isfinite(c.bnorm)) { finish(c, GABP_ERR_INVALID_ARG); break; }
-      if (c.mode == CTL_FP64) {
-        c.phase = PH_FULL64;
-        c.write_x = (c.check_every <= 1) || (c.max_iter <= 1);
-      } else if (c.mode == CTL_PREC) {
-        // precisions only: zero right-hand side, unit scale
-        c.rn = 1.0;
-        c.inv_rn = 1.0;
-        c.outer = 1;
-        c.phase = PH_FULL32;
-      } else {
-        c.rn = c.bnorm;
-        if (c.rn < c.thr || c.bnorm == 0.0) { finish(c, GABP_OK); break; }
-        c.inv_rn = 1.0 / c.rn;
-        c.outer = 1;
-        c.phase = c.frozen ? PH_MEAN : PH_FULL32;
-      }
-      break;
-    }
-    case CK_SWEEP64: {
-      if (c.mode == CTL_ROUNDS) {
-        // the pass after `rounds_target` sweeps only infers and leaves the
-        // state alone, so the last round's messages stay in m64[par_m]
-        if (c.sweeps < c.rounds_target) { c.sweeps++; c.par_m ^= 1; c.first = 0; }
-        break;
-      }
-      c.sweeps++;
-      c.sweeps_full++;
-      c.par_m ^= 1;
-      c.first = 0;
-      if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
-      if (c.write_x) c.phase = PH_CHECK64;
-      const int next = c.sweeps + 1;
-      c.write_x = (next % c.check_every == 0) || next >= c.max_iter;
-      break;
-    }
-    case CK_CHECK64:
-    case CK_REFINE: {
-      c.checks++;
-      const double rn = dv(r->max_r), rrel = dv(r->max_rrel);
-      r->max_r = 0;
-      r->max_rrel = 0;
-      c.residual = rn;
-      if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
-      // batched handles: every system meets its own relative rule
-      const bool met = c.batched ? (c.rel ? rrel < c.tol : rn < c.tol) : rn < c.thr;
-      if (met) { finish(c, GABP_OK); break; }
-      if (diverged(rn, c.bnorm)) { finish(c, GABP_ERR_DIVERGED); break; }
-      if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
-      if (kind == CK_CHECK64) { c.phase = PH_FULL64; break; }
-      // next refinement step: solve A d = r / ||r|| from zero mean messages
-      c.outer++;
-      c.rn = rn;
-      c.inv_rn = 1.0 / rn;
-      c.k = 0;
-      c.stall = 0;
-      c.prev_dd = INFINITY;
-      c.prev_dP = INFINITY;
-      c.first = 1;
-      c.phase = c.frozen ? PH_MEAN : PH_FULL32;
-      break;
-    }
-    case CK_SWEEP32:
-    case CK_MEAN: {
-      if (kind == CK_SWEEP32) {
-        c.sweeps_full++;
-        if (c.pending_freeze) { c.frozen = 1; c.pending_freeze = 0; c.par_e ^= 1; }
-        else c.par_m ^= 1;
-      } else {
-        c.sweeps_mean++;
-        c.par_e ^= 1;
-      }
-      if (c.mode == CTL_PREC && c.frozen) {
-        c.sweeps++;
-        if (r->breakdown) finish(c, GABP_ERR_BREAKDOWN);
-        else finish(c, GABP_OK);
-        break;
-      }
-      c.par_mon ^= 1;
-      c.first = 0;
-      c.sweeps++;
-      c.k++;
-      const double mx = dv(r->max_x), mdx = dv(r->max_dx);
-      const double mP = dv(r->max_P), mdP = dv(r->max_dP);
-      r->max_x = 0; r->max_dx = 0; r->max_P = 0; r->max_dP = 0;
-      if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
-      const double dd = mdx / fmax(mx, DBL_MIN);
-      if (!isfinite(dd)) { finish(c, GABP_ERR_DIVERGED); break; }
-      if (kind == CK_SWEEP32 && !c.frozen && !c.pending_freeze) {
-        // Precision convergence: relative change of the node precisions,
-        // remaining error extrapolated with the observed contraction rate.
-        const double dP = mdP / fmax(mP, DBL_MIN);
-        const double rho = dP / c.prev_dP;
-        const double errP = dP == 0.0 ? 0.0 : (rho < 1.0 ? dP * rho / (1.0 - rho) : INFINITY);
-        if (c.k >= 3 && (errP < 1e-6 || dP < 1e-7 || (rho >= 1.0 && dP < 1e-5))) c.pending_freeze = 1;
-        c.prev_dP = dP;
-      }
-      const double rho_d = dd / c.prev_dd;
-      const double err_d = dd == 0.0 ? 0.0 : (rho_d < 1.0 ? dd * rho_d / (1.0 - rho_d) : INFINITY);
-      c.stall = rho_d >= 1.0 ? c.stall + 1 : 0;
-      c.prev_dd = dd;
-      const bool inner_done =
-          c.frozen && c.k >= 3 && (err_d < c.inner_tol || (c.stall >= 2 && dd < 1e-4));
-      if (inner_done || c.sweeps >= c.max_iter) c.phase = PH_REFINE;
-      else c.phase = c.frozen ? PH_MEAN : PH_FULL32;
-      break;
-    }
-    case CK_INITK: {
-      // per-column ||b_k||, thresholds and scales
-      double worst = 0.0;
-      bool all_done = true, bad = false;
-      for (int k = 0; k < c.K; ++k) {
-        const double bn = dv(c.cols.bmax[k]);
-        c.cols.bmax[k] = 0;
-        c.cols.bnorm[k] = bn;
-        c.cols.thr[k] = c.rel ? c.tol * bn : c.tol;
-        c.cols.rn[k] = bn;
-        c.cols.inv_rn[k] = bn > 0.0 ? 1.0 / bn : 0.0;
-        bad |= !isfinite(bn);
-        all_done &= bn < c.cols.thr[k] || bn == 0.0;
-        worst = fmax(worst, bn);
-      }
-      c.bnorm = worst;
-      c.residual = worst;
-      if (bad) { finish(c, GABP_ERR_INVALID_ARG); break; }
-      if (all_done) { finish(c, GABP_OK); break; }
-      c.outer = 1;
-      c.first = 1;
-      c.phase = PH_MEANK;
-      break;
-    }
-    case CK_MEANK: {
-      c.sweeps_mean++;
-      c.par_e ^= 1;
-      c.first = 0;
-      c.sweeps++;
-      c.k++;
-      const double mx = dv(r->max_x), mdx = dv(r->max_dx);
-      r->max_x = 0; r->max_dx = 0;
-      const double dd = mdx / fmax(mx, DBL_MIN);
-      if (!isfinite(dd)) { finish(c, GABP_ERR_DIVERGED); break; }
-      const double rho_d = dd / c.prev_dd;
-      const double err_d = dd == 0.0 ? 0.0 : (rho_d < 1.0 ? dd * rho_d / (1.0 - rho_d) : INFINITY);
-      c.stall = rho_d >= 1.0 ? c.stall + 1 : 0;
-      c.prev_dd = dd;
-      const bool inner_done = c.k >= 3 && (err_d < c.inner_tol || (c.stall >= 2 && dd < 1e-4));
-      c.phase = (inner_done || c.sweeps >= c.max_iter) ? PH_REFINEK : PH_MEANK;
-      break;
-    }
-    case CK_REFINEK: {
-      c.checks++;
-      double worst = 0.0;
-      bool all_done = true, bad = false;
-      for (int k = 0; k < c.K; ++k) {
-        const double rn = dv(c.cols.rmax[k]);
-        c.cols.rmax[k] = 0;
-        c.cols.rn[k] = rn;
-        c.cols.inv_rn[k] = rn > 0.0 ? 1.0 / rn : 0.0;
-        all_done &= rn < c.cols.thr[k];
-        bad |= diverged(rn, c.cols.bnorm[k]);
-        worst = fmax(worst, rn);
-      }
-      c.residual = worst;
-      if (all_done) { finish(c, GABP_OK); break; }
-      if (bad) { finish(c, GABP_ERR_DIVERGED); break; }
-      if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
-      c.outer++;
-      c.k = 0;
-      c.stall = 0;
-      c.prev_dd = INFINITY;
-      c.first = 1;
-      c.phase = PH_MEANK;
-      break;
-    }
-  }
-  // Hard bound on controller steps: the loop ends even if a rule misfires.
-  if (!c.done && c.mode != CTL_ROUNDS && c.steps > 4 * c.max_iter + 64)
-    finish(c, GABP_ERR_NOT_CONVERGED);
-  if (c.in_graph) {
-    cudaGraphSetConditional(c.h_phase, c.done ? 0u : static_cast<unsigned>(c.phase));
-    cudaGraphSetConditional(c.h_while, c.done ? 0u : 1u);
-  }
-}
-
-// Called by every thread at the end of a controlling launch.  No waiting:
-// each block bumps a counter after its atomics; the block that brings it to
-// gridDim.x runs the controller.
-__device__ void last_block_control(Ctl *ctl, DevScalars *red, int kind) {
-  __shared__ int is_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(&ctl->blocks_done, 1u);
-    is_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (is_last && threadIdx.x == 0) {
-    __threadfence();
-    ctl->blocks_done = 0;
-    control(*ctl, red, kind);
-    __threadfence();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Solve set-up: ||b||_inf; in the mixed modes also x = 0 and r = b.
@@ -466,19 +157,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
           dst),
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
-}
-// L2 eviction policies (createpolicy): the once-per-sweep streams (A, c, rev,
-// row pointers) are loaded evict-first so that the message buffers, which are
-// read back on the next sweep, stay resident in the 126 MB L2.
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_last() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
 }
 __device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uint32_t bytes,
                                               uint32_t bar, uint64_t policy) {
@@ -584,17 +262,6 @@ __device__ bool run_tiles(int32_t ntiles, unsigned char *smem, uint32_t stage_by
   return ok;
 }
 
-// 1/d in FP64: an FP32 reciprocal seed (relative error e0 < 2^-22), then the
-// cubic Newton-Raphson step y (1 + e + e^2) with e = 1 - d y, whose error is
-// e0^3 < 2^-66 before rounding.  Outside the FP32 normal range (or for
-// zero / non-finite d) the IEEE division is used.
-__device__ __forceinline__ double recip64(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
-  const double y = static_cast<double>(__frcp_rn(static_cast<float>(d)));
-  const double e = fma(-d, y, 1.0);
-  return fma(y, fma(e, e, e), y);
-}
 
 // ---------------------------------------------------------------------------
 // FP64 full sweep: new (P, eta) for every directed edge, plus (when asked)
@@ -1523,6 +1190,11 @@ int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars
 int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
   (void)B;
   return launch_residual(g, st, nullptr, ctl, red, CK_CHECK64);
+}
+
+int launch_refine_update(int32_t n, cudaStream_t st, Buffers B, Ctl *ctl) {
+  refine_update_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, B, ctl);
+  return 1;
 }
 
 int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {

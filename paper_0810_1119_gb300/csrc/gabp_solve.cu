@@ -91,8 +91,44 @@ void ensure_common(gabp_handle h) {
   if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 }
 
+// Dense Section VII batches: grid-sized message buffers and node sums.
+void ensure_dense64(gabp_handle h) {
+  Dense &d = *h->dense;
+  if (d.have64) return;
+  DenseView &v = d.v;
+  for (int k = 0; k < 2; ++k) {
+    ensure(&v.Mz64[k], d.pairs);
+    ensure(&v.Mx64[k], d.pairs);
+    ensure(&v.sum64[k], d.nodes);
+  }
+  d.have64 = true;
+}
+
+void ensure_dense32(gabp_handle h) {
+  Dense &d = *h->dense;
+  if (d.have32) return;
+  DenseView &v = d.v;
+  Buffers &B = h->buf;
+  const size_t hb = (d.pairs + kPad) * (is_bf16(h) ? sizeof(__nv_bfloat162) : sizeof(float2));
+  for (int k = 0; k < 2; ++k) {
+    ensure(&v.M32[k], d.pairs);
+    ensure(&v.sum32[k], d.nodes);
+    ensure(&v.sumE[k], d.nodes);
+    CK(cudaMalloc(&v.H[k], hb));
+    CK(cudaMemset(v.H[k], 0, hb));
+  }
+  ensure(&v.C32, d.pairs);
+  const size_t n = h->g.n;
+  ensure(&B.invP32, n);
+  ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
+  ensure(&B.r64, n);
+  ensure(&B.rhs32, n);
+  d.have32 = true;
+}
+
 void ensure64(gabp_handle h) {
   ensure_common(h);
+  if (h->dense) { ensure_dense64(h); return; }
   if (h->have64) return;
   ensure(&h->buf.m64[0], h->g.E);
   ensure(&h->buf.m64[1], h->g.E);
@@ -101,6 +137,7 @@ void ensure64(gabp_handle h) {
 
 void ensure32(gabp_handle h) {
   ensure_common(h);
+  if (h->dense) { ensure_dense32(h); return; }
   if (h->have32) return;
   const size_t n = h->g.n, E = h->g.E;
   Buffers &B = h->buf;
@@ -161,6 +198,19 @@ void run(gabp_handle h, int kind, F &&f) {
 // Kernels of one phase on stream st (used by both drivers).
 int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
   const Graph &g = h->g;
+  if (h->dense) {
+    const Dense &d = *h->dense;
+    switch (phase) {
+      case PH_FULL64: return launch_dense_full64(d, st, h->buf, h->ctl, h->red);
+      case PH_CHECK64: return launch_dense_residual(d, st, nullptr, h->ctl, h->red, false);
+      case PH_FULL32: return launch_dense_full32(d, st, h->buf, h->ctl, h->red, is_bf16(h));
+      case PH_MEAN: return launch_dense_mean(d, st, h->buf, h->ctl, h->red, is_bf16(h));
+      case PH_REFINE:
+        return launch_refine_update(g.n, st, h->buf, h->ctl) +
+               launch_dense_residual(d, st, h->buf.r64, h->ctl, h->red, true);
+    }
+    return 0;
+  }
   switch (phase) {
     case PH_FULL64: return launch_sweep64(g, st, h->buf, h->ctl, h->red);
     case PH_CHECK64: return launch_check64(g, st, h->buf, h->ctl, h->red);
@@ -271,6 +321,11 @@ void init_ctl(gabp_handle h, int mode, const double *b, double *x, double tol, i
   }
   c.first = 1;
   c.prev_dd = std::numeric_limits<double>::infinity();
+  c.best_dd = std::numeric_limits<double>::infinity();
+  // BF16 mean messages carry ~3 significant digits: inner solves level off
+  // near 1e-2 relative change, where the refinement takes over
+  c.floor_dd = is_bf16(h) ? 3e-2 : 1e-4;
+  c.plateau = is_bf16(h) ? 16 : 0;
   c.prev_dP = std::numeric_limits<double>::infinity();
   c.status = GABP_ERR_NOT_CONVERGED;
 }
@@ -474,9 +529,103 @@ void release(gabp_handle h) {
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   cudaFree(h->lsq_K); cudaFree(h->lsq_aug_off); cudaFree(h->lsq_y_off); cudaFree(h->lsq_x_off);
   cudaFree(h->lsq_rhs); cudaFree(h->lsq_x);
+  if (h->dense) {
+    DenseView &v = h->dense->v;
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(v.M32[k]); cudaFree(v.Mz64[k]); cudaFree(v.Mx64[k]); cudaFree(v.H[k]);
+      cudaFree(v.sum32[k]); cudaFree(v.sum64[k]); cudaFree(v.sumE[k]);
+    }
+    cudaFree(v.C32);
+    cudaFree(const_cast<float *>(v.S32));
+    cudaFree(const_cast<double *>(v.S64));
+    cudaFree(h->dense->sys);
+    delete h->dense;
+    h->dense = nullptr;
+  }
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
+}
+
+// Dense bipartite form of a Section VII batch: S uploaded as given (row-major
+// N_s x K_s per system, which is the grid layout of the dense kernels) in FP64
+// for the residual and FP32 for the sweeps; systems listed largest first so
+// that the CTAs that claim them finish together.
+void build_dense(gabp_handle h, int32_t nsys, const int32_t *K, const int32_t *N, const double *S,
+                 const double *psi, const std::vector<int64_t> &node_off) {
+  Dense *d = new Dense;
+  h->dense = d;
+  std::vector<DenseSys> sys(nsys);
+  int64_t pairs = 0, nodes = 0;
+  for (int32_t s = 0; s < nsys; ++s) {
+    sys[s] = DenseSys{K[s], N[s], s, 0, pairs, nodes, psi[s]};
+    pairs += static_cast<int64_t>(K[s]) * N[s];
+    nodes += K[s] + N[s];
+    d->maxK = std::max(d->maxK, K[s]);
+    d->maxN = std::max(d->maxN, N[s]);
+  }
+  int64_t nnz = 0;
+  std::vector<float> S32(pairs);
+  for (int64_t p = 0; p < pairs; ++p) {
+    S32[p] = static_cast<float>(S[p]);
+    nnz += S[p] != 0.0;
+  }
+  std::stable_sort(sys.begin(), sys.end(), [](const DenseSys &a, const DenseSys &b) {
+    return static_cast<int64_t>(a.K) * a.N > static_cast<int64_t>(b.K) * b.N;
+  });
+  std::vector<int32_t> sys_of_row(nodes);
+  for (int32_t s = 0; s < nsys; ++s)
+    for (int64_t i = node_off[s]; i < node_off[s + 1]; ++i) sys_of_row[i] = s;
+  d->nsys = nsys;
+  d->pairs = pairs;
+  d->nodes = nodes;
+  Graph &g = h->g;
+  g.n = static_cast<int32_t>(nodes);
+  g.E = 2 * nnz;
+  g.nsys = nsys;
+  g.h_sys_row_off = node_off;
+  cudaStream_t st = h->stream;
+  CK(cudaMalloc(reinterpret_cast<void **>(&g.sys_of_row), sizeof(int32_t) * nodes));
+  CK(cudaMemcpyAsync(g.sys_of_row, sys_of_row.data(), sizeof(int32_t) * nodes,
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMalloc(reinterpret_cast<void **>(&g.sys_bmax), sizeof(unsigned long long) * nsys));
+  CK(cudaMemsetAsync(g.sys_bmax, 0, sizeof(unsigned long long) * nsys, st));
+  CK(cudaMalloc(reinterpret_cast<void **>(&d->sys), sizeof(DenseSys) * nsys));
+  CK(cudaMemcpyAsync(d->sys, sys.data(), sizeof(DenseSys) * nsys, cudaMemcpyHostToDevice, st));
+  float *S32d = nullptr;
+  double *S64d = nullptr;
+  ensure(&S32d, pairs);
+  ensure(&S64d, pairs);
+  d->v.S32 = S32d;   // owned by the handle from here on
+  d->v.S64 = S64d;
+  CK(cudaMemcpyAsync(S32d, S32.data(), sizeof(float) * pairs, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(S64d, S, sizeof(double) * pairs, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  d->v.sys = d->sys;
+  d->v.nsys = nsys;
+  d->v.sys_of_row = g.sys_of_row;
+  d->v.sys_bmax = g.sys_bmax;
+  prepare_dense_kernels(is_bf16(h));
+}
+
+// A handle with validated options and no matrix yet.
+gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
+  gabp_handle h = new (std::nothrow) gabp_s;
+  if (!h) return GABP_ERR_OOM;
+  if (opt) h->opt = *opt; else gabp_default_options(&h->opt);
+  if (h->opt.precision < GABP_PREC_FP64 || h->opt.precision > GABP_PREC_MIXED_BF16) {
+    delete h;
+    g_create_error = "unknown precision mode";
+    return GABP_ERR_INVALID_ARG;
+  }
+  if (!(h->opt.damping >= 0.0 && h->opt.damping < 1.0)) {
+    delete h;
+    g_create_error = "damping must lie in [0, 1)";
+    return GABP_ERR_INVALID_ARG;
+  }
+  h->stream = static_cast<cudaStream_t>(h->opt.stream);
+  *out = h;
+  return GABP_OK;
 }
 
 }  // namespace
@@ -497,20 +646,8 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
   if (!out) return GABP_ERR_INVALID_ARG;
   *out = nullptr;
   g_create_error.clear();
-  gabp_handle h = new (std::nothrow) gabp_s;
-  if (!h) return GABP_ERR_OOM;
-  if (opt) h->opt = *opt; else gabp_default_options(&h->opt);
-  if (h->opt.precision < GABP_PREC_FP64 || h->opt.precision > GABP_PREC_MIXED_BF16) {
-    delete h;
-    g_create_error = "unknown precision mode";
-    return GABP_ERR_INVALID_ARG;
-  }
-  if (!(h->opt.damping >= 0.0 && h->opt.damping < 1.0)) {
-    delete h;
-    g_create_error = "damping must lie in [0, 1)";
-    return GABP_ERR_INVALID_ARG;
-  }
-  h->stream = static_cast<cudaStream_t>(h->opt.stream);
+  gabp_handle h = nullptr;
+  if (const gabp_status s0 = new_handle(opt, &h); s0 != GABP_OK) return s0;
   h->user_nnz = nnz;
   gabp_status s = guarded(h, [&] {
     std::string msg;
@@ -594,18 +731,43 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
       g_create_error = "gabp_create_lsq_batched: K_s, N_s >= 1 and psi_s > 0 required";
       return GABP_ERR_INVALID_ARG;
     }
-  std::vector<int64_t> row_ptr, sys_off;
-  std::vector<int32_t> col;
-  std::vector<double> val;
-  try {
-    build_lsq_csr(nsys, K_host, N_host, S_host, psi_host, row_ptr, col, val, sys_off);
-  } catch (const std::bad_alloc &) {
-    return GABP_ERR_OOM;
-  }
+  bool dense = !opt || opt->lsq_form == 0;
+  for (int32_t s = 0; s < nsys && dense; ++s)
+    dense = K_host[s] <= kDenseMaxK && N_host[s] <= kDenseMaxN;
   gabp_handle h = nullptr;
-  gabp_status s = gabp_create_batched(&h, nsys, sys_off.data(), static_cast<int64_t>(col.size()),
-                                      row_ptr.data(), col.data(), val.data(), opt);
-  if (s != GABP_OK) return s;
+  gabp_status s = GABP_OK;
+  std::vector<int64_t> sys_off(1, 0);
+  if (dense) {
+    int64_t nodes = 0;
+    for (int32_t k = 0; k < nsys; ++k) sys_off.push_back(nodes += K_host[k] + N_host[k]);
+    if (nodes >= (int64_t{1} << 31) - 64) {
+      g_create_error = "gabp_create_lsq_batched: more than 2^31 - 64 unknowns";
+      return GABP_ERR_INVALID_ARG;
+    }
+    s = new_handle(opt, &h);
+    if (s != GABP_OK) return s;
+    s = guarded(h, [&] {
+      build_dense(h, nsys, K_host, N_host, S_host, psi_host, sys_off);
+      return GABP_OK;
+    });
+    if (s != GABP_OK) {
+      g_create_error = h->last_error;
+      gabp_destroy(h);
+      return s;
+    }
+  } else {
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+    std::vector<double> val;
+    try {
+      build_lsq_csr(nsys, K_host, N_host, S_host, psi_host, row_ptr, col, val, sys_off);
+    } catch (const std::bad_alloc &) {
+      return GABP_ERR_OOM;
+    }
+    s = gabp_create_batched(&h, nsys, sys_off.data(), static_cast<int64_t>(col.size()),
+                            row_ptr.data(), col.data(), val.data(), opt);
+    if (s != GABP_OK) return s;
+  }
   s = guarded(h, [&] {
     std::vector<int64_t> y_off(nsys + 1, 0), x_off(nsys + 1, 0);
     for (int32_t k = 0; k < nsys; ++k) {
@@ -701,9 +863,11 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
   if (!h) return GABP_ERR_INVALID_ARG;
   if (!B_dev || !X_dev || nrhs < 1 || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: invalid argument");
-  if (h->opt.precision != GABP_PREC_FP64 && nrhs > 256)
+  // dense Section VII batches solve the columns one after another
+  const bool shared_precisions = h->opt.precision != GABP_PREC_FP64 && !h->dense;
+  if (shared_precisions && nrhs > 256)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: at most 256 right-hand sides per call");
-  if (h->opt.precision != GABP_PREC_FP64)
+  if (shared_precisions)
     return guarded(h, [&] { return solve_multi_mixed(h, B_dev, X_dev, nrhs, tol, max_iter, iters); });
   return guarded(h, [&] {
     const int64_t n = h->g.n;
@@ -747,7 +911,10 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
     CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
     // `rounds` message sweeps, then one pass that only writes the means.
-    for (int32_t t = 0; t <= rounds; ++t) launch_sweep64(h->g, st, h->buf, h->ctl, h->red);
+    for (int32_t t = 0; t <= rounds; ++t) {
+      if (h->dense) launch_dense_full64(*h->dense, st, h->buf, h->ctl, h->red);
+      else launch_sweep64(h->g, st, h->buf, h->ctl, h->red);
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     DevScalars red{};
@@ -761,6 +928,9 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
 
 gabp_status gabp_get_messages(gabp_handle h, double *P_host, double *mu_host) {
   if (!h || !P_host || !mu_host) return GABP_ERR_INVALID_ARG;
+  if (h->dense)
+    return fail(h, GABP_ERR_INVALID_ARG,
+                "gabp_get_messages: a dense Section VII batch has no caller CSR to lay messages out on");
   return guarded(h, [&] {
     const Graph &g = h->g;
     std::memset(P_host, 0, sizeof(double) * h->user_nnz);

@@ -42,7 +42,7 @@ class GabpOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("residual_kind", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("reserved_i", ctypes.c_int32 * 2),
+                ("lsq_form", ctypes.c_int32), ("reserved_i", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("damping", ctypes.c_double), ("reserved_d", ctypes.c_double * 3)]
 
