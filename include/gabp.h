@@ -70,19 +70,26 @@ typedef struct {
   int32_t precision;      /* gabp_precision */
   int32_t residual_kind;  /* gabp_residual_kind */
   int32_t check_every;    /* sweeps between convergence checks; 0 = automatic */
-  int32_t group_lanes;    /* lanes per row in the sweep kernels (1..32, power of 2); 0 = automatic */
-  int32_t autotune;       /* 1 = time the candidate launch shapes once at create and keep the fastest */
+  int32_t group_lanes;    /* lanes per row of the FP64 sweep (2..32, power of 2); 0 = automatic */
+  int32_t autotune;       /* 1 = time the candidate launch shapes once at create and keep the
+                             fastest (see gabp_get_tuning); dimensions pinned below stay pinned */
   int32_t profile;        /* 1 = bracket every kernel with CUDA events and report the times in gabp_stats */
   int32_t lsq_form;       /* gabp_create_lsq_batched: 0 = dense bipartite kernels when every
                              K_s <= 256 and N_s <= 1024, else the general CSR path;
                              1 = always the general CSR path */
-  int32_t reserved_i;
+  int32_t tile_slots;     /* CSR form: slots per row tile of the FP32 sweeps (32..1024); 0 = 1024 */
   double inner_tol;       /* mixed modes: relative accuracy asked of each inner FP32 solve; 0 = 1e-6 */
   void *stream;           /* cudaStream_t used by every call on the handle; NULL = legacy default */
   double damping;         /* gamma in [0, 1): each new message's information P_ij mu_ij becomes
                              gamma * previous + (1 - gamma) * new (precisions undamped); a fixed
                              point is unchanged.  0 = the plain rule of Alg. 2. */
-  double reserved_d[3];
+  int32_t tile_rows;      /* CSR form: rows per row tile (1..256); 0 = 256 */
+  int32_t heavy_degree;   /* CSR form: a tile holding a row of higher degree runs slot-parallel
+                             instead of thread-per-row (>= 1); 0 = 64 */
+  int32_t dense_rows;     /* dense Section VII form: grid rows each warp loads ahead in the FP32
+                             sweeps (1, 2 or 4); 0 = 2 */
+  int32_t reserved_i;
+  double reserved_d;
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */
@@ -222,6 +229,35 @@ gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *x
 
 /* Statistics of the last solve on the handle. */
 gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats);
+
+/*
+ * Launch shapes of a handle.  (The paper has no counterpart: these choices
+ * belong to the GPU mapping of the Alg. 2 sweep.)  With
+ * gabp_options.autotune = 1, gabp_create* times the candidates on the
+ * handle's own matrix, with zero messages, and keeps the fastest:
+ *   CSR form, mixed precisions: the degree above which a row tile runs
+ *     slot-parallel ("heavy") instead of thread-per-row (16, 32, 64, 128 or
+ *     never), then the tile shape (slots x rows: 1024 x 256, 512 x 256,
+ *     512 x 128, 256 x 64), scored by 4 mean sweeps + 1 full sweep;
+ *   CSR form, FP64: lanes per row of the FP64 sweep (2 .. 32);
+ *   dense Section VII form, mixed precisions: grid rows each warp loads
+ *     ahead (1, 2 or 4) in the mean sweep and in the full sweep.
+ * Without autotune the defaults are reported (tuned = 0).
+ */
+typedef struct {
+  int32_t tuned;            /* 1 = chosen by timing at create */
+  int32_t candidates;       /* launch shapes timed */
+  int32_t tile_slots;       /* CSR form: slots per row tile (FP32 sweeps, residual) */
+  int32_t tile_rows;        /* CSR form: rows per row tile */
+  int32_t heavy_degree;     /* CSR form: tiles with a row above this degree run slot-parallel */
+  int32_t group_lanes;      /* CSR form: lanes per row of the FP64 sweep */
+  int32_t dense_rows_mean;  /* dense form: grid rows loaded ahead per warp, mean sweep */
+  int32_t dense_rows_full;  /* dense form: the same, full sweeps */
+  double tune_ms;           /* host time spent tuning */
+  double reserved[3];
+} gabp_tuning;
+
+gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning);
 
 /*
  * Instrumentation for parity tests.  Runs exactly `rounds` synchronous FP64

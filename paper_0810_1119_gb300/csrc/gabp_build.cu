@@ -56,6 +56,37 @@ int next_pow2(int v) {
 }  // namespace
 
 // Returns GABP_OK or an error with *msg set.
+// Row tiles of the FP32 sweeps and the residual: at most `slots` slots and
+// `rows` rows per tile (a longer row is a tile of its own), the tile-local
+// row id of every slot, and the heavy flag of every tile that holds a row of
+// degree above `heavy_degree`.  Replaces the previous tiles.
+cudaError_t set_row_tiles(Graph &g, int slots, int rows, int heavy_degree, cudaStream_t st) {
+  const int64_t n = g.n;
+  const std::vector<int2> tb = make_tiles(g.h_rp, n, slots, rows);
+  std::vector<uint16_t> lrow(g.E);
+  for (size_t t = 0; t + 1 < tb.size(); ++t)
+    for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
+      for (int32_t sl = g.h_rp[r]; sl < g.h_rp[r + 1]; ++sl)
+        lrow[sl] = static_cast<uint16_t>(r - tb[t].x);
+  std::vector<uint8_t> heavy(tb.size() - 1, 0);
+  for (size_t t = 0; t + 1 < tb.size(); ++t)
+    for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
+      if (g.h_rp[r + 1] - g.h_rp[r] > heavy_degree) heavy[t] = 1;
+  cudaFree(g.tiles_big); cudaFree(g.lrow_big); cudaFree(g.heavy_big);
+  g.tiles_big = nullptr;
+  g.lrow_big = nullptr;
+  g.heavy_big = nullptr;
+  g.ntiles_big = static_cast<int32_t>(tb.size() - 1);
+  g.tile_slots = slots;
+  g.tile_rows = rows;
+  g.heavy_degree = heavy_degree;
+  cudaError_t ce = upload(&g.tiles_big, tb.data(), tb.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.lrow_big, lrow.data(), lrow.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.heavy_big, heavy.data(), heavy.size(), st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  return ce;
+}
+
 gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr,
                         const int32_t *col, const double *val, const int64_t *rev,
                         const gabp_options &opt, cudaStream_t st, std::string *msg) {
@@ -164,24 +195,12 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
   g.group = std::min(32, std::max(2, next_pow2(G)));
   int big_s, big_r, small_s, small_r;
   tile_sizes(&big_s, &big_r, &small_s, &small_r);
-  const std::vector<int2> tb = make_tiles(g.h_rp, n, big_s, big_r);
   const std::vector<int2> ts = make_tiles(g.h_rp, n, small_s, small_r);
-  g.ntiles_big = static_cast<int32_t>(tb.size() - 1);
   g.ntiles_small = static_cast<int32_t>(ts.size() - 1);
-  // Tile-local row id of every slot (rows of a tile number < 2^16).
-  std::vector<uint16_t> lrow(E);
-  for (size_t t = 0; t + 1 < tb.size(); ++t)
-    for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
-      for (int32_t sl = g.h_rp[r]; sl < g.h_rp[r + 1]; ++sl)
-        lrow[sl] = static_cast<uint16_t>(r - tb[t].x);
-  std::vector<uint8_t> heavy(tb.size() - 1, 0);
-  for (size_t t = 0; t + 1 < tb.size(); ++t)
-    for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
-      if (g.h_rp[r + 1] - g.h_rp[r] > kHeavyDegree) heavy[t] = 1;
-  cudaError_t ce = upload(&g.tiles_big, tb.data(), tb.size(), st);
+  if (opt.tile_slots > 0) big_s = opt.tile_slots;
+  if (opt.tile_rows > 0) big_r = opt.tile_rows;
+  cudaError_t ce = set_row_tiles(g, big_s, big_r, opt.heavy_degree > 0 ? opt.heavy_degree : kHeavyDegree, st);
   if (ce == cudaSuccess) ce = upload(&g.tiles_small, ts.data(), ts.size(), st);
-  if (ce == cudaSuccess) ce = upload(&g.lrow_big, lrow.data(), lrow.size(), st);
-  if (ce == cudaSuccess) ce = upload(&g.heavy_big, heavy.data(), heavy.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.rp, g.h_rp.data(), g.h_rp.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.col, g.h_col.data(), g.h_col.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.rev, g.h_rev.data(), g.h_rev.size(), st);

@@ -154,7 +154,7 @@ __device__ __forceinline__ Split split_of(int K) {
 // messages eta_ij = c (h~_i - eta_ji) are written (storage E) instead of full
 // messages.
 // ---------------------------------------------------------------------------
-template <class T, class E>
+template <class T, class E, int U>
 __global__ void __launch_bounds__(kDenseBlock)
 dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   using V = T2<T>;
@@ -292,23 +292,24 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
           atomicAdd(&az[j].y, re);
         }
       };
-      const Quad<T> zero{T(0), T(0), T(0), T(0)};
-      for (int j = w.g; j < N; j += 2 * w.rg) {
-        const int j2 = j + w.rg;
-        T a0 = T(0), a1 = T(0);
-        Quad<T> m0 = zero, m1 = zero;
-        if (w.lane_on) {
-          const int64_t p0 = base + static_cast<int64_t>(j) * K;
-          a0 = __ldcs(Sg + p0);
-          if (!first) m0 = io.ld(p0);
-          if (j2 < N) {
-            const int64_t p1 = p0 + static_cast<int64_t>(w.rg) * K;
-            a1 = __ldcs(Sg + p1);
-            if (!first) m1 = io.ld(p1);
+      // U rows of the group per step: all loads first, then the updates
+      for (int j0 = w.g; j0 < N; j0 += U * w.rg) {
+        T a[U];
+        Quad<T> m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + u * w.rg;
+          a[u] = T(0);
+          m[u] = Quad<T>{T(0), T(0), T(0), T(0)};
+          if (w.lane_on && j < N) {
+            const int64_t p = base + static_cast<int64_t>(j) * K;
+            a[u] = __ldcs(Sg + p);
+            if (!first) m[u] = io.ld(p);
           }
         }
-        one(j, a0, m0);
-        if (j2 < N) one(j2, a1, m1);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (j0 + u * w.rg < N) one(j0 + u * w.rg, a[u], m[u]);
       }
       if (w.lane_on) {
         atomicAdd(&ax[w.r].x, cP.value());
@@ -339,7 +340,7 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
 //     eta_z' = c_z (h~_r - eta_x),   eta_x' = c_x (h~_j - eta_z),
 // h~_i = r_i / ||r|| + sumEta_i, d_i = h~_i / P~_i (frozen 1/P~_i).
 // ---------------------------------------------------------------------------
-template <class E>
+template <class E, int U>
 __global__ void __launch_bounds__(kDenseBlock)
 dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ float tx[kDenseMaxK], tz[kDenseMaxN];   // h~ of this round
@@ -399,21 +400,22 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
         re = group_sum<32>(re);
         if (lane == 0) atomicAdd(&az[j], re);
       };
-      for (int j = w.g; j < N; j += 2 * w.rg) {
-        const int j2 = j + w.rg;
-        float2 c0 = make_float2(0.f, 0.f), c1 = c0, h0 = c0, h1 = c0;
-        if (w.lane_on) {
-          const int64_t p0 = base + static_cast<int64_t>(j) * K;
-          c0 = __ldcs(C + p0);
-          if (!first) h0 = ld_h(h_in + p0);
-          if (j2 < N) {
-            const int64_t p1 = p0 + static_cast<int64_t>(w.rg) * K;
-            c1 = __ldcs(C + p1);
-            if (!first) h1 = ld_h(h_in + p1);
+      for (int j0 = w.g; j0 < N; j0 += U * w.rg) {
+        float2 c[U], hv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + u * w.rg;
+          c[u] = make_float2(0.f, 0.f);
+          hv[u] = c[u];
+          if (w.lane_on && j < N) {
+            const int64_t p = base + static_cast<int64_t>(j) * K;
+            c[u] = __ldcs(C + p);
+            if (!first) hv[u] = ld_h(h_in + p);
           }
         }
-        one(j, c0, h0);
-        if (j2 < N) one(j2, c1, h1);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (j0 + u * w.rg < N) one(j0 + u * w.rg, c[u], hv[u]);
       }
       if (w.lane_on) atomicAdd(&ax[w.r], cE.value());
     }
@@ -519,33 +521,45 @@ int dense_grid(Kern kernel, int32_t nsys) {
 
 }  // namespace
 
+// Rows each warp loads ahead: 1, 2 or 4 (the autotuner's choice).
+#define GABP_ROWS_DISPATCH(U, ...)                        \
+  do {                                                    \
+    if ((U) >= 4) { constexpr int UR = 4; __VA_ARGS__; }   \
+    else if ((U) == 1) { constexpr int UR = 1; __VA_ARGS__; } \
+    else { constexpr int UR = 2; __VA_ARGS__; }            \
+  } while (0)
+
 int launch_dense_full64(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
-  auto k = dense_full_kernel<double, float2>;
+  auto k = dense_full_kernel<double, float2, 2>;
   k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
   return 1;
 }
 
 int launch_dense_full32(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                         bool bf16) {
-  if (bf16) {
-    auto k = dense_full_kernel<float, __nv_bfloat162>;
-    k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
-  } else {
-    auto k = dense_full_kernel<float, float2>;
-    k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
-  }
+  GABP_ROWS_DISPATCH(d.rows_full, {
+    if (bf16) {
+      auto k = dense_full_kernel<float, __nv_bfloat162, UR>;
+      k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+    } else {
+      auto k = dense_full_kernel<float, float2, UR>;
+      k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+    }
+  });
   return 1;
 }
 
 int launch_dense_mean(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                       bool bf16) {
-  if (bf16)
-    dense_mean_kernel<__nv_bfloat162>
-        <<<dense_grid(dense_mean_kernel<__nv_bfloat162>, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl,
-                                                                                        red);
-  else
-    dense_mean_kernel<float2><<<dense_grid(dense_mean_kernel<float2>, d.nsys), kDenseBlock, 0, st>>>(
-        d.v, B, ctl, red);
+  GABP_ROWS_DISPATCH(d.rows_mean, {
+    if (bf16) {
+      auto k = dense_mean_kernel<__nv_bfloat162, UR>;
+      k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+    } else {
+      auto k = dense_mean_kernel<float2, UR>;
+      k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+    }
+  });
   return 1;
 }
 
@@ -559,14 +573,18 @@ int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *c
 // Caches the occupancy of every dense kernel (done at create time, before
 // any graph is recorded).
 void prepare_dense_kernels(bool bf16) {
-  dense_grid(dense_full_kernel<double, float2>, 1);
+  dense_grid(dense_full_kernel<double, float2, 2>, 1);
   dense_grid(dense_residual_kernel, 1);
-  if (bf16) {
-    dense_grid(dense_full_kernel<float, __nv_bfloat162>, 1);
-    dense_grid(dense_mean_kernel<__nv_bfloat162>, 1);
-  } else {
-    dense_grid(dense_full_kernel<float, float2>, 1);
-    dense_grid(dense_mean_kernel<float2>, 1);
+  for (int u : {1, 2, 4}) {
+    GABP_ROWS_DISPATCH(u, {
+      if (bf16) {
+        dense_grid(dense_full_kernel<float, __nv_bfloat162, UR>, 1);
+        dense_grid(dense_mean_kernel<__nv_bfloat162, UR>, 1);
+      } else {
+        dense_grid(dense_full_kernel<float, float2, UR>, 1);
+        dense_grid(dense_mean_kernel<float2, UR>, 1);
+      }
+    });
   }
 }
 

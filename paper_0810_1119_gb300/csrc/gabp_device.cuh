@@ -156,6 +156,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
         c.phase = PH_FULL32;
       } else {
         c.rn = c.bnorm;
+        c.best_rn = c.bnorm;
         if (c.rn < c.thr || c.bnorm == 0.0) { finish(c, GABP_OK); break; }
         c.inv_rn = 1.0 / c.rn;
         c.outer = 1;
@@ -194,6 +195,10 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (diverged(rn, c.bnorm)) { finish(c, GABP_ERR_DIVERGED); break; }
       if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
       if (kind == CK_CHECK64) { c.phase = PH_FULL64; break; }
+      // Refinement that stopped paying: four outer steps without halving the
+      // residual (inner solves no more accurate than their storage allows).
+      if (rn < 0.5 * c.best_rn) { c.best_rn = rn; c.outer_stall = 0; }
+      else if (++c.outer_stall >= 4) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
       // next refinement step: solve A d = r / ||r|| from zero mean messages
       c.outer++;
       c.rn = rn;
@@ -277,6 +282,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       }
       c.bnorm = worst;
       c.residual = worst;
+      c.best_rn = worst;
       if (bad) { finish(c, GABP_ERR_INVALID_ARG); break; }
       if (all_done) { finish(c, GABP_OK); break; }
       c.outer = 1;
@@ -319,6 +325,8 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (all_done) { finish(c, GABP_OK); break; }
       if (bad) { finish(c, GABP_ERR_DIVERGED); break; }
       if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
+      if (worst < 0.5 * c.best_rn) { c.best_rn = worst; c.outer_stall = 0; }
+      else if (++c.outer_stall >= 4) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
       c.outer++;
       c.k = 0;
       c.stall = 0;

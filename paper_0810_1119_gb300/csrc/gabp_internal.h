@@ -100,6 +100,8 @@ struct Ctl {
   int since_best;               // sweeps since best_dd last shrank by 10 %
   int plateau;                  // > 0: an inner solve also ends after this many such sweeps
   double floor_dd;              // relative change below which a stall ends an inner solve
+  double best_rn;               // smallest FP64 residual of the refinement so far
+  int outer_stall;              // refinement steps since best_rn last halved
   double bnorm, thr, rn, inv_rn, residual;
   int status, done;
   unsigned int blocks_done;     // last-block detection counter
@@ -159,6 +161,7 @@ struct Graph {
   uint8_t *heavy_big = nullptr;
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
+  int tile_slots = 0, tile_rows = 0, heavy_degree = 0;   // row tiles of the FP32 sweeps
   int max_degree = 0;
   // batched handles (independent systems along the diagonal)
   int32_t nsys = 0;
@@ -242,6 +245,7 @@ struct Dense {
   DenseView v{};
   DenseSys *sys = nullptr;      // device, largest systems first
   bool have64 = false, have32 = false;
+  int rows_mean = 2, rows_full = 2;   // grid rows each warp loads ahead (1, 2 or 4)
 };
 
 int launch_dense_full64(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
@@ -270,6 +274,7 @@ int launch_lsq_extract(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row
                        const int64_t *aug_off, const int32_t *K, const int64_t *x_off,
                        const double *x_aug, double *xhat);
 void free_graph(Graph &g);
+cudaError_t set_row_tiles(Graph &g, int slots, int rows, int heavy_degree, cudaStream_t st);
 
 }  // namespace gabp
 
@@ -304,6 +309,7 @@ struct gabp_s {
   size_t capK = 0;                     // columns the multi buffers hold
   gabp::MultiCols cols{};              // device per-column arrays (capK each)
   gabp::Dense *dense = nullptr;        // Section VII batches in dense bipartite form
+  gabp_tuning tuning{};                // launch shapes (chosen by the autotuner or default)
   cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
 
   // profiling (gabp_options.profile): pairs of events around kernels

@@ -24,6 +24,7 @@
 #include "gabp_internal.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -608,6 +609,136 @@ void build_dense(gabp_handle h, int32_t nsys, const int32_t *K, const int32_t *N
   prepare_dense_kernels(is_bf16(h));
 }
 
+// ---- autotuner ----
+// Milliseconds per launch of `launch` (CUDA events on the handle's stream,
+// after one untimed launch).
+template <class F>
+float time_launches(gabp_handle h, int reps, F &&launch) {
+  cudaEvent_t a, z;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&z));
+  launch();
+  CK(cudaEventRecord(a, h->stream));
+  for (int k = 0; k < reps; ++k) launch();
+  CK(cudaEventRecord(z, h->stream));
+  CK(cudaEventSynchronize(z));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, a, z));
+  CK(cudaEventDestroy(a));
+  CK(cudaEventDestroy(z));
+  CK(cudaGetLastError());
+  return ms / reps;
+}
+
+// Control block for timing sweeps outside a solve: mixed mode, frozen
+// precisions, not the first sweep (so every launch streams its inputs), b and
+// x pointing at a scratch vector that the timed kernels never write.
+void tuning_ctl(gabp_handle h) {
+  ensure(&h->bbuf, h->g.n);
+  init_ctl(h, CTL_MIXED, h->bbuf, h->bbuf, 1e-10, 1 << 30, false);
+  Ctl &c = *h->ctl_host;
+  c.first = 0;
+  c.frozen = 1;
+  c.rn = 1.0;
+  c.inv_rn = 1.0;
+  c.check_every = 1 << 30;
+  CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), h->stream));
+}
+
+void fill_tuning(gabp_handle h) {
+  gabp_tuning &t = h->tuning;
+  t.tile_slots = h->g.tile_slots;
+  t.tile_rows = h->g.tile_rows;
+  t.heavy_degree = h->g.heavy_degree;
+  t.group_lanes = h->g.group;
+  t.dense_rows_mean = h->dense ? h->dense->rows_mean : 0;
+  t.dense_rows_full = h->dense ? h->dense->rows_full : 0;
+}
+
+// Times the candidate launch shapes on the handle's own matrix (zero
+// messages: the traffic and the work per launch do not depend on the values)
+// and keeps the fastest.  Runs at create, before any solve graph is recorded.
+void autotune(gabp_handle h) {
+  const auto t0 = std::chrono::steady_clock::now();
+  gabp_tuning &T = h->tuning;
+  Graph &g = h->g;
+  const bool mixed = h->opt.precision != GABP_PREC_FP64;
+  const bool bf16 = is_bf16(h);
+  if (h->dense) {
+    if (mixed && h->opt.dense_rows == 0) {
+      Dense &d = *h->dense;
+      ensure32(h);
+      float best = 1e30f;
+      int pick = 2;
+      for (int u : {1, 2, 4}) {
+        d.rows_mean = u;
+        tuning_ctl(h);
+        const float ms = time_launches(h, 3, [&] { launch_dense_mean(d, h->stream, h->buf, h->ctl, h->red, bf16); });
+        ++T.candidates;
+        if (ms < best) { best = ms; pick = u; }
+      }
+      d.rows_mean = pick;
+      best = 1e30f;
+      pick = 2;
+      for (int u : {1, 2, 4}) {
+        d.rows_full = u;
+        tuning_ctl(h);
+        const float ms = time_launches(h, 2, [&] { launch_dense_full32(d, h->stream, h->buf, h->ctl, h->red, bf16); });
+        ++T.candidates;
+        if (ms < best) { best = ms; pick = u; }
+      }
+      d.rows_full = pick;
+    }
+  } else if (mixed) {
+    ensure32(h);
+    auto score = [&](int slots, int rows, int heavy) {
+      CK(set_row_tiles(g, slots, rows, heavy, h->stream));
+      tuning_ctl(h);
+      const float tm = time_launches(h, 3, [&] { launch_mean(g, h->stream, h->buf, h->ctl, h->red, bf16); });
+      const float tf = time_launches(h, 2, [&] { launch_sweep32(g, h->stream, h->buf, h->ctl, h->red, bf16); });
+      ++T.candidates;
+      return 4.0 * tm + tf;
+    };
+    const int slots0 = g.tile_slots, rows0 = g.tile_rows;
+    double best = 1e300;
+    int heavy = g.heavy_degree;
+    if (h->opt.heavy_degree == 0) {
+      for (int hd : {16, 32, 64, 128, 1 << 30}) {
+        const double sc = score(slots0, rows0, hd);
+        if (sc < best) { best = sc; heavy = hd; }
+      }
+    } else {
+      best = score(slots0, rows0, heavy);
+    }
+    int slots = slots0, rows = rows0;
+    if (h->opt.tile_slots == 0 && h->opt.tile_rows == 0) {
+      const int shapes[][2] = {{512, 256}, {512, 128}, {256, 64}};
+      for (const auto &sh : shapes) {
+        const double sc = score(sh[0], sh[1], heavy);
+        if (sc < best) { best = sc; slots = sh[0]; rows = sh[1]; }
+      }
+    }
+    CK(set_row_tiles(g, slots, rows, heavy, h->stream));
+  } else if (h->opt.group_lanes == 0) {
+    ensure64(h);
+    float best = 1e30f;
+    int pick = g.group;
+    for (int G : {2, 4, 8, 16, 32}) {
+      g.group = G;
+      prepare_kernels(G, false);
+      tuning_ctl(h);
+      const float ms = time_launches(h, 3, [&] { launch_sweep64(g, h->stream, h->buf, h->ctl, h->red); });
+      ++T.candidates;
+      if (ms < best) { best = ms; pick = G; }
+    }
+    g.group = pick;
+  }
+  T.tuned = 1;
+  fill_tuning(h);
+  T.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 // A handle with validated options and no matrix yet.
 gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
   gabp_handle h = new (std::nothrow) gabp_s;
@@ -621,6 +752,15 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
   if (!(h->opt.damping >= 0.0 && h->opt.damping < 1.0)) {
     delete h;
     g_create_error = "damping must lie in [0, 1)";
+    return GABP_ERR_INVALID_ARG;
+  }
+  const gabp_options &o = h->opt;
+  if (o.tile_slots < 0 || (o.tile_slots > 0 && (o.tile_slots < 32 || o.tile_slots > 1024)) ||
+      o.tile_rows < 0 || o.tile_rows > 256 || o.heavy_degree < 0 ||
+      !(o.dense_rows == 0 || o.dense_rows == 1 || o.dense_rows == 2 || o.dense_rows == 4)) {
+    delete h;
+    g_create_error = "launch shape out of range (tile_slots 32..1024, tile_rows 1..256, "
+                     "heavy_degree >= 1, dense_rows 1, 2 or 4; 0 = automatic)";
     return GABP_ERR_INVALID_ARG;
   }
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
@@ -656,6 +796,10 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
     if (r != GABP_OK) h->last_error = msg;
     return r;
   });
+  if (s == GABP_OK) {
+    fill_tuning(h);
+    if (h->opt.autotune) s = guarded(h, [&] { autotune(h); return GABP_OK; });
+  }
   if (s != GABP_OK) {
     g_create_error = h->last_error;
     release(h);
@@ -748,6 +892,9 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
     if (s != GABP_OK) return s;
     s = guarded(h, [&] {
       build_dense(h, nsys, K_host, N_host, S_host, psi_host, sys_off);
+      if (h->opt.dense_rows > 0) h->dense->rows_mean = h->dense->rows_full = h->opt.dense_rows;
+      fill_tuning(h);
+      if (h->opt.autotune) autotune(h);
       return GABP_OK;
     });
     if (s != GABP_OK) {
@@ -891,6 +1038,12 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
     if (worst != GABP_OK) h->last_error = msg;
     return worst;
   });
+}
+
+gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning) {
+  if (!h || !tuning) return GABP_ERR_INVALID_ARG;
+  *tuning = h->tuning;
+  return GABP_OK;
 }
 
 gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats) {

