@@ -196,10 +196,11 @@ def run_gabp(args):
     # A second handle with profile=1 runs the same kernels from the host
     # driver with CUDA events around every kernel: it gives the per-kernel
     # device times of the roofline figure.
-    mixed = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32)
-    mixed_prof = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32,
-                                      profile=True)
-    fp64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64)
+    # Launch shapes are picked by the library's autotuner at create time
+    # (outside the timed region); the profiled pass reuses the same handle.
+    mixed = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32,
+                                 autotune=True)
+    fp64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64, autotune=True)
     stream = torch.cuda.current_stream()
 
     def timed_solves(solver, steps):
@@ -221,7 +222,6 @@ def run_gabp(args):
     for _ in range(args.warmup):
         timed_solves(mixed, 1)
         timed_solves(fp64, 1)
-        timed_solves(mixed_prof, 1)
 
     def barrier():
         if dist is not None:
@@ -237,7 +237,9 @@ def run_gabp(args):
     ms_fp64, st_fp64 = timed_solves(fp64, max(1, min(args.steps, args.fp64_steps)))
     barrier()
     clocks = sampler.stop() if sampler else None
-    _, st_prof = timed_solves(mixed_prof, args.steps)
+    gabp.gabp_set_profile(mixed.handle, True)
+    _, st_prof = timed_solves(mixed, args.steps)
+    gabp.gabp_set_profile(mixed.handle, False)
 
     # end to end through the host-buffer entry point
     b_host = torch.tensor(b, dtype=torch.float64).pin_memory()
@@ -319,12 +321,12 @@ def run_gabp(args):
                     "ms_per_step": 1e3 * e2e_s / args.steps},
             "gpu_launches": launches,
             "clocks": clocks,
+            "tuning": {"mixed": mixed.tuning(), "fp64": fp64.tuning()},
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(m, b, args.cpu_rounds)
         print(json.dumps(line), flush=True)
     mixed.close()
-    mixed_prof.close()
     fp64.close()
     if dist is not None:
         dist.destroy_process_group()
@@ -348,7 +350,7 @@ def run_multi(args):
     B = torch.tensor(W.normal_rhs(n, 5, k=K), device="cuda")
     X = torch.empty_like(B)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32)
+    s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32, autotune=True)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         gabp.gabp_solve_multi(s.handle, B, X, TOL, 5000)
@@ -390,6 +392,71 @@ def run_multi(args):
     return 0
 
 
+def run_poisson32(args):
+    """2D Poisson 5-point Laplacian on a 32 x 32 grid (n = 1024, 3968 directed
+    edges), b ~ U[-1, 1]; plain synchronous FP64 GaBP until ||A x - b||_inf <
+    1e-10 (absolute).  The system is ~100 KB, so the solve is latency-bound
+    (thousands of short sweeps): reported as time to solution and sweeps/s,
+    with the mixed-precision solve of the same system and the oracle's
+    solve on the host cores beside it."""
+    import torch
+    import oracle
+    torch.cuda.set_device(0)
+    from paper_0810_1119_gb300 import build_lib
+    build_lib.build()
+    from paper_0810_1119_gb300 import gabp
+    from paper_0810_1119_gb300 import workloads as W
+    m = W.poisson2d(32)
+    b = W.uniform_rhs(m.n, 0)
+    E = m.n_directed_edges
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("fp64", gabp.PREC_FP64), ("mixed_fp32", gabp.PREC_MIXED_FP32)):
+        s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=prec,
+                                 residual_kind=gabp.RESIDUAL_ABS, autotune=True)
+        for _ in range(args.warmup):
+            gabp.gabp_solve(s.handle, bt, xt, TOL, 100000)
+        ms = []
+        for _ in range(args.steps):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gabp.gabp_solve(s.handle, bt, xt, TOL, 100000)
+            z.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(z))
+        st = s.stats()
+        out[name] = {"ms": statistics.mean(ms), "stats": st, "x": xt.cpu().numpy(),
+                     "tuning": s.tuning()}
+        s.close()
+    t0 = time.perf_counter()
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_ABS, max_rounds=100000, tol=TOL)
+    cpu_s = time.perf_counter() - t0
+    f = out["fp64"]
+    st = f["stats"]
+    line = {"metric": "time to ||Ax-b||_inf < 1e-10, plain FP64 GaBP (2D Poisson 32x32)",
+            "value": f["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": f["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2D Poisson 5-point 32x32 (n=1024), b~U[-1,1], abs 1e-10",
+                       "n": m.n, "directed_edges": E, "bound": "latency (system fits in L2)"},
+            "sweeps": st["sweeps_total"], "residual_checks": st["residual_checks"],
+            "sweeps_per_s": st["sweeps_total"] / (f["ms"] * 1e-3),
+            "edge_updates_per_s": E * st["sweeps_total"] / (f["ms"] * 1e-3),
+            "us_per_sweep": 1e3 * f["ms"] / st["sweeps_total"],
+            "final_abs_residual": st["residual"],
+            "max_rel_err_vs_oracle": float(np.abs(f["x"] - ref["x"]).max() / np.abs(ref["x"]).max()),
+            "mixed_fp32": {"ms": out["mixed_fp32"]["ms"],
+                           "sweeps": out["mixed_fp32"]["stats"]["sweeps_total"],
+                           "outer": out["mixed_fp32"]["stats"]["outer_steps"]},
+            "tuning": f["tuning"],
+            "cpu_baseline": {"value": 1e3 * cpu_s, "unit": "ms", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": f"the full solve ({ref['rounds']} rounds)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_detect(args):
     """Batched uneven linear detection: 4096 systems, K ~ U{16..256}, N = 2K,
     S = +-1/sqrt(N), x in {+-1}, y = S x + noise at 10 dB.  Every system is
@@ -410,6 +477,7 @@ def run_detect(args):
     o.precision = gabp.PREC_MIXED_FP32
     o.damping = args.damping
     o.lsq_form = args.lsq_form
+    o.autotune = 1
     o.stream = gabp.current_stream_handle()
     t0 = time.perf_counter()
     h = gabp.gabp_create_lsq_batched([d.S for d in systems], [d.sigma2 for d in systems], o)
@@ -440,14 +508,13 @@ def run_detect(args):
         A, bb = systems[k].dense_system()
         closed = np.linalg.solve(A, bb)
         errs.append(float(np.abs(got[offs[k]:offs[k + 1]] - closed).max() / np.abs(closed).max()))
+    # profiled pass of the same handle (host driver, CUDA events around every
+    # kernel): per-kind kernel times for the roofline of the mean sweep
+    tuning = gabp.gabp_get_tuning(h)
+    gabp.gabp_set_profile(h, True)
+    gabp.gabp_solve_lsq_batched(h, y, xh, TOL, 20000)
+    sp = gabp.gabp_get_stats(h)
     gabp.gabp_destroy(h)
-    # profiled pass (host driver, CUDA events around every kernel): per-kind
-    # kernel times of the same solve for the roofline of the mean sweep
-    o.profile = 1
-    hp = gabp.gabp_create_lsq_batched([d.S for d in systems], [d.sigma2 for d in systems], o)
-    gabp.gabp_solve_lsq_batched(hp, y, xh, TOL, 20000)
-    sp = gabp.gabp_get_stats(hp)
-    gabp.gabp_destroy(hp)
     hbm, peak_src = _peaks()
     pairs = E // 2
     dense = args.lsq_form == 0
@@ -476,7 +543,8 @@ def run_detect(args):
             "form": "dense bipartite grid" if dense else "CSR tiles",
             "max_rel_err_vs_closed_form_sample": max(errs), "roofline": roof,
             "kernel_ms_per_step": {"mean": sp["ms_mean"], "full32": sp["ms_full"],
-                                   "residual": sp["ms_residual"], "other": sp["ms_other"]}}
+                                   "residual": sp["ms_residual"], "other": sp["ms_other"]},
+            "tuning": tuning}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -491,8 +559,8 @@ def main():
     ap.add_argument("--cpu-rounds", type=int, default=10)
     ap.add_argument("--ref-rounds", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="er1e6", choices=["er1e6", "multi64", "detect"],
-                    help="er1e6: the headline line; multi64 / detect: extra lines")
+    ap.add_argument("--workload", default="er1e6", choices=["er1e6", "multi64", "detect", "poisson32"],
+                    help="er1e6: the headline line; multi64 / detect / poisson32: extra lines")
     ap.add_argument("--nsys", type=int, default=4096)
     ap.add_argument("--lsq-form", type=int, default=0, choices=[0, 1],
                     help="detect: 0 = dense bipartite kernels, 1 = general CSR path")
@@ -505,6 +573,8 @@ def main():
         return run_multi(args)
     if args.workload == "detect":
         return run_detect(args)
+    if args.workload == "poisson32":
+        return run_poisson32(args)
     return run_gabp(args)
 
 

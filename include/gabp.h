@@ -88,8 +88,12 @@ typedef struct {
                              instead of thread-per-row (>= 1); 0 = 64 */
   int32_t dense_rows;     /* dense Section VII form: grid rows each warp loads ahead in the FP32
                              sweeps (1, 2 or 4); 0 = 2 */
+  int32_t small_form;     /* FP64 solves of systems that fit one thread-block cluster's shared
+                             memory (<= 16 x 3584 off-diagonal entries, <= 16 x 1024 rows):
+                             0 = the whole solve in one cluster launch, 1 = always a launch
+                             per sweep */
+  int32_t cluster_ctas;   /* CTAs of that cluster (2, 4, 8 or 16); 0 = automatic */
   int32_t reserved_i;
-  double reserved_d;
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */
@@ -231,6 +235,14 @@ gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *x
 gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats);
 
 /*
+ * Turns per-kernel timing on (1) or off (0) for the handle's later solves,
+ * like gabp_options.profile at create.  With timing on, a solve is driven
+ * from the host with CUDA events around every kernel (the same kernels and
+ * launch shapes as the graph driver) and gabp_stats reports the times.
+ */
+gabp_status gabp_set_profile(gabp_handle h, int32_t on);
+
+/*
  * Launch shapes of a handle.  (The paper has no counterpart: these choices
  * belong to the GPU mapping of the Alg. 2 sweep.)  With
  * gabp_options.autotune = 1, gabp_create* times the candidates on the
@@ -253,6 +265,8 @@ typedef struct {
   int32_t group_lanes;      /* CSR form: lanes per row of the FP64 sweep */
   int32_t dense_rows_mean;  /* dense form: grid rows loaded ahead per warp, mean sweep */
   int32_t dense_rows_full;  /* dense form: the same, full sweeps */
+  int32_t cluster_ctas;     /* small FP64 systems: CTAs of the resident cluster (0 = not used) */
+  int32_t reserved_i;
   double tune_ms;           /* host time spent tuning */
   double reserved[3];
 } gabp_tuning;

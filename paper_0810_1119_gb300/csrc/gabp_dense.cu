@@ -51,10 +51,8 @@ __device__ __forceinline__ T2<T> mk2(T a, T b) {
 __device__ __forceinline__ float rcp(float d) { return 1.0f / d; }
 __device__ __forceinline__ double rcp(double d) { return recip64(d); }
 
-template <class T>
-__device__ __forceinline__ bool bad(T d) {
-  return !(d != T(0)) || !isfinite(d);
-}
+__device__ __forceinline__ bool bad(float d) { return !(d != 0.0f) || !isfinite(d); }
+__device__ __forceinline__ bool bad(double d) { return zero_or_nonfinite(d); }
 
 // Both directed messages of one grid position.
 template <class T>

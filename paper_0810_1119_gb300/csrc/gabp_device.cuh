@@ -103,14 +103,24 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
 }
 // 1/d in FP64: an FP32 reciprocal seed (relative error e0 < 2^-22), then the
 // cubic Newton-Raphson step y (1 + e + e^2) with e = 1 - d y, whose error is
-// e0^3 < 2^-66 before rounding.  Outside the FP32 normal range (or for
-// zero / non-finite d) the IEEE division is used.
+// e0^3 < 2^-66 before rounding.  For |d| outside [2^-99, 2^99) (where the
+// FP32 seed could under- or overflow), zero or non-finite d, the IEEE
+// division is used.  The range test reads the exponent field with integer
+// instructions: on GB300 every FP64 compare would occupy the slow FP64 pipe.
 __device__ __forceinline__ double recip64(double d) {
-  const double ad = fabs(d);
-  if (!(ad > 1e-30 && ad < 1e30)) return 1.0 / d;
+  const unsigned ex = static_cast<unsigned>(__double_as_longlong(d) >> 52) & 0x7FFu;
+  if (ex - 924u > 1121u - 924u) return 1.0 / d;
   const double y = static_cast<double>(__frcp_rn(static_cast<float>(d)));
   const double e = fma(-d, y, 1.0);
   return fma(y, fma(e, e, e), y);
+}
+
+// d == 0 or d not finite (the breakdown of Alg. 2's division), tested on the
+// bit pattern with integer instructions.
+__device__ __forceinline__ bool zero_or_nonfinite(double d) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d)) &
+                               0x7FFFFFFFFFFFFFFFull;
+  return u == 0ull || u >= 0x7FF0000000000000ull;
 }
 
 // ---------------------------------------------------------------------------

@@ -258,6 +258,42 @@ int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *c
 int launch_refine_update(int32_t n, cudaStream_t st, Buffers B, Ctl *ctl);
 void prepare_dense_kernels(bool bf16);
 
+// ---- whole FP64 solves of small systems in one cluster launch (gabp_resident.cu) ----
+constexpr int kResidentMaxCluster = 16;   // CTAs of the cluster (16 needs the non-portable size)
+constexpr int kResidentMaxSlots = 3584;   // incoming-message slots per CTA
+constexpr int kResidentMaxRows = 1024;    // rows per CTA
+
+struct ResidentOut {
+  int32_t status, sweeps, checks, pad;
+  double residual, bnorm;
+};
+
+// Rows [row0[c], row0[c+1]) belong to CTA c.  For every slot s (incoming
+// message of its row): dst[s] = (CTA << 24) | local slot of rev[s] in that
+// CTA, colp[s] = (CTA << 16) | local row of col[s].
+struct ResidentView {
+  const int32_t *row0;
+  const int32_t *rp;
+  const double *a64, *diag64;
+  const int32_t *dst, *colp;
+  const double *b;
+  double *x;
+  int32_t smax, rmax;
+  int32_t check_every, max_iter, rel;
+  double tol, damping;
+  ResidentOut *out;
+};
+
+struct Resident {
+  int C = 0;                     // cluster size in use (0 = not eligible)
+  int smax = 0, rmax = 0;
+  int32_t *row0 = nullptr, *dst = nullptr, *colp = nullptr;
+  ResidentOut *out = nullptr;    // device
+};
+
+uint32_t resident_smem_bytes(int smax, int rmax);
+cudaError_t launch_resident64(const ResidentView &v, int C, cudaStream_t st);
+
 // ---- graph builder (gabp_build.cu) ----
 gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr,
                         const int32_t *col, const double *val, const int64_t *rev,
@@ -310,6 +346,7 @@ struct gabp_s {
   gabp::MultiCols cols{};              // device per-column arrays (capK each)
   gabp::Dense *dense = nullptr;        // Section VII batches in dense bipartite form
   gabp_tuning tuning{};                // launch shapes (chosen by the autotuner or default)
+  gabp::Resident res{};                // small FP64 systems: one cluster launch per solve
   cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
 
   // profiling (gabp_options.profile): pairs of events around kernels

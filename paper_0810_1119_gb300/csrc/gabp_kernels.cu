@@ -319,7 +319,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const double gam = ctl->damping;
   auto emit = [&](double a, double2 m, int32_t dst, double TP, double Th) {
     const double d = TP - m.x;   // P_{i\j} = P~_i - P_ji
-    brk |= !(d != 0.0) || !isfinite(d);
+    brk |= zero_or_nonfinite(d);
     const double inv = recip64(d);
     double eta = -a * (Th - m.y) * inv;
     // damping: blend with this message's previous value (slot dst of "in")

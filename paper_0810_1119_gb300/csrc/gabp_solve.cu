@@ -85,6 +85,10 @@ gabp_status guarded(gabp_handle h, F &&f) {
 
 bool is_bf16(gabp_handle h) { return h->opt.precision == GABP_PREC_MIXED_BF16; }
 
+void free_resident(Resident &r);
+gabp_status resident_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                           int32_t *iters, bool *ran);
+
 void ensure_common(gabp_handle h) {
   ensure(&h->red, 1);
   ensure(&h->ctl, 1);
@@ -409,6 +413,11 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
                        int32_t *iters) {
   const bool mixed = h->opt.precision != GABP_PREC_FP64;
   const int mode = mixed ? CTL_MIXED : CTL_FP64;
+  if (!mixed && h->res.C > 0 && !h->opt.profile && h->g.nsys == 0 && !h->dense) {
+    bool ran = false;
+    const gabp_status s = resident_solve(h, b, x, tol, max_iter, iters, &ran);
+    if (ran) return s;
+  }
   if (mixed) ensure32(h); else ensure64(h);
   h->stats = gabp_stats{};
   init_ctl(h, mode, b, x, tol, max_iter, false);
@@ -543,6 +552,7 @@ void release(gabp_handle h) {
     delete h->dense;
     h->dense = nullptr;
   }
+  free_resident(h->res);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
@@ -609,6 +619,145 @@ void build_dense(gabp_handle h, int32_t nsys, const int32_t *K, const int32_t *N
   prepare_dense_kernels(is_bf16(h));
 }
 
+// ---- small FP64 systems: the whole solve in one cluster launch ----
+// Rows cut into C parts of about E / C slots each (cut points on the slot
+// prefix sums); false if a part exceeds the per-CTA limits.
+bool plan_resident(const Graph &g, int C, std::vector<int32_t> &row0, int *smax, int *rmax) {
+  const int64_t n = g.n, E = g.E;
+  row0.assign(C + 1, 0);
+  for (int c = 1; c < C; ++c) {
+    const int64_t target = E * c / C;
+    const int64_t r = std::lower_bound(g.h_rp.begin(), g.h_rp.begin() + n + 1, target) - g.h_rp.begin();
+    row0[c] = static_cast<int32_t>(std::max<int64_t>(row0[c - 1], std::min<int64_t>(r, n)));
+  }
+  row0[C] = static_cast<int32_t>(n);
+  *smax = *rmax = 0;
+  for (int c = 0; c < C; ++c) {
+    *rmax = std::max(*rmax, row0[c + 1] - row0[c]);
+    *smax = std::max(*smax, g.h_rp[row0[c + 1]] - g.h_rp[row0[c]]);
+  }
+  return *rmax <= kResidentMaxRows && *smax <= kResidentMaxSlots && *smax >= 1;
+}
+
+void free_resident(Resident &r) {
+  cudaFree(r.row0); cudaFree(r.dst); cudaFree(r.colp); cudaFree(r.out);
+  r = Resident{};
+}
+
+// Builds the cluster-resident layout for C CTAs; returns false (and leaves
+// the handle without one) if the system does not fit.
+bool build_resident(gabp_handle h, int C) {
+  const Graph &g = h->g;
+  std::vector<int32_t> row0;
+  int smax = 0, rmax = 0;
+  if (C < 1 || C > kResidentMaxCluster || !plan_resident(g, C, row0, &smax, &rmax)) return false;
+  const int64_t n = g.n, E = g.E;
+  std::vector<int32_t> part(n);
+  for (int c = 0; c < C; ++c)
+    for (int32_t i = row0[c]; i < row0[c + 1]; ++i) part[i] = c;
+  std::vector<int32_t> dst(E), colp(E);
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t s = g.h_rp[i]; s < g.h_rp[i + 1]; ++s) {
+      const int32_t j = g.h_col[s], pj = part[j];
+      dst[s] = (pj << 24) | (g.h_rev[s] - g.h_rp[row0[pj]]);
+      colp[s] = (pj << 16) | (j - row0[pj]);
+    }
+  free_resident(h->res);
+  Resident &r = h->res;
+  ensure(&r.row0, C + 1);
+  ensure(&r.dst, E);
+  ensure(&r.colp, E);
+  ensure(&r.out, 1);
+  CK(cudaMemcpyAsync(r.row0, row0.data(), sizeof(int32_t) * (C + 1), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(r.dst, dst.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(r.colp, colp.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  r.C = C;
+  r.smax = smax;
+  r.rmax = rmax;
+  return true;
+}
+
+// Default cluster: about 512 slots per CTA (2 .. 16 CTAs), grown until the
+// parts fit.
+void setup_resident(gabp_handle h) {
+  const Graph &g = h->g;
+  if (h->opt.small_form != 0 || g.E < 1 ||
+      g.E > static_cast<int64_t>(kResidentMaxCluster) * kResidentMaxSlots ||
+      g.n > kResidentMaxCluster * kResidentMaxRows)
+    return;
+  if (h->opt.cluster_ctas > 0) {
+    build_resident(h, h->opt.cluster_ctas);
+    return;
+  }
+  int C = 2;
+  while (C < kResidentMaxCluster && g.E > static_cast<int64_t>(C) * 512) C *= 2;
+  for (; C <= kResidentMaxCluster; C *= 2)
+    if (build_resident(h, C)) return;
+}
+
+ResidentView resident_view(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                           int check_every) {
+  const Graph &g = h->g;
+  const Resident &r = h->res;
+  ResidentView v{};
+  v.row0 = r.row0;
+  v.rp = g.rp;
+  v.a64 = g.a64;
+  v.diag64 = g.diag64;
+  v.dst = r.dst;
+  v.colp = r.colp;
+  v.b = b;
+  v.x = x;
+  v.smax = r.smax;
+  v.rmax = r.rmax;
+  v.check_every = check_every;
+  v.max_iter = max_iter;
+  v.rel = h->opt.residual_kind == GABP_RESIDUAL_REL;
+  v.tol = tol;
+  v.damping = h->opt.damping;
+  v.out = r.out;
+  return v;
+}
+
+// One-launch FP64 solve.  *ran = false when the device cannot place the
+// cluster (the handle then keeps to the per-sweep path).
+gabp_status resident_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
+                           int32_t *iters, bool *ran) {
+  const int check_every = h->opt.check_every > 0 ? h->opt.check_every : 4;
+  const ResidentView v = resident_view(h, b, x, tol, max_iter, check_every);
+  const cudaError_t ce = launch_resident64(v, h->res.C, h->stream);
+  if (ce == cudaErrorInvalidConfiguration) {
+    free_resident(h->res);
+    h->tuning.cluster_ctas = 0;
+    *ran = false;
+    return GABP_OK;
+  }
+  CK(ce);
+  *ran = true;
+  ResidentOut o{};
+  CK(cudaMemcpyAsync(&o, h->res.out, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  gabp_stats &S = h->stats;
+  S = gabp_stats{};
+  S.sweeps_total = S.sweeps_full = o.sweeps;
+  S.outer_steps = 1;
+  S.residual_checks = o.checks;
+  S.status = o.status;
+  S.residual = o.residual;
+  S.rhs_norm = o.bnorm;
+  S.n = h->g.n;
+  S.edges = h->g.E;
+  S.kernel_launches = 1;
+  if (iters) *iters = o.sweeps;
+  const gabp_status st = static_cast<gabp_status>(o.status);
+  if (st != GABP_OK)
+    return fail(h, st, std::string("FP64 solve: ") + gabp_status_string(st) + ", residual " +
+                           std::to_string(o.residual) + " after " + std::to_string(o.sweeps) +
+                           " sweeps");
+  return GABP_OK;
+}
+
 // ---- autotuner ----
 // Milliseconds per launch of `launch` (CUDA events on the handle's stream,
 // after one untimed launch).
@@ -654,6 +803,7 @@ void fill_tuning(gabp_handle h) {
   t.group_lanes = h->g.group;
   t.dense_rows_mean = h->dense ? h->dense->rows_mean : 0;
   t.dense_rows_full = h->dense ? h->dense->rows_full : 0;
+  t.cluster_ctas = h->res.C;
 }
 
 // Times the candidate launch shapes on the handle's own matrix (zero
@@ -720,6 +870,26 @@ void autotune(gabp_handle h) {
       }
     }
     CK(set_row_tiles(g, slots, rows, heavy, h->stream));
+  }
+  if (!mixed && h->res.C > 0 && h->opt.cluster_ctas == 0) {
+    // cluster size of the one-launch FP64 solve: 64 sweeps each, no early stop
+    ensure(&h->bbuf, g.n);
+    float best = 1e30f;
+    int pick = h->res.C;
+    for (int C : {2, 4, 8, 16}) {
+      if (!build_resident(h, C)) continue;
+      const ResidentView v = resident_view(h, h->bbuf, h->bbuf, 0.0, 64, 64);
+      bool placed = true;
+      const float ms = time_launches(h, 2, [&] {
+        if (placed && launch_resident64(v, C, h->stream) == cudaErrorInvalidConfiguration) placed = false;
+      });
+      CK(cudaGetLastError());
+      ++T.candidates;
+      if (placed && ms < best) { best = ms; pick = C; }
+    }
+    if (!build_resident(h, pick)) free_resident(h->res);
+  }
+  if (h->dense || mixed) {
   } else if (h->opt.group_lanes == 0) {
     ensure64(h);
     float best = 1e30f;
@@ -757,10 +927,12 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
   const gabp_options &o = h->opt;
   if (o.tile_slots < 0 || (o.tile_slots > 0 && (o.tile_slots < 32 || o.tile_slots > 1024)) ||
       o.tile_rows < 0 || o.tile_rows > 256 || o.heavy_degree < 0 ||
+      !(o.cluster_ctas == 0 || o.cluster_ctas == 2 || o.cluster_ctas == 4 || o.cluster_ctas == 8 ||
+        o.cluster_ctas == 16) ||
       !(o.dense_rows == 0 || o.dense_rows == 1 || o.dense_rows == 2 || o.dense_rows == 4)) {
     delete h;
     g_create_error = "launch shape out of range (tile_slots 32..1024, tile_rows 1..256, "
-                     "heavy_degree >= 1, dense_rows 1, 2 or 4; 0 = automatic)";
+                     "heavy_degree >= 1, dense_rows 1, 2 or 4, cluster_ctas 2..16; 0 = automatic)";
     return GABP_ERR_INVALID_ARG;
   }
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
@@ -796,6 +968,12 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
     if (r != GABP_OK) h->last_error = msg;
     return r;
   });
+  if (s == GABP_OK) {
+    s = guarded(h, [&] {
+      if (h->opt.precision == GABP_PREC_FP64) setup_resident(h);
+      return GABP_OK;
+    });
+  }
   if (s == GABP_OK) {
     fill_tuning(h);
     if (h->opt.autotune) s = guarded(h, [&] { autotune(h); return GABP_OK; });
@@ -1038,6 +1216,12 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
     if (worst != GABP_OK) h->last_error = msg;
     return worst;
   });
+}
+
+gabp_status gabp_set_profile(gabp_handle h, int32_t on) {
+  if (!h || (on != 0 && on != 1)) return GABP_ERR_INVALID_ARG;
+  h->opt.profile = on;
+  return GABP_OK;
 }
 
 gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning) {

@@ -35,7 +35,8 @@ EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_str
             "gabp_solve", "gabp_solve_host", "gabp_solve_multi", "gabp_get_stats",
             "gabp_run_rounds", "gabp_get_messages", "gabp_last_error", "gabp_status_string",
             "gabp_version", "gabp_create_batched", "gabp_create_lsq_batched",
-            "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc", "gabp_get_tuning")
+            "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc", "gabp_get_tuning",
+            "gabp_set_profile")
 
 
 class GabpOptions(ctypes.Structure):
@@ -46,7 +47,8 @@ class GabpOptions(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("damping", ctypes.c_double), ("tile_rows", ctypes.c_int32),
                 ("heavy_degree", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
-                ("reserved_i", ctypes.c_int32), ("reserved_d", ctypes.c_double)]
+                ("small_form", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32)]
 
 
 class GabpStats(ctypes.Structure):
@@ -68,10 +70,11 @@ class GabpTuning(ctypes.Structure):
                 ("tile_slots", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
                 ("heavy_degree", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
                 ("dense_rows_mean", ctypes.c_int32), ("dense_rows_full", ctypes.c_int32),
+                ("cluster_ctas", ctypes.c_int32), ("reserved_i", ctypes.c_int32),
                 ("tune_ms", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
 class GabpError(RuntimeError):
@@ -121,6 +124,7 @@ def load(path: str = LIB_PATH):
         "gabp_run_rounds_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp,
                                                    ctypes.c_int32, vp, vp]),
         "gabp_get_tuning": (ctypes.c_int, [H, ctypes.POINTER(GabpTuning)]),
+        "gabp_set_profile": (ctypes.c_int, [H, ctypes.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -276,6 +280,10 @@ def gabp_get_stats(h) -> dict:
     return s.as_dict()
 
 
+def gabp_set_profile(h, on: bool):
+    _check(h, load().gabp_set_profile(h, 1 if on else 0))
+
+
 def gabp_get_tuning(h) -> dict:
     t = GabpTuning()
     _check(h, load().gabp_get_tuning(h, ctypes.byref(t)))
@@ -322,8 +330,10 @@ class Solver:
     def from_csr(cls, row_ptr, col, val, rev=None, *, precision=PREC_FP64,
                  residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=1e-6,
                  profile=False, damping=0.0, stream: int | None = None, autotune=False,
-                 tile_slots=0, tile_rows=0, heavy_degree=0):
+                 tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0):
         o = gabp_default_options()
+        o.small_form = small_form
+        o.cluster_ctas = cluster_ctas
         o.autotune = 1 if autotune else 0
         o.tile_slots = tile_slots
         o.tile_rows = tile_rows

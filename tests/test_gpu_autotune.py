@@ -108,7 +108,8 @@ def test_autotune_fp64_lanes_keep_round_parity(G):
     b = W.normal_rhs(m.n, 4)
     s = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=0, autotune=True)
     t = s.tuning()
-    assert t["tuned"] == 1 and t["candidates"] == 5 and t["group_lanes"] in {2, 4, 8, 16, 32}
+    # 5 lane counts, plus the cluster sizes that fit (one-launch solves)
+    assert t["tuned"] == 1 and t["candidates"] >= 5 and t["group_lanes"] in {2, 4, 8, 16, 32}
     bt = torch.tensor(b, device="cuda")
     xt = torch.empty_like(bt)
     for r in (1, 4, 11):

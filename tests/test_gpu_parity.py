@@ -306,7 +306,9 @@ def test_graph_and_host_drivers_agree(G, precision):
     bt = torch.tensor(b, device="cuda")
     out = []
     for profile in (False, True):
-        s = _solver(G, m, precision=precision, profile=profile)
+        # small_form=1: the per-sweep path in both (the one-launch cluster
+        # solve of small FP64 systems has no host-driven twin)
+        s = _solver(G, m, precision=precision, profile=profile, small_form=1)
         xt, it = s.solve(bt, tol=1e-10, max_iter=5000)
         st = s.stats()
         out.append((xt.cpu().numpy(), it, st))
