@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -56,6 +57,35 @@ BYTES = {
     "full64": (44, 24),    # A 8 + (P,eta) in 16 + rev 4 + (P,eta) out 16 | diag 8 + b 8 + x out 8
     "residual": (20, 32),  # A 8 + col 4 + x[col] 8 | diag 8 + x 8 + b 8 + r 8
 }
+
+
+# DRAM traffic of the dominant kernels from ncu captures (dram__bytes_read.sum
+# + dram__bytes_write.sum per launch; ncu flushes caches between replays, so
+# these are cold-cache figures), valid only for the kernel sources they were
+# taken on: a changed source makes the figure null.  Commands and numbers:
+# profiles/mean_kernel_er1e6.md and profiles/dense_mean_kernel_detect1024.md.
+TRAFFIC = {
+    "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "40a38cbe6ce0d36b",
+             "bytes_per_launch": 173.565696e6},
+    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "3dd517d7a0e51186",
+                   "bytes_per_pair": 23.1059},
+}
+
+
+def _traffic(kind, units=None):
+    import hashlib
+    t = TRAFFIC.get(kind)
+    if t is None:
+        return None
+    d = hashlib.sha256()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_0810_1119_gb300", "csrc", f), "rb") as fh:
+            d.update(fh.read())
+    if d.hexdigest()[:16] != t["sha"]:
+        return None
+    if "bytes_per_launch" in t:
+        return t["bytes_per_launch"]
+    return t["bytes_per_pair"] * units
 
 
 def _env_rank():
@@ -310,7 +340,7 @@ def run_gabp(args):
             "roofline": {"bound": "hbm", "kernel": kernel_names[dom],
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None,
-                         "peak_source": peak_kind, "traffic": None,
+                         "peak_source": peak_kind, "traffic": _traffic(dom),
                          "bytes_per_launch": bytes_launch, "launches": n_k,
                          "mean_launch_us": 1e3 * ms_k / max(n_k, 1),
                          "timing": "CUDA events around every kernel in a profiled pass "
@@ -457,6 +487,98 @@ def run_poisson32(args):
     return 0
 
 
+def run_poisson3d(args):
+    """3D Poisson 7-point Laplacian on a p^3 grid (p = 256: n = 16.8M, 100M
+    directed edges), b ~ U[-1, 1]; FP32 messages (and the BF16 mean-storage
+    variant) inside FP64 refinement to 1e-10 relative residual, beside the
+    plain FP64 sweep.  Convergence takes O(p^2) sweeps (~1e5 at p = 256), so
+    with --max-iter below that the run reports the measured per-sweep times
+    and the residual reached, and extrapolates the time to 1e-10 from the
+    observed FP64 residual contraction (labelled as such)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_0810_1119_gb300 import build_lib
+    build_lib.build()
+    from paper_0810_1119_gb300 import gabp
+    from paper_0810_1119_gb300 import workloads as W
+    p = args.p
+    t0 = time.perf_counter()
+    m = W.poisson3d(p)
+    b = W.uniform_rhs(m.n, 0)
+    gen_s = time.perf_counter() - t0
+    E = m.n_directed_edges
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    stream = torch.cuda.current_stream()
+    hbm, peak_src = _peaks()
+    res = {}
+    for name, prec in (("mixed_fp32", gabp.PREC_MIXED_FP32), ("mixed_bf16", gabp.PREC_MIXED_BF16),
+                       ("fp64", gabp.PREC_FP64)):
+        t0 = time.perf_counter()
+        s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=prec, autotune=True)
+        build_s = time.perf_counter() - t0
+        ms, st, err = [], None, ""
+        for step in range(max(1, args.steps)):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            try:
+                gabp.gabp_solve(s.handle, bt, xt, TOL, args.max_iter)
+            except gabp.GabpError as e:
+                err = e.name
+            z.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(z))
+            st = s.stats()
+        r = {"ms": statistics.mean(ms), "status": err or "GABP_OK", "sweeps": st["sweeps_total"],
+             "sweeps_full": st["sweeps_full"], "sweeps_mean": st["sweeps_mean"],
+             "outer": st["outer_steps"], "rel_residual": st["residual"] / st["rhs_norm"],
+             "handle_build_s": build_s, "tuning": s.tuning()}
+        # per-kernel times from a profiled pass capped at a few hundred sweeps
+        gabp.gabp_set_profile(s.handle, True)
+        try:
+            gabp.gabp_solve(s.handle, bt, xt, TOL, min(args.max_iter, 300))
+        except gabp.GabpError:
+            pass
+        sp = s.stats()
+        gabp.gabp_set_profile(s.handle, False)
+        if prec == gabp.PREC_FP64:
+            per = 1e3 * sp["ms_full"] / max(1, sp["sweeps_full"])
+            r["us_per_full_sweep"] = per
+            r["full_sweep_frac"] = (BYTES["full64"][0] * E + BYTES["full64"][1] * m.n) / (per * 1e-6) / 1e9 / hbm
+        else:
+            if sp["sweeps_mean"]:
+                per = 1e3 * sp["ms_mean"] / sp["sweeps_mean"]
+                eb = 14 if prec == gabp.PREC_MIXED_BF16 else 16   # BF16: eta in/out 2 + 2
+                r["us_per_mean_sweep"] = per
+                r["mean_sweep_frac"] = (eb * E + BYTES["mean"][1] * m.n) / (per * 1e-6) / 1e9 / hbm
+            if sp["sweeps_full"]:
+                r["us_per_full_sweep"] = 1e3 * sp["ms_full"] / sp["sweeps_full"]
+        res[name] = r
+        s.close()
+    f64 = res["fp64"]
+    mixed = res["mixed_fp32"]
+    extrap = None
+    if f64["status"] != "GABP_OK" and 0 < f64["rel_residual"] < 1:
+        # residual contraction per sweep observed over the capped FP64 run
+        rho = f64["rel_residual"] ** (1.0 / f64["sweeps"])
+        need = math.log(TOL) / math.log(rho)
+        extrap = {"fp64_sweeps_to_1e-10": need,
+                  "fp64_ms": need * f64["ms"] / f64["sweeps"],
+                  "mixed_fp32_ms_at_same_sweeps": need * mixed["ms"] / max(1, mixed["sweeps"]),
+                  "basis": "FP64 residual contraction over the capped run (extrapolated)"}
+    line = {"metric": f"time to 1e-10 relative residual, 3D Poisson {p}^3 (mixed FP32 + FP64 refinement)",
+            "value": mixed["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 0,
+            "ms_per_step": mixed["ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"3D Poisson 7-point {p}^3, b~U[-1,1], 1e-10 rel. residual",
+                       "n": m.n, "directed_edges": E, "max_iter": args.max_iter,
+                       "generate_s": gen_s},
+            "runs": res, "extrapolation": extrap,
+            "edge_updates_per_s_mixed": E * mixed["sweeps"] / (mixed["ms"] * 1e-3)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_detect(args):
     """Batched uneven linear detection: 4096 systems, K ~ U{16..256}, N = 2K,
     S = +-1/sqrt(N), x in {+-1}, y = S x + noise at 10 dB.  Every system is
@@ -527,7 +649,8 @@ def run_detect(args):
     roof = {"bound": "hbm", "kernel": "dense_mean_kernel (mean-only sweep)" if dense else "mean_kernel",
             "achieved": bytes_mean / (mean_us * 1e-6) / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": bytes_mean / (mean_us * 1e-6) / 1e9 / hbm, "peak_source": peak_src,
-            "traffic": None, "bytes_per_launch": bytes_mean, "mean_launch_us": mean_us,
+            "traffic": _traffic("dense_mean", pairs) if dense else None,
+            "bytes_per_launch": bytes_mean, "mean_launch_us": mean_us,
             "full_sweep_us": full_us,
             "full_sweep_frac": bytes_full / (full_us * 1e-6) / 1e9 / hbm,
             "timing": "CUDA events around every kernel in a profiled pass of the same solve (host driver)"}
@@ -559,8 +682,11 @@ def main():
     ap.add_argument("--cpu-rounds", type=int, default=10)
     ap.add_argument("--ref-rounds", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="er1e6", choices=["er1e6", "multi64", "detect", "poisson32"],
-                    help="er1e6: the headline line; multi64 / detect / poisson32: extra lines")
+    ap.add_argument("--p", type=int, default=128, help="poisson3d: grid side")
+    ap.add_argument("--max-iter", type=int, default=200000, help="poisson3d: sweep cap per solve")
+    ap.add_argument("--workload", default="er1e6",
+                    choices=["er1e6", "multi64", "detect", "poisson32", "poisson3d"],
+                    help="er1e6: the headline line; multi64 / detect / poisson32 / poisson3d: extra lines")
     ap.add_argument("--nsys", type=int, default=4096)
     ap.add_argument("--lsq-form", type=int, default=0, choices=[0, 1],
                     help="detect: 0 = dense bipartite kernels, 1 = general CSR path")
@@ -575,6 +701,8 @@ def main():
         return run_detect(args)
     if args.workload == "poisson32":
         return run_poisson32(args)
+    if args.workload == "poisson3d":
+        return run_poisson3d(args)
     return run_gabp(args)
 
 
