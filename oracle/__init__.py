@@ -14,6 +14,10 @@ Contents
 * ``residual_inf``  -- ||b - A x||_inf (Section II, residual definition).
 * ``augment_lsq``   -- the symmetric augmented system of Section VII
                        (``augment.py``).
+* ``aitken``, ``gabp_aitken`` -- Aitken's Delta^2 extrapolation of the
+                       tentative means (Section V, convergence acceleration),
+                       applied per node to the means of rounds t - 2s, t - s
+                       and t.
 
 Every function is pinned by CPU tests (``tests/test_oracle_*.py``) to values
 the paper prints, closed forms and brute force -- not to itself.
@@ -161,3 +165,32 @@ def num_threads() -> int:
 
 def set_num_threads(k: int) -> None:
     _load().oracle_set_num_threads(int(k))
+
+
+def aitken(x0, x1, x2):
+    """Aitken's Delta^2 per node (Section V, convergence acceleration):
+    y = x0 - (x1 - x0)^2 / (x2 - 2 x1 + x0) for three iterates of a sequence
+    that converges linearly.  Where the second difference is not above the
+    rounding level of the iterates (|x2 - 2 x1 + x0| <= 64 eps max|x_k|) the
+    formula carries no information and the latest iterate x2 is kept."""
+    x0 = np.asarray(x0, dtype=np.float64)
+    x1 = np.asarray(x1, dtype=np.float64)
+    x2 = np.asarray(x2, dtype=np.float64)
+    d1 = x1 - x0
+    den = (x2 - x1) - d1
+    scale = np.maximum(np.maximum(np.abs(x0), np.abs(x1)), np.abs(x2))
+    ok = np.abs(den) > 64.0 * np.finfo(np.float64).eps * scale
+    y = np.where(ok, x0 - d1 * d1 / np.where(ok, den, 1.0), x2)
+    return y
+
+
+def gabp_aitken(row_ptr, col, val, b, rounds: int, stride: int = 2, damping: float = 0.0):
+    """Aitken-extrapolated means after `rounds` synchronous rounds: the
+    Delta^2 of the tentative means of rounds rounds - 2 stride,
+    rounds - stride and rounds (plain means when rounds < 2 stride)."""
+    if rounds < 2 * stride:
+        return gabp(row_ptr, col, val, b, max_rounds=rounds, damping=damping)["x"]
+    xs = [gabp(row_ptr, col, val, b, max_rounds=r, damping=damping)["x"]
+          for r in (rounds - 2 * stride, rounds - stride, rounds)]
+    return aitken(*xs)
+

@@ -312,3 +312,51 @@ def test_damping_keeps_the_solution_and_rescues_divergence():
     # precisions are not damped: identical to the plain run's
     np.testing.assert_allclose(damped["Pi"], oracle.gabp(rp, cl, vl, rhs, max_rounds=damped["rounds"])["Pi"],
                                rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Aitken's Delta^2 (Section V, convergence acceleration)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("a", [0.5, -0.9, 0.99, -0.3])
+def test_aitken_is_exact_on_one_geometric_mode(a):
+    """For x_n = L + c a^n (any |a| < 1, either sign) the Delta^2 formula
+    returns L exactly: the defining property the paper states.  In floating
+    point the second difference is c a^n (1 - a)^2, formed from iterates of
+    size |L|, so the result carries ~eps / (1 - a)^2 of relative rounding."""
+    rng = np.random.default_rng(3)
+    L = rng.standard_normal(50)
+    c = rng.standard_normal(50)
+    n = 7
+    xs = [L + c * a ** k for k in (n, n + 1, n + 2)]
+    y = oracle.aitken(*xs)
+    tol = 100 * np.finfo(float).eps / (1 - a) ** 2
+    assert np.abs(y - L).max() <= tol * np.abs(L).max()
+
+
+def test_aitken_keeps_the_latest_iterate_without_curvature():
+    x = np.array([1.0, -2.0, 3.0])
+    assert np.array_equal(oracle.aitken(x, x, x), x)             # converged: Delta = 0
+    lin0, lin1, lin2 = x, x + 1e-3, x + 2e-3                      # second difference 0
+    assert np.array_equal(oracle.aitken(lin0, lin1, lin2), lin2)
+
+
+def test_aitken_on_gabp_means_solves_poisson_in_fewer_rounds():
+    """Synchronous GaBP on the 2D Poisson grid (a bipartite graph): the
+    tentative means' error carries a component that flips sign every round,
+    so Delta^2 over rounds two apart (stride 2) is what accelerates: the
+    extrapolated means meet 1e-10 in well under 60 % of the plain rounds
+    (the paper's Table for 2D Poisson: 134 plain vs 25 Aitken rounds)."""
+    m = W.poisson2d(10)
+    b = W.uniform_rhs(m.n, 0)
+
+    def first_round(extrapolate):
+        for r in range(8, 600, 4):
+            x = oracle.gabp_aitken(m.row_ptr, m.col, m.val, b, r, 2) if extrapolate else \
+                oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=r)["x"]
+            if oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10:
+                return r
+        return None
+
+    plain, acc = first_round(False), first_round(True)
+    assert plain is not None and acc is not None
+    assert acc <= 0.6 * plain, (plain, acc)
