@@ -93,7 +93,13 @@ typedef struct {
                              0 = the whole solve in one cluster launch, 1 = always a launch
                              per sweep */
   int32_t cluster_ctas;   /* CTAs of that cluster (2, 4, 8 or 16); 0 = automatic */
-  int32_t reserved_i;
+  int32_t aitken;         /* FP64 solves and gabp_run_rounds: Aitken's Delta^2 (Section V,
+                             convergence acceleration) on the tentative means of rounds
+                             t - 2s, t - s and t with stride s = aitken (1..64); the stop rule
+                             and the returned x use the extrapolated means.  On grid
+                             (bipartite) graphs the synchronous schedule's error flips sign
+                             every round: s = 2 accelerates there, s = 1 does not.
+                             0 = off (dense Section VII handles: always off) */
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */

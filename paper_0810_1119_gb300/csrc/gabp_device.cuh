@@ -135,6 +135,14 @@ __device__ void finish(Ctl &c, int status) {
   c.phase = PH_DONE;
 }
 
+// FP64 sweeps: whether sweep `t` (1-based) writes the tentative means, and
+// where (the Aitken ring, or x).
+__device__ void plan_means(Ctl &c, int t) {
+  const bool check = (t % c.check_every == 0) || t >= c.max_iter;
+  c.write_x = check || (c.aitken > 0 && t % c.aitken == 0);
+  c.xw = c.aitken > 0 ? c.ring[c.nw % 3] : c.x;
+}
+
 __device__ bool diverged(double rn, double bnorm) {
   return !isfinite(rn) || rn > 1e30 * fmax(bnorm, DBL_MIN);
 }
@@ -157,7 +165,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (!isfinite(c.bnorm)) { finish(c, GABP_ERR_INVALID_ARG); break; }
       if (c.mode == CTL_FP64) {
         c.phase = PH_FULL64;
-        c.write_x = (c.check_every <= 1) || (c.max_iter <= 1);
+        plan_means(c, 1);
       } else if (c.mode == CTL_PREC) {
         // precisions only: zero right-hand side, unit scale
         c.rn = 1.0;
@@ -178,7 +186,14 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (c.mode == CTL_ROUNDS) {
         // the pass after `rounds_target` sweeps only infers and leaves the
         // state alone, so the last round's messages stay in m64[par_m]
-        if (c.sweeps < c.rounds_target) { c.sweeps++; c.par_m ^= 1; c.first = 0; }
+        const bool infer_pass = c.sweeps >= c.rounds_target;
+        if (!infer_pass) { c.sweeps++; c.par_m ^= 1; c.first = 0; }
+        // Aitken: the means of rounds R - 2s, R - s and R go to the ring
+        if ((c.write_x || infer_pass) && c.aitken > 0) c.nw++;
+        const int R = c.rounds_target, s2 = 2 * c.aitken;
+        const bool ait = c.aitken > 0 && R >= s2;
+        c.write_x = ait && (c.sweeps == R - s2 || c.sweeps == R - c.aitken);
+        c.xw = ait ? c.ring[c.nw % 3] : c.x;
         break;
       }
       c.sweeps++;
@@ -186,9 +201,10 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       c.par_m ^= 1;
       c.first = 0;
       if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
-      if (c.write_x) c.phase = PH_CHECK64;
-      const int next = c.sweeps + 1;
-      c.write_x = (next % c.check_every == 0) || next >= c.max_iter;
+      if (c.write_x && c.aitken > 0) c.nw++;
+      c.check_now = (c.sweeps % c.check_every == 0) || c.sweeps >= c.max_iter;
+      if (c.check_now) c.phase = PH_CHECK64;
+      plan_means(c, c.sweeps + 1);
       break;
     }
     case CK_CHECK64:

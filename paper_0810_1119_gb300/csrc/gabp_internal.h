@@ -106,6 +106,13 @@ struct Ctl {
   int status, done;
   unsigned int blocks_done;     // last-block detection counter
   unsigned int work_next;       // dense batches: next system to claim (reset by the last block)
+  // Aitken's Delta^2 on the tentative means (FP64 sweeps): every `aitken`
+  // sweeps the means go to ring[nw % 3]; a check extrapolates the last three
+  // into x.  aitken = 0: the means go straight to x.
+  int aitken, nw;
+  double *ring[3];
+  double *xw;                   // where the next sweep that writes means writes them
+  int check_now;                // the sweep just run is followed by a residual check
   int K;                        // CTL_MULTI: right-hand sides
   const double *Bm;             // CTL_MULTI: n x K right-hand sides (row-major)
   double *Xm;                   // CTL_MULTI: n x K solutions (row-major)
@@ -181,7 +188,8 @@ struct Graph {
 // last block.
 int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
 int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
-int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                   bool aitken);
 int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
 int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
 int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
@@ -256,12 +264,13 @@ int launch_dense_mean(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevS
 int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *ctl,
                           DevScalars *red, bool refine);
 int launch_refine_update(int32_t n, cudaStream_t st, Buffers B, Ctl *ctl);
+int launch_aitken(int32_t n, cudaStream_t st, Ctl *ctl, double *out);
 void prepare_dense_kernels(bool bf16);
 
 // ---- whole FP64 solves of small systems in one cluster launch (gabp_resident.cu) ----
 constexpr int kResidentMaxCluster = 16;   // CTAs of the cluster (16 needs the non-portable size)
-constexpr int kResidentMaxSlots = 3584;   // incoming-message slots per CTA
-constexpr int kResidentMaxRows = 1024;    // rows per CTA
+constexpr int kResidentMaxSlots = 3072;   // incoming-message slots per CTA
+constexpr int kResidentMaxRows = 896;     // rows per CTA
 
 struct ResidentOut {
   int32_t status, sweeps, checks, pad;
@@ -272,6 +281,7 @@ struct ResidentOut {
 // message of its row): dst[s] = (CTA << 24) | local slot of rev[s] in that
 // CTA, colp[s] = (CTA << 16) | local row of col[s].
 struct ResidentView {
+  int32_t aitken;                // Delta^2 stride over the tentative means (0 = off)
   const int32_t *row0;
   const int32_t *rp;
   const double *a64, *diag64;
@@ -347,6 +357,7 @@ struct gabp_s {
   gabp::Dense *dense = nullptr;        // Section VII batches in dense bipartite form
   gabp_tuning tuning{};                // launch shapes (chosen by the autotuner or default)
   gabp::Resident res{};                // small FP64 systems: one cluster launch per solve
+  double *ring[3] = {};                // Aitken: the last three FP64 tentative means
   cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
 
   // profiling (gabp_options.profile): pairs of events around kernels

@@ -287,14 +287,14 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   bool write_x, write_msgs;
   if (ctl->mode == CTL_ROUNDS) {
     const bool infer_only = ctl->sweeps >= ctl->rounds_target;
-    write_x = infer_only;
+    write_x = infer_only || ctl->write_x != 0;
     write_msgs = !infer_only;
   } else {
     write_x = ctl->write_x != 0;
     write_msgs = true;
   }
   const double *__restrict__ b = ctl->b;
-  double *__restrict__ x = ctl->x;
+  double *__restrict__ x = ctl->xw;   // x itself, or a slot of the Aitken ring
   const double2 *__restrict__ min = (par ? B.m64[1] : B.m64[0]);
   double2 *__restrict__ mout = (par ? B.m64[0] : B.m64[1]);
   const int gl = threadIdx.x % G;
@@ -704,6 +704,34 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   if (!ok) atomicOr(&red->timeout, 1);
   block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
   last_block_control(ctl, red, CK_MEAN);
+}
+
+// Aitken's Delta^2 per node on the last three tentative means in the ring
+// (Section V, convergence acceleration): y = x0 - (x1 - x0)^2 / (x2 - 2 x1
+// + x0), or the latest mean x2 where the second difference is at rounding
+// level (|x2 - 2 x1 + x0| <= 64 eps max|x_k|) or fewer than three means exist.
+// out = nullptr: the solve's x (read from the control block, so a recorded
+// graph serves every solve).
+__global__ void __launch_bounds__(kBlock) aitken_kernel(int32_t n, const Ctl *ctl, double *out) {
+  const int nw = ctl->nw;
+  if (nw < 1) return;
+  double *__restrict__ dst = out ? out : ctl->x;
+  const double *__restrict__ x2 = ctl->ring[(nw - 1) % 3];
+  const double *__restrict__ x1 = ctl->ring[(nw + 1) % 3];   // (nw - 2) mod 3
+  const double *__restrict__ x0 = ctl->ring[nw % 3];         // (nw - 3) mod 3
+  const bool have3 = nw >= 3;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double c2 = x2[i];
+    double y = c2;
+    if (have3) {
+      const double c0 = x0[i], c1 = x1[i];
+      const double d1 = c1 - c0, den = (c2 - c1) - d1;
+      const double scale = fmax(fmax(fabs(c0), fabs(c1)), fabs(c2));
+      if (fabs(den) > 64.0 * DBL_EPSILON * scale) y = c0 - d1 * d1 / den;
+    }
+    dst[i] = y;
+  }
 }
 
 // x_i += ||r|| d_i (FP64), d_i from the latest monitor.
@@ -1187,9 +1215,18 @@ int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars
   return 1;
 }
 
-int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                   bool aitken) {
   (void)B;
-  return launch_residual(g, st, nullptr, ctl, red, CK_CHECK64);
+  if (!aitken) return launch_residual(g, st, nullptr, ctl, red, CK_CHECK64);
+  // extrapolated means into x, then the residual of x
+  aitken_kernel<<<flat_grid(g.n), kBlock, 0, st>>>(g.n, ctl, nullptr);
+  return 1 + launch_residual(g, st, nullptr, ctl, red, CK_CHECK64);
+}
+
+int launch_aitken(int32_t n, cudaStream_t st, Ctl *ctl, double *out) {
+  aitken_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, ctl, out);
+  return 1;
 }
 
 int launch_refine_update(int32_t n, cudaStream_t st, Buffers B, Ctl *ctl) {

@@ -32,7 +32,7 @@ constexpr int kResBlock = 256;
 // Shared-memory layout of every CTA of the cluster (the same offsets in all,
 // so a remote address is the local offset in another CTA's window).
 struct ResLayout {
-  uint32_t m0, m1, a, dst, colp, lrow, lrp, dg, bb, tp, x0, x1, red, bytes;
+  uint32_t m0, m1, a, dst, colp, lrow, lrp, dg, bb, tp, r0, r1, r2, y0, y1, red, bytes;
 };
 __host__ __device__ inline ResLayout res_layout(int smax, int rmax) {
   ResLayout L;
@@ -47,9 +47,12 @@ __host__ __device__ inline ResLayout res_layout(int smax, int rmax) {
   L.dg = up(L.lrp + 4u * (rmax + 1));
   L.bb = up(L.dg + 8u * rmax);
   L.tp = up(L.bb + 8u * rmax);
-  L.x0 = up(L.tp + 16u * rmax);
-  L.x1 = up(L.x0 + 8u * rmax);
-  L.red = up(L.x1 + 8u * rmax);
+  L.r0 = up(L.tp + 16u * rmax);   // Aitken ring of tentative means
+  L.r1 = up(L.r0 + 8u * rmax);
+  L.r2 = up(L.r1 + 8u * rmax);
+  L.y0 = up(L.r2 + 8u * rmax);     // checked means (extrapolated or not), by check parity
+  L.y1 = up(L.y0 + 8u * rmax);
+  L.red = up(L.y1 + 8u * rmax);
   L.bytes = up(L.red + 8u * 4 * kResidentMaxCluster);
   return L;
 }
@@ -78,7 +81,9 @@ __global__ void __launch_bounds__(kResBlock) resident64_kernel(ResidentView v) {
   double *dg = reinterpret_cast<double *>(sm + L.dg);
   double *bb = reinterpret_cast<double *>(sm + L.bb);
   double2 *tp = reinterpret_cast<double2 *>(sm + L.tp);   // (P~_i, h~_i) of this sweep
-  double *xs[2] = {reinterpret_cast<double *>(sm + L.x0), reinterpret_cast<double *>(sm + L.x1)};
+  double *ring[3] = {reinterpret_cast<double *>(sm + L.r0), reinterpret_cast<double *>(sm + L.r1),
+                     reinterpret_cast<double *>(sm + L.r2)};
+  double *xs[2] = {reinterpret_cast<double *>(sm + L.y0), reinterpret_cast<double *>(sm + L.y1)};
   double *red = reinterpret_cast<double *>(sm + L.red);   // CTA 0: [parity][max r | breakdown][C]
   const int tid = threadIdx.x;
   __shared__ unsigned long long part[2];
@@ -114,6 +119,8 @@ __global__ void __launch_bounds__(kResBlock) resident64_kernel(ResidentView v) {
   cl.sync();   // red0 is rewritten by the first check
 
   const double gam = v.damping;
+  const int ait = v.aitken;   // Delta^2 stride (0 = off)
+  int nw = 0;                 // tentative means written to the ring
   int status = GABP_ERR_NOT_CONVERGED, checks = 0, sweeps = 0, pending = -1, pending_sweeps = 0;
   double rn = bnorm;
   bool brk = false;
@@ -137,8 +144,11 @@ __global__ void __launch_bounds__(kResBlock) resident64_kernel(ResidentView v) {
   for (int it = 0; it < v.max_iter; ++it) {
     const int cur = it & 1;
     const bool first = it == 0;
-    const bool write_x = ((it + 1) % v.check_every == 0) || it + 1 >= v.max_iter;
+    const bool write_x = ((it + 1) % v.check_every == 0) || it + 1 >= v.max_iter;   // a check
+    const bool to_ring = ait > 0 && (write_x || (it + 1) % ait == 0);
     double *xw = xs[checks & 1];
+    double *rw = ring[nw % 3];
+    const double *rp1 = ring[(nw + 2) % 3], *rp2 = ring[(nw + 1) % 3];   // written 1 and 2 steps ago
     const double2 *min = m[cur];
     for (int k = tid; k < R; k += kResBlock) {
       double sP = 0.0, sH = 0.0;
@@ -149,7 +159,20 @@ __global__ void __launch_bounds__(kResBlock) resident64_kernel(ResidentView v) {
         }
       const double TP = dg[k] + sP, Th = bb[k] + sH;
       tp[k] = make_double2(TP, Th);
-      if (write_x) xw[k] = Th / TP;
+      if (to_ring || write_x) {
+        const double xi = Th / TP;
+        if (to_ring) rw[k] = xi;
+        if (write_x) {
+          double y = xi;
+          if (ait > 0 && nw >= 2) {   // Delta^2 of the means of rounds t - 2s, t - s, t
+            const double c0 = rp2[k], c1 = rp1[k];
+            const double d1 = c1 - c0, den = (xi - c1) - d1;
+            const double scale = fmax(fmax(fabs(c0), fabs(c1)), fabs(xi));
+            if (fabs(den) > 64.0 * DBL_EPSILON * scale) y = c0 - d1 * d1 / den;
+          }
+          xw[k] = y;
+        }
+      }
     }
     __syncthreads();
     for (int32_t s = tid; s < S; s += kResBlock) {
@@ -167,6 +190,7 @@ __global__ void __launch_bounds__(kResBlock) resident64_kernel(ResidentView v) {
       cl.map_shared_rank(m[cur ^ 1], to >> 24)[to & 0xFFFFFF] = make_double2(-(as * as) * inv, eta);
     }
     cl.sync();   // round it + 1 delivered everywhere; x of this sweep visible
+    if (to_ring) ++nw;
     if (pending >= 0) {
       const bool stop = decide(pending);
       pending = -1;

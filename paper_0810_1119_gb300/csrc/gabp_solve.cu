@@ -218,7 +218,9 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
   }
   switch (phase) {
     case PH_FULL64: return launch_sweep64(g, st, h->buf, h->ctl, h->red);
-    case PH_CHECK64: return launch_check64(g, st, h->buf, h->ctl, h->red);
+    case PH_CHECK64:
+      return launch_check64(g, st, h->buf, h->ctl, h->red,
+                            h->opt.aitken > 0 && h->opt.precision == GABP_PREC_FP64);
     case PH_FULL32: return launch_sweep32(g, st, h->buf, h->ctl, h->red, is_bf16(h));
     case PH_MEAN: return launch_mean(g, st, h->buf, h->ctl, h->red, is_bf16(h));
     case PH_REFINE: return launch_refine(g, st, h->buf, h->ctl, h->red);
@@ -323,6 +325,19 @@ void init_ctl(gabp_handle h, int mode, const double *b, double *x, double tol, i
   if (in_graph) {
     c.h_while = h->cond[mode][0];
     c.h_phase = h->cond[mode][1];
+  }
+  c.xw = x;
+  // Aitken's Delta^2 on the FP64 tentative means (per-sweep CSR path)
+  if (h->opt.aitken > 0 && h->opt.precision == GABP_PREC_FP64 && !h->dense &&
+      (mode == CTL_FP64 || mode == CTL_ROUNDS)) {
+    const int s = h->opt.aitken;
+    for (int k = 0; k < 3; ++k) {
+      ensure(&h->ring[k], h->g.n);
+      c.ring[k] = h->ring[k];
+    }
+    c.aitken = s;
+    int ce = std::max(c.check_every, 2 * s);
+    c.check_every = (ce + s - 1) / s * s;
   }
   c.first = 1;
   c.prev_dd = std::numeric_limits<double>::infinity();
@@ -553,6 +568,7 @@ void release(gabp_handle h) {
     h->dense = nullptr;
   }
   free_resident(h->res);
+  for (double *&r : h->ring) { cudaFree(r); r = nullptr; }
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
@@ -724,8 +740,11 @@ ResidentView resident_view(gabp_handle h, const double *b, double *x, double tol
 // cluster (the handle then keeps to the per-sweep path).
 gabp_status resident_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                            int32_t *iters, bool *ran) {
-  const int check_every = h->opt.check_every > 0 ? h->opt.check_every : 4;
-  const ResidentView v = resident_view(h, b, x, tol, max_iter, check_every);
+  int check_every = h->opt.check_every > 0 ? h->opt.check_every : 4;
+  const int ait = h->opt.aitken;
+  if (ait > 0) check_every = (std::max(check_every, 2 * ait) + ait - 1) / ait * ait;
+  ResidentView v = resident_view(h, b, x, tol, max_iter, check_every);
+  v.aitken = ait;
   const cudaError_t ce = launch_resident64(v, h->res.C, h->stream);
   if (ce == cudaErrorInvalidConfiguration) {
     free_resident(h->res);
@@ -928,11 +947,11 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
   if (o.tile_slots < 0 || (o.tile_slots > 0 && (o.tile_slots < 32 || o.tile_slots > 1024)) ||
       o.tile_rows < 0 || o.tile_rows > 256 || o.heavy_degree < 0 ||
       !(o.cluster_ctas == 0 || o.cluster_ctas == 2 || o.cluster_ctas == 4 || o.cluster_ctas == 8 ||
-        o.cluster_ctas == 16) ||
+        o.cluster_ctas == 16) || o.aitken < 0 || o.aitken > 64 ||
       !(o.dense_rows == 0 || o.dense_rows == 1 || o.dense_rows == 2 || o.dense_rows == 4)) {
     delete h;
     g_create_error = "launch shape out of range (tile_slots 32..1024, tile_rows 1..256, "
-                     "heavy_degree >= 1, dense_rows 1, 2 or 4, cluster_ctas 2..16; 0 = automatic)";
+                     "heavy_degree >= 1, dense_rows 1, 2 or 4, cluster_ctas 2..16, aitken 0..64; 0 = automatic)";
     return GABP_ERR_INVALID_ARG;
   }
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
@@ -1244,7 +1263,12 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
     cudaStream_t st = h->stream;
     ensure64(h);
     init_ctl(h, CTL_ROUNDS, b_dev, x_dev, 0.0, rounds, false);
-    h->ctl_host->rounds_target = rounds;
+    Ctl &c = *h->ctl_host;
+    c.rounds_target = rounds;
+    // Aitken: the means of rounds R - 2s, R - s and R go to the ring
+    const bool ait = c.aitken > 0 && rounds >= 2 * c.aitken;
+    c.write_x = ait && (rounds == 2 * c.aitken);   // round 0 = R - 2s
+    c.xw = ait ? c.ring[0] : x_dev;
     CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
     // `rounds` message sweeps, then one pass that only writes the means.
@@ -1252,6 +1276,7 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
       if (h->dense) launch_dense_full64(*h->dense, st, h->buf, h->ctl, h->red);
       else launch_sweep64(h->g, st, h->buf, h->ctl, h->red);
     }
+    if (ait) launch_aitken(h->g.n, st, h->ctl, x_dev);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     DevScalars red{};

@@ -48,7 +48,7 @@ class GabpOptions(ctypes.Structure):
                 ("damping", ctypes.c_double), ("tile_rows", ctypes.c_int32),
                 ("heavy_degree", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
                 ("small_form", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
-                ("reserved_i", ctypes.c_int32)]
+                ("aitken", ctypes.c_int32)]
 
 
 class GabpStats(ctypes.Structure):
@@ -330,8 +330,10 @@ class Solver:
     def from_csr(cls, row_ptr, col, val, rev=None, *, precision=PREC_FP64,
                  residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=1e-6,
                  profile=False, damping=0.0, stream: int | None = None, autotune=False,
-                 tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0):
+                 tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0,
+                 aitken=0):
         o = gabp_default_options()
+        o.aitken = aitken
         o.small_form = small_form
         o.cluster_ctas = cluster_ctas
         o.autotune = 1 if autotune else 0

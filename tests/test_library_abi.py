@@ -120,7 +120,7 @@ def test_launch_shape_options_are_validated():
     from paper_0810_1119_gb300 import gabp as G
     m = W.poisson2d(4)
     for field, value in (("tile_slots", 16), ("tile_slots", 2048), ("tile_rows", 300),
-                         ("heavy_degree", -1), ("dense_rows", 3), ("cluster_ctas", 3)):
+                         ("heavy_degree", -1), ("dense_rows", 3), ("cluster_ctas", 3), ("aitken", -1)):
         o = G.gabp_default_options()
         setattr(o, field, value)
         with pytest.raises(G.GabpError) as ei:
