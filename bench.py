@@ -170,6 +170,18 @@ def _cpu_baseline(m, b, rounds: int):
                       f"{dt:.2f} s"}
 
 
+def reduce_over_ranks(dist, times, counts, device):
+    """Whole-job figures of a replicated run: the slowest rank's times (MAX)
+    and the units of work of all ranks (SUM).  Works with any process group
+    (NCCL with CUDA tensors, gloo with CPU tensors)."""
+    import torch
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(list(counts), dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t.cpu()], [float(v) for v in c.cpu()]
+
+
 def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
@@ -293,12 +305,9 @@ def run_gabp(args):
     e2e_updates = sum(E * it for it in e2e_sweeps)
     e2e_s = sum(e2e_t)
     if dist is not None:
-        t = torch.tensor([tot_ms, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([updates, e2e_updates, launches], dtype=torch.float64, device=dev)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        tot_ms, e2e_s = float(t[0]), float(t[1])
-        updates, e2e_updates, launches = float(u[0]), float(u[1]), int(u[2])
+        (tot_ms, e2e_s), (updates, e2e_updates, launches) = reduce_over_ranks(
+            dist, [tot_ms, e2e_s], [updates, e2e_updates, launches], dev)
+        launches = int(launches)
 
     if rank == 0:
         hbm, peak_kind = _peaks()
