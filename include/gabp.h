@@ -78,7 +78,9 @@ typedef struct {
                              K_s <= 256 and N_s <= 1024, else the general CSR path;
                              1 = always the general CSR path */
   int32_t tile_slots;     /* CSR form: slots per row tile of the FP32 sweeps (32..1024); 0 = 1024 */
-  double inner_tol;       /* mixed modes: relative accuracy asked of each inner FP32 solve; 0 = 1e-6 */
+  double inner_tol;       /* mixed modes: relative accuracy asked of an inner FP32 solve (for one
+                             system the last refinement step asks only what the stop rule still
+                             needs); 0 = automatic: 1e-7, or 1e-6 for batched handles */
   void *stream;           /* cudaStream_t used by every call on the handle; NULL = legacy default */
   double damping;         /* gamma in [0, 1): each new message's information P_ij mu_ij becomes
                              gamma * previous + (1 - gamma) * new (precisions undamped); a fixed
@@ -125,7 +127,7 @@ typedef struct {
 } gabp_stats;
 
 /* Fills *opt with the defaults: FP64, relative residual, automatic check
- * interval and launch shape, no autotuning, inner_tol 1e-6, NULL stream. */
+ * interval and launch shape, no autotuning, automatic inner_tol, NULL stream. */
 void gabp_default_options(gabp_options *opt);
 
 /*

@@ -174,7 +174,8 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
         c.phase = PH_FULL32;
       } else {
         c.rn = c.bnorm;
-        c.best_rn = c.bnorm;
+        c.best_rn = INFINITY;
+        c.outer_stall = -1;   // the first refinement check sets the reference
         if (c.rn < c.thr || c.bnorm == 0.0) { finish(c, GABP_OK); break; }
         c.inv_rn = 1.0 / c.rn;
         c.outer = 1;
@@ -221,14 +222,27 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (diverged(rn, c.bnorm)) { finish(c, GABP_ERR_DIVERGED); break; }
       if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
       if (kind == CK_CHECK64) { c.phase = PH_FULL64; break; }
-      // Refinement that stopped paying: four outer steps without halving the
-      // residual (inner solves no more accurate than their storage allows).
-      if (rn < 0.5 * c.best_rn) { c.best_rn = rn; c.outer_stall = 0; }
-      else if (++c.outer_stall >= 4) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
-      // next refinement step: solve A d = r / ||r|| from zero mean messages
+      // Refinement that stopped paying: eight outer steps without a 10 %
+      // smaller residual (inner solves no more accurate than their storage
+      // allows, e.g. BF16 messages on an ill-conditioned system).  Slow but
+      // real progress -- a batch whose slowest system gains a little per
+      // step -- keeps going.
+      {
+        // progress in the measure the stop rule uses (batches: worst relative)
+        const double prog = (c.batched && c.rel) ? rrel : rn;
+        if (c.outer_stall < 0 || prog < 0.9 * c.best_rn) { c.best_rn = prog; c.outer_stall = 0; }
+        else if (++c.outer_stall >= 8) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
+      }
+      // next refinement step: solve A d = r / ||r|| from zero mean messages.
+      // One system: the inner solve only has to shrink the residual by the
+      // factor the stop rule still needs (0.3 margin), never more than
+      // inner_tol.  A batch keeps inner_tol: its inner accuracy is measured
+      // against the largest system's residual, which says nothing about the
+      // smallest system's own relative rule.
       c.outer++;
       c.rn = rn;
       c.inv_rn = 1.0 / rn;
+      c.inner_goal = c.batched ? c.inner_tol : fmax(c.inner_tol, 0.3 * c.thr / fmax(rn, DBL_MIN));
       c.k = 0;
       c.stall = 0;
       c.prev_dd = INFINITY;
@@ -286,7 +300,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       else c.since_best++;
       const bool plateau = c.plateau > 0 && c.since_best >= c.plateau && dd < c.floor_dd;
       const bool inner_done = c.frozen && c.k >= 3 &&
-                              (err_d < c.inner_tol || (c.stall >= 2 && dd < c.floor_dd) || plateau);
+                              (err_d < c.inner_goal || (c.stall >= 2 && dd < c.floor_dd) || plateau);
       if (inner_done || c.sweeps >= c.max_iter) c.phase = PH_REFINE;
       else c.phase = c.frozen ? PH_MEAN : PH_FULL32;
       break;
@@ -330,7 +344,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       const double err_d = dd == 0.0 ? 0.0 : (rho_d < 1.0 ? dd * rho_d / (1.0 - rho_d) : INFINITY);
       c.stall = rho_d >= 1.0 ? c.stall + 1 : 0;
       c.prev_dd = dd;
-      const bool inner_done = c.k >= 3 && (err_d < c.inner_tol || (c.stall >= 2 && dd < 1e-4));
+      const bool inner_done = c.k >= 3 && (err_d < c.inner_goal || (c.stall >= 2 && dd < 1e-4));
       c.phase = (inner_done || c.sweeps >= c.max_iter) ? PH_REFINEK : PH_MEANK;
       break;
     }
@@ -351,13 +365,19 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (all_done) { finish(c, GABP_OK); break; }
       if (bad) { finish(c, GABP_ERR_DIVERGED); break; }
       if (c.sweeps >= c.max_iter) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
-      if (worst < 0.5 * c.best_rn) { c.best_rn = worst; c.outer_stall = 0; }
-      else if (++c.outer_stall >= 4) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
+      if (worst < 0.9 * c.best_rn) { c.best_rn = worst; c.outer_stall = 0; }
+      else if (++c.outer_stall >= 8) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
       c.outer++;
       c.k = 0;
       c.stall = 0;
       c.prev_dd = INFINITY;
       c.first = 1;
+      {
+        double need = INFINITY;   // the column furthest from its threshold sets the goal
+        for (int k = 0; k < c.K; ++k)
+          if (c.cols.rn[k] > 0.0) need = fmin(need, c.cols.thr[k] / c.cols.rn[k]);
+        c.inner_goal = fmax(c.inner_tol, 0.3 * need);
+      }
       c.phase = PH_MEANK;
       break;
     }

@@ -83,6 +83,7 @@ struct Ctl {
   int max_iter;
   int check_every;
   double inner_tol;
+  double inner_goal;            // accuracy asked of the current inner solve (<= what the stop rule needs)
   int in_graph;             // 1 = set the graph's conditional handles
   int batched;              // 1 = independent systems, relative rule per system
   double damping;           // gamma: eta <- gamma eta_old + (1 - gamma) eta_new

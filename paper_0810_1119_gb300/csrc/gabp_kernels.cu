@@ -396,17 +396,18 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 // local row ids (heavy tiles).  Per-row values are read straight from global
 // memory by the thread that owns the row (coalesced).
 // ---------------------------------------------------------------------------
+template <int TSL>
 struct Layout32 {
-  static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
+  static constexpr int TS = TSL, TR = kTileRowsBig;
   static constexpr uint32_t m = 0, a = m + region(TS, 8), rev = a + region(TS, 4),
                             lr = rev + region(TS, 4), rp = lr + region(TS, 2),
                             bytes = rp + region(TR + 1, 4);
 };
 
-template <class T>
+template <class T, int TSL>
 __global__ void __launch_bounds__(kTileBlock)
 sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
-  using L = Layout32;
+  using L = Layout32<TSL>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ float2 tot[2][L::TR];   // heavy tiles: per-row sums, double-buffered
@@ -569,18 +570,18 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 // d_i = h~_i / P~_i.  Records d_i and its change.
 // Staged per tile: eta in, c, rev, and row pointers or local row ids.
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, int TSL>
 struct LayoutMean {
-  static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
+  static constexpr int TS = TSL, TR = kTileRowsBig;
   static constexpr uint32_t e = 0, c = e + region(TS, sizeof(T)), rev = c + region(TS, 4),
                             lr = rev + region(TS, 4), rp = lr + region(TS, 2),
                             bytes = rp + region(TR + 1, 4);
 };
 
-template <class T>
+template <class T, int TSL>
 __global__ void __launch_bounds__(kTileBlock)
 mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
-  using L = LayoutMean<T>;
+  using L = LayoutMean<T, TSL>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ float tot[2][L::TR];    // heavy tiles: per-row sums, double-buffered
@@ -751,15 +752,17 @@ __global__ void __launch_bounds__(kBlock) refine_update_kernel(int32_t n, Buffer
 // memory.  Phase 2: one thread per row sums its products (one FP64 add per
 // slot) and forms r_i.
 // ---------------------------------------------------------------------------
+template <int TSL>
 struct LayoutRes {
-  static constexpr int TS = kTileSlotsBig, TR = kTileRowsBig;
+  static constexpr int TS = TSL, TR = kTileRowsBig;
   static constexpr uint32_t a = 0, col = a + region(TS, 8), rp = col + region(TS, 4),
                             dg = rp + region(TR + 1, 4), bytes = dg + region(TR, 8);
 };
 
+template <int TSL>
 __global__ void __launch_bounds__(kTileBlock)
 residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars *red, int kind) {
-  using L = LayoutRes;
+  using L = LayoutRes<TSL>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[2];
   const double *__restrict__ b = ctl->b;
@@ -1164,10 +1167,19 @@ void launch64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *
                ctl, red);
 }
 
+// The FP32 sweeps and the residual come in two shared-memory sizes: tiles of
+// at most 1024 slots, or at most 512 (half the staging, twice the resident
+// CTAs).  The row tiles' slot limit picks the variant.
+#define GABP_TS_DISPATCH(g, ...)                                     \
+  do {                                                               \
+    if ((g).tile_slots > 0 && (g).tile_slots <= 512) { constexpr int TSZ = 512; __VA_ARGS__; } \
+    else { constexpr int TSZ = kTileSlotsBig; __VA_ARGS__; }         \
+  } while (0)
+
 int launch_residual(const Graph &g, cudaStream_t st, double *r_out, Ctl *ctl, DevScalars *red,
                     int kind) {
-  launch_tiled(residual64_kernel, 2 * LayoutRes::bytes, g.ntiles_big, kTileBlock, st, g.view(),
-               r_out, ctl, red, kind);
+  GABP_TS_DISPATCH(g, launch_tiled(residual64_kernel<TSZ>, 2 * LayoutRes<TSZ>::bytes, g.ntiles_big,
+                                   kTileBlock, st, g.view(), r_out, ctl, red, kind));
   return 1;
 }
 
@@ -1196,22 +1208,27 @@ int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScal
 
 int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                    bool bf16) {
-  const size_t smem = 2 * Layout32::bytes;
-  if (bf16)
-    launch_tiled(sweep32_kernel<__nv_bfloat16>, smem, g.ntiles_big, kTileBlock, st, g.view(), B,
-                 ctl, red);
-  else
-    launch_tiled(sweep32_kernel<float>, smem, g.ntiles_big, kTileBlock, st, g.view(), B, ctl, red);
+  GABP_TS_DISPATCH(g, {
+    const size_t smem = 2 * Layout32<TSZ>::bytes;
+    if (bf16)
+      launch_tiled(sweep32_kernel<__nv_bfloat16, TSZ>, smem, g.ntiles_big, kTileBlock, st,
+                   g.view(), B, ctl, red);
+    else
+      launch_tiled(sweep32_kernel<float, TSZ>, smem, g.ntiles_big, kTileBlock, st, g.view(), B,
+                   ctl, red);
+  });
   return 1;
 }
 
 int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16) {
-  if (bf16)
-    launch_tiled(mean_kernel<__nv_bfloat16>, 2 * LayoutMean<__nv_bfloat16>::bytes, g.ntiles_big,
-                 kTileBlock, st, g.view(), B, ctl, red);
-  else
-    launch_tiled(mean_kernel<float>, 2 * LayoutMean<float>::bytes, g.ntiles_big, kTileBlock, st,
-                 g.view(), B, ctl, red);
+  GABP_TS_DISPATCH(g, {
+    if (bf16)
+      launch_tiled(mean_kernel<__nv_bfloat16, TSZ>, 2 * LayoutMean<__nv_bfloat16, TSZ>::bytes,
+                   g.ntiles_big, kTileBlock, st, g.view(), B, ctl, red);
+    else
+      launch_tiled(mean_kernel<float, TSZ>, 2 * LayoutMean<float, TSZ>::bytes, g.ntiles_big,
+                   kTileBlock, st, g.view(), B, ctl, red);
+  });
   return 1;
 }
 
@@ -1284,13 +1301,20 @@ void prepare_kernels(int group, bool bf16) {
     case 16: prepare_group<16>(); break;
     default: prepare_group<32>(); break;
   }
-  resident_blocks(residual64_kernel, 2 * LayoutRes::bytes, kTileBlock);
-  if (bf16) {
-    resident_blocks(sweep32_kernel<__nv_bfloat16>, 2 * Layout32::bytes, kTileBlock);
-    resident_blocks(mean_kernel<__nv_bfloat16>, 2 * LayoutMean<__nv_bfloat16>::bytes, kTileBlock);
-  } else {
-    resident_blocks(sweep32_kernel<float>, 2 * Layout32::bytes, kTileBlock);
-    resident_blocks(mean_kernel<float>, 2 * LayoutMean<float>::bytes, kTileBlock);
+  for (int ts : {512, kTileSlotsBig}) {
+    Graph probe;
+    probe.tile_slots = ts;
+    GABP_TS_DISPATCH(probe, {
+      resident_blocks(residual64_kernel<TSZ>, 2 * LayoutRes<TSZ>::bytes, kTileBlock);
+      if (bf16) {
+        resident_blocks(sweep32_kernel<__nv_bfloat16, TSZ>, 2 * Layout32<TSZ>::bytes, kTileBlock);
+        resident_blocks(mean_kernel<__nv_bfloat16, TSZ>, 2 * LayoutMean<__nv_bfloat16, TSZ>::bytes,
+                        kTileBlock);
+      } else {
+        resident_blocks(sweep32_kernel<float, TSZ>, 2 * Layout32<TSZ>::bytes, kTileBlock);
+        resident_blocks(mean_kernel<float, TSZ>, 2 * LayoutMean<float, TSZ>::bytes, kTileBlock);
+      }
+    });
   }
 }
 

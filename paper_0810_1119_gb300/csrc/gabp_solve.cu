@@ -319,7 +319,8 @@ void init_ctl(gabp_handle h, int mode, const double *b, double *x, double tol, i
   c.mode = mode;
   c.max_iter = max_iter;
   c.check_every = h->opt.check_every > 0 ? h->opt.check_every : 4;
-  c.inner_tol = h->opt.inner_tol > 0 ? h->opt.inner_tol : 1e-6;
+  c.inner_tol = h->opt.inner_tol > 0 ? h->opt.inner_tol : (h->g.nsys > 0 ? 1e-6 : 1e-7);
+  c.inner_goal = c.inner_tol;
   c.damping = h->opt.damping;
   c.in_graph = in_graph ? 1 : 0;
   if (in_graph) {
@@ -968,7 +969,7 @@ void gabp_default_options(gabp_options *opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->precision = GABP_PREC_FP64;
   opt->residual_kind = GABP_RESIDUAL_REL;
-  opt->inner_tol = 1e-6;
+  opt->inner_tol = 0.0;   // automatic
 }
 
 gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t *row_ptr_host,

@@ -328,7 +328,7 @@ class Solver:
 
     @classmethod
     def from_csr(cls, row_ptr, col, val, rev=None, *, precision=PREC_FP64,
-                 residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=1e-6,
+                 residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=0.0,
                  profile=False, damping=0.0, stream: int | None = None, autotune=False,
                  tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0,
                  aitken=0):

@@ -165,8 +165,8 @@ def test_oversized_system_takes_the_csr_path(G):
 
 def test_bf16_refinement_that_stalls_stops_early(G):
     """BF16 mean messages on the 10 dB batch: the solve either reaches 1e-10
-    or stops once four refinement steps in a row fail to halve the FP64
-    residual -- long before the sweep budget."""
+    or stops once eight refinement steps in a row fail to shrink the FP64
+    residual by 10 % -- long before the sweep budget."""
     systems = W.detection_batch(40, 16, 130, 10.0, seed=2)
     h = _handle(G, [(d.S, d.sigma2, d.y) for d in systems], precision=2)
     y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
