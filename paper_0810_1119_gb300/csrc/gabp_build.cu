@@ -72,10 +72,24 @@ cudaError_t set_row_tiles(Graph &g, int slots, int rows, int heavy_degree, cudaS
   for (size_t t = 0; t + 1 < tb.size(); ++t)
     for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
       if (g.h_rp[r + 1] - g.h_rp[r] > heavy_degree) heavy[t] = 1;
-  cudaFree(g.tiles_big); cudaFree(g.lrow_big); cudaFree(g.heavy_big);
+  // Row order inside every tile, longest rows first (stable): the warps of a
+  // thread-per-row pass then take rows of similar length.
+  std::vector<uint8_t> rord(n + kPad, 0);
+  std::vector<int32_t> idx;
+  for (size_t t = 0; t + 1 < tb.size(); ++t) {
+    const int32_t r0 = tb[t].x, nr = tb[t + 1].x - r0;
+    idx.resize(nr);
+    for (int32_t k = 0; k < nr; ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+      return g.h_rp[r0 + a + 1] - g.h_rp[r0 + a] > g.h_rp[r0 + b + 1] - g.h_rp[r0 + b];
+    });
+    for (int32_t k = 0; k < nr; ++k) rord[r0 + k] = static_cast<uint8_t>(idx[k]);
+  }
+  cudaFree(g.tiles_big); cudaFree(g.lrow_big); cudaFree(g.heavy_big); cudaFree(g.rord);
   g.tiles_big = nullptr;
   g.lrow_big = nullptr;
   g.heavy_big = nullptr;
+  g.rord = nullptr;
   g.ntiles_big = static_cast<int32_t>(tb.size() - 1);
   g.tile_slots = slots;
   g.tile_rows = rows;
@@ -83,6 +97,7 @@ cudaError_t set_row_tiles(Graph &g, int slots, int rows, int heavy_degree, cudaS
   cudaError_t ce = upload(&g.tiles_big, tb.data(), tb.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.lrow_big, lrow.data(), lrow.size(), st);
   if (ce == cudaSuccess) ce = upload(&g.heavy_big, heavy.data(), heavy.size(), st);
+  if (ce == cudaSuccess) ce = upload(&g.rord, rord.data(), rord.size(), st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   return ce;
 }
@@ -258,6 +273,8 @@ void free_graph(Graph &g) {
   g.sys_of_row = nullptr;
   g.sys_bmax = nullptr;
   cudaFree(g.tiles_big); cudaFree(g.tiles_small); cudaFree(g.lrow_big); cudaFree(g.heavy_big);
+  cudaFree(g.rord);
+  g.rord = nullptr;
   g.tiles_big = g.tiles_small = nullptr;
   g.lrow_big = nullptr;
   g.heavy_big = nullptr;

@@ -147,6 +147,7 @@ struct GraphView {
   const int2 *tiles_big, *tiles_small;
   const uint16_t *lrow_big;     // tile-local row id of every slot (big tiles)
   const uint8_t *heavy_big;     // 1 if the big tile holds a row of degree > kHeavyDegree
+  const uint8_t *rord;          // per tile: its rows' local indices, longest rows first
   int32_t ntiles_big, ntiles_small;
   int32_t n;
   // batched handles: system of every row, per-system max |b| (bit patterns)
@@ -167,6 +168,7 @@ struct Graph {
   int2 *tiles_big = nullptr, *tiles_small = nullptr;
   uint16_t *lrow_big = nullptr;
   uint8_t *heavy_big = nullptr;
+  uint8_t *rord = nullptr;
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
   int tile_slots = 0, tile_rows = 0, heavy_degree = 0;   // row tiles of the FP32 sweeps
@@ -178,9 +180,9 @@ struct Graph {
   std::vector<int64_t> h_sys_row_off;
 
   GraphView view() const {
-    return GraphView{rp,          rev,      col,       a64,        diag64,       a32, diag32, tiles_big,
-                     tiles_small, lrow_big, heavy_big, ntiles_big, ntiles_small, n,   sys_of_row,
-                     sys_bmax};
+    return GraphView{rp,        rev,        col,          a64, diag64,     a32,     diag32,
+                     tiles_big, tiles_small, lrow_big,    heavy_big, rord, ntiles_big,
+                     ntiles_small, n,        sys_of_row, sys_bmax};
   }
 };
 

@@ -401,7 +401,7 @@ struct Layout32 {
   static constexpr int TS = TSL, TR = kTileRowsBig;
   static constexpr uint32_t m = 0, a = m + region(TS, 8), rev = a + region(TS, 4),
                             lr = rev + region(TS, 4), rp = lr + region(TS, 2),
-                            bytes = rp + region(TR + 1, 4);
+                            ro = rp + region(TR + 1, 4), bytes = ro + region(TR, 1);
 };
 
 template <class T, int TSL>
@@ -433,13 +433,18 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
     const bool heavy = g.heavy_big[t] != 0;
     const uint32_t tx = (first ? 0 : Seg<float2>::bytes(tb.s0, ns)) +
-                        (heavy ? Seg<uint16_t>::bytes(tb.s0, ns) : Seg<int32_t>::bytes(tb.r0, nr + 1)) +
+                        (heavy ? Seg<uint16_t>::bytes(tb.s0, ns)
+                               : Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<uint8_t>::bytes(tb.r0, nr)) +
                         Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
     if (!first) Seg<float2>::copy(base + L::m, min, tb.s0, ns, bar, pol_keep);
-    if (heavy) Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
-    else Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
+    if (heavy) {
+      Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
+    } else {
+      Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
+      Seg<uint8_t>::copy(base + L::ro, g.rord, tb.r0, nr, bar, pol_stream);
+    }
     Seg<float>::copy(base + L::a, g.a32, tb.s0, ns, bar, pol_stream);
     Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar, pol_stream);
   };
@@ -509,11 +514,13 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const float *as = Seg<float>::at(stage + L::a, tb.s0);
     const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
     if (!g.heavy_big[t]) {
-      // light tile: one thread per row does the sums, the node and the sends
+      // light tile: one thread per row does the sums, the node and the sends;
+      // rows taken in the tile's degree order, so a warp's rows are alike
       const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+      const uint8_t *ro = Seg<uint8_t>::at(stage + L::ro, tb.r0);
       if (__syncthreads_or(!got)) return true;
-      for (int32_t k = tid; k < nr; k += NT) {
-        const int32_t i = tb.r0 + k;
+      for (int32_t q = tid; q < nr; q += NT) {
+        const int32_t k = ro[q], i = tb.r0 + k;
         const float dgi = g.diag32[i], rhs = rhs_at(i);
         const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
         float sP = 0.f, sH = 0.f;
@@ -575,7 +582,7 @@ struct LayoutMean {
   static constexpr int TS = TSL, TR = kTileRowsBig;
   static constexpr uint32_t e = 0, c = e + region(TS, sizeof(T)), rev = c + region(TS, 4),
                             lr = rev + region(TS, 4), rp = lr + region(TS, 2),
-                            bytes = rp + region(TR + 1, 4);
+                            ro = rp + region(TR + 1, 4), bytes = ro + region(TR, 1);
 };
 
 template <class T, int TSL>
@@ -604,13 +611,18 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
     const bool heavy = g.heavy_big[t] != 0;
     const uint32_t tx = (first ? 0 : Seg<T>::bytes(tb.s0, ns)) +
-                        (heavy ? Seg<uint16_t>::bytes(tb.s0, ns) : Seg<int32_t>::bytes(tb.r0, nr + 1)) +
+                        (heavy ? Seg<uint16_t>::bytes(tb.s0, ns)
+                               : Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<uint8_t>::bytes(tb.r0, nr)) +
                         Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
     if (!first) Seg<T>::copy(base + L::e, ein, tb.s0, ns, bar, pol_keep);
-    if (heavy) Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
-    else Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
+    if (heavy) {
+      Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
+    } else {
+      Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
+      Seg<uint8_t>::copy(base + L::ro, g.rord, tb.r0, nr, bar, pol_stream);
+    }
     Seg<float>::copy(base + L::c, B.c32, tb.s0, ns, bar, pol_stream);
     Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar, pol_stream);
   };
@@ -658,11 +670,13 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const float *cs = Seg<float>::at(stage + L::c, tb.s0);
     const int32_t *rv = Seg<int32_t>::at(stage + L::rev, tb.s0);
     if (!g.heavy_big[t]) {
-      // light tile: one thread per row does the sum, the node and the sends
+      // light tile: one thread per row does the sum, the node and the sends;
+      // rows taken in the tile's degree order, so a warp's rows are alike
       const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
+      const uint8_t *ro = Seg<uint8_t>::at(stage + L::ro, tb.r0);
       if (__syncthreads_or(!got)) return true;
-      for (int32_t k = tid; k < nr; k += NT) {
-        const int32_t i = tb.r0 + k;
+      for (int32_t q = tid; q < nr; q += NT) {
+        const int32_t k = ro[q], i = tb.r0 + k;
         const float rhs = rhs_at(i);
         const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
         float sH = 0.f;
@@ -756,7 +770,8 @@ template <int TSL>
 struct LayoutRes {
   static constexpr int TS = TSL, TR = kTileRowsBig;
   static constexpr uint32_t a = 0, col = a + region(TS, 8), rp = col + region(TS, 4),
-                            dg = rp + region(TR + 1, 4), bytes = dg + region(TR, 8);
+                            dg = rp + region(TR + 1, 4), ro = dg + region(TR, 8),
+                            bytes = ro + region(TR, 1);
 };
 
 template <int TSL>
@@ -776,13 +791,15 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
     const uint32_t tx = Seg<double>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
-                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr);
+                        Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr) +
+                        Seg<uint8_t>::bytes(tb.r0, nr);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
     Seg<double>::copy(base + L::a, g.a64, tb.s0, ns, bar, pol_stream);
     Seg<int32_t>::copy(base + L::col, g.col, tb.s0, ns, bar, pol_stream);
     Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar, pol_stream);
     Seg<double>::copy(base + L::dg, g.diag64, tb.r0, nr, bar, pol_stream);
+    Seg<uint8_t>::copy(base + L::ro, g.rord, tb.r0, nr, bar, pol_stream);
   };
 
   auto node = [&](int32_t i, double dgi, double acc) {
@@ -811,10 +828,13 @@ residual64_kernel(GraphView g, double *__restrict__ r_out, Ctl *ctl, DevScalars 
     const int32_t *cs = Seg<int32_t>::at(stage + L::col, tb.s0);
     const int32_t *rp = Seg<int32_t>::at(stage + L::rp, tb.r0);
     const double *dg = Seg<double>::at(stage + L::dg, tb.r0);
+    const uint8_t *ro = Seg<uint8_t>::at(stage + L::ro, tb.r0);
     if (!g.heavy_big[t]) {
-      // light tile: one thread per row, gathers unrolled for memory parallelism
+      // light tile: one thread per row (in the tile's degree order), gathers
+      // unrolled for memory parallelism
       if (__syncthreads_or(!got)) return true;
-      for (int32_t k = tid; k < nr; k += NT) {
+      for (int32_t q = tid; q < nr; q += NT) {
+        const int32_t k = ro[q];
         const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
         double acc = 0.0;
         int32_t s = rs;
