@@ -73,8 +73,6 @@ __device__ __forceinline__ V seg_sum(V v, int key, bool &head) {
 // Storage type of the mean messages: FP32, or BF16 with FP32 arithmetic.
 __device__ __forceinline__ float ld_eta(const float *p) { return *p; }
 __device__ __forceinline__ float ld_eta(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-__device__ __forceinline__ void st_eta(float *p, float v) { *p = v; }
-__device__ __forceinline__ void st_eta(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 
 // ---------------------------------------------------------------------------
