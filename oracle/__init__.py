@@ -14,6 +14,8 @@ Contents
 * ``residual_inf``  -- ||b - A x||_inf (Section II, residual definition).
 * ``augment_lsq``   -- the symmetric augmented system of Section VII
                        (``augment.py``).
+* ``gabp_serial``   -- the serial schedule of Section III-C over a given node
+                       order (``greedy_colouring`` gives colour classes).
 * ``aitken``, ``gabp_aitken`` -- Aitken's Delta^2 extrapolation of the
                        tentative means (Section V, convergence acceleration),
                        applied per node to the means of rounds t - 2s, t - s
@@ -73,6 +75,11 @@ def _bind(lib):
                                 ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                 f64p, f64p, f64p, f64p, ctypes.POINTER(ctypes.c_int),
                                 ctypes.c_double]
+    lib.oracle_gabp_serial.restype = ctypes.c_int
+    lib.oracle_gabp_serial.argtypes = [ctypes.c_int64, i64p, i32p, f64p, f64p, i64p,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       f64p, f64p, f64p, f64p, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.c_double]
     lib.oracle_residual_inf.restype = ctypes.c_double
     lib.oracle_residual_inf.argtypes = [ctypes.c_int64, i64p, i32p, f64p, f64p, f64p, f64p]
     lib.oracle_num_threads.restype = ctypes.c_int
@@ -145,6 +152,49 @@ def gabp(row_ptr, col, val, b, *, variant=BROADCAST, stop=STOP_FIXED, max_rounds
     if want_messages:
         out["P"], out["mu"] = P, mu
     return out
+
+
+def gabp_serial(row_ptr, col, val, b, *, order=None, stop=STOP_FIXED, max_rounds=1, tol=0.0,
+                want_messages=False, damping=0.0, lib=None):
+    """GaBP under the serial schedule (Section III-C): every round visits the
+    nodes in ``order`` (default: natural), each one computing its totals
+    from the latest messages and overwriting its outgoing messages.  Output
+    as ``gabp``."""
+    row_ptr, col, val = _csr_arrays(row_ptr, col, val)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = row_ptr.shape[0] - 1
+    nnz = int(row_ptr[-1])
+    order_a = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+    x = np.empty(n)
+    Pi = np.empty(n)
+    P = np.empty(nnz) if want_messages else None
+    mu = np.empty(nnz) if want_messages else None
+    rounds = ctypes.c_int(0)
+    st = (lib or _load()).oracle_gabp_serial(
+        n, _ptr(row_ptr, ctypes.c_int64), _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double),
+        _ptr(b, ctypes.c_double), _ptr(order_a, ctypes.c_int64), stop, int(max_rounds), float(tol),
+        _ptr(x, ctypes.c_double), _ptr(Pi, ctypes.c_double), _ptr(P, ctypes.c_double),
+        _ptr(mu, ctypes.c_double), ctypes.byref(rounds), float(damping))
+    out = {"x": x, "Pi": Pi, "rounds": rounds.value, "status": STATUS[st]}
+    if want_messages:
+        out["P"], out["mu"] = P, mu
+    return out
+
+
+def greedy_colouring(row_ptr, col):
+    """Colour classes of the graph of A (no two adjacent nodes share a
+    colour), greedy in natural order.  Returns an int array of colours."""
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col)
+    n = row_ptr.shape[0] - 1
+    c = -np.ones(n, dtype=np.int64)
+    for i in range(n):
+        used = {int(c[j]) for j in col[row_ptr[i]:row_ptr[i + 1]] if j != i and c[j] >= 0}
+        k = 0
+        while k in used:
+            k += 1
+        c[i] = k
+    return c
 
 
 def residual_inf(row_ptr, col, val, b, x):

@@ -17,7 +17,10 @@
  *     directly), used only as a cross-check on tiny inputs;
  *   - the Jacobi reduction (the GaBP/Jacobi proposition of Section VI-C):
  *     precision messages held at zero and the message from j included;
- *   - the marginal means and precisions of Algorithm 1/2, step 4.
+ *   - the marginal means and precisions of Algorithm 1/2, step 4;
+ *   - the serial schedule of Section III-C (oracle_gabp_serial): nodes
+ *     visited one after another in a given order, each computing its
+ *     totals from the latest messages and overwriting its outgoing ones.
  *
  * Storage: A is a full symmetric CSR matrix with the diagonal stored and the
  * column indices of each row strictly increasing.  The message on the
@@ -272,6 +275,97 @@ int oracle_gabp(int variant, int64_t n, const int64_t *row_ptr, const int32_t *c
   if (msgMu) memcpy(msgMu, M0, sizeof(double) * (size_t)nnz);
 done:
   free(diag_pos); free(twin); free(P0); free(M0); free(P1); free(M1); free(xr);
+  return status;
+}
+
+/*
+ * One round of the serial schedule (Section III-C): node i = order[k] for
+ * k = 0..n-1 forms P~_i and mu~_i from the current incoming messages (the
+ * ones of nodes visited earlier in this round are already new) and
+ * overwrites its outgoing messages in place, by the rules of Algorithm 2.
+ * `order` NULL means 0, 1, ..., n-1.  Returns OR_OK or OR_BREAKDOWN.
+ */
+static int serial_round(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                        const double *val, const double *b, const int64_t *diag_pos,
+                        const int64_t *twin, const int64_t *order, double *P, double *M,
+                        double gamma) {
+  int status = OR_OK;
+  (void)col;
+  for (int64_t k = 0; k < n; ++k) {
+    const int64_t i = order ? order[k] : k;
+    const double Pii = val[diag_pos[i]];
+    const double muii = b[i] / Pii;
+    double Psum = Pii, hsum = Pii * muii;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      if (twin[e] < 0) continue;
+      Psum += P[twin[e]];
+      hsum += P[twin[e]] * M[twin[e]];
+    }
+    const double Pt = Psum, mut = hsum / Psum;
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      if (twin[e] < 0) { P[e] = 0.0; M[e] = 0.0; continue; }
+      const double Aij = val[e];
+      const double Pji = P[twin[e]], muji = M[twin[e]];
+      const double denom = Pt - Pji;
+      if (denom == 0.0 || !isfinite(denom)) status = OR_BREAKDOWN;
+      const double Pn = -Aij * Aij / denom;
+      double Mn = (Pt * mut - Pji * muji) / Aij;
+      if (gamma > 0.0) Mn = (gamma * (P[e] * M[e]) + (1.0 - gamma) * (Pn * Mn)) / Pn;
+      P[e] = Pn;
+      M[e] = Mn;
+    }
+  }
+  return status;
+}
+
+/*
+ * GaBP under the serial schedule from zero messages; arguments and outputs
+ * as oracle_gabp (broadcast form only), plus the visiting order (NULL = the
+ * natural order).  A round is one pass over all nodes.
+ */
+int oracle_gabp_serial(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                       const double *b, const int64_t *order, int stop, int max_rounds, double tol,
+                       double *x, double *Pi, double *msgP, double *msgMu, int *rounds,
+                       double gamma) {
+  const int64_t nnz = row_ptr[n];
+  const size_t m = (size_t)(nnz > 0 ? nnz : 1);
+  int64_t *diag_pos = malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *twin = malloc(sizeof(int64_t) * m);
+  double *P = calloc(m, sizeof(double)), *M = calloc(m, sizeof(double));
+  double *Pp = calloc(m, sizeof(double)), *Mp = calloc(m, sizeof(double));
+  double *xr = malloc(sizeof(double) * (size_t)n);
+  int status = oracle_check_csr(n, row_ptr, col, val, diag_pos, twin);
+  *rounds = 0;
+  if (status != OR_OK) goto done;
+  double bnorm = 0.0;
+  for (int64_t i = 0; i < n; ++i) bnorm = fmax(bnorm, fabs(b[i]));
+  infer(OR_BROADCAST, n, row_ptr, val, b, diag_pos, twin, P, M, x, Pi);
+  status = (stop == OR_STOP_FIXED && max_rounds == 0) ? OR_OK : OR_NOT_CONVERGED;
+  for (int t = 1; t <= max_rounds; ++t) {
+    memcpy(Pp, P, sizeof(double) * m);
+    memcpy(Mp, M, sizeof(double) * m);
+    int s = serial_round(n, row_ptr, col, val, b, diag_pos, twin, order, P, M, gamma);
+    *rounds = t;
+    if (s != OR_OK) { status = s; break; }
+    infer(OR_BROADCAST, n, row_ptr, val, b, diag_pos, twin, P, M, x, Pi);
+    if (stop == OR_STOP_FIXED) { status = (t == max_rounds) ? OR_OK : OR_NOT_CONVERGED; continue; }
+    if (stop == OR_STOP_MSG) {
+      double change = 0.0;
+      for (int64_t e = 0; e < nnz; ++e) {
+        change = fmax(change, fabs(P[e] - Pp[e]));
+        change = fmax(change, fabs(M[e] - Mp[e]));
+      }
+      if (change < tol) { status = OR_OK; break; }
+    } else {
+      double r = oracle_residual_inf(n, row_ptr, col, val, b, x, xr);
+      if (stop == OR_STOP_RES_REL) r = (bnorm > 0.0) ? r / bnorm : r;
+      if (r < tol) { status = OR_OK; break; }
+    }
+  }
+  if (msgP) memcpy(msgP, P, sizeof(double) * (size_t)nnz);
+  if (msgMu) memcpy(msgMu, M, sizeof(double) * (size_t)nnz);
+done:
+  free(diag_pos); free(twin); free(P); free(M); free(Pp); free(Mp); free(xr);
   return status;
 }
 

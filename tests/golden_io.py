@@ -39,7 +39,8 @@ def toy_tree():
 
 def paper_systems():
     """dict name -> dict with 'A' (float array, scale applied), 'A_exact' and
-    optional 'b', 'solution', 'spectral_radius', 'parallel_gabp_iterations'."""
+    optional 'b', 'solution', 'spectral_radius', 'parallel_gabp_iterations',
+    'serial_gabp_iterations'."""
     systems, cur = {}, None
     for line in _lines("paper_systems.txt"):
         key, rest = line.split(None, 1)
@@ -53,7 +54,7 @@ def paper_systems():
             cur[key] = [_num(t) for t in rest.split()]
         elif key == "spectral_radius":
             cur[key] = float(rest)
-        elif key == "parallel_gabp_iterations":
+        elif key in ("parallel_gabp_iterations", "serial_gabp_iterations"):
             cur[key] = int(rest)
     for s in systems.values():
         exact = [[v * s.get("scale", 1) for v in row] for row in s["matrix"]]

@@ -360,3 +360,79 @@ def test_aitken_on_gabp_means_solves_poisson_in_fewer_rounds():
     plain, acc = first_round(False), first_round(True)
     assert plain is not None and acc is not None
     assert acc <= 0.6 * plain, (plain, acc)
+
+
+# ---------------------------------------------------------------------------
+# Serial schedule (Section III-C)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["R3", "R4", "nonPSD"])
+def test_serial_iteration_counts_same_order(name):
+    """Soft pin like the parallel counts: the paper's serial GaBP counts (16,
+    13, 25) with the message-change rule at 1e-6, natural node order, and
+    fewer rounds than the parallel schedule on the same system."""
+    s = paper_systems()[name]
+    m = _csr(s["A"])
+    r = oracle.gabp_serial(m.row_ptr, m.col, m.val, s["b"], stop=oracle.STOP_MSG,
+                           max_rounds=2000, tol=1e-6)
+    assert r["status"] == "ok"
+    paper = s["serial_gabp_iterations"]
+    assert paper / 2 <= r["rounds"] <= paper * 2, (r["rounds"], paper)
+    par = oracle.gabp(m.row_ptr, m.col, m.val, s["b"], stop=oracle.STOP_MSG, max_rounds=2000,
+                      tol=1e-6)
+    assert r["rounds"] < par["rounds"]
+
+
+def test_serial_poisson_count_same_order():
+    p = 10
+    m = W.poisson2d(p)
+    b = np.full(m.n, 1.0 / (p + 1) ** 2)
+    r = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_MSG, max_rounds=5000,
+                           tol=1e-6)
+    assert r["status"] == "ok"
+    paper = paper_systems()["poisson_p3"]["serial_gabp_iterations"]
+    assert paper / 3 <= r["rounds"] <= paper * 3, r["rounds"]
+
+
+@pytest.mark.parametrize("name", ["R3", "R4", "nonPSD", "poisson_p3"])
+def test_serial_schedule_converges_to_the_solution(name):
+    s = paper_systems()[name]
+    m = _csr(s["A"])
+    r = oracle.gabp_serial(m.row_ptr, m.col, m.val, s["b"], stop=oracle.STOP_RES_ABS,
+                           max_rounds=2000, tol=1e-14)
+    assert r["status"] == "ok"
+    np.testing.assert_allclose(r["x"], np.linalg.solve(s["A"], s["b"]), rtol=1e-12, atol=1e-13)
+
+
+def test_colour_classes_give_the_same_serial_round_in_any_inner_order():
+    """Nodes of one colour class are not adjacent, so the order inside a
+    class does not matter: two orders with the same sequence of classes give
+    the same messages and means, bit for bit (the colour-block schedule the
+    GPU runs is one serial schedule)."""
+    m = W.er_sdd(400, 6, 1.1, 3)
+    b = W.normal_rhs(m.n, 1)
+    c = oracle.greedy_colouring(m.row_ptr, m.col)
+    assert all(c[i] != c[j] for i in range(m.n) for j in m.col[m.row_ptr[i]:m.row_ptr[i + 1]] if j != i)
+    fwd = np.argsort(c, kind="stable")
+    rev_in_class = np.concatenate([np.flatnonzero(c == k)[::-1] for k in range(c.max() + 1)])
+    a = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, order=fwd, max_rounds=7, want_messages=True)
+    z = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, order=rev_in_class, max_rounds=7,
+                           want_messages=True)
+    assert np.array_equal(a["x"], z["x"])
+    assert np.array_equal(a["P"], z["P"]) and np.array_equal(a["mu"], z["mu"])
+    # and a different class sequence is a different schedule
+    other = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, max_rounds=7)
+    assert not np.array_equal(a["x"], other["x"])
+
+
+def test_serial_round_on_a_path_propagates_left_to_right_in_one_round():
+    """On a path graph visited left to right, every message i -> i+1 of the
+    first round already carries all the information to its left: it equals
+    the converged message (the synchronous schedule needs i rounds for it)."""
+    m = W.path_graph(12, 4)
+    b = W.normal_rhs(m.n, 2)
+    one = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, max_rounds=1, want_messages=True)
+    conv = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, max_rounds=40, want_messages=True)
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    fwd = m.col == rows + 1                      # entries (i, i+1): messages i -> i+1
+    np.testing.assert_allclose(one["P"][fwd], conv["P"][fwd], rtol=1e-13)
+    np.testing.assert_allclose(one["mu"][fwd], conv["mu"][fwd], rtol=1e-12, atol=1e-14)
