@@ -44,6 +44,7 @@ sys.path.insert(0, ROOT)
 N_NODES = 1_000_000
 AVG_DEGREE = 8
 DOMINANCE = 1.1
+SCHEDULES = {0: "synchronous (Alg. 2)", 1: "colour-serial (Section III-C)"}
 TOL = 1e-10
 METRIC = "GaBP edge-message updates/s (mixed FP32+FP64 refinement solve to 1e-10 rel. residual)"
 UNIT = "edge-updates/s"
@@ -241,8 +242,9 @@ def run_gabp(args):
     # Launch shapes are picked by the library's autotuner at create time
     # (outside the timed region); the profiled pass reuses the same handle.
     mixed = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32,
-                                 autotune=True)
-    fp64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64, autotune=True)
+                                 autotune=True, schedule=args.schedule)
+    fp64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64, autotune=True,
+                                schedule=args.schedule)
     stream = torch.cuda.current_stream()
 
     def timed_solves(solver, steps):
@@ -333,7 +335,7 @@ def run_gabp(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": m.n, "directed_edges": E,
+            "config": {"workload": WORKLOAD, "n": m.n, "directed_edges": E, "schedule": SCHEDULES[args.schedule],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "flushed (256 MiB write) before every step",
                        "precision": "FP32 messages, FP64 residual refinement"},
@@ -473,7 +475,8 @@ def run_poisson32(args):
     for name, prec, ait in (("fp64", gabp.PREC_FP64, 0), ("fp64_aitken2", gabp.PREC_FP64, 2),
                             ("mixed_fp32", gabp.PREC_MIXED_FP32, 0)):
         s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=prec,
-                                 residual_kind=gabp.RESIDUAL_ABS, autotune=True, aitken=ait)
+                                 residual_kind=gabp.RESIDUAL_ABS, autotune=True, aitken=ait,
+                                 schedule=args.schedule)
         for _ in range(args.warmup):
             gabp.gabp_solve(s.handle, bt, xt, TOL, 100000)
         ms = []
@@ -498,6 +501,7 @@ def run_poisson32(args):
             "ms_per_step": f["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": "2D Poisson 5-point 32x32 (n=1024), b~U[-1,1], abs 1e-10",
+                       "schedule": SCHEDULES[args.schedule],
                        "n": m.n, "directed_edges": E, "bound": "latency (system fits in L2)"},
             "sweeps": st["sweeps_total"], "residual_checks": st["residual_checks"],
             "sweeps_per_s": st["sweeps_total"] / (f["ms"] * 1e-3),
@@ -548,7 +552,8 @@ def run_poisson3d(args):
     for name, prec in (("mixed_fp32", gabp.PREC_MIXED_FP32), ("mixed_bf16", gabp.PREC_MIXED_BF16),
                        ("fp64", gabp.PREC_FP64)):
         t0 = time.perf_counter()
-        s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=prec, autotune=True)
+        s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=prec, autotune=True,
+                                 schedule=args.schedule)
         build_s = time.perf_counter() - t0
         ms, st, err = [], None, ""
         cap = args.fp64_max_iter if (prec == gabp.PREC_FP64 and args.fp64_max_iter) else args.max_iter
@@ -609,6 +614,7 @@ def run_poisson3d(args):
             "ms_per_step": mixed["ms"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"3D Poisson 7-point {p}^3, b~U[-1,1], 1e-10 rel. residual",
+                       "schedule": SCHEDULES[args.schedule],
                        "n": m.n, "directed_edges": E, "max_iter": args.max_iter,
                        "generate_s": gen_s},
             "runs": res, "extrapolation": extrap,
@@ -724,6 +730,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=200000, help="poisson3d: sweep cap per solve")
     ap.add_argument("--fp64-max-iter", type=int, default=0,
                     help="poisson3d: separate sweep cap for the FP64 comparison (0 = --max-iter)")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
+                    help="er1e6, poisson32, poisson3d: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")
     ap.add_argument("--workload", default="er1e6",
                     choices=["er1e6", "multi64", "detect", "poisson32", "poisson3d"],

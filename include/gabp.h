@@ -102,6 +102,15 @@ typedef struct {
                              (bipartite) graphs the synchronous schedule's error flips sign
                              every round: s = 2 accelerates there, s = 1 does not.
                              0 = off (dense Section VII handles: always off) */
+  int32_t schedule;       /* 0 = synchronous (the parallel schedule of Section III-C, two message
+                             buffers); 1 = colour-serial: rows are coloured greedily in the
+                             caller's order (no two neighbours share a colour) and every sweep
+                             updates the colour classes one after another in place, each using
+                             the latest messages -- the serial schedule of Section III-C with
+                             nodes visited by colour, which needs about half the sweeps on grid
+                             and other two-colourable graphs.  Not for batched handles; small
+                             FP64 systems then take the per-sweep path. */
+  int32_t reserved_i;
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */

@@ -31,18 +31,28 @@ cudaError_t upload(T **dst, const T *src, size_t count, cudaStream_t st) {
 
 // Greedy row tiles: consecutive rows while the tile keeps <= max_slots slots
 // and <= max_rows rows; a row with more than max_slots slots is alone.
+// With colour classes (bounds = class row offsets), no tile spans two
+// classes, and *first_tile[c] is the first tile of class c.
 std::vector<int2> make_tiles(const std::vector<int32_t> &rp, int64_t n, int max_slots,
-                             int max_rows) {
+                             int max_rows, const std::vector<int32_t> *bounds = nullptr,
+                             std::vector<int32_t> *first_tile = nullptr) {
   std::vector<int2> t;
-  int64_t r = 0;
-  while (r < n) {
-    const int32_t s0 = rp[r];
-    int64_t end = r + 1;
-    if (rp[r + 1] - s0 <= max_slots)
-      while (end < n && end - r < max_rows && rp[end + 1] - s0 <= max_slots) ++end;
-    t.push_back(make_int2(static_cast<int>(r), s0));
-    r = end;
+  std::vector<int32_t> cuts = bounds ? *bounds : std::vector<int32_t>{0, static_cast<int32_t>(n)};
+  if (first_tile) first_tile->clear();
+  for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+    if (first_tile) first_tile->push_back(static_cast<int32_t>(t.size()));
+    int64_t r = cuts[c];
+    const int64_t hi = cuts[c + 1];
+    while (r < hi) {
+      const int32_t s0 = rp[r];
+      int64_t end = r + 1;
+      if (rp[r + 1] - s0 <= max_slots)
+        while (end < hi && end - r < max_rows && rp[end + 1] - s0 <= max_slots) ++end;
+      t.push_back(make_int2(static_cast<int>(r), s0));
+      r = end;
+    }
   }
+  if (first_tile) first_tile->push_back(static_cast<int32_t>(t.size()));
   t.push_back(make_int2(static_cast<int>(n), rp[n]));
   return t;
 }
@@ -62,7 +72,8 @@ int next_pow2(int v) {
 // degree above `heavy_degree`.  Replaces the previous tiles.
 cudaError_t set_row_tiles(Graph &g, int slots, int rows, int heavy_degree, cudaStream_t st) {
   const int64_t n = g.n;
-  const std::vector<int2> tb = make_tiles(g.h_rp, n, slots, rows);
+  const std::vector<int2> tb =
+      make_tiles(g.h_rp, n, slots, rows, g.ncol > 0 ? &g.col_rows : nullptr, &g.col_tiles_big);
   std::vector<uint16_t> lrow(g.E);
   for (size_t t = 0; t + 1 < tb.size(); ++t)
     for (int32_t r = tb[t].x; r < tb[t + 1].x; ++r)
@@ -210,7 +221,8 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
   g.group = std::min(32, std::max(2, next_pow2(G)));
   int big_s, big_r, small_s, small_r;
   tile_sizes(&big_s, &big_r, &small_s, &small_r);
-  const std::vector<int2> ts = make_tiles(g.h_rp, n, small_s, small_r);
+  const std::vector<int2> ts = make_tiles(g.h_rp, n, small_s, small_r,
+                                          g.ncol > 0 ? &g.col_rows : nullptr, &g.col_tiles_small);
   g.ntiles_small = static_cast<int32_t>(ts.size() - 1);
   if (opt.tile_slots > 0) big_s = opt.tile_slots;
   if (opt.tile_rows > 0) big_r = opt.tile_rows;

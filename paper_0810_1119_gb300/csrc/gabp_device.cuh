@@ -407,7 +407,7 @@ __device__ void last_block_control(Ctl *ctl, DevScalars *red, int kind) {
     __threadfence();
     ctl->blocks_done = 0;
     ctl->work_next = 0;
-    control(*ctl, red, kind);
+    if (kind != 0) control(*ctl, red, kind);   // 0: a colour pass that is not a sweep's last
     __threadfence();
   }
 }

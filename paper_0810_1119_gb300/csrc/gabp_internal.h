@@ -153,6 +153,9 @@ struct GraphView {
   // batched handles: system of every row, per-system max |b| (bit patterns)
   const int32_t *sys_of_row;
   unsigned long long *sys_bmax;
+  // colour schedule: this launch is one colour class's pass over its tiles,
+  // in place in a single message buffer; only a sweep's last pass controls
+  int32_t in_place, no_control;
 };
 
 struct Graph {
@@ -172,6 +175,10 @@ struct Graph {
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
   int tile_slots = 0, tile_rows = 0, heavy_degree = 0;   // row tiles of the FP32 sweeps
+  // colour schedule: rows renumbered by colour class; class c holds rows
+  // [col_rows[c], col_rows[c+1]) and tiles [col_tiles_*[c], col_tiles_*[c+1])
+  int ncol = 0;
+  std::vector<int32_t> col_rows, col_tiles_big, col_tiles_small;
   int max_degree = 0;
   // batched handles (independent systems along the diagonal)
   int32_t nsys = 0;
@@ -182,7 +189,21 @@ struct Graph {
   GraphView view() const {
     return GraphView{rp,        rev,        col,          a64, diag64,     a32,     diag32,
                      tiles_big, tiles_small, lrow_big,    heavy_big, rord, ntiles_big,
-                     ntiles_small, n,        sys_of_row, sys_bmax};
+                     ntiles_small, n,        sys_of_row, sys_bmax, 0,   0};
+  }
+  // The view of colour class c's pass (colour schedule): its tiles only.
+  GraphView colour_view(int c) const {
+    GraphView v = view();
+    const int32_t b0 = col_tiles_big[c], b1 = col_tiles_big[c + 1];
+    const int32_t s0 = col_tiles_small[c], s1 = col_tiles_small[c + 1];
+    v.tiles_big = tiles_big + b0;
+    v.heavy_big = heavy_big + b0;
+    v.ntiles_big = b1 - b0;
+    v.tiles_small = tiles_small + s0;
+    v.ntiles_small = s1 - s0;
+    v.in_place = 1;
+    v.no_control = c + 1 < ncol;
+    return v;
   }
 };
 
@@ -190,11 +211,16 @@ struct Graph {
 // launched; the last kernel of every launcher runs the controller in its
 // last block.
 int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
-int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                   const GraphView *view = nullptr);
 int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                    bool aitken);
-int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
-int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16);
+int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16,
+                   const GraphView *view = nullptr);
+int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16,
+                const GraphView *view = nullptr);
+int launch_permute(int32_t n, cudaStream_t st, const int32_t *perm, const double *src, double *dst,
+                   bool scatter);
 int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
 int launch_init_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
 int launch_mean_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
@@ -361,6 +387,9 @@ struct gabp_s {
   gabp_tuning tuning{};                // launch shapes (chosen by the autotuner or default)
   gabp::Resident res{};                // small FP64 systems: one cluster launch per solve
   double *ring[3] = {};                // Aitken: the last three FP64 tentative means
+  // colour schedule (Section III-C serial schedule by colour classes)
+  int32_t *perm = nullptr;             // device: caller's row of renumbered row i
+  double *bperm = nullptr, *xperm = nullptr;   // device: b and x in the renumbered order
   cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
 
   // profiling (gabp_options.profile): pairs of events around kernels

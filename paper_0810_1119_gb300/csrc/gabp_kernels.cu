@@ -282,6 +282,9 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ __align__(8) uint64_t bars[2];
   const int par = ctl->par_m;
   const bool first = ctl->first != 0;
+  // incoming messages known to be zero (skip reading them): the first sweep of
+  // a synchronous solve; an in-place colour schedule reads its zeroed buffer
+  const bool zin = first && !g.in_place;
   bool write_x, write_msgs;
   if (ctl->mode == CTL_ROUNDS) {
     const bool infer_only = ctl->sweeps >= ctl->rounds_target;
@@ -302,12 +305,12 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const TileBounds tb = tile_at(g.tiles_small, t);
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
-    const uint32_t tx = (first ? 0 : Seg<double2>::bytes(tb.s0, ns)) +
+    const uint32_t tx = (zin ? 0 : Seg<double2>::bytes(tb.s0, ns)) +
                         Seg<double>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns) +
                         Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<double>::bytes(tb.r0, nr);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (!first) Seg<double2>::copy(base + L::m, min, tb.s0, ns, bar);
+    if (!zin) Seg<double2>::copy(base + L::m, min, tb.s0, ns, bar);
     Seg<double>::copy(base + L::a, g.a64, tb.s0, ns, bar);
     Seg<int32_t>::copy(base + L::rev, g.rev, tb.s0, ns, bar);
     Seg<int32_t>::copy(base + L::rp, g.rp, tb.r0, nr + 1, bar);
@@ -321,7 +324,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const double inv = recip64(d);
     double eta = -a * (Th - m.y) * inv;
     // damping: blend with this message's previous value (slot dst of "in")
-    if (gam > 0.0) eta = gam * (first ? 0.0 : min[dst].y) + (1.0 - gam) * eta;
+    if (gam > 0.0) eta = gam * (zin ? 0.0 : min[dst].y) + (1.0 - gam) * eta;
     mout[dst] = make_double2(-(a * a) * inv, eta);
   };
 
@@ -333,7 +336,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       // one long row, straight from global memory, the whole CTA on it
       const int32_t i = tb.r0;
       double sP = 0.0, sH = 0.0;
-      if (!first)
+      if (!zin)
         for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += blockDim.x) {
           const double2 m = min[s];
           sP += m.x;
@@ -345,7 +348,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       if (write_x && threadIdx.x == 0) x[i] = Th / TP;
       if (write_msgs)
         for (int32_t s = tb.s0 + threadIdx.x; s < tb.s1; s += blockDim.x)
-          emit(g.a64[s], first ? make_double2(0.0, 0.0) : min[s], g.rev[s], TP, Th);
+          emit(g.a64[s], zin ? make_double2(0.0, 0.0) : min[s], g.rev[s], TP, Th);
       return false;
     }
     const double2 *ms = Seg<double2>::at(stage + L::m, tb.s0);
@@ -358,7 +361,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       const bool valid = lr < nr;
       const int32_t rs = valid ? rp[lr] - tb.s0 : 0, re = valid ? rp[lr + 1] - tb.s0 : 0;
       double sP = 0.0, sH = 0.0;
-      if (!first)
+      if (!zin)
         for (int32_t s = rs + gl; s < re; s += G) {
           sP += ms[s].x;
           sH += ms[s].y;
@@ -371,7 +374,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       if (write_x && gl == 0) x[i] = Th / TP;
       if (!write_msgs) continue;
       for (int32_t s = rs + gl; s < re; s += G)
-        emit(as[s], first ? make_double2(0.0, 0.0) : ms[s], rv[s], TP, Th);
+        emit(as[s], zin ? make_double2(0.0, 0.0) : ms[s], rv[s], TP, Th);
     }
     return false;
   };
@@ -379,7 +382,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const bool ok = run_tiles(g.ntiles_small, smem, L::bytes, bars, issue, work);
   if (brk) atomicOr(&red->breakdown, 1);
   if (!ok) atomicOr(&red->timeout, 1);
-  last_block_control(ctl, red, CK_SWEEP64);
+  last_block_control(ctl, red, g.no_control ? 0 : CK_SWEEP64);
 }
 
 // ---------------------------------------------------------------------------
@@ -412,6 +415,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ float2 nd[L::TR];       // heavy tiles: (A_ii, rhs_i) of the tile's rows
   const int pm = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
+  const bool zin = first && !g.in_place;   // incoming messages known to be zero
   const bool freeze = ctl->pending_freeze != 0;
   const double inv_rn = ctl->inv_rn;
   const float2 *__restrict__ min = (pm ? B.m32[1] : B.m32[0]);
@@ -430,13 +434,13 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
     const bool heavy = g.heavy_big[t] != 0;
-    const uint32_t tx = (first ? 0 : Seg<float2>::bytes(tb.s0, ns)) +
+    const uint32_t tx = (zin ? 0 : Seg<float2>::bytes(tb.s0, ns)) +
                         (heavy ? Seg<uint16_t>::bytes(tb.s0, ns)
                                : Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<uint8_t>::bytes(tb.r0, nr)) +
                         Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (!first) Seg<float2>::copy(base + L::m, min, tb.s0, ns, bar, pol_keep);
+    if (!zin) Seg<float2>::copy(base + L::m, min, tb.s0, ns, bar, pol_keep);
     if (heavy) {
       Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
     } else {
@@ -469,7 +473,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     brk |= !(d != 0.0f) || !isfinite(d);
     const float inv = 1.0f / d;
     // damping: blend the information with this message's previous value
-    const float old_eta = (gam > 0.f && !first) ? min[dst].y : 0.f;
+    const float old_eta = (gam > 0.f && !zin) ? min[dst].y : 0.f;
     if (freeze) {
       const float c = -a * inv;
       B.c32[s] = c;
@@ -493,7 +497,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       if (__syncthreads_or(!got)) return true;
       const int32_t i = tb.r0;
       float sP = 0.f, sH = 0.f;
-      if (!first)
+      if (!zin)
         for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) {
           const float2 m = min[s];
           sP += m.x;
@@ -505,7 +509,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       const float TP = g.diag32[i] + sP, Th = rhs + sH;
       if (tid == 0) node(i, TP, Th, rhs);
       for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT)
-        emit(s, g.a32[s], first ? make_float2(0.f, 0.f) : min[s], g.rev[s], TP, Th);
+        emit(s, g.a32[s], zin ? make_float2(0.f, 0.f) : min[s], g.rev[s], TP, Th);
       return false;
     }
     const float2 *ms = Seg<float2>::at(stage + L::m, tb.s0);
@@ -522,7 +526,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
         const float dgi = g.diag32[i], rhs = rhs_at(i);
         const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
         float sP = 0.f, sH = 0.f;
-        if (!first)
+        if (!zin)
           for (int32_t s = rs; s < re; ++s) {
             sP += ms[s].x;
             sH += ms[s].y;
@@ -530,14 +534,14 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
         const float TP = dgi + sP, Th = rhs + sH;
         node(i, TP, Th, rhs);
         for (int32_t s = rs; s < re; ++s)
-          emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], TP, Th);
+          emit(tb.s0 + s, as[s], zin ? make_float2(0.f, 0.f) : ms[s], rv[s], TP, Th);
       }
       return false;
     }
     // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
     for (int32_t k = tid; k < nr; k += NT) nd[k] = make_float2(g.diag32[tb.r0 + k], rhs_at(tb.r0 + k));
-    if (!first) {
+    if (!zin) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
         const int32_t s = base + (tid & 31);
         const bool v = s < ns;
@@ -555,7 +559,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       node(tb.r0 + k, nd[k].x + tc[k].x, nd[k].y + tc[k].y, nd[k].y);
     for (int32_t s = tid; s < ns; s += NT) {
       const int k = lrow[s];
-      emit(tb.s0 + s, as[s], first ? make_float2(0.f, 0.f) : ms[s], rv[s], nd[k].x + tc[k].x,
+      emit(tb.s0 + s, as[s], zin ? make_float2(0.f, 0.f) : ms[s], rv[s], nd[k].x + tc[k].x,
            nd[k].y + tc[k].y);
     }
     return false;
@@ -566,7 +570,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   if (!ok) atomicOr(&red->timeout, 1);
   block_max4(widen(mdd), widen(md), widen(mdP), widen(mP), &red->max_dx, &red->max_x,
              &red->max_dP, &red->max_P);
-  last_block_control(ctl, red, CK_SWEEP32);
+  last_block_control(ctl, red, g.no_control ? 0 : CK_SWEEP32);
 }
 
 // ---------------------------------------------------------------------------
@@ -593,6 +597,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ float rhs_s[L::TR];     // heavy tiles: rhs of the tile's rows
   const int pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
+  const bool zin = first && !g.in_place;   // incoming messages known to be zero
   const double inv_rn = ctl->inv_rn;
   const T *__restrict__ ein = static_cast<const T *>((pe ? B.e[1] : B.e[0]));
   T *__restrict__ eout = static_cast<T *>((pe ? B.e[0] : B.e[1]));
@@ -608,13 +613,13 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     const int64_t ns = tb.s1 - tb.s0, nr = tb.r1 - tb.r0;
     if (ns > L::TS) { mbar_expect_tx(bar, 0); return; }
     const bool heavy = g.heavy_big[t] != 0;
-    const uint32_t tx = (first ? 0 : Seg<T>::bytes(tb.s0, ns)) +
+    const uint32_t tx = (zin ? 0 : Seg<T>::bytes(tb.s0, ns)) +
                         (heavy ? Seg<uint16_t>::bytes(tb.s0, ns)
                                : Seg<int32_t>::bytes(tb.r0, nr + 1) + Seg<uint8_t>::bytes(tb.r0, nr)) +
                         Seg<float>::bytes(tb.s0, ns) + Seg<int32_t>::bytes(tb.s0, ns);
     mbar_expect_tx(bar, tx);
     const uint32_t base = smem_u32(stage);
-    if (!first) Seg<T>::copy(base + L::e, ein, tb.s0, ns, bar, pol_keep);
+    if (!zin) Seg<T>::copy(base + L::e, ein, tb.s0, ns, bar, pol_keep);
     if (heavy) {
       Seg<uint16_t>::copy(base + L::lr, g.lrow_big, tb.s0, ns, bar, pol_stream);
     } else {
@@ -631,7 +636,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const float gam = static_cast<float>(ctl->damping);
   // eta_ij sent to slot dst: damped with its previous value when gamma > 0
   auto send = [&](int32_t dst, float v) {
-    if (gam > 0.f) v = gam * (first ? 0.f : ld_eta(ein + dst)) + (1.f - gam) * v;
+    if (gam > 0.f) v = gam * (zin ? 0.f : ld_eta(ein + dst)) + (1.f - gam) * v;
     st_keep(eout + dst, v, pol_keep);
   };
   auto node = [&](int32_t i, float Th, float rhs) {
@@ -653,13 +658,13 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
       if (__syncthreads_or(!got)) return true;
       const int32_t i = tb.r0;
       float sH = 0.f;
-      if (!first)
+      if (!zin)
         for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) sH += ld_eta(ein + s);
       sH = block_sum(sH);
       const float rhs = rhs_at(i), Th = rhs + sH;
       if (tid == 0) node(i, Th, rhs);
       for (int32_t s = tb.s0 + tid; s < tb.s1; s += NT) {
-        const float e = first ? 0.f : ld_eta(ein + s);
+        const float e = zin ? 0.f : ld_eta(ein + s);
         send(g.rev[s], B.c32[s] * (Th - e));
       }
       return false;
@@ -678,11 +683,11 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
         const float rhs = rhs_at(i);
         const int32_t rs = rp[k] - tb.s0, re = rp[k + 1] - tb.s0;
         float sH = 0.f;
-        if (!first)
+        if (!zin)
           for (int32_t s = rs; s < re; ++s) sH += ld_eta(es + s);
         const float Th = rhs + sH;
         node(i, Th, rhs);
-        if (first)
+        if (zin)
           for (int32_t s = rs; s < re; ++s) send(rv[s], cs[s] * Th);
         else
           for (int32_t s = rs; s < re; ++s)
@@ -693,7 +698,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
     for (int32_t k = tid; k < nr; k += NT) rhs_s[k] = rhs_at(tb.r0 + k);
-    if (!first) {
+    if (!zin) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
         const int32_t s = base + (tid & 31);
         const bool v = s < ns;
@@ -707,7 +712,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     for (int32_t k = tid; k < nr; k += NT) node(tb.r0 + k, rhs_s[k] + tc[k], rhs_s[k]);
     for (int32_t s = tid; s < ns; s += NT) {
       const int k = lrow[s];
-      const float e = first ? 0.f : ld_eta(es + s);
+      const float e = zin ? 0.f : ld_eta(es + s);
       send(rv[s], cs[s] * (rhs_s[k] + tc[k] - e));
     }
     return false;
@@ -716,7 +721,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const bool ok = run_tiles(g.ntiles_big, smem, L::bytes, bars, issue, work);
   if (!ok) atomicOr(&red->timeout, 1);
   block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
-  last_block_control(ctl, red, CK_MEAN);
+  last_block_control(ctl, red, g.no_control ? 0 : CK_MEAN);
 }
 
 // Aitken's Delta^2 per node on the last three tentative means in the ring
@@ -1180,9 +1185,8 @@ void launch_tiled(K kernel, size_t smem, int32_t ntiles, int threads, cudaStream
 }
 
 template <int G>
-void launch64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
-  launch_tiled(sweep64_kernel<G>, 2 * Layout64::bytes, g.ntiles_small, kBlock, st, g.view(), B,
-               ctl, red);
+void launch64(const GraphView &v, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  launch_tiled(sweep64_kernel<G>, 2 * Layout64::bytes, v.ntiles_small, kBlock, st, v, B, ctl, red);
 }
 
 // The FP32 sweeps and the residual come in two shared-memory sizes: tiles of
@@ -1213,40 +1217,65 @@ int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars
   return 1;
 }
 
-int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                   const GraphView *view) {
+  const GraphView v = view ? *view : g.view();
   switch (g.group) {
-    case 2: launch64<2>(g, st, B, ctl, red); break;
-    case 4: launch64<4>(g, st, B, ctl, red); break;
-    case 8: launch64<8>(g, st, B, ctl, red); break;
-    case 16: launch64<16>(g, st, B, ctl, red); break;
-    default: launch64<32>(g, st, B, ctl, red); break;
+    case 2: launch64<2>(v, st, B, ctl, red); break;
+    case 4: launch64<4>(v, st, B, ctl, red); break;
+    case 8: launch64<8>(v, st, B, ctl, red); break;
+    case 16: launch64<16>(v, st, B, ctl, red); break;
+    default: launch64<32>(v, st, B, ctl, red); break;
   }
   return 1;
 }
 
 int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
-                   bool bf16) {
+                   bool bf16, const GraphView *view) {
+  const GraphView v = view ? *view : g.view();
   GABP_TS_DISPATCH(g, {
     const size_t smem = 2 * Layout32<TSZ>::bytes;
     if (bf16)
-      launch_tiled(sweep32_kernel<__nv_bfloat16, TSZ>, smem, g.ntiles_big, kTileBlock, st,
-                   g.view(), B, ctl, red);
-    else
-      launch_tiled(sweep32_kernel<float, TSZ>, smem, g.ntiles_big, kTileBlock, st, g.view(), B,
+      launch_tiled(sweep32_kernel<__nv_bfloat16, TSZ>, smem, v.ntiles_big, kTileBlock, st, v, B,
                    ctl, red);
+    else
+      launch_tiled(sweep32_kernel<float, TSZ>, smem, v.ntiles_big, kTileBlock, st, v, B, ctl, red);
   });
   return 1;
 }
 
-int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16) {
+int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16,
+                const GraphView *view) {
+  const GraphView v = view ? *view : g.view();
   GABP_TS_DISPATCH(g, {
     if (bf16)
       launch_tiled(mean_kernel<__nv_bfloat16, TSZ>, 2 * LayoutMean<__nv_bfloat16, TSZ>::bytes,
-                   g.ntiles_big, kTileBlock, st, g.view(), B, ctl, red);
+                   v.ntiles_big, kTileBlock, st, v, B, ctl, red);
     else
-      launch_tiled(mean_kernel<float, TSZ>, 2 * LayoutMean<float, TSZ>::bytes, g.ntiles_big,
-                   kTileBlock, st, g.view(), B, ctl, red);
+      launch_tiled(mean_kernel<float, TSZ>, 2 * LayoutMean<float, TSZ>::bytes, v.ntiles_big,
+                   kTileBlock, st, v, B, ctl, red);
   });
+  return 1;
+}
+
+// Colour schedule: b into the renumbered order, x back to the caller's.
+__global__ void permute_gather_kernel(int32_t n, const int32_t *__restrict__ perm,
+                                      const double *__restrict__ src, double *__restrict__ dst) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[i] = src[perm[i]];
+}
+__global__ void permute_scatter_kernel(int32_t n, const int32_t *__restrict__ perm,
+                                       const double *__restrict__ src, double *__restrict__ dst) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[perm[i]] = src[i];
+}
+
+int launch_permute(int32_t n, cudaStream_t st, const int32_t *perm, const double *src, double *dst,
+                   bool scatter) {
+  if (scatter) permute_scatter_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, perm, src, dst);
+  else permute_gather_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, perm, src, dst);
   return 1;
 }
 

@@ -86,6 +86,7 @@ gabp_status guarded(gabp_handle h, F &&f) {
 bool is_bf16(gabp_handle h) { return h->opt.precision == GABP_PREC_MIXED_BF16; }
 
 void free_resident(Resident &r);
+void zero_messages(gabp_handle h, cudaStream_t st, bool full);
 gabp_status resident_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                            int32_t *iters, bool *ran);
 
@@ -216,6 +217,21 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     }
     return 0;
   }
+  if (g.ncol > 0 && (phase == PH_FULL64 || phase == PH_FULL32 || phase == PH_MEAN)) {
+    // colour schedule: one in-place pass per class (both parities alias one buffer)
+    Buffers B = h->buf;
+    B.m64[1] = B.m64[0];
+    B.m32[1] = B.m32[0];
+    B.e[1] = B.e[0];
+    int k = 0;
+    for (int c = 0; c < g.ncol; ++c) {
+      const GraphView v = g.colour_view(c);
+      if (phase == PH_FULL64) k += launch_sweep64(g, st, B, h->ctl, h->red, &v);
+      else if (phase == PH_FULL32) k += launch_sweep32(g, st, B, h->ctl, h->red, is_bf16(h), &v);
+      else k += launch_mean(g, st, B, h->ctl, h->red, is_bf16(h), &v);
+    }
+    return k;
+  }
   switch (phase) {
     case PH_FULL64: return launch_sweep64(g, st, h->buf, h->ctl, h->red);
     case PH_CHECK64:
@@ -223,15 +239,30 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
                             h->opt.aitken > 0 && h->opt.precision == GABP_PREC_FP64);
     case PH_FULL32: return launch_sweep32(g, st, h->buf, h->ctl, h->red, is_bf16(h));
     case PH_MEAN: return launch_mean(g, st, h->buf, h->ctl, h->red, is_bf16(h));
-    case PH_REFINE: return launch_refine(g, st, h->buf, h->ctl, h->red);
+    case PH_REFINE: {
+      const int k = launch_refine(g, st, h->buf, h->ctl, h->red);
+      if (g.ncol > 0) zero_messages(h, st, false);   // the next inner solve starts from zero
+      return k;
+    }
     case PH_MEANK: return launch_mean_multi(g, st, h->buf, h->ctl, h->red, h->graph_K);
     case PH_REFINEK: return launch_refine_multi(g, st, h->buf, h->ctl, h->red, h->graph_K);
   }
   return 0;
 }
 
+// Colour schedule: the in-place passes read their message buffer from the
+// start of an inner solve on, so it must hold zeros then.
+void zero_messages(gabp_handle h, cudaStream_t st, bool full) {
+  const size_t E = h->g.E + kPad;
+  const Buffers &B = h->buf;
+  if (full && B.m64[0]) CK(cudaMemsetAsync(B.m64[0], 0, sizeof(double2) * E, st));
+  if (full && B.m32[0]) CK(cudaMemsetAsync(B.m32[0], 0, sizeof(float2) * E, st));
+  if (B.e[0]) CK(cudaMemsetAsync(B.e[0], 0, (is_bf16(h) ? 2 : 4) * E, st));
+}
+
 int launch_mode_init(gabp_handle h, cudaStream_t st, int mode) {
   if (mode == CTL_MULTI) return launch_init_multi(h->g, st, h->buf, h->ctl, h->red, h->graph_K);
+  if (h->g.ncol > 0) zero_messages(h, st, true);
   return launch_init(h->g, st, h->buf, h->ctl, h->red);
 }
 
@@ -396,8 +427,8 @@ void run_mode(gabp_handle h, int mode, int32_t max_iter) {
     CK(cudaStreamSynchronize(st));
     const Ctl &c = *h->ctl_host;
     const int per_check = (mode == CTL_MIXED || mode == CTL_MULTI) ? 2 : 1;
-    h->stats.kernel_launches +=
-        1 + static_cast<int64_t>(c.sweeps) + static_cast<int64_t>(c.checks) * per_check;
+    h->stats.kernel_launches += 1 + static_cast<int64_t>(c.sweeps) * std::max(1, h->g.ncol) +
+                                static_cast<int64_t>(c.checks) * per_check;
   } else {
     run(h, K_OTHER, [&] { return launch_mode_init(h, st, mode); });
     const int64_t cap = 4 * static_cast<int64_t>(max_iter) + 128;
@@ -436,12 +467,22 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
   }
   if (mixed) ensure32(h); else ensure64(h);
   h->stats = gabp_stats{};
+  double *x_out = x;
+  if (h->g.ncol > 0) {   // colour schedule: solve in the renumbered order
+    launch_permute(h->g.n, h->stream, h->perm, b, h->bperm, false);
+    b = h->bperm;
+    x = h->xperm;
+  }
   init_ctl(h, mode, b, x, tol, max_iter, false);
   if (h->g.nsys > 0) {
     h->ctl_host->batched = 1;
     CK(cudaMemsetAsync(h->g.sys_bmax, 0, sizeof(unsigned long long) * h->g.nsys, h->stream));
   }
   run_mode(h, mode, max_iter);
+  if (h->g.ncol > 0) {
+    launch_permute(h->g.n, h->stream, h->perm, h->xperm, x_out, true);
+    CK(cudaStreamSynchronize(h->stream));
+  }
   finish_stats(h);
   if (iters) *iters = h->ctl_host->sweeps;
   return report(h, mixed ? "mixed solve" : "FP64 solve");
@@ -570,6 +611,9 @@ void release(gabp_handle h) {
   }
   free_resident(h->res);
   for (double *&r : h->ring) { cudaFree(r); r = nullptr; }
+  cudaFree(h->perm); cudaFree(h->bperm); cudaFree(h->xperm);
+  h->perm = nullptr;
+  h->bperm = h->xperm = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
@@ -699,7 +743,7 @@ bool build_resident(gabp_handle h, int C) {
 // parts fit.
 void setup_resident(gabp_handle h) {
   const Graph &g = h->g;
-  if (h->opt.small_form != 0 || g.E < 1 ||
+  if (h->opt.small_form != 0 || h->g.ncol > 0 || g.E < 1 ||
       g.E > static_cast<int64_t>(kResidentMaxCluster) * kResidentMaxSlots ||
       g.n > kResidentMaxCluster * kResidentMaxRows)
     return;
@@ -929,6 +973,73 @@ void autotune(gabp_handle h) {
   T.tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// Colour schedule: greedy colouring in the caller's row order (the lowest
+// colour no earlier neighbour holds; every off-diagonal CSR entry counts as
+// an edge), then rows renumbered by (colour, row).  Fills the renumbered CSR
+// (columns sorted), the class row offsets, the permutation and, per
+// renumbered entry, the caller's entry.
+struct ColourPlan {
+  std::vector<int32_t> perm, iperm, bounds, col;
+  std::vector<int64_t> rp, pos;
+  std::vector<double> val;
+};
+
+bool plan_colours(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                  const double *val, ColourPlan &p, std::string *msg) {
+  if (n < 1 || !row_ptr || !col || !val || row_ptr[0] != 0 || row_ptr[n] != nnz) {
+    *msg = "invalid CSR";
+    return false;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (row_ptr[i + 1] < row_ptr[i]) { *msg = "row_ptr not monotone"; return false; }
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+      if (col[e] < 0 || col[e] >= n) { *msg = "column index out of range"; return false; }
+  }
+  std::vector<int32_t> colour(n, -1), stamp;
+  int32_t ncol = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t c = col[e] != i ? colour[col[e]] : -1;
+      if (c >= 0) {
+        if (static_cast<size_t>(c) >= stamp.size()) stamp.resize(c + 1, -1);
+        stamp[c] = static_cast<int32_t>(i);
+      }
+    }
+    int32_t c = 0;
+    while (static_cast<size_t>(c) < stamp.size() && stamp[c] == i) ++c;
+    colour[i] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  p.bounds.assign(ncol + 1, 0);
+  for (int64_t i = 0; i < n; ++i) p.bounds[colour[i] + 1]++;
+  for (int32_t c = 0; c < ncol; ++c) p.bounds[c + 1] += p.bounds[c];
+  p.perm.resize(n);
+  p.iperm.resize(n);
+  std::vector<int32_t> next(p.bounds.begin(), p.bounds.end() - 1);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t k = next[colour[i]]++;
+    p.perm[k] = static_cast<int32_t>(i);
+    p.iperm[i] = k;
+  }
+  p.rp.assign(1, 0);
+  p.col.clear(); p.val.clear(); p.pos.clear();
+  p.col.reserve(nnz); p.val.reserve(nnz); p.pos.reserve(nnz);
+  std::vector<std::pair<int32_t, int64_t>> row;
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t i = p.perm[k];
+    row.clear();
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) row.emplace_back(p.iperm[col[e]], e);
+    std::sort(row.begin(), row.end());
+    for (const auto &ce : row) {
+      p.col.push_back(ce.first);
+      p.val.push_back(val[ce.second]);
+      p.pos.push_back(ce.second);
+    }
+    p.rp.push_back(static_cast<int64_t>(p.col.size()));
+  }
+  return true;
+}
+
 // A handle with validated options and no matrix yet.
 gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
   gabp_handle h = new (std::nothrow) gabp_s;
@@ -948,11 +1059,12 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
   if (o.tile_slots < 0 || (o.tile_slots > 0 && (o.tile_slots < 32 || o.tile_slots > 1024)) ||
       o.tile_rows < 0 || o.tile_rows > 256 || o.heavy_degree < 0 ||
       !(o.cluster_ctas == 0 || o.cluster_ctas == 2 || o.cluster_ctas == 4 || o.cluster_ctas == 8 ||
-        o.cluster_ctas == 16) || o.aitken < 0 || o.aitken > 64 ||
+        o.cluster_ctas == 16) || o.aitken < 0 || o.aitken > 64 || o.schedule < 0 || o.schedule > 1 ||
       !(o.dense_rows == 0 || o.dense_rows == 1 || o.dense_rows == 2 || o.dense_rows == 4)) {
     delete h;
     g_create_error = "launch shape out of range (tile_slots 32..1024, tile_rows 1..256, "
-                     "heavy_degree >= 1, dense_rows 1, 2 or 4, cluster_ctas 2..16, aitken 0..64; 0 = automatic)";
+                     "heavy_degree >= 1, dense_rows 1, 2 or 4, cluster_ctas 2..16, aitken 0..64, schedule 0..1; "
+                     "0 = automatic)";
     return GABP_ERR_INVALID_ARG;
   }
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
@@ -983,6 +1095,27 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
   h->user_nnz = nnz;
   gabp_status s = guarded(h, [&] {
     std::string msg;
+    if (h->opt.schedule == 1) {
+      // colour schedule: build the graph of the renumbered matrix
+      ColourPlan cp;
+      if (!plan_colours(n, nnz, row_ptr_host, col_host, val_host, cp, &msg)) {
+        h->last_error = msg;
+        return GABP_ERR_INVALID_ARG;
+      }
+      h->g.ncol = static_cast<int>(cp.bounds.size()) - 1;
+      h->g.col_rows = cp.bounds;
+      gabp_status r = build_graph(h->g, n, nnz, cp.rp.data(), cp.col.data(), cp.val.data(), nullptr,
+                                  h->opt, h->stream, &msg);
+      if (r != GABP_OK) { h->last_error = msg; return r; }
+      for (int64_t &q : h->g.h_user_pos) q = cp.pos[q];   // message export: the caller's entries
+      ensure(&h->perm, n);
+      ensure(&h->bperm, n);
+      ensure(&h->xperm, n);
+      CK(cudaMemcpyAsync(h->perm, cp.perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      return GABP_OK;
+    }
     gabp_status r = build_graph(h->g, n, nnz, row_ptr_host, col_host, val_host, rev_host, h->opt,
                                 h->stream, &msg);
     if (r != GABP_OK) h->last_error = msg;
@@ -1015,6 +1148,10 @@ gabp_status gabp_create_batched(gabp_handle *out, int32_t nsys, const int64_t *s
   *out = nullptr;
   if (nsys < 1 || !sys_row_off_host) {
     g_create_error = "gabp_create_batched: nsys < 1 or null offsets";
+    return GABP_ERR_INVALID_ARG;
+  }
+  if (opt && opt->schedule != 0) {
+    g_create_error = "gabp_create_batched: the colour schedule is not available for batched handles";
     return GABP_ERR_INVALID_ARG;
   }
   // block-diagonal structure is checked on the host before any device work
@@ -1066,6 +1203,10 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
   *out = nullptr;
   if (nsys < 1 || !K_host || !N_host || !S_host || !psi_host) {
     g_create_error = "gabp_create_lsq_batched: invalid argument";
+    return GABP_ERR_INVALID_ARG;
+  }
+  if (opt && opt->schedule != 0) {
+    g_create_error = "gabp_create_lsq_batched: the colour schedule is not available for batched handles";
     return GABP_ERR_INVALID_ARG;
   }
   for (int32_t s = 0; s < nsys; ++s)
@@ -1209,7 +1350,7 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
   if (!B_dev || !X_dev || nrhs < 1 || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: invalid argument");
   // dense Section VII batches solve the columns one after another
-  const bool shared_precisions = h->opt.precision != GABP_PREC_FP64 && !h->dense;
+  const bool shared_precisions = h->opt.precision != GABP_PREC_FP64 && !h->dense && h->g.ncol == 0;
   if (shared_precisions && nrhs > 256)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: at most 256 right-hand sides per call");
   if (shared_precisions)
@@ -1263,6 +1404,13 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
   return guarded(h, [&] {
     cudaStream_t st = h->stream;
     ensure64(h);
+    double *x_user = x_dev;
+    if (h->g.ncol > 0) {   // colour schedule: renumbered order, messages from zero
+      launch_permute(h->g.n, st, h->perm, b_dev, h->bperm, false);
+      b_dev = h->bperm;
+      x_dev = h->xperm;
+      CK(cudaMemsetAsync(h->buf.m64[0], 0, sizeof(double2) * (h->g.E + kPad), st));
+    }
     init_ctl(h, CTL_ROUNDS, b_dev, x_dev, 0.0, rounds, false);
     Ctl &c = *h->ctl_host;
     c.rounds_target = rounds;
@@ -1274,16 +1422,26 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
     CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
     // `rounds` message sweeps, then one pass that only writes the means.
     for (int32_t t = 0; t <= rounds; ++t) {
-      if (h->dense) launch_dense_full64(*h->dense, st, h->buf, h->ctl, h->red);
-      else launch_sweep64(h->g, st, h->buf, h->ctl, h->red);
+      if (h->dense) {
+        launch_dense_full64(*h->dense, st, h->buf, h->ctl, h->red);
+      } else if (h->g.ncol > 0 && t < rounds) {
+        launch_phase(h, st, PH_FULL64);   // one round: the colour passes
+      } else if (h->g.ncol > 0) {
+        Buffers B = h->buf;               // the means of the last round: one buffer
+        B.m64[1] = B.m64[0];
+        launch_sweep64(h->g, st, B, h->ctl, h->red);
+      } else {
+        launch_sweep64(h->g, st, h->buf, h->ctl, h->red);   // (the last pass only infers)
+      }
     }
     if (ait) launch_aitken(h->g.n, st, h->ctl, x_dev);
+    if (h->g.ncol > 0) launch_permute(h->g.n, st, h->perm, h->xperm, x_user, true);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     DevScalars red{};
     CK(cudaMemcpyAsync(&red, h->red, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    h->m64_cur = h->ctl_host->par_m;
+    h->m64_cur = h->g.ncol > 0 ? 0 : h->ctl_host->par_m;
     if (red.breakdown) return fail(h, GABP_ERR_BREAKDOWN, "breakdown during rounds");
     return GABP_OK;
   });

@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "GABP_OK", 1: "GABP_ERR_INVALID_ARG", 2: "GABP_ERR_NOT_SYMMET
                 9: "GABP_ERR_TIMEOUT"}
 PREC_FP64, PREC_MIXED_FP32, PREC_MIXED_BF16 = 0, 1, 2
 RESIDUAL_ABS, RESIDUAL_REL = 0, 1
+SCHEDULE_SYNC, SCHEDULE_COLOUR = 0, 1
 
 # Every symbol include/gabp.h declares (checked by the CPU tests).
 EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_stream",
@@ -48,7 +49,8 @@ class GabpOptions(ctypes.Structure):
                 ("damping", ctypes.c_double), ("tile_rows", ctypes.c_int32),
                 ("heavy_degree", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
                 ("small_form", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
-                ("aitken", ctypes.c_int32)]
+                ("aitken", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("reserved_i", ctypes.c_int32)]
 
 
 class GabpStats(ctypes.Structure):
@@ -331,8 +333,9 @@ class Solver:
                  residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=0.0,
                  profile=False, damping=0.0, stream: int | None = None, autotune=False,
                  tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0,
-                 aitken=0):
+                 aitken=0, schedule=0):
         o = gabp_default_options()
+        o.schedule = schedule
         o.aitken = aitken
         o.small_form = small_form
         o.cluster_ctas = cluster_ctas
