@@ -643,6 +643,7 @@ def run_detect(args):
     o.precision = gabp.PREC_MIXED_FP32
     o.damping = args.damping
     o.lsq_form = args.lsq_form
+    o.schedule = args.schedule
     o.autotune = 1
     o.stream = gabp.current_stream_handle()
     t0 = time.perf_counter()
@@ -684,16 +685,26 @@ def run_detect(args):
     hbm, peak_src = _peaks()
     pairs = E // 2
     dense = args.lsq_form == 0
-    # dense form, per grid position (two directed edges): mean sweep c 8 + eta in 8 +
-    # eta out 8; full sweep S 4 + messages in 16 + out 16; per node ~ 24 B
-    bytes_mean = (24 * pairs if dense else 16 * E) + 24 * st["n"]
-    bytes_full = (36 * pairs if dense else 24 * E) + 24 * st["n"]
+    serial = args.schedule == 1
+    # dense form, per grid position (two directed edges), synchronous: mean sweep
+    # c 8 + eta in 8 + eta out 8; full sweep S 4 + messages in 16 + out 16.
+    # Serial: only the z -> x^ messages are read and written (mean c 8 + 4 + 4,
+    # full S 4 + 8 + 8); damping adds the x^ -> z ones (mean 8, full 16).
+    # Per node ~ 24 B.
+    if dense and serial:
+        damped = args.damping > 0
+        per_mean, per_full = (24, 36) if damped else (16, 20)
+    else:
+        per_mean, per_full = (24, 36) if dense else (16, 24)
+    bytes_mean = (per_mean * pairs if dense else per_mean * E) + 24 * st["n"]
+    bytes_full = (per_full * pairs if dense else per_full * E) + 24 * st["n"]
     mean_us = 1e3 * sp["ms_mean"] / max(1, sp["sweeps_mean"])
     full_us = 1e3 * sp["ms_full"] / max(1, sp["sweeps_full"])
-    roof = {"bound": "hbm", "kernel": "dense_mean_kernel (mean-only sweep)" if dense else "mean_kernel",
+    kname = ("dense_mean_serial_kernel" if serial else "dense_mean_kernel") if dense else "mean_kernel"
+    roof = {"bound": "hbm", "kernel": kname + " (mean-only sweep)",
             "achieved": bytes_mean / (mean_us * 1e-6) / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": bytes_mean / (mean_us * 1e-6) / 1e9 / hbm, "peak_source": peak_src,
-            "traffic": _traffic("dense_mean", pairs) if dense else None,
+            "traffic": _traffic("dense_mean_serial" if serial else "dense_mean", pairs) if dense else None,
             "bytes_per_launch": bytes_mean, "mean_launch_us": mean_us,
             "full_sweep_us": full_us,
             "full_sweep_frac": bytes_full / (full_us * 1e-6) / 1e9 / hbm,
@@ -704,7 +715,7 @@ def run_detect(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched detection: {nsys} systems, K~U{{16..256}}, N=2K, 10 dB, augmented form",
                        "augmented_rows": st["n"], "directed_edges": E, "systems": nsys,
-                       "damping": args.damping},
+                       "damping": args.damping, "schedule": SCHEDULES[args.schedule]},
             "sweeps": {"full": st["sweeps_full"], "mean": st["sweeps_mean"], "outer": st["outer_steps"]},
             "time_to_solution_ms": t, "handle_build_s": build_s,
             "form": "dense bipartite grid" if dense else "CSR tiles",
@@ -731,7 +742,7 @@ def main():
     ap.add_argument("--fp64-max-iter", type=int, default=0,
                     help="poisson3d: separate sweep cap for the FP64 comparison (0 = --max-iter)")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
-                    help="er1e6, poisson32, poisson3d: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
+                    help="er1e6, poisson32, poisson3d, detect: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")
     ap.add_argument("--workload", default="er1e6",
                     choices=["er1e6", "multi64", "detect", "poisson32", "poisson3d"],

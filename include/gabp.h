@@ -108,8 +108,11 @@ typedef struct {
                              updates the colour classes one after another in place, each using
                              the latest messages -- the serial schedule of Section III-C with
                              nodes visited by colour, which needs about half the sweeps on grid
-                             and other two-colourable graphs.  Not for batched handles; small
-                             FP64 systems then take the per-sweep path. */
+                             and other two-colourable graphs.  Small FP64 systems then take the
+                             per-sweep path.  gabp_create_batched: not available.
+                             gabp_create_lsq_batched: dense form only (lsq_form 0 and every
+                             system within its limits); the classes are all x^ nodes, then all
+                             z nodes, so a sweep still streams each grid once. */
   int32_t reserved_i;
 } gabp_options;
 

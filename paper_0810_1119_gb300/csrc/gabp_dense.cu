@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 namespace gabp {
@@ -143,10 +144,150 @@ __device__ __forceinline__ Split split_of(int K) {
 }
 
 // ---------------------------------------------------------------------------
+// Per-round state of a full sweep, shared by the synchronous and the serial
+// kernels: the buffers that hold the node sums of the last sweep and receive
+// those of this one, the flags of the round, and the node work.  Node i of
+// the round has the totals P~_i = A_ii + sumP_i and h~_i = rhs_i + sumEta_i
+// (A_ii = 1 for x^, -psi for z; rhs_i = b_i in FP64, the scaled residual in
+// the mixed modes).  FP32 rounds also keep the monitors of the tentative
+// means d_i = h~_i / P~_i and, at the freeze, 1/P~_i.
+// ---------------------------------------------------------------------------
+template <class T>
+struct FullRound {
+  using V = T2<T>;
+  static constexpr bool kF64 = sizeof(T) == 8;
+  bool first, write_x = false, write_msgs = true, freeze = false;
+  double inv_rn;
+  const double *__restrict__ b;
+  double *__restrict__ x;
+  T gam;
+  const V *__restrict__ sum_in;
+  V *__restrict__ sum_out;
+  float *__restrict__ sumE_out;   // freeze: sums of the first mean messages
+  const float2 *__restrict__ mon_prev;
+  float2 *__restrict__ mon_out;
+  uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;
+
+  __device__ FullRound(const DenseView &d, const Buffers &B, const Ctl *ctl) {
+    const int par = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
+    first = ctl->first != 0;
+    if (kF64) {
+      if (ctl->mode == CTL_ROUNDS) {
+        write_x = ctl->sweeps >= ctl->rounds_target;   // the infer-only pass
+        write_msgs = !write_x;
+      } else {
+        write_x = ctl->write_x != 0;
+      }
+    } else {
+      freeze = ctl->pending_freeze != 0;
+    }
+    inv_rn = ctl->inv_rn;
+    b = ctl->b;
+    x = ctl->x;
+    gam = static_cast<T>(ctl->damping);
+    if constexpr (kF64) {
+      sum_in = par ? d.sum64[1] : d.sum64[0];
+      sum_out = par ? d.sum64[0] : d.sum64[1];
+    } else {
+      sum_in = par ? d.sum32[1] : d.sum32[0];
+      sum_out = par ? d.sum32[0] : d.sum32[1];
+    }
+    sumE_out = pe ? d.sumE[0] : d.sumE[1];
+    mon_prev = pmon ? B.mon32[1] : B.mon32[0];
+    mon_out = pmon ? B.mon32[0] : B.mon32[1];
+  }
+
+  // Totals (P~_i, h~_i) of node i; *rhs receives rhs_i.
+  __device__ __forceinline__ V node(int64_t i, T aii, const Buffers &B, T *rhs) {
+    const V sm = first ? mk2<T>(T(0), T(0)) : sum_in[i];
+    if constexpr (kF64) {
+      const T bi = b[i];
+      const T TP = aii + sm.x, Th = bi + sm.y;
+      if (write_x) x[i] = Th / TP;
+      *rhs = bi;
+      return mk2<T>(TP, Th);
+    } else {
+      const float r = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+      const float TP = aii + sm.x, Th = r + sm.y;
+      const float2 prev = first ? make_float2(0.f, 0.f) : mon_prev[i];
+      const float di = Th / TP;
+      mon_out[i] = make_float2(TP, di);
+      mdd = fmax_bits(mdd, di - prev.y);
+      md = fmax_bits(md, di);
+      mdP = fmax_bits(mdP, TP - prev.x);
+      mP = fmax_bits(mP, TP);
+      if (freeze) B.invP32[i] = 1.0f / TP;
+      if (first) B.rhs32[i] = r;
+      *rhs = r;
+      return mk2<T>(TP, Th);
+    }
+  }
+
+  // Sums of node i over the messages this round sent to it.
+  __device__ __forceinline__ void put_sum(int64_t i, V v) const {
+    if (!kF64 && freeze) sumE_out[i] = static_cast<float>(v.y);
+    else sum_out[i] = v;
+  }
+
+  __device__ void finish(Ctl *ctl, DevScalars *red, bool brk) {
+    if (brk) atomicOr(&red->breakdown, 1);
+    if constexpr (kF64) {
+      last_block_control(ctl, red, CK_SWEEP64);
+    } else {
+      block_max4(widen(mdd), widen(md), widen(mdP), widen(mP), &red->max_dx, &red->max_x,
+                 &red->max_dP, &red->max_P);
+      last_block_control(ctl, red, CK_SWEEP32);
+    }
+  }
+};
+
+// Per-round state of a mean-only sweep (frozen precisions, FP32): node i has
+// h~_i = rhs_i + sumEta_i and d_i = h~_i / P~_i with the frozen 1/P~_i.
+struct MeanRound {
+  bool first;
+  double inv_rn;
+  float gam;
+  const float *__restrict__ sum_in;
+  float *__restrict__ sum_out;
+  const float2 *__restrict__ mon_prev;
+  float2 *__restrict__ mon_out;
+  uint32_t mdd = 0, md = 0;
+
+  __device__ MeanRound(const DenseView &d, const Buffers &B, const Ctl *ctl) {
+    const int pe = ctl->par_e, pmon = ctl->par_mon;
+    first = ctl->first != 0;
+    inv_rn = ctl->inv_rn;
+    gam = static_cast<float>(ctl->damping);
+    sum_in = pe ? d.sumE[1] : d.sumE[0];
+    sum_out = pe ? d.sumE[0] : d.sumE[1];
+    mon_prev = pmon ? B.mon32[1] : B.mon32[0];
+    mon_out = pmon ? B.mon32[0] : B.mon32[1];
+  }
+
+  // h~_i of node i; *rhs receives rhs_i.
+  __device__ __forceinline__ float node(int64_t i, const Buffers &B, float *rhs) {
+    const float r = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+    const float Th = r + (first ? 0.f : sum_in[i]);
+    const float prev = first ? 0.f : mon_prev[i].y;
+    const float di = Th * B.invP32[i];
+    mon_out[i] = make_float2(0.f, di);
+    mdd = fmax_bits(mdd, di - prev);
+    md = fmax_bits(md, di);
+    if (first) B.rhs32[i] = r;
+    *rhs = r;
+    return Th;
+  }
+
+  __device__ void finish(Ctl *ctl, DevScalars *red) {
+    block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
+    last_block_control(ctl, red, CK_MEAN);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Full sweep, T = double (FP64 solves and gabp_run_rounds) or float (mixed
-// modes, with the precision freeze).  Node i of the round: P~_i = A_ii +
-// sumP_i, h~_i = b_i + sumEta_i (A_ii = 1 for x^, -psi for z); the messages
-// of Alg. 2,
+// modes, with the precision freeze), synchronous schedule (Alg. 2).  The
+// messages of Alg. 2 at grid position (j, r), from the totals of the round:
 //     P_ij = -S^2 / (P~_i - P_ji),   eta_ij = -S (h~_i - eta_ji) / (P~_i - P_ji).
 // FP32 freeze: c = -S / (P~_i - P_ji) is stored and the first mean-only
 // messages eta_ij = c (h~_i - eta_ji) are written (storage E) instead of full
@@ -160,47 +301,24 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ V tx[kDenseMaxK], tz[kDenseMaxN];   // (P~, h~) of this round
   __shared__ V ax[kDenseMaxK], az[kDenseMaxN];   // sums of the new messages
   __shared__ int32_t cur;
-  const int par = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
-  const bool first = ctl->first != 0;
-  bool write_x = false, write_msgs = true, freeze = false;
-  if (kF64) {
-    if (ctl->mode == CTL_ROUNDS) {
-      write_x = ctl->sweeps >= ctl->rounds_target;   // the infer-only pass
-      write_msgs = !write_x;
-    } else {
-      write_x = ctl->write_x != 0;
-    }
-  } else {
-    freeze = ctl->pending_freeze != 0;
-  }
-  const double inv_rn = ctl->inv_rn;
-  const double *__restrict__ b = ctl->b;
-  double *__restrict__ x = ctl->x;
-  const T gam = static_cast<T>(ctl->damping);
+  FullRound<T> R(d, B, ctl);
+  const int par = ctl->par_m, pe = ctl->par_e;
+  const bool first = R.first, freeze = R.freeze;
+  const T gam = R.gam;
   const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
                                   : reinterpret_cast<const T *>(d.S32);
   FullIO<T> io;
-  const V *__restrict__ sum_in;
-  V *__restrict__ sum_out;
   if constexpr (kF64) {
     io.inz = par ? d.Mz64[1] : d.Mz64[0];
     io.inx = par ? d.Mx64[1] : d.Mx64[0];
     io.outz = par ? d.Mz64[0] : d.Mz64[1];
     io.outx = par ? d.Mx64[0] : d.Mx64[1];
-    sum_in = par ? d.sum64[1] : d.sum64[0];
-    sum_out = par ? d.sum64[0] : d.sum64[1];
   } else {
     io.in = par ? d.M32[1] : d.M32[0];
     io.out = par ? d.M32[0] : d.M32[1];
-    sum_in = par ? d.sum32[1] : d.sum32[0];
-    sum_out = par ? d.sum32[0] : d.sum32[1];
   }
-  // freeze outputs: mean messages and their sums go to the other mean buffer
+  // freeze outputs: mean messages go to the other mean buffer
   E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
-  float *__restrict__ sumE_out = pe ? d.sumE[0] : d.sumE[1];
-  const float2 *__restrict__ mon_prev = pmon ? B.mon32[1] : B.mon32[0];
-  float2 *__restrict__ mon_out = pmon ? B.mon32[0] : B.mon32[1];
-  uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;
   bool brk = false;
   const int tid = threadIdx.x, lane = tid & 31;
 
@@ -211,33 +329,13 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     const int K = sy.K, N = sy.N;
     // ---- node work of the round ----
     for (int k = tid; k < K + N; k += kDenseBlock) {
-      const int64_t i = sy.node0 + k;
-      const T aii = k < K ? T(1) : static_cast<T>(-sy.psi);
-      const V sm = first ? mk2<T>(T(0), T(0)) : sum_in[i];
-      T TP, Th;
-      if constexpr (kF64) {
-        TP = aii + sm.x;
-        Th = b[i] + sm.y;
-        if (write_x) x[i] = Th / TP;
-      } else {
-        const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
-        TP = aii + sm.x;
-        Th = rhs + sm.y;
-        const float2 prev = first ? make_float2(0.f, 0.f) : mon_prev[i];
-        const float di = Th / TP;
-        mon_out[i] = make_float2(TP, di);
-        mdd = fmax_bits(mdd, di - prev.y);
-        md = fmax_bits(md, di);
-        mdP = fmax_bits(mdP, TP - prev.x);
-        mP = fmax_bits(mP, TP);
-        if (freeze) B.invP32[i] = 1.0f / TP;
-        if (first) B.rhs32[i] = rhs;
-      }
-      if (k < K) { tx[k] = mk2<T>(TP, Th); ax[k] = mk2<T>(T(0), T(0)); }
-      else { tz[k - K] = mk2<T>(TP, Th); az[k - K] = mk2<T>(T(0), T(0)); }
+      T rhs;
+      const V t = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
+      if (k < K) { tx[k] = t; ax[k] = mk2<T>(T(0), T(0)); }
+      else { tz[k - K] = t; az[k - K] = mk2<T>(T(0), T(0)); }
     }
     __syncthreads();
-    if (!write_msgs) continue;
+    if (!R.write_msgs) continue;
     // ---- grid pass ----
     const Split w = split_of(K);
     if (w.warp_on) {
@@ -316,27 +414,16 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     }
     __syncthreads();
     // ---- sums of the new round ----
-    for (int k = tid; k < K + N; k += kDenseBlock) {
-      const V v = k < K ? ax[k] : az[k - K];
-      if (!kF64 && freeze) sumE_out[sy.node0 + k] = static_cast<float>(v.y);
-      else sum_out[sy.node0 + k] = v;
-    }
+    for (int k = tid; k < K + N; k += kDenseBlock)
+      R.put_sum(sy.node0 + k, k < K ? ax[k] : az[k - K]);
   }
-  if (brk) atomicOr(&red->breakdown, 1);
-  if constexpr (kF64) {
-    last_block_control(ctl, red, CK_SWEEP64);
-  } else {
-    block_max4(widen(mdd), widen(md), widen(mdP), widen(mP), &red->max_dx, &red->max_x,
-               &red->max_dP, &red->max_P);
-    last_block_control(ctl, red, CK_SWEEP32);
-  }
+  R.finish(ctl, red, brk);
 }
 
 // ---------------------------------------------------------------------------
 // Mean-only sweep with frozen precisions (FP32 arithmetic; storage E = float2
-// or __nv_bfloat162 per grid position):
-//     eta_z' = c_z (h~_r - eta_x),   eta_x' = c_x (h~_j - eta_z),
-// h~_i = r_i / ||r|| + sumEta_i, d_i = h~_i / P~_i (frozen 1/P~_i).
+// or __nv_bfloat162 per grid position), synchronous schedule:
+//     eta_z' = c_z (h~_r - eta_x),   eta_x' = c_x (h~_j - eta_z).
 // ---------------------------------------------------------------------------
 template <class E, int U>
 __global__ void __launch_bounds__(kDenseBlock)
@@ -344,18 +431,13 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ float tx[kDenseMaxK], tz[kDenseMaxN];   // h~ of this round
   __shared__ float ax[kDenseMaxK], az[kDenseMaxN];   // sums of the new messages
   __shared__ int32_t cur;
-  const int pe = ctl->par_e, pmon = ctl->par_mon;
-  const bool first = ctl->first != 0;
-  const double inv_rn = ctl->inv_rn;
-  const float gam = static_cast<float>(ctl->damping);
+  MeanRound R(d, B, ctl);
+  const int pe = ctl->par_e;
+  const bool first = R.first;
+  const float gam = R.gam;
   const E *__restrict__ h_in = static_cast<const E *>(pe ? d.H[1] : d.H[0]);
   E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
-  const float *__restrict__ sum_in = pe ? d.sumE[1] : d.sumE[0];
-  float *__restrict__ sum_out = pe ? d.sumE[0] : d.sumE[1];
-  const float2 *__restrict__ mon_prev = pmon ? B.mon32[1] : B.mon32[0];
-  float2 *__restrict__ mon_out = pmon ? B.mon32[0] : B.mon32[1];
   const float2 *__restrict__ C = d.C32;
-  uint32_t mdd = 0, md = 0;
   const int tid = threadIdx.x, lane = tid & 31;
 
   for (;;) {
@@ -364,15 +446,8 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     const DenseSys sy = d.sys[s];
     const int K = sy.K, N = sy.N;
     for (int k = tid; k < K + N; k += kDenseBlock) {
-      const int64_t i = sy.node0 + k;
-      const float rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
-      const float Th = rhs + (first ? 0.f : sum_in[i]);
-      const float prev = first ? 0.f : mon_prev[i].y;
-      const float di = Th * B.invP32[i];
-      mon_out[i] = make_float2(0.f, di);
-      mdd = fmax_bits(mdd, di - prev);
-      md = fmax_bits(md, di);
-      if (first) B.rhs32[i] = rhs;
+      float rhs;
+      const float Th = R.node(sy.node0 + k, B, &rhs);
       if (k < K) { tx[k] = Th; ax[k] = 0.f; }
       else { tz[k - K] = Th; az[k - K] = 0.f; }
     }
@@ -419,10 +494,315 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     }
     __syncthreads();
     for (int k = tid; k < K + N; k += kDenseBlock)
-      sum_out[sy.node0 + k] = k < K ? ax[k] : az[k - K];
+      R.sum_out[sy.node0 + k] = k < K ? ax[k] : az[k - K];
   }
-  block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
-  last_block_control(ctl, red, CK_MEAN);
+  R.finish(ctl, red);
+}
+
+// ---------------------------------------------------------------------------
+// Serial schedule (Section III-C) in the dense form, with the nodes visited
+// class by class: every x^_r first, then every z_j (no two nodes of a class
+// are joined, so the order inside a class does not matter).
+//   x^ class:  Mz'(j, r) from the totals of x^_r -- the column sums the last
+//              sweep left -- and Mx(j, r);
+//   z class:   the totals of z_j are the row sums of Mz'(j, .), and
+//              Mx'(j, r) follows from them and Mz'(j, r).
+// One warp therefore takes a whole row j, lanes on columns lane + 32 q
+// (q < Q): it forms Mz'(j, .) in registers, sums the row across the warp,
+// and forms Mx'(j, .) -- the sweep still streams the grid once.  Mz is read
+// again only for damping (its previous information), so without damping it
+// is never stored.  Messages are updated in place: every grid position is
+// read and written by the same lane within a sweep.
+// Planar layout, pair p = pair0 + j K + r:
+//   FP64:   Mx64[0][p] = (Px, eta_x), Mz64[0][p] = (Pz, eta_z);
+//   FP32:   float2 planes (Px, eta_x) at M32[0], (Pz, eta_z) after them;
+//   mean:   eta_x plane at H[0], eta_z plane after it (storage E1).
+// The node sums the sweep leaves are exactly the totals the serial round
+// ends with: x^ from the new Mx', z from the new Mz'.
+// ---------------------------------------------------------------------------
+template <class E> struct Half;
+template <> struct Half<float2> { using t = float; };
+template <> struct Half<__nv_bfloat162> { using t = __nv_bfloat16; };
+
+__device__ __forceinline__ float ld1(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float ld1(const __nv_bfloat16 *p) { return __bfloat162float(__ldcs(p)); }
+__device__ __forceinline__ void st1(float *p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st1(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
+
+// Columns each lane holds for a system of K columns: 1, 2, 4 or 8.
+template <class F>
+__device__ __forceinline__ void by_columns(int K, F &&f) {
+  const int kq = (K + 31) >> 5;
+  if (kq > 4) f(std::integral_constant<int, 8>{});
+  else if (kq > 2) f(std::integral_constant<int, 4>{});
+  else if (kq > 1) f(std::integral_constant<int, 2>{});
+  else f(std::integral_constant<int, 1>{});
+}
+
+template <class T, class E1, int Q>
+__device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__restrict__ Sg,
+                                                 T2<T> *__restrict__ mx, T2<T> *__restrict__ mz,
+                                                 float2 *__restrict__ C, E1 *__restrict__ hx,
+                                                 E1 *__restrict__ hz, const T2<T> *tx,
+                                                 const T *zr, T2<T> *ax, FullRound<T> &R,
+                                                 bool &brk) {
+  using V = T2<T>;
+  constexpr bool kF64 = sizeof(T) == 8;
+  constexpr int U = 8 / Q;   // rows in flight per warp step: U Q loads per lane and array
+  const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool first = R.first, freeze = !kF64 && R.freeze, damp = R.gam > T(0);
+  const T gam = R.gam;
+  const T aii = static_cast<T>(-sy.psi);
+  V xr[Q];
+  ColSum<T> cP[Q], cE[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    xr[q] = r < K ? tx[r] : mk2<T>(T(1), T(0));
+  }
+  for (int j0 = w * U; j0 < N; j0 += kDenseWarps * U) {
+    T a[U][Q], ezo[U][Q];
+    V m[U][Q];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = j0 + u, r = lane + 32 * q;
+        a[u][q] = T(0);
+        ezo[u][q] = T(0);
+        m[u][q] = mk2<T>(T(0), T(0));
+        if (j < N && r < K) {
+          const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+          a[u][q] = __ldcs(Sg + p);
+          if (!first) {
+            m[u][q] = __ldcs(mx + p);
+            if (damp) ezo[u][q] = __ldcs(mz + p).y;
+          }
+        }
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u;
+      if (j >= N) break;   // the same for every lane of the warp
+      // x^_r -> z_j for the columns of this lane, and the totals of z_j
+      T pz[Q], ez[Q], cz[Q];
+      T sP = T(0), sE = T(0);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        pz[q] = ez[q] = cz[q] = T(0);
+        const T av = a[u][q];
+        if (av != T(0)) {
+          const T dz = xr[q].x - m[u][q].x;   // P~_r - P_{z_j -> x_r}
+          brk |= bad(dz);
+          const T iz = rcp(dz);
+          pz[q] = -(av * av) * iz;
+          if (freeze) {
+            cz[q] = -av * iz;
+            ez[q] = cz[q] * (xr[q].y - m[u][q].y);
+          } else {
+            ez[q] = -av * (xr[q].y - m[u][q].y) * iz;
+          }
+          if (damp) ez[q] = gam * ezo[u][q] + (T(1) - gam) * ez[q];
+        }
+        sP += pz[q];
+        sE += ez[q];
+      }
+      sP = group_sum<32>(sP);
+      sE = group_sum<32>(sE);
+      const T TPz = aii + sP, Thz = zr[j] + sE;
+      // z_j -> x^_r
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        if (r >= K) continue;
+        const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+        const T av = a[u][q];
+        T px = T(0), ex = T(0), cx = T(0);
+        if (av != T(0)) {
+          const T dx = TPz - pz[q];   // P~_j - P_{x_r -> z_j}
+          brk |= bad(dx);
+          const T ix = rcp(dx);
+          px = -(av * av) * ix;
+          if (freeze) {
+            cx = -av * ix;
+            ex = cx * (Thz - ez[q]);
+          } else {
+            ex = -av * (Thz - ez[q]) * ix;
+          }
+          if (damp) ex = gam * m[u][q].y + (T(1) - gam) * ex;
+        }
+        if (freeze) {
+          C[p] = make_float2(static_cast<float>(cz[q]), static_cast<float>(cx));
+          st1(hx + p, static_cast<float>(ex));
+          if (damp) st1(hz + p, static_cast<float>(ez[q]));
+        } else {
+          __stcs(mx + p, mk2<T>(px, ex));
+          if (damp) __stcs(mz + p, mk2<T>(pz[q], ez[q]));
+        }
+        cP[q].add(px);
+        cE[q].add(ex);
+      }
+      if (lane == 0) R.put_sum(sy.node0 + sy.K + j, mk2<T>(sP, sE));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    if (r < K) {
+      atomicAdd(&ax[r].x, cP[q].value());
+      atomicAdd(&ax[r].y, cE[q].value());
+    }
+  }
+}
+
+template <class T, class E>
+__global__ void __launch_bounds__(kDenseBlock)
+dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
+  using V = T2<T>;
+  using E1 = typename Half<E>::t;
+  constexpr bool kF64 = sizeof(T) == 8;
+  __shared__ V tx[kDenseMaxK], ax[kDenseMaxK];   // totals of x^ / sums of the new Mx'
+  __shared__ T zr[kDenseMaxN];                   // rhs of z
+  __shared__ int32_t cur;
+  FullRound<T> R(d, B, ctl);
+  const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
+                                  : reinterpret_cast<const T *>(d.S32);
+  V *mx, *mz;
+  if constexpr (kF64) {
+    mx = d.Mx64[0];
+    mz = d.Mz64[0];
+  } else {
+    mx = reinterpret_cast<float2 *>(d.M32[0]);
+    mz = mx + d.pairs;
+  }
+  E1 *hx = static_cast<E1 *>(d.H[0]);
+  E1 *hz = hx + d.pairs;
+  bool brk = false;
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    const int32_t s = claim(ctl, &cur);
+    if (s >= d.nsys) break;
+    const DenseSys sy = d.sys[s];
+    const int K = sy.K, N = sy.N;
+    for (int k = tid; k < K + N; k += kDenseBlock) {
+      T rhs;
+      const V t = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
+      if (k < K) { tx[k] = t; ax[k] = mk2<T>(T(0), T(0)); }
+      else zr[k - K] = rhs;
+    }
+    __syncthreads();
+    if (!R.write_msgs) continue;
+    by_columns(K, [&](auto q) {
+      full_serial_rows<T, E1, decltype(q)::value>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, ax, R,
+                                                  brk);
+    });
+    __syncthreads();
+    for (int k = tid; k < K; k += kDenseBlock) R.put_sum(sy.node0 + k, ax[k]);
+  }
+  R.finish(ctl, red, brk);
+}
+
+template <class E1, int Q>
+__device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float2 *__restrict__ C,
+                                                 E1 *__restrict__ hx, E1 *__restrict__ hz,
+                                                 const float *tx, const float *zr, float *ax,
+                                                 MeanRound &R) {
+  constexpr int U = 8 / Q;
+  const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool first = R.first, damp = R.gam > 0.f;
+  const float gam = R.gam;
+  float hr[Q];
+  ColSum<float> cE[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    hr[q] = r < K ? tx[r] : 0.f;
+  }
+  for (int j0 = w * U; j0 < N; j0 += kDenseWarps * U) {
+    float2 c[U][Q];
+    float ho[U][Q], zo[U][Q];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = j0 + u, r = lane + 32 * q;
+        c[u][q] = make_float2(0.f, 0.f);
+        ho[u][q] = zo[u][q] = 0.f;
+        if (j < N && r < K) {
+          const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+          c[u][q] = __ldcs(C + p);
+          if (!first) {
+            ho[u][q] = ld1(hx + p);
+            if (damp) zo[u][q] = ld1(hz + p);
+          }
+        }
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u;
+      if (j >= N) break;   // the same for every lane of the warp
+      float ez[Q];
+      float sE = 0.f;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        ez[q] = c[u][q].x * (hr[q] - ho[u][q]);
+        if (damp) ez[q] = gam * zo[u][q] + (1.f - gam) * ez[q];
+        sE += ez[q];
+      }
+      sE = group_sum<32>(sE);
+      const float Thz = zr[j] + sE;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        if (r >= K) continue;
+        const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+        float ex = c[u][q].y * (Thz - ez[q]);
+        if (damp) ex = gam * ho[u][q] + (1.f - gam) * ex;
+        st1(hx + p, ex);
+        if (damp) st1(hz + p, ez[q]);
+        cE[q].add(ex);
+      }
+      if (lane == 0) R.sum_out[sy.node0 + sy.K + j] = sE;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    if (r < K) atomicAdd(&ax[r], cE[q].value());
+  }
+}
+
+template <class E1>
+__global__ void __launch_bounds__(kDenseBlock)
+dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
+  __shared__ float tx[kDenseMaxK], ax[kDenseMaxK];   // h~ of x^ / sums of the new eta_x
+  __shared__ float zr[kDenseMaxN];                   // rhs of z
+  __shared__ int32_t cur;
+  MeanRound R(d, B, ctl);
+  E1 *hx = static_cast<E1 *>(d.H[0]);
+  E1 *hz = hx + d.pairs;
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    const int32_t s = claim(ctl, &cur);
+    if (s >= d.nsys) break;
+    const DenseSys sy = d.sys[s];
+    const int K = sy.K, N = sy.N;
+    for (int k = tid; k < K + N; k += kDenseBlock) {
+      float rhs;
+      const float Th = R.node(sy.node0 + k, B, &rhs);
+      if (k < K) { tx[k] = Th; ax[k] = 0.f; }
+      else zr[k - K] = rhs;
+    }
+    __syncthreads();
+    by_columns(K, [&](auto q) {
+      mean_serial_rows<E1, decltype(q)::value>(sy, d.C32, hx, hz, tx, zr, ax, R);
+    });
+    __syncthreads();
+    for (int k = tid; k < K; k += kDenseBlock) R.sum_out[sy.node0 + k] = ax[k];
+  }
+  R.finish(ctl, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -528,13 +908,19 @@ int dense_grid(Kern kernel, int32_t nsys) {
   } while (0)
 
 int launch_dense_full64(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
-  auto k = dense_full_kernel<double, float2, 2>;
+  auto k = d.serial ? dense_full_serial_kernel<double, float2> : dense_full_kernel<double, float2, 2>;
   k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
   return 1;
 }
 
 int launch_dense_full32(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                         bool bf16) {
+  if (d.serial) {
+    auto k = bf16 ? dense_full_serial_kernel<float, __nv_bfloat162>
+                  : dense_full_serial_kernel<float, float2>;
+    k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+    return 1;
+  }
   GABP_ROWS_DISPATCH(d.rows_full, {
     if (bf16) {
       auto k = dense_full_kernel<float, __nv_bfloat162, UR>;
@@ -549,6 +935,11 @@ int launch_dense_full32(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, De
 
 int launch_dense_mean(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                       bool bf16) {
+  if (d.serial) {
+    auto k = bf16 ? dense_mean_serial_kernel<__nv_bfloat16> : dense_mean_serial_kernel<float>;
+    k<<<dense_grid(k, d.nsys), kDenseBlock, 0, st>>>(d.v, B, ctl, red);
+    return 1;
+  }
   GABP_ROWS_DISPATCH(d.rows_mean, {
     if (bf16) {
       auto k = dense_mean_kernel<__nv_bfloat162, UR>;
@@ -572,7 +963,15 @@ int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *c
 // any graph is recorded).
 void prepare_dense_kernels(bool bf16) {
   dense_grid(dense_full_kernel<double, float2, 2>, 1);
+  dense_grid(dense_full_serial_kernel<double, float2>, 1);
   dense_grid(dense_residual_kernel, 1);
+  if (bf16) {
+    dense_grid(dense_full_serial_kernel<float, __nv_bfloat162>, 1);
+    dense_grid(dense_mean_serial_kernel<__nv_bfloat16>, 1);
+  } else {
+    dense_grid(dense_full_serial_kernel<float, float2>, 1);
+    dense_grid(dense_mean_serial_kernel<float>, 1);
+  }
   for (int u : {1, 2, 4}) {
     GABP_ROWS_DISPATCH(u, {
       if (bf16) {

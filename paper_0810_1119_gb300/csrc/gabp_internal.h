@@ -258,10 +258,12 @@ constexpr int kDenseMaxN = 1024;
 //                 Px/eta_x = message z_j -> x^_r;
 //   mean sweeps:  (eta_z, eta_x) with frozen coefficients (c_z, c_x).
 // Per node: the sums over its incoming messages of the round held in the
-// buffer of the same parity (sumP, sum eta).
+// buffer of the same parity (sumP, sum eta).  The serial schedule keeps the
+// messages in place in the buffers of index 0, one plane per direction.
 struct DenseView {
   const DenseSys *sys;
   int32_t nsys;
+  int64_t pairs;
   const float *S32;
   const double *S64;
   float4 *M32[2];
@@ -283,6 +285,7 @@ struct Dense {
   DenseSys *sys = nullptr;      // device, largest systems first
   bool have64 = false, have32 = false;
   int rows_mean = 2, rows_full = 2;   // grid rows each warp loads ahead (1, 2 or 4)
+  bool serial = false;                // serial schedule, class x^ then class z
 };
 
 int launch_dense_full64(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);

@@ -103,8 +103,10 @@ void ensure_dense64(gabp_handle h) {
   if (d.have64) return;
   DenseView &v = d.v;
   for (int k = 0; k < 2; ++k) {
-    ensure(&v.Mz64[k], d.pairs);
-    ensure(&v.Mx64[k], d.pairs);
+    if (k == 0 || !d.serial) {   // the serial schedule updates messages in place
+      ensure(&v.Mz64[k], d.pairs);
+      ensure(&v.Mx64[k], d.pairs);
+    }
     ensure(&v.sum64[k], d.nodes);
   }
   d.have64 = true;
@@ -117,9 +119,10 @@ void ensure_dense32(gabp_handle h) {
   Buffers &B = h->buf;
   const size_t hb = (d.pairs + kPad) * (is_bf16(h) ? sizeof(__nv_bfloat162) : sizeof(float2));
   for (int k = 0; k < 2; ++k) {
-    ensure(&v.M32[k], d.pairs);
     ensure(&v.sum32[k], d.nodes);
     ensure(&v.sumE[k], d.nodes);
+    if (k == 1 && d.serial) continue;   // the serial schedule updates messages in place
+    ensure(&v.M32[k], d.pairs);
     CK(cudaMalloc(&v.H[k], hb));
     CK(cudaMemset(v.H[k], 0, hb));
   }
@@ -675,6 +678,7 @@ void build_dense(gabp_handle h, int32_t nsys, const int32_t *K, const int32_t *N
   CK(cudaStreamSynchronize(st));
   d->v.sys = d->sys;
   d->v.nsys = nsys;
+  d->v.pairs = pairs;
   d->v.sys_of_row = g.sys_of_row;
   d->v.sys_bmax = g.sys_bmax;
   prepare_dense_kernels(is_bf16(h));
@@ -865,8 +869,9 @@ void fill_tuning(gabp_handle h) {
   t.tile_rows = h->g.tile_rows;
   t.heavy_degree = h->g.heavy_degree;
   t.group_lanes = h->g.group;
-  t.dense_rows_mean = h->dense ? h->dense->rows_mean : 0;
-  t.dense_rows_full = h->dense ? h->dense->rows_full : 0;
+  const bool rows = h->dense && !h->dense->serial;   // the serial kernels take whole rows
+  t.dense_rows_mean = rows ? h->dense->rows_mean : 0;
+  t.dense_rows_full = rows ? h->dense->rows_full : 0;
   t.cluster_ctas = h->res.C;
 }
 
@@ -880,7 +885,7 @@ void autotune(gabp_handle h) {
   const bool mixed = h->opt.precision != GABP_PREC_FP64;
   const bool bf16 = is_bf16(h);
   if (h->dense) {
-    if (mixed && h->opt.dense_rows == 0) {
+    if (mixed && h->opt.dense_rows == 0 && !h->dense->serial) {
       Dense &d = *h->dense;
       ensure32(h);
       float best = 1e30f;
@@ -1205,10 +1210,6 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
     g_create_error = "gabp_create_lsq_batched: invalid argument";
     return GABP_ERR_INVALID_ARG;
   }
-  if (opt && opt->schedule != 0) {
-    g_create_error = "gabp_create_lsq_batched: the colour schedule is not available for batched handles";
-    return GABP_ERR_INVALID_ARG;
-  }
   for (int32_t s = 0; s < nsys; ++s)
     if (K_host[s] < 1 || N_host[s] < 1 || !(psi_host[s] > 0.0) || !std::isfinite(psi_host[s])) {
       g_create_error = "gabp_create_lsq_batched: K_s, N_s >= 1 and psi_s > 0 required";
@@ -1217,6 +1218,11 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
   bool dense = !opt || opt->lsq_form == 0;
   for (int32_t s = 0; s < nsys && dense; ++s)
     dense = K_host[s] <= kDenseMaxK && N_host[s] <= kDenseMaxN;
+  if (opt && opt->schedule != 0 && !dense) {
+    g_create_error = "gabp_create_lsq_batched: the colour schedule needs the dense form (lsq_form 0, "
+                     "K_s <= 256 and N_s <= 1024)";
+    return GABP_ERR_INVALID_ARG;
+  }
   gabp_handle h = nullptr;
   gabp_status s = GABP_OK;
   std::vector<int64_t> sys_off(1, 0);
@@ -1231,6 +1237,7 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
     if (s != GABP_OK) return s;
     s = guarded(h, [&] {
       build_dense(h, nsys, K_host, N_host, S_host, psi_host, sys_off);
+      h->dense->serial = h->opt.schedule == 1;
       if (h->opt.dense_rows > 0) h->dense->rows_mean = h->dense->rows_full = h->opt.dense_rows;
       fill_tuning(h);
       if (h->opt.autotune) autotune(h);

@@ -110,12 +110,86 @@ def test_colour_solves_need_fewer_sweeps(G, precision, name, make):
         assert sweeps[1] < sweeps[0], sweeps
 
 
-def test_colour_schedule_is_refused_for_batches(G):
-    m = W.poisson2d(5)
+# ---------------------------------------------------------------------------
+# Section VII batches in the dense form: the classes are every x^ node, then
+# every z node, which is the natural order of each augmented system, so the
+# reference is the oracle's serial schedule in natural order on the
+# block-diagonal augmented CSR.
+# ---------------------------------------------------------------------------
+def _lsq(shapes, seed, zero_frac=0.0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for N, K in shapes:
+        S = rng.choice([-1.0, 1.0], size=(N, K)) / np.sqrt(N)
+        if zero_frac > 0:
+            S[rng.random((N, K)) < zero_frac] = 0.0
+        out.append((S, float(rng.uniform(0.05, 0.5)), rng.standard_normal(N)))
+    return out
+
+
+def _block_diag(systems):
+    rows, cols, vals, off = [], [], [], [0]
+    for S, psi, y in systems:
+        rp, cl, vl, _ = oracle.augment_lsq(S, psi, y)
+        n = len(rp) - 1
+        rows.append(np.repeat(np.arange(n), np.diff(rp)) + off[-1])
+        cols.append(cl.astype(np.int64) + off[-1])
+        vals.append(vl)
+        off.append(off[-1] + n)
+    return W.csr_from_coo(off[-1], np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
+def _lsq_handle(G, systems, precision, schedule, damping=0.0):
     o = G.gabp_default_options()
-    o.schedule = 1
-    with pytest.raises(G.GabpError):
-        G.gabp_create_batched(np.array([0, m.n]), m.row_ptr, m.col, m.val, o)
-    d = W.detection_batch(1, 8, 8, 10.0, seed=1)[0]
-    with pytest.raises(G.GabpError):
-        G.gabp_create_lsq_batched([d.S], [d.sigma2], o)
+    o.precision = precision
+    o.damping = damping
+    o.schedule = schedule
+    o.stream = G.current_stream_handle()
+    return G.gabp_create_lsq_batched([s[0] for s in systems], [s[1] for s in systems], o)
+
+
+# one column chunk, 2, 4 and 8 chunks per lane, K not a multiple of 32, the
+# largest K and N, N = 1, N < 8 (idle warps)
+LSQ_SHAPES = [(10, 1), (1, 5), (62, 31), (66, 33), (128, 64), (200, 100), (1024, 256), (512, 256),
+              (70, 130), (3, 97), (300, 200)]
+
+
+@pytest.mark.parametrize("damping", [0.0, 0.4])
+def test_dense_serial_rounds_match_serial_oracle(G, damping):
+    systems = _lsq(LSQ_SHAPES, seed=3, zero_frac=0.1)
+    m = _block_diag(systems)
+    b = W.normal_rhs(m.n, 5)
+    h = _lsq_handle(G, systems, precision=0, schedule=1, damping=damping)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    for r in (0, 1, 2, 5, 9):
+        G.gabp_run_rounds(h, bt, r, xt)
+        ref = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, max_rounds=r, damping=damping)
+        assert _rel(xt.cpu().numpy(), ref["x"]) <= 1e-12, r
+    assert G.gabp_get_tuning(h)["dense_rows_mean"] == 0
+    G.gabp_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_dense_serial_solve_matches_closed_form_in_fewer_sweeps(G, precision):
+    """Serial (gamma 0.1) against synchronous (gamma 0.3, the damping the
+    synchronous schedule needs on this 10 dB batch); BF16 mean storage at
+    0 dB, undamped, where refinement recovers its rounding."""
+    snr = 0.0 if precision == 2 else 10.0
+    systems = W.detection_batch(40, 16, 130, snr, seed=2)
+    trip = [(d.S, d.sigma2, d.y) for d in systems]
+    y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
+    sweeps = {}
+    for sched, gam in ((0, 0.0 if precision == 2 else 0.3), (1, 0.0 if precision == 2 else 0.1)):
+        h = _lsq_handle(G, trip, precision, sched, gam)
+        xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
+        G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 20000)
+        got = xh.cpu().numpy()
+        off = 0
+        for d in systems:
+            A, bb = d.dense_system()
+            assert _rel(got[off:off + d.K], np.linalg.solve(A, bb)) < 1e-8
+            off += d.K
+        sweeps[sched] = G.gabp_get_stats(h)["sweeps_total"]
+        G.gabp_destroy(h)
+    assert sweeps[1] < sweeps[0], sweeps

@@ -120,10 +120,32 @@ def test_launch_shape_options_are_validated():
     from paper_0810_1119_gb300 import gabp as G
     m = W.poisson2d(4)
     for field, value in (("tile_slots", 16), ("tile_slots", 2048), ("tile_rows", 300),
-                         ("heavy_degree", -1), ("dense_rows", 3), ("cluster_ctas", 3), ("aitken", -1)):
+                         ("heavy_degree", -1), ("dense_rows", 3), ("cluster_ctas", 3), ("aitken", -1),
+                         ("schedule", 2), ("schedule", -1)):
         o = G.gabp_default_options()
         setattr(o, field, value)
         with pytest.raises(G.GabpError) as ei:
             G.gabp_create(m.row_ptr, m.col, m.val, None, o)
         assert ei.value.name == "GABP_ERR_INVALID_ARG"
         assert "launch shape" in str(ei.value)
+
+
+def test_colour_schedule_refusals_are_host_checks(lib):
+    """The colour schedule is refused for block-diagonal batches and for
+    Section VII batches outside the dense form, before any device work."""
+    from paper_0810_1119_gb300 import gabp as G
+    o = G.gabp_default_options()
+    o.schedule = 1
+    m = W.poisson2d(4)
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_batched([0, m.n], m.row_ptr, m.col, m.val, o)
+    assert ei.value.name == "GABP_ERR_INVALID_ARG"
+    S = np.ones((4, 2)) / 2.0
+    o.lsq_form = 1                                   # general CSR form
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_lsq_batched([S], 0.1, o)
+    assert "dense form" in str(ei.value)
+    o.lsq_form = 0                                   # K = 300 is beyond the dense kernels
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_lsq_batched([S, np.ones((300, 300)) / 300.0], 0.1, o)
+    assert "dense form" in str(ei.value)
