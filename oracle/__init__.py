@@ -79,7 +79,7 @@ def _bind(lib):
     lib.oracle_gabp_serial.argtypes = [ctypes.c_int64, i64p, i32p, f64p, f64p, i64p,
                                        ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                        f64p, f64p, f64p, f64p, ctypes.POINTER(ctypes.c_int),
-                                       ctypes.c_double]
+                                       ctypes.c_double, ctypes.POINTER(ctypes.c_uint8)]
     lib.oracle_residual_inf.restype = ctypes.c_double
     lib.oracle_residual_inf.argtypes = [ctypes.c_int64, i64p, i32p, f64p, f64p, f64p, f64p]
     lib.oracle_num_threads.restype = ctypes.c_int
@@ -155,16 +155,20 @@ def gabp(row_ptr, col, val, b, *, variant=BROADCAST, stop=STOP_FIXED, max_rounds
 
 
 def gabp_serial(row_ptr, col, val, b, *, order=None, stop=STOP_FIXED, max_rounds=1, tol=0.0,
-                want_messages=False, damping=0.0, lib=None):
+                want_messages=False, damping=0.0, damp_from=None, lib=None):
     """GaBP under the serial schedule (Section III-C): every round visits the
     nodes in ``order`` (default: natural), each one computing its totals
-    from the latest messages and overwriting its outgoing messages.  Output
-    as ``gabp``."""
+    from the latest messages and overwriting its outgoing messages.
+    ``damp_from`` (boolean per node, default all) limits the damping blend to
+    the messages those nodes send.  Output as ``gabp``."""
     row_ptr, col, val = _csr_arrays(row_ptr, col, val)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = row_ptr.shape[0] - 1
     nnz = int(row_ptr[-1])
     order_a = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+    mask = None if damp_from is None else np.ascontiguousarray(damp_from, dtype=np.uint8)
+    if mask is not None and mask.shape != (row_ptr.shape[0] - 1,):
+        raise ValueError("damp_from needs one flag per node")
     x = np.empty(n)
     Pi = np.empty(n)
     P = np.empty(nnz) if want_messages else None
@@ -174,7 +178,7 @@ def gabp_serial(row_ptr, col, val, b, *, order=None, stop=STOP_FIXED, max_rounds
         n, _ptr(row_ptr, ctypes.c_int64), _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double),
         _ptr(b, ctypes.c_double), _ptr(order_a, ctypes.c_int64), stop, int(max_rounds), float(tol),
         _ptr(x, ctypes.c_double), _ptr(Pi, ctypes.c_double), _ptr(P, ctypes.c_double),
-        _ptr(mu, ctypes.c_double), ctypes.byref(rounds), float(damping))
+        _ptr(mu, ctypes.c_double), ctypes.byref(rounds), float(damping), _ptr(mask, ctypes.c_uint8))
     out = {"x": x, "Pi": Pi, "rounds": rounds.value, "status": STATUS[st]}
     if want_messages:
         out["P"], out["mu"] = P, mu

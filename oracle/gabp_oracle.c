@@ -288,11 +288,12 @@ done:
 static int serial_round(int64_t n, const int64_t *row_ptr, const int32_t *col,
                         const double *val, const double *b, const int64_t *diag_pos,
                         const int64_t *twin, const int64_t *order, double *P, double *M,
-                        double gamma) {
+                        double gamma, const unsigned char *damp_from) {
   int status = OR_OK;
   (void)col;
   for (int64_t k = 0; k < n; ++k) {
     const int64_t i = order ? order[k] : k;
+    const double g = (damp_from && !damp_from[i]) ? 0.0 : gamma;
     const double Pii = val[diag_pos[i]];
     const double muii = b[i] / Pii;
     double Psum = Pii, hsum = Pii * muii;
@@ -310,7 +311,7 @@ static int serial_round(int64_t n, const int64_t *row_ptr, const int32_t *col,
       if (denom == 0.0 || !isfinite(denom)) status = OR_BREAKDOWN;
       const double Pn = -Aij * Aij / denom;
       double Mn = (Pt * mut - Pji * muji) / Aij;
-      if (gamma > 0.0) Mn = (gamma * (P[e] * M[e]) + (1.0 - gamma) * (Pn * Mn)) / Pn;
+      if (g > 0.0) Mn = (g * (P[e] * M[e]) + (1.0 - g) * (Pn * Mn)) / Pn;
       P[e] = Pn;
       M[e] = Mn;
     }
@@ -321,12 +322,15 @@ static int serial_round(int64_t n, const int64_t *row_ptr, const int32_t *col,
 /*
  * GaBP under the serial schedule from zero messages; arguments and outputs
  * as oracle_gabp (broadcast form only), plus the visiting order (NULL = the
- * natural order).  A round is one pass over all nodes.
+ * natural order).  A round is one pass over all nodes.  damp_from (NULL =
+ * every node) restricts the damping blend to the messages sent by the nodes
+ * i with damp_from[i] != 0; the others send their undamped message.  The
+ * fixed point does not depend on it.
  */
 int oracle_gabp_serial(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                        const double *b, const int64_t *order, int stop, int max_rounds, double tol,
                        double *x, double *Pi, double *msgP, double *msgMu, int *rounds,
-                       double gamma) {
+                       double gamma, const unsigned char *damp_from) {
   const int64_t nnz = row_ptr[n];
   const size_t m = (size_t)(nnz > 0 ? nnz : 1);
   int64_t *diag_pos = malloc(sizeof(int64_t) * (size_t)n);
@@ -344,7 +348,7 @@ int oracle_gabp_serial(int64_t n, const int64_t *row_ptr, const int32_t *col, co
   for (int t = 1; t <= max_rounds; ++t) {
     memcpy(Pp, P, sizeof(double) * m);
     memcpy(Mp, M, sizeof(double) * m);
-    int s = serial_round(n, row_ptr, col, val, b, diag_pos, twin, order, P, M, gamma);
+    int s = serial_round(n, row_ptr, col, val, b, diag_pos, twin, order, P, M, gamma, damp_from);
     *rounds = t;
     if (s != OR_OK) { status = s; break; }
     infer(OR_BROADCAST, n, row_ptr, val, b, diag_pos, twin, P, M, x, Pi);
