@@ -644,6 +644,7 @@ def run_detect(args):
     o.damping = args.damping
     o.lsq_form = args.lsq_form
     o.schedule = args.schedule
+    o.damp_scope = args.damp_scope
     o.autotune = 1
     o.stream = gabp.current_stream_handle()
     t0 = time.perf_counter()
@@ -689,10 +690,10 @@ def run_detect(args):
     # dense form, per grid position (two directed edges), synchronous: mean sweep
     # c 8 + eta in 8 + eta out 8; full sweep S 4 + messages in 16 + out 16.
     # Serial: only the z -> x^ messages are read and written (mean c 8 + 4 + 4,
-    # full S 4 + 8 + 8); damping adds the x^ -> z ones (mean 8, full 16).
-    # Per node ~ 24 B.
+    # full S 4 + 8 + 8); damping on every message adds the x^ -> z ones (mean 8,
+    # full 16).  Per node ~ 24 B.
     if dense and serial:
-        damped = args.damping > 0
+        damped = args.damping > 0 and args.damp_scope == 0
         per_mean, per_full = (24, 36) if damped else (16, 20)
     else:
         per_mean, per_full = (24, 36) if dense else (16, 24)
@@ -715,7 +716,8 @@ def run_detect(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched detection: {nsys} systems, K~U{{16..256}}, N=2K, 10 dB, augmented form",
                        "augmented_rows": st["n"], "directed_edges": E, "systems": nsys,
-                       "damping": args.damping, "schedule": SCHEDULES[args.schedule]},
+                       "damping": args.damping, "schedule": SCHEDULES[args.schedule],
+                       "damp_scope": "z -> x^ messages only" if args.damp_scope else "every message"},
             "sweeps": {"full": st["sweeps_full"], "mean": st["sweeps_mean"], "outer": st["outer_steps"]},
             "time_to_solution_ms": t, "handle_build_s": build_s,
             "form": "dense bipartite grid" if dense else "CSR tiles",
@@ -743,6 +745,8 @@ def main():
                     help="poisson3d: separate sweep cap for the FP64 comparison (0 = --max-iter)")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="er1e6, poisson32, poisson3d, detect: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
+    ap.add_argument("--damp-scope", type=int, default=0, choices=[0, 1],
+                    help="detect with --schedule 1: 0 damp every message, 1 only those the last class sends")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")
     ap.add_argument("--workload", default="er1e6",
                     choices=["er1e6", "multi64", "detect", "poisson32", "poisson3d"],

@@ -113,7 +113,10 @@ typedef struct {
                              gabp_create_lsq_batched: dense form only (lsq_form 0 and every
                              system within its limits); the classes are all x^ nodes, then all
                              z nodes, so a sweep still streams each grid once. */
-  int32_t reserved_i;
+  int32_t damp_scope;     /* which messages `damping` blends: 0 = every information message;
+                             1 = only those the last colour class sends (schedule = 1 only;
+                             in the dense Section VII form: the z -> x^ messages, so the
+                             x^ -> z ones are never stored).  The fixed point is the same. */
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */

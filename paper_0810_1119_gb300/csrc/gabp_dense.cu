@@ -157,6 +157,7 @@ struct FullRound {
   using V = T2<T>;
   static constexpr bool kF64 = sizeof(T) == 8;
   bool first, write_x = false, write_msgs = true, freeze = false;
+  bool damp_all;                  // damping blends the x^ -> z messages too
   double inv_rn;
   const double *__restrict__ b;
   double *__restrict__ x;
@@ -185,6 +186,7 @@ struct FullRound {
     b = ctl->b;
     x = ctl->x;
     gam = static_cast<T>(ctl->damping);
+    damp_all = d.damp_scope == 0;
     if constexpr (kF64) {
       sum_in = par ? d.sum64[1] : d.sum64[0];
       sum_out = par ? d.sum64[0] : d.sum64[1];
@@ -245,6 +247,7 @@ struct FullRound {
 // h~_i = rhs_i + sumEta_i and d_i = h~_i / P~_i with the frozen 1/P~_i.
 struct MeanRound {
   bool first;
+  bool damp_all;                  // damping blends the x^ -> z messages too
   double inv_rn;
   float gam;
   const float *__restrict__ sum_in;
@@ -258,6 +261,7 @@ struct MeanRound {
     first = ctl->first != 0;
     inv_rn = ctl->inv_rn;
     gam = static_cast<float>(ctl->damping);
+    damp_all = d.damp_scope == 0;
     sum_in = pe ? d.sumE[1] : d.sumE[0];
     sum_out = pe ? d.sumE[0] : d.sumE[1];
     mon_prev = pmon ? B.mon32[1] : B.mon32[0];
@@ -510,8 +514,8 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
 // One warp therefore takes a whole row j, lanes on columns lane + 32 q
 // (q < Q): it forms Mz'(j, .) in registers, sums the row across the warp,
 // and forms Mx'(j, .) -- the sweep still streams the grid once.  Mz is read
-// again only for damping (its previous information), so without damping it
-// is never stored.  Messages are updated in place: every grid position is
+// again only for damping (its previous information), so it is stored only
+// when damping blends it (damp_scope 0).  Messages are updated in place: every grid position is
 // read and written by the same lane within a sweep.
 // Planar layout, pair p = pair0 + j K + r:
 //   FP64:   Mx64[0][p] = (Px, eta_x), Mz64[0][p] = (Pz, eta_z);
@@ -550,7 +554,9 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
   constexpr bool kF64 = sizeof(T) == 8;
   constexpr int U = 8 / Q;   // rows in flight per warp step: U Q loads per lane and array
   const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const bool first = R.first, freeze = !kF64 && R.freeze, damp = R.gam > T(0);
+  // damp_x: blend the z -> x^ messages; damp_z: the x^ -> z ones as well
+  const bool first = R.first, freeze = !kF64 && R.freeze;
+  const bool damp_x = R.gam > T(0), damp_z = damp_x && R.damp_all;
   const T gam = R.gam;
   const T aii = static_cast<T>(-sy.psi);
   V xr[Q];
@@ -576,7 +582,7 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
           a[u][q] = __ldcs(Sg + p);
           if (!first) {
             m[u][q] = __ldcs(mx + p);
-            if (damp) ezo[u][q] = __ldcs(mz + p).y;
+            if (damp_z) ezo[u][q] = __ldcs(mz + p).y;
           }
         }
       }
@@ -602,7 +608,7 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
           } else {
             ez[q] = -av * (xr[q].y - m[u][q].y) * iz;
           }
-          if (damp) ez[q] = gam * ezo[u][q] + (T(1) - gam) * ez[q];
+          if (damp_z) ez[q] = gam * ezo[u][q] + (T(1) - gam) * ez[q];
         }
         sP += pz[q];
         sE += ez[q];
@@ -629,15 +635,15 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
           } else {
             ex = -av * (Thz - ez[q]) * ix;
           }
-          if (damp) ex = gam * m[u][q].y + (T(1) - gam) * ex;
+          if (damp_x) ex = gam * m[u][q].y + (T(1) - gam) * ex;
         }
         if (freeze) {
           C[p] = make_float2(static_cast<float>(cz[q]), static_cast<float>(cx));
           st1(hx + p, static_cast<float>(ex));
-          if (damp) st1(hz + p, static_cast<float>(ez[q]));
+          if (damp_z) st1(hz + p, static_cast<float>(ez[q]));
         } else {
           __stcs(mx + p, mk2<T>(px, ex));
-          if (damp) __stcs(mz + p, mk2<T>(pz[q], ez[q]));
+          if (damp_z) __stcs(mz + p, mk2<T>(pz[q], ez[q]));
         }
         cP[q].add(px);
         cE[q].add(ex);
@@ -710,7 +716,7 @@ __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float
                                                  MeanRound &R) {
   constexpr int U = 8 / Q;
   const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const bool first = R.first, damp = R.gam > 0.f;
+  const bool first = R.first, damp_x = R.gam > 0.f, damp_z = damp_x && R.damp_all;
   const float gam = R.gam;
   float hr[Q];
   ColSum<float> cE[Q];
@@ -734,7 +740,7 @@ __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float
           c[u][q] = __ldcs(C + p);
           if (!first) {
             ho[u][q] = ld1(hx + p);
-            if (damp) zo[u][q] = ld1(hz + p);
+            if (damp_z) zo[u][q] = ld1(hz + p);
           }
         }
       }
@@ -747,7 +753,7 @@ __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         ez[q] = c[u][q].x * (hr[q] - ho[u][q]);
-        if (damp) ez[q] = gam * zo[u][q] + (1.f - gam) * ez[q];
+        if (damp_z) ez[q] = gam * zo[u][q] + (1.f - gam) * ez[q];
         sE += ez[q];
       }
       sE = group_sum<32>(sE);
@@ -758,9 +764,9 @@ __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float
         if (r >= K) continue;
         const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
         float ex = c[u][q].y * (Thz - ez[q]);
-        if (damp) ex = gam * ho[u][q] + (1.f - gam) * ex;
+        if (damp_x) ex = gam * ho[u][q] + (1.f - gam) * ex;
         st1(hx + p, ex);
-        if (damp) st1(hz + p, ez[q]);
+        if (damp_z) st1(hz + p, ez[q]);
         cE[q].add(ex);
       }
       if (lane == 0) R.sum_out[sy.node0 + sy.K + j] = sE;

@@ -154,8 +154,9 @@ struct GraphView {
   const int32_t *sys_of_row;
   unsigned long long *sys_bmax;
   // colour schedule: this launch is one colour class's pass over its tiles,
-  // in place in a single message buffer; only a sweep's last pass controls
-  int32_t in_place, no_control;
+  // in place in a single message buffer; only a sweep's last pass controls;
+  // with damping limited to the last class the other passes do not blend
+  int32_t in_place, no_control, no_damp;
 };
 
 struct Graph {
@@ -179,6 +180,7 @@ struct Graph {
   // [col_rows[c], col_rows[c+1]) and tiles [col_tiles_*[c], col_tiles_*[c+1])
   int ncol = 0;
   std::vector<int32_t> col_rows, col_tiles_big, col_tiles_small;
+  bool damp_last = false;   // damping blends only what the last class sends
   int max_degree = 0;
   // batched handles (independent systems along the diagonal)
   int32_t nsys = 0;
@@ -189,7 +191,7 @@ struct Graph {
   GraphView view() const {
     return GraphView{rp,        rev,        col,          a64, diag64,     a32,     diag32,
                      tiles_big, tiles_small, lrow_big,    heavy_big, rord, ntiles_big,
-                     ntiles_small, n,        sys_of_row, sys_bmax, 0,   0};
+                     ntiles_small, n,        sys_of_row, sys_bmax, 0,   0, 0};
   }
   // The view of colour class c's pass (colour schedule): its tiles only.
   GraphView colour_view(int c) const {
@@ -203,6 +205,7 @@ struct Graph {
     v.ntiles_small = s1 - s0;
     v.in_place = 1;
     v.no_control = c + 1 < ncol;
+    v.no_damp = damp_last && c + 1 < ncol;
     return v;
   }
 };
@@ -264,6 +267,7 @@ struct DenseView {
   const DenseSys *sys;
   int32_t nsys;
   int64_t pairs;
+  int32_t damp_scope;           // 1: damping blends only the z -> x^ messages (serial)
   const float *S32;
   const double *S64;
   float4 *M32[2];

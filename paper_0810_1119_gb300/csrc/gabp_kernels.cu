@@ -317,7 +317,7 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     Seg<double>::copy(base + L::dg, g.diag64, tb.r0, nr, bar);
   };
 
-  const double gam = ctl->damping;
+  const double gam = g.no_damp ? 0.0 : ctl->damping;
   auto emit = [&](double a, double2 m, int32_t dst, double TP, double Th) {
     const double d = TP - m.x;   // P_{i\j} = P~_i - P_ji
     brk |= zero_or_nonfinite(d);
@@ -467,7 +467,7 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     if (freeze) B.invP32[i] = 1.0f / TP;
     if (first) B.rhs32[i] = rhs;
   };
-  const float gam = static_cast<float>(ctl->damping);
+  const float gam = g.no_damp ? 0.f : static_cast<float>(ctl->damping);
   auto emit = [&](int32_t s, float a, float2 m, int32_t dst, float TP, float Th) {
     const float d = TP - m.x;   // P_{i\j} = P~_i - P_ji
     brk |= !(d != 0.0f) || !isfinite(d);
@@ -633,7 +633,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   auto rhs_at = [&](int32_t i) {
     return first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
   };
-  const float gam = static_cast<float>(ctl->damping);
+  const float gam = g.no_damp ? 0.f : static_cast<float>(ctl->damping);
   // eta_ij sent to slot dst: damped with its previous value when gamma > 0
   auto send = [&](int32_t dst, float v) {
     if (gam > 0.f) v = gam * (zin ? 0.f : ld_eta(ein + dst)) + (1.f - gam) * v;

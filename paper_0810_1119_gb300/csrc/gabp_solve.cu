@@ -1072,6 +1072,11 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
                      "0 = automatic)";
     return GABP_ERR_INVALID_ARG;
   }
+  if (o.damp_scope < 0 || o.damp_scope > 1 || (o.damp_scope == 1 && o.schedule != 1)) {
+    delete h;
+    g_create_error = "damp_scope must be 0, or 1 with schedule = 1";
+    return GABP_ERR_INVALID_ARG;
+  }
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   *out = h;
   return GABP_OK;
@@ -1109,6 +1114,7 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
       }
       h->g.ncol = static_cast<int>(cp.bounds.size()) - 1;
       h->g.col_rows = cp.bounds;
+      h->g.damp_last = h->opt.damp_scope == 1;
       gabp_status r = build_graph(h->g, n, nnz, cp.rp.data(), cp.col.data(), cp.val.data(), nullptr,
                                   h->opt, h->stream, &msg);
       if (r != GABP_OK) { h->last_error = msg; return r; }
@@ -1238,6 +1244,7 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
     s = guarded(h, [&] {
       build_dense(h, nsys, K_host, N_host, S_host, psi_host, sys_off);
       h->dense->serial = h->opt.schedule == 1;
+      h->dense->v.damp_scope = h->opt.damp_scope;
       if (h->opt.dense_rows > 0) h->dense->rows_mean = h->dense->rows_full = h->opt.dense_rows;
       fill_tuning(h);
       if (h->opt.autotune) autotune(h);

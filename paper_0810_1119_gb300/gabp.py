@@ -50,7 +50,7 @@ class GabpOptions(ctypes.Structure):
                 ("heavy_degree", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
                 ("small_form", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
                 ("aitken", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("reserved_i", ctypes.c_int32)]
+                ("damp_scope", ctypes.c_int32)]
 
 
 class GabpStats(ctypes.Structure):
@@ -333,9 +333,10 @@ class Solver:
                  residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=0.0,
                  profile=False, damping=0.0, stream: int | None = None, autotune=False,
                  tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0,
-                 aitken=0, schedule=0):
+                 aitken=0, schedule=0, damp_scope=0):
         o = gabp_default_options()
         o.schedule = schedule
+        o.damp_scope = damp_scope
         o.aitken = aitken
         o.small_form = small_form
         o.cluster_ctas = cluster_ctas

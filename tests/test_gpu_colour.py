@@ -86,6 +86,28 @@ def test_colour_rounds_match_serial_oracle(G, name, damping):
     s.close()
 
 
+@pytest.mark.parametrize("name", ["poisson2d_33", "er_4000", "star_1500_long_row"])
+def test_colour_rounds_with_damping_on_the_last_class(G, name):
+    """damp_scope = 1: only the messages the last colour class sends are
+    blended -- the oracle's serial schedule with that class as its mask."""
+    m = CASES[name]()
+    b = W.normal_rhs(m.n, 6)
+    c = oracle.greedy_colouring(m.row_ptr, m.col)
+    order = np.argsort(c, kind="stable")
+    s = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=0, schedule=1, damping=0.4,
+                          damp_scope=1)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    for r in (1, 2, 6):
+        G.gabp_run_rounds(s.handle, bt, r, xt)
+        ref = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, order=order, max_rounds=r,
+                                 want_messages=True, damping=0.4, damp_from=c == c.max())
+        P, mu = G.gabp_get_messages(s.handle, m.nnz)
+        assert _rel(xt.cpu().numpy(), ref["x"]) <= 1e-12, r
+        assert _rel(P, ref["P"]) <= 1e-12 and _rel(mu, ref["mu"]) <= 1e-12, r
+    s.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 @pytest.mark.parametrize("name,make", [("poisson2d_48", lambda: W.poisson2d(48)),
                                        ("poisson3d_16", lambda: W.poisson3d(16)),
@@ -139,11 +161,12 @@ def _block_diag(systems):
     return W.csr_from_coo(off[-1], np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
 
 
-def _lsq_handle(G, systems, precision, schedule, damping=0.0):
+def _lsq_handle(G, systems, precision, schedule, damping=0.0, damp_scope=0):
     o = G.gabp_default_options()
     o.precision = precision
     o.damping = damping
     o.schedule = schedule
+    o.damp_scope = damp_scope
     o.stream = G.current_stream_handle()
     return G.gabp_create_lsq_batched([s[0] for s in systems], [s[1] for s in systems], o)
 
@@ -154,17 +177,21 @@ LSQ_SHAPES = [(10, 1), (1, 5), (62, 31), (66, 33), (128, 64), (200, 100), (1024,
               (70, 130), (3, 97), (300, 200)]
 
 
-@pytest.mark.parametrize("damping", [0.0, 0.4])
-def test_dense_serial_rounds_match_serial_oracle(G, damping):
+@pytest.mark.parametrize("damping,scope", [(0.0, 0), (0.4, 0), (0.4, 1)])
+def test_dense_serial_rounds_match_serial_oracle(G, damping, scope):
+    """scope 1 blends only what the z nodes send: the oracle's mask is the z
+    rows of every augmented system."""
     systems = _lsq(LSQ_SHAPES, seed=3, zero_frac=0.1)
     m = _block_diag(systems)
+    z = np.concatenate([np.arange(S.shape[1] + S.shape[0]) >= S.shape[1] for S, _, _ in systems])
     b = W.normal_rhs(m.n, 5)
-    h = _lsq_handle(G, systems, precision=0, schedule=1, damping=damping)
+    h = _lsq_handle(G, systems, precision=0, schedule=1, damping=damping, damp_scope=scope)
     bt = torch.tensor(b, device="cuda")
     xt = torch.empty_like(bt)
     for r in (0, 1, 2, 5, 9):
         G.gabp_run_rounds(h, bt, r, xt)
-        ref = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, max_rounds=r, damping=damping)
+        ref = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, max_rounds=r, damping=damping,
+                                 damp_from=z if scope else None)
         assert _rel(xt.cpu().numpy(), ref["x"]) <= 1e-12, r
     assert G.gabp_get_tuning(h)["dense_rows_mean"] == 0
     G.gabp_destroy(h)
@@ -172,16 +199,19 @@ def test_dense_serial_rounds_match_serial_oracle(G, damping):
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_dense_serial_solve_matches_closed_form_in_fewer_sweeps(G, precision):
-    """Serial (gamma 0.1) against synchronous (gamma 0.3, the damping the
-    synchronous schedule needs on this 10 dB batch); BF16 mean storage at
-    0 dB, undamped, where refinement recovers its rounding."""
+    """Serial (gamma 0.1 on every message, or 0.2 on the z -> x^ messages
+    only) against synchronous (gamma 0.3, the damping the synchronous
+    schedule needs on this 10 dB batch); BF16 mean storage at 0 dB,
+    undamped, where refinement recovers its rounding."""
     snr = 0.0 if precision == 2 else 10.0
     systems = W.detection_batch(40, 16, 130, snr, seed=2)
     trip = [(d.S, d.sigma2, d.y) for d in systems]
     y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
     sweeps = {}
-    for sched, gam in ((0, 0.0 if precision == 2 else 0.3), (1, 0.0 if precision == 2 else 0.1)):
-        h = _lsq_handle(G, trip, precision, sched, gam)
+    runs = ((0, 0.0 if precision == 2 else 0.3, 0), (1, 0.0 if precision == 2 else 0.1, 0),
+            (1, 0.0 if precision == 2 else 0.2, 1))
+    for k, (sched, gam, scope) in enumerate(runs):
+        h = _lsq_handle(G, trip, precision, sched, gam, scope)
         xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
         G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 20000)
         got = xh.cpu().numpy()
@@ -190,6 +220,6 @@ def test_dense_serial_solve_matches_closed_form_in_fewer_sweeps(G, precision):
             A, bb = d.dense_system()
             assert _rel(got[off:off + d.K], np.linalg.solve(A, bb)) < 1e-8
             off += d.K
-        sweeps[sched] = G.gabp_get_stats(h)["sweeps_total"]
+        sweeps[k] = G.gabp_get_stats(h)["sweeps_total"]
         G.gabp_destroy(h)
-    assert sweeps[1] < sweeps[0], sweeps
+    assert sweeps[1] < sweeps[0] and sweeps[2] < sweeps[0], sweeps

@@ -149,3 +149,14 @@ def test_colour_schedule_refusals_are_host_checks(lib):
     with pytest.raises(G.GabpError) as ei:
         G.gabp_create_lsq_batched([S, np.ones((300, 300)) / 300.0], 0.1, o)
     assert "dense form" in str(ei.value)
+
+
+def test_damp_scope_is_validated(lib):
+    from paper_0810_1119_gb300 import gabp as G
+    m = W.poisson2d(4)
+    for schedule, scope in ((0, 1), (1, 2), (1, -1)):
+        o = G.gabp_default_options()
+        o.schedule, o.damp_scope = schedule, scope
+        with pytest.raises(G.GabpError) as ei:
+            G.gabp_create(m.row_ptr, m.col, m.val, None, o)
+        assert "damp_scope" in str(ei.value)
