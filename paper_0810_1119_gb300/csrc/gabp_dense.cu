@@ -559,15 +559,9 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
   const bool damp_x = R.gam > T(0), damp_z = damp_x && R.damp_all;
   const T gam = R.gam;
   const T aii = static_cast<T>(-sy.psi);
-  V xr[Q];
   ColSum<T> cP[Q], cE[Q];
-#pragma unroll
-  for (int q = 0; q < Q; ++q) {
-    const int r = lane + 32 * q;
-    xr[q] = r < K ? tx[r] : mk2<T>(T(1), T(0));
-  }
   for (int j0 = w * U; j0 < N; j0 += kDenseWarps * U) {
-    T a[U][Q], ezo[U][Q];
+    T a[U][Q];
     V m[U][Q];
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -575,15 +569,11 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
       for (int q = 0; q < Q; ++q) {
         const int j = j0 + u, r = lane + 32 * q;
         a[u][q] = T(0);
-        ezo[u][q] = T(0);
         m[u][q] = mk2<T>(T(0), T(0));
         if (j < N && r < K) {
           const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
           a[u][q] = __ldcs(Sg + p);
-          if (!first) {
-            m[u][q] = __ldcs(mx + p);
-            if (damp_z) ezo[u][q] = __ldcs(mz + p).y;
-          }
+          if (!first) m[u][q] = __ldcs(mx + p);
         }
       }
 #pragma unroll
@@ -591,24 +581,31 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
       const int j = j0 + u;
       if (j >= N) break;   // the same for every lane of the warp
       // x^_r -> z_j for the columns of this lane, and the totals of z_j
-      T pz[Q], ez[Q], cz[Q];
+      // (freeze: c_z goes to C.x at once, c_x follows into C.y)
+      T pz[Q], ez[Q];
       T sP = T(0), sE = T(0);
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        pz[q] = ez[q] = cz[q] = T(0);
+        pz[q] = ez[q] = T(0);
+        const int r = lane + 32 * q;
         const T av = a[u][q];
+        const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
         if (av != T(0)) {
-          const T dz = xr[q].x - m[u][q].x;   // P~_r - P_{z_j -> x_r}
+          const V xr = tx[r];
+          const T dz = xr.x - m[u][q].x;   // P~_r - P_{z_j -> x_r}
           brk |= bad(dz);
           const T iz = rcp(dz);
           pz[q] = -(av * av) * iz;
           if (freeze) {
-            cz[q] = -av * iz;
-            ez[q] = cz[q] * (xr[q].y - m[u][q].y);
+            const T cz = -av * iz;
+            reinterpret_cast<float *>(C)[2 * p] = static_cast<float>(cz);
+            ez[q] = cz * (xr.y - m[u][q].y);
           } else {
-            ez[q] = -av * (xr[q].y - m[u][q].y) * iz;
+            ez[q] = -av * (xr.y - m[u][q].y) * iz;
           }
-          if (damp_z) ez[q] = gam * ezo[u][q] + (T(1) - gam) * ez[q];
+          if (damp_z) ez[q] = gam * (first ? T(0) : __ldcs(mz + p).y) + (T(1) - gam) * ez[q];
+        } else if (freeze && r < K) {
+          reinterpret_cast<float *>(C)[2 * p] = 0.f;
         }
         sP += pz[q];
         sE += ez[q];
@@ -638,7 +635,7 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
           if (damp_x) ex = gam * m[u][q].y + (T(1) - gam) * ex;
         }
         if (freeze) {
-          C[p] = make_float2(static_cast<float>(cz[q]), static_cast<float>(cx));
+          reinterpret_cast<float *>(C)[2 * p + 1] = static_cast<float>(cx);
           st1(hx + p, static_cast<float>(ex));
           if (damp_z) st1(hz + p, static_cast<float>(ez[q]));
         } else {
@@ -661,8 +658,9 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
   }
 }
 
+// FP32: three CTAs of 256 threads per SM (at most 85 registers a thread).
 template <class T, class E>
-__global__ void __launch_bounds__(kDenseBlock)
+__global__ void __launch_bounds__(kDenseBlock, sizeof(T) == 4 ? 3 : 1)
 dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   using V = T2<T>;
   using E1 = typename Half<E>::t;
@@ -815,18 +813,66 @@ dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
 // FP64 residual of the augmented systems, r = b - R~ x:
 //     x^ rows:  r_r = b_r - (x_r + sum_j S_jr z_j),
 //     z rows:   r_j = b_j - (sum_r S_jr x_r - psi z_j),
-// with max |r| and, per system, max |r| / ||b_s||_inf.
+// with max |r| and, per system, max |r| / ||b_s||_inf.  One warp per grid
+// row (lanes on columns lane + 32 q, as in the serial sweeps): the row sum
+// has a single writer, and each warp's column sums go to its own slice of
+// `part`, added in warp order -- no atomics, the same result every run.
 // ---------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ void residual_rows(const DenseSys &sy, const double *__restrict__ S64,
+                                              const double *vx, const double *vz, double *az,
+                                              double *part) {
+  constexpr int U = 8 / Q;
+  const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double xr[Q], col[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    xr[q] = r < K ? vx[r] : 0.0;
+    col[q] = 0.0;
+  }
+  for (int j0 = w * U; j0 < N; j0 += kDenseWarps * U) {
+    double a[U][Q];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = j0 + u, r = lane + 32 * q;
+        a[u][q] = (j < N && r < K) ? __ldcs(S64 + sy.pair0 + static_cast<int64_t>(j) * K + r) : 0.0;
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u;
+      if (j >= N) break;   // the same for every lane of the warp
+      const double zj = vz[j];
+      double row = 0.0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        row += a[u][q] * xr[q];
+        col[q] += a[u][q] * zj;
+      }
+      row = group_sum<32>(row);
+      if (lane == 0) az[j] = row;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    if (r < K) part[w * kDenseMaxK + r] = col[q];
+  }
+}
+
 __global__ void __launch_bounds__(kDenseBlock)
 dense_residual_kernel(DenseView d, double *__restrict__ r_out, Ctl *ctl, DevScalars *red,
                       int kind) {
-  __shared__ double vx[kDenseMaxK], vz[kDenseMaxN];
-  __shared__ double ax[kDenseMaxK], az[kDenseMaxN];
+  __shared__ double vx[kDenseMaxK], vz[kDenseMaxN];   // x^ and z of the system
+  __shared__ double az[kDenseMaxN];                   // sum_r S_jr x_r per row
+  __shared__ double part[kDenseWarps * kDenseMaxK];   // per warp: sum_j S_jr z_j
   __shared__ int32_t cur;
   const double *__restrict__ b = ctl->b;
   const double *__restrict__ x = ctl->x;
   unsigned long long mr = 0, mrel = 0;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
   for (;;) {
     const int32_t s = claim(ctl, &cur);
     if (s >= d.nsys) break;
@@ -834,32 +880,26 @@ dense_residual_kernel(DenseView d, double *__restrict__ r_out, Ctl *ctl, DevScal
     const int K = sy.K, N = sy.N;
     for (int k = tid; k < K + N; k += kDenseBlock) {
       const double v = x[sy.node0 + k];
-      if (k < K) { vx[k] = v; ax[k] = 0.0; }
-      else { vz[k - K] = v; az[k - K] = 0.0; }
+      if (k < K) vx[k] = v;
+      else vz[k - K] = v;
     }
+    for (int k = tid; k < kDenseWarps * K; k += kDenseBlock)
+      part[(k / K) * kDenseMaxK + k % K] = 0.0;   // warps without rows leave theirs at zero
     __syncthreads();
-    const Split w = split_of(K);
-    if (w.warp_on) {
-      const double xr = w.lane_on ? vx[w.r] : 0.0;
-      double col = 0.0;
-      const int64_t base = sy.pair0 + w.r;
-      for (int j = w.g; j < N; j += w.rg) {
-        double row = 0.0;
-        if (w.lane_on) {
-          const double a = __ldcs(d.S64 + base + static_cast<int64_t>(j) * K);
-          row = a * xr;
-          col += a * vz[j];
-        }
-        row = group_sum<32>(row);
-        if (lane == 0) atomicAdd(&az[j], row);
-      }
-      if (w.lane_on) atomicAdd(&ax[w.r], col);
-    }
+    by_columns(K, [&](auto q) { residual_rows<decltype(q)::value>(sy, d.S64, vx, vz, az, part); });
     __syncthreads();
     const double bs = dv(d.sys_bmax[sy.orig]);
     for (int k = tid; k < K + N; k += kDenseBlock) {
       const int64_t i = sy.node0 + k;
-      const double Ax = k < K ? vx[k] + ax[k] : az[k - K] - sy.psi * vz[k - K];
+      double Ax;
+      if (k < K) {
+        double c = 0.0;
+#pragma unroll
+        for (int w = 0; w < kDenseWarps; ++w) c += part[w * kDenseMaxK + k];
+        Ax = vx[k] + c;
+      } else {
+        Ax = az[k - K] - sy.psi * vz[k - K];
+      }
       const double ri = b[i] - Ax;
       if (r_out) r_out[i] = ri;
       mr = umax(mr, bits(fabs(ri)));

@@ -412,5 +412,95 @@ __device__ void last_block_control(Ctl *ctl, DevScalars *red, int kind) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory staging with cp.async.bulk on an mbarrier.  Every wait is
+// bounded: after kWaitLimit polls it gives up and returns false.
+// ---------------------------------------------------------------------------
+constexpr int kWaitLimit = 1 << 22;   // try_wait polls before giving up
+
+__host__ __device__ constexpr uint32_t r128(uint64_t b) {
+  return static_cast<uint32_t>((b + 127) & ~uint64_t{127});
+}
+// Bytes of a staged array of `count` elements of size `es` (plus slack for
+// the 16-byte rounding of the copy's start and end).
+__host__ __device__ constexpr uint32_t region(int count, int es) {
+  return r128(static_cast<uint64_t>(count + 32) * es);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uint32_t bytes,
+                                              uint32_t bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
+      "[%0], [%1], %2, [%3], %4;" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One staged array: elements [first, first + count) of `base`, copied from
+// the 16-byte boundary at or below `first` to the one at or above the end.
+template <class E>
+struct Seg {
+  static constexpr int64_t kPer = 16 / static_cast<int64_t>(sizeof(E));
+  __device__ static uint32_t bytes(int64_t first, int64_t count) {
+    const int64_t a0 = first - first % kPer;
+    const int64_t a1 = (first + count + kPer - 1) / kPer * kPer;
+    return static_cast<uint32_t>((a1 - a0) * static_cast<int64_t>(sizeof(E)));
+  }
+  __device__ static void copy(uint32_t dst, const E *base, int64_t first, int64_t count,
+                              uint32_t bar) {
+    const uint32_t b = bytes(first, count);
+    if (b) bulk_g2s(dst, base + (first - first % kPer), b, bar);
+  }
+  __device__ static void copy(uint32_t dst, const E *base, int64_t first, int64_t count,
+                              uint32_t bar, uint64_t policy) {
+    const uint32_t b = bytes(first, count);
+    if (b) bulk_g2s_hint(dst, base + (first - first % kPer), b, bar, policy);
+  }
+  // Shared-memory pointer to element `first` of a staged run.
+  __device__ static E *at(unsigned char *region_ptr, int64_t first) {
+    return reinterpret_cast<E *>(region_ptr) + first % kPer;
+  }
+};
+
 }  // namespace
 }  // namespace gabp

@@ -166,9 +166,12 @@ def test_oversized_system_takes_the_csr_path(G):
 def test_bf16_refinement_that_stalls_stops_early(G):
     """BF16 mean messages on the 10 dB batch: the solve either reaches 1e-10
     or stops once eight refinement steps in a row fail to shrink the FP64
-    residual by 10 % -- long before the sweep budget."""
+    residual by 10 % -- long before the sweep budget.  Damped (gamma 0.3):
+    undamped, one system of this batch does not converge at all, and the
+    erratic residuals of its inner solves can beat the best by 10 % by
+    chance, which is not the stall this test is about."""
     systems = W.detection_batch(40, 16, 130, 10.0, seed=2)
-    h = _handle(G, [(d.S, d.sigma2, d.y) for d in systems], precision=2)
+    h = _handle(G, [(d.S, d.sigma2, d.y) for d in systems], precision=2, damping=0.3)
     y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
     xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
     try:
