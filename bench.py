@@ -391,7 +391,8 @@ def run_multi(args):
     B = torch.tensor(W.normal_rhs(n, 5, k=K), device="cuda")
     X = torch.empty_like(B)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32, autotune=True)
+    s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32, autotune=True,
+                             schedule=args.schedule)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         gabp.gabp_solve_multi(s.handle, B, X, TOL, 5000)
@@ -423,7 +424,7 @@ def run_multi(args):
             "traffic": None, "bytes_per_launch": bytes_meanK, "mean_launch_us": meanK_us,
             "timing": "CUDA events around every kernel in a profiled pass of the same solve (host driver)"}
     # FP64 comparison: the 64 columns solved one after another by FP64 sweeps
-    s64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64)
+    s64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64, schedule=args.schedule)
     torch.cuda.synchronize()
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -436,7 +437,7 @@ def run_multi(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "multi-RHS: ER n=2e6 avg-degree 10 SDD (dominance 1.05), 64 RHS b~N(0,1), 1e-10 rel. residual per column",
-                       "n": n, "directed_edges": E, "nrhs": K},
+                       "n": n, "directed_edges": E, "nrhs": K, "schedule": SCHEDULES[args.schedule]},
             "sweeps": {"precision": st["sweeps_full"], "mean_K_columns": st["sweeps_mean"],
                        "outer": st["outer_steps"]},
             "time_to_solution_ms": {"mixed_multi": t, "fp64_column_by_column": t64,
@@ -744,7 +745,7 @@ def main():
     ap.add_argument("--fp64-max-iter", type=int, default=0,
                     help="poisson3d: separate sweep cap for the FP64 comparison (0 = --max-iter)")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
-                    help="er1e6, poisson32, poisson3d, detect: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
+                    help="all workloads: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
     ap.add_argument("--damp-scope", type=int, default=0, choices=[0, 1],
                     help="detect with --schedule 1: 0 damp every message, 1 only those the last class sends")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")

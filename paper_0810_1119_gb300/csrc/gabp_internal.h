@@ -157,6 +157,7 @@ struct GraphView {
   // in place in a single message buffer; only a sweep's last pass controls;
   // with damping limited to the last class the other passes do not blend
   int32_t in_place, no_control, no_damp;
+  int32_t row0, row1;           // rows of the row-per-warp kernels: [row0, row1)
 };
 
 struct Graph {
@@ -191,7 +192,8 @@ struct Graph {
   GraphView view() const {
     return GraphView{rp,        rev,        col,          a64, diag64,     a32,     diag32,
                      tiles_big, tiles_small, lrow_big,    heavy_big, rord, ntiles_big,
-                     ntiles_small, n,        sys_of_row, sys_bmax, 0,   0, 0};
+                     ntiles_small, n,        sys_of_row, sys_bmax, 0,   0, 0,
+                     0,         n};
   }
   // The view of colour class c's pass (colour schedule): its tiles only.
   GraphView colour_view(int c) const {
@@ -206,6 +208,8 @@ struct Graph {
     v.in_place = 1;
     v.no_control = c + 1 < ncol;
     v.no_damp = damp_last && c + 1 < ncol;
+    v.row0 = col_rows[c];
+    v.row1 = col_rows[c + 1];
     return v;
   }
 };
@@ -222,11 +226,13 @@ int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScal
                    const GraphView *view = nullptr);
 int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, bool bf16,
                 const GraphView *view = nullptr);
-int launch_permute(int32_t n, cudaStream_t st, const int32_t *perm, const double *src, double *dst,
-                   bool scatter);
+// Rows of `width` doubles: dst[i] = src[perm[i]] (gather) or dst[perm[i]] = src[i] (scatter).
+int launch_permute(int32_t n, int32_t width, cudaStream_t st, const int32_t *perm, const double *src,
+                   double *dst, bool scatter);
 int launch_refine(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
 int launch_init_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
-int launch_mean_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
+int launch_mean_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K,
+                      const GraphView *view = nullptr);
 int launch_refine_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K);
 void prepare_kernels(int group, bool bf16);
 void tile_sizes(int *big_slots, int *big_rows, int *small_slots, int *small_rows);
@@ -397,6 +403,8 @@ struct gabp_s {
   // colour schedule (Section III-C serial schedule by colour classes)
   int32_t *perm = nullptr;             // device: caller's row of renumbered row i
   double *bperm = nullptr, *xperm = nullptr;   // device: b and x in the renumbered order
+  double *bKperm = nullptr, *xKperm = nullptr; // device: n x K right-hand sides and solutions, renumbered
+  size_t capKperm = 0;
   cudaStream_t cap_stream = nullptr;   // private stream used to record graphs
 
   // profiling (gabp_options.profile): pairs of events around kernels

@@ -850,9 +850,12 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   const int pe = ctl->par_e;
   const bool first = ctl->first != 0;
+  // messages known to be zero (skip reading them): the first sweep of a
+  // synchronous inner solve; an in-place colour pass reads its zeroed buffer
+  const bool zin = first && !g.in_place;
   const float *__restrict__ ein = pe ? B.eK[1] : B.eK[0];
   float *__restrict__ eout = pe ? B.eK[0] : B.eK[1];
-  const float gam = static_cast<float>(ctl->damping);
+  const float gam = g.no_damp ? 0.f : static_cast<float>(ctl->damping);
   double irn[NC];
 #pragma unroll
   for (int j = 0; j < NC; ++j) {
@@ -860,7 +863,7 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
     irn[j] = (first && c < K) ? ctl->cols.inv_rn[c] : 0.0;
   }
   uint32_t mdd = 0, md = 0;
-  for (int64_t i = warp; i < g.n; i += nwarps) {
+  for (int64_t i = g.row0 + warp; i < g.row1; i += nwarps) {
     const int32_t rs = g.rp[i], re = g.rp[i + 1];
     float th[NC];
 #pragma unroll
@@ -876,7 +879,7 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
         th[j] = B.rhsK[idx];
       }
     }
-    if (!first) {
+    if (!zin) {
       // four slots' messages in flight per lane before they are added
       int32_t s = rs;
       for (; s + 4 <= re; s += 4) {
@@ -924,7 +927,7 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
           const int c = lane + 32 * j;
-          v[u][j] = (first || c >= K) ? 0.f : ein[static_cast<int64_t>(s + u) * K + c];
+          v[u][j] = (zin || c >= K) ? 0.f : ein[static_cast<int64_t>(s + u) * K + c];
         }
       }
 #pragma unroll
@@ -934,7 +937,7 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
           const int c = lane + 32 * j;
           if (c >= K) continue;
           float out = cs[u] * (th[j] - v[u][j]);
-          if (gam > 0.f) out = gam * (first ? 0.f : ein[dst[u] + c]) + (1.f - gam) * out;
+          if (gam > 0.f) out = gam * (zin ? 0.f : ein[dst[u] + c]) + (1.f - gam) * out;
           eout[dst[u] + c] = out;
         }
     }
@@ -945,15 +948,15 @@ mean_multi_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red, int K) {
       for (int j = 0; j < NC; ++j) {
         const int c = lane + 32 * j;
         if (c >= K) continue;
-        const float e = first ? 0.f : ein[static_cast<int64_t>(s) * K + c];
+        const float e = zin ? 0.f : ein[static_cast<int64_t>(s) * K + c];
         float out = cs * (th[j] - e);
-        if (gam > 0.f) out = gam * (first ? 0.f : ein[dst + c]) + (1.f - gam) * out;
+        if (gam > 0.f) out = gam * (zin ? 0.f : ein[dst + c]) + (1.f - gam) * out;
         eout[dst + c] = out;
       }
     }
   }
   block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
-  last_block_control(ctl, red, CK_MEANK);
+  last_block_control(ctl, red, g.no_control ? 0 : CK_MEANK);
 }
 
 // X += ||r_k|| D (FP64).
@@ -1174,23 +1177,25 @@ int launch_mean(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars
 }
 
 // Colour schedule: b into the renumbered order, x back to the caller's.
-__global__ void permute_gather_kernel(int32_t n, const int32_t *__restrict__ perm,
+// Element t of an n x width array: row t / width, column t % width.
+__global__ void permute_gather_kernel(int64_t total, int32_t width, const int32_t *__restrict__ perm,
                                       const double *__restrict__ src, double *__restrict__ dst) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    dst[i] = src[perm[i]];
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[t] = src[static_cast<int64_t>(perm[t / width]) * width + t % width];
 }
-__global__ void permute_scatter_kernel(int32_t n, const int32_t *__restrict__ perm,
+__global__ void permute_scatter_kernel(int64_t total, int32_t width, const int32_t *__restrict__ perm,
                                        const double *__restrict__ src, double *__restrict__ dst) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    dst[perm[i]] = src[i];
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[static_cast<int64_t>(perm[t / width]) * width + t % width] = src[t];
 }
 
-int launch_permute(int32_t n, cudaStream_t st, const int32_t *perm, const double *src, double *dst,
-                   bool scatter) {
-  if (scatter) permute_scatter_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, perm, src, dst);
-  else permute_gather_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, perm, src, dst);
+int launch_permute(int32_t n, int32_t width, cudaStream_t st, const int32_t *perm, const double *src,
+                   double *dst, bool scatter) {
+  const int64_t total = static_cast<int64_t>(n) * width;
+  if (scatter) permute_scatter_kernel<<<flat_grid(total), kBlock, 0, st>>>(total, width, perm, src, dst);
+  else permute_gather_kernel<<<flat_grid(total), kBlock, 0, st>>>(total, width, perm, src, dst);
   return 1;
 }
 
@@ -1236,10 +1241,13 @@ int launch_init_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevS
   return 1;
 }
 
-int launch_mean_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K) {
-  const int grid = static_cast<int>(std::min<int64_t>((static_cast<int64_t>(g.n) * 32 + kBlock - 1) / kBlock,
+int launch_mean_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red, int K,
+                      const GraphView *view) {
+  const GraphView v = view ? *view : g.view();
+  const int64_t rows = v.row1 - v.row0;
+  const int grid = static_cast<int>(std::min<int64_t>((rows * 32 + kBlock - 1) / kBlock,
                                                       static_cast<int64_t>(num_sms()) * 8));
-  GABP_NC_DISPATCH(K, (mean_multi_kernel<NC><<<std::max(grid, 1), kBlock, 0, st>>>(g.view(), B, ctl, red, K)));
+  GABP_NC_DISPATCH(K, (mean_multi_kernel<NC><<<std::max(grid, 1), kBlock, 0, st>>>(v, B, ctl, red, K)));
   return 1;
 }
 

@@ -87,6 +87,7 @@ bool is_bf16(gabp_handle h) { return h->opt.precision == GABP_PREC_MIXED_BF16; }
 
 void free_resident(Resident &r);
 void zero_messages(gabp_handle h, cudaStream_t st, bool full);
+void zero_multi_messages(gabp_handle h, cudaStream_t st);
 gabp_status resident_solve(gabp_handle h, const double *b, double *x, double tol, int32_t max_iter,
                            int32_t *iters, bool *ran);
 
@@ -220,18 +221,21 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     }
     return 0;
   }
-  if (g.ncol > 0 && (phase == PH_FULL64 || phase == PH_FULL32 || phase == PH_MEAN)) {
+  if (g.ncol > 0 &&
+      (phase == PH_FULL64 || phase == PH_FULL32 || phase == PH_MEAN || phase == PH_MEANK)) {
     // colour schedule: one in-place pass per class (both parities alias one buffer)
     Buffers B = h->buf;
     B.m64[1] = B.m64[0];
     B.m32[1] = B.m32[0];
     B.e[1] = B.e[0];
+    B.eK[1] = B.eK[0];
     int k = 0;
     for (int c = 0; c < g.ncol; ++c) {
       const GraphView v = g.colour_view(c);
       if (phase == PH_FULL64) k += launch_sweep64(g, st, B, h->ctl, h->red, &v);
       else if (phase == PH_FULL32) k += launch_sweep32(g, st, B, h->ctl, h->red, is_bf16(h), &v);
-      else k += launch_mean(g, st, B, h->ctl, h->red, is_bf16(h), &v);
+      else if (phase == PH_MEAN) k += launch_mean(g, st, B, h->ctl, h->red, is_bf16(h), &v);
+      else k += launch_mean_multi(g, st, B, h->ctl, h->red, h->graph_K, &v);
     }
     return k;
   }
@@ -248,7 +252,11 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
       return k;
     }
     case PH_MEANK: return launch_mean_multi(g, st, h->buf, h->ctl, h->red, h->graph_K);
-    case PH_REFINEK: return launch_refine_multi(g, st, h->buf, h->ctl, h->red, h->graph_K);
+    case PH_REFINEK: {
+      const int k = launch_refine_multi(g, st, h->buf, h->ctl, h->red, h->graph_K);
+      if (g.ncol > 0) zero_multi_messages(h, st);   // the next inner solves start from zero
+      return k;
+    }
   }
   return 0;
 }
@@ -263,8 +271,16 @@ void zero_messages(gabp_handle h, cudaStream_t st, bool full) {
   if (B.e[0]) CK(cudaMemsetAsync(B.e[0], 0, (is_bf16(h) ? 2 : 4) * E, st));
 }
 
+// The K-column mean messages of the multi right-hand-side solve (colour schedule).
+void zero_multi_messages(gabp_handle h, cudaStream_t st) {
+  CK(cudaMemsetAsync(h->buf.eK[0], 0, sizeof(float) * h->g.E * h->graph_K, st));
+}
+
 int launch_mode_init(gabp_handle h, cudaStream_t st, int mode) {
-  if (mode == CTL_MULTI) return launch_init_multi(h->g, st, h->buf, h->ctl, h->red, h->graph_K);
+  if (mode == CTL_MULTI) {
+    if (h->g.ncol > 0) zero_multi_messages(h, st);
+    return launch_init_multi(h->g, st, h->buf, h->ctl, h->red, h->graph_K);
+  }
   if (h->g.ncol > 0) zero_messages(h, st, true);
   return launch_init(h->g, st, h->buf, h->ctl, h->red);
 }
@@ -472,7 +488,7 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
   h->stats = gabp_stats{};
   double *x_out = x;
   if (h->g.ncol > 0) {   // colour schedule: solve in the renumbered order
-    launch_permute(h->g.n, h->stream, h->perm, b, h->bperm, false);
+    launch_permute(h->g.n, 1, h->stream, h->perm, b, h->bperm, false);
     b = h->bperm;
     x = h->xperm;
   }
@@ -483,7 +499,7 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
   }
   run_mode(h, mode, max_iter);
   if (h->g.ncol > 0) {
-    launch_permute(h->g.n, h->stream, h->perm, h->xperm, x_out, true);
+    launch_permute(h->g.n, 1, h->stream, h->perm, h->xperm, x_out, true);
     CK(cudaStreamSynchronize(h->stream));
   }
   finish_stats(h);
@@ -526,6 +542,22 @@ gabp_status solve_multi_mixed(gabp_handle h, const double *B, double *X, int32_t
     if (iters) *iters = prec_sweeps;
     return s;
   }
+  double *X_user = X;
+  if (h->g.ncol > 0) {   // colour schedule: the columns in the renumbered row order
+    const size_t nk = static_cast<size_t>(h->g.n) * K;
+    if (h->capKperm < nk) {
+      cudaFree(h->bKperm);
+      cudaFree(h->xKperm);
+      h->bKperm = h->xKperm = nullptr;
+      h->capKperm = 0;
+      ensure(&h->bKperm, nk);
+      ensure(&h->xKperm, nk);
+      h->capKperm = nk;
+    }
+    launch_permute(h->g.n, K, h->stream, h->perm, B, h->bKperm, false);
+    B = h->bKperm;
+    X = h->xKperm;
+  }
   init_ctl(h, CTL_MULTI, nullptr, nullptr, tol, std::max(1, max_iter - prec_sweeps), false);
   Ctl &c = *h->ctl_host;
   c.K = K;
@@ -534,6 +566,7 @@ gabp_status solve_multi_mixed(gabp_handle h, const double *B, double *X, int32_t
   c.cols = h->cols;
   c.frozen = 1;
   run_mode(h, CTL_MULTI, max_iter);
+  if (h->g.ncol > 0) launch_permute(h->g.n, K, h->stream, h->perm, X, X_user, true);
   finish_stats(h);
   h->stats.sweeps_full = prec_sweeps;
   h->stats.sweeps_total = prec_sweeps + h->ctl_host->sweeps;
@@ -615,8 +648,10 @@ void release(gabp_handle h) {
   free_resident(h->res);
   for (double *&r : h->ring) { cudaFree(r); r = nullptr; }
   cudaFree(h->perm); cudaFree(h->bperm); cudaFree(h->xperm);
+  cudaFree(h->bKperm); cudaFree(h->xKperm);
   h->perm = nullptr;
-  h->bperm = h->xperm = nullptr;
+  h->bperm = h->xperm = h->bKperm = h->xKperm = nullptr;
+  h->capKperm = 0;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->ev.clear();
@@ -1364,7 +1399,7 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
   if (!B_dev || !X_dev || nrhs < 1 || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: invalid argument");
   // dense Section VII batches solve the columns one after another
-  const bool shared_precisions = h->opt.precision != GABP_PREC_FP64 && !h->dense && h->g.ncol == 0;
+  const bool shared_precisions = h->opt.precision != GABP_PREC_FP64 && !h->dense;
   if (shared_precisions && nrhs > 256)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: at most 256 right-hand sides per call");
   if (shared_precisions)
@@ -1420,7 +1455,7 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
     ensure64(h);
     double *x_user = x_dev;
     if (h->g.ncol > 0) {   // colour schedule: renumbered order, messages from zero
-      launch_permute(h->g.n, st, h->perm, b_dev, h->bperm, false);
+      launch_permute(h->g.n, 1, st, h->perm, b_dev, h->bperm, false);
       b_dev = h->bperm;
       x_dev = h->xperm;
       CK(cudaMemsetAsync(h->buf.m64[0], 0, sizeof(double2) * (h->g.E + kPad), st));
@@ -1449,7 +1484,7 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
       }
     }
     if (ait) launch_aitken(h->g.n, st, h->ctl, x_dev);
-    if (h->g.ncol > 0) launch_permute(h->g.n, st, h->perm, h->xperm, x_user, true);
+    if (h->g.ncol > 0) launch_permute(h->g.n, 1, st, h->perm, h->xperm, x_user, true);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     DevScalars red{};

@@ -132,6 +132,32 @@ def test_colour_solves_need_fewer_sweeps(G, precision, name, make):
         assert sweeps[1] < sweeps[0], sweeps
 
 
+@pytest.mark.parametrize("name,make", [("poisson2d_40", lambda: W.poisson2d(40)),
+                                       ("er_ragged_isolated", lambda: W.er_sdd(3001, 3, 1.05, 2))])
+def test_colour_multi_rhs_matches_synchronous(G, name, make):
+    """37 right-hand sides: precisions once (colour passes), then the
+    K-column mean sweeps one colour class at a time; every column meets
+    1e-10 and agrees with the synchronous multi-RHS solve."""
+    m = make()
+    K = 37
+    Bh = W.normal_rhs(m.n, 9, k=K)
+    Bt = torch.tensor(Bh, device="cuda")
+    out, stats = {}, {}
+    for sched in (0, 1):
+        s = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=1, schedule=sched)
+        X = torch.empty_like(Bt)
+        G.gabp_solve_multi(s.handle, Bt, X, 1e-10, 20000)
+        out[sched] = X.cpu().numpy()
+        stats[sched] = s.stats()
+        s.close()
+    for k in range(K):
+        x = out[1][:, k]
+        assert oracle.residual_inf(m.row_ptr, m.col, m.val, Bh[:, k], x) < 1e-10 * np.abs(Bh[:, k]).max()
+        assert _rel(x, out[0][:, k]) < 1e-8
+    if name.startswith("poisson"):
+        assert stats[1]["sweeps_mean"] < stats[0]["sweeps_mean"], stats
+
+
 # ---------------------------------------------------------------------------
 # Section VII batches in the dense form: the classes are every x^ node, then
 # every z node, which is the natural order of each augmented system, so the
