@@ -64,12 +64,15 @@ BYTES = {
 # + dram__bytes_write.sum per launch; ncu flushes caches between replays, so
 # these are cold-cache figures), valid only for the kernel sources they were
 # taken on: a changed source makes the figure null.  Commands and numbers:
-# profiles/mean_kernel_er1e6.md and profiles/dense_mean_kernel_detect1024.md.
+# profiles/mean_kernel_er1e6.md, profiles/dense_mean_kernel_detect1024.md and
+# profiles/dense_serial_detect1024.md.
 TRAFFIC = {
-    "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "684a2a6b9fa08f8d",
-             "bytes_per_launch": 174.49e6},
-    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "340efe891741605d",
-                   "bytes_per_pair": 23.097},
+    "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "f7f18d076fe46b79",
+             "bytes_per_launch": 174.59e6},
+    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "ef4785c46d22def4",
+                   "bytes_per_pair": 23.05},
+    "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "ef4785c46d22def4",
+                          "bytes_per_pair": 15.17},
 }
 
 
@@ -325,7 +328,7 @@ def run_gabp(args):
         per_edge, per_node = BYTES[dom]
         bytes_launch = per_edge * E + per_node * m.n
         achieved = bytes_launch * n_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None
-        kernel_names = {"mean": "mean32_kernel (FP32 mean-only sweep)",
+        kernel_names = {"mean": "mean_kernel<float> (FP32 mean-only sweep)",
                         "full32": "sweep32_kernel (FP32 full sweep)",
                         "residual": "residual64_kernel (FP64 residual)"}
         fp64_ms = statistics.mean(ms_fp64)
