@@ -313,6 +313,7 @@ void prepare_dense_kernels(bool bf16);
 constexpr int kResidentMaxCluster = 16;   // CTAs of the cluster (16 needs the non-portable size)
 constexpr int kResidentMaxSlots = 3072;   // incoming-message slots per CTA
 constexpr int kResidentMaxRows = 896;     // rows per CTA
+constexpr int kResidentMaxColours = 16;   // colour classes of the colour schedule
 
 struct ResidentOut {
   int32_t status, sweeps, checks, pad;
@@ -334,6 +335,10 @@ struct ResidentView {
   int32_t check_every, max_iter, rel;
   double tol, damping;
   ResidentOut *out;
+  // colour schedule (ncol > 0): rows [cb[c], cb[c+1]) form class c; one pass
+  // per class, in place; damp_last: only the last class's messages blend
+  int32_t ncol, damp_last;
+  int32_t cb[kResidentMaxColours + 1];
 };
 
 struct Resident {

@@ -15,6 +15,12 @@
 //
 // The arithmetic per message is that of the CSR FP64 sweep (same reciprocal,
 // same damping rule), so a solve stops after the same number of sweeps.
+//
+// Colour schedule (v.ncol > 0): the rows are renumbered by colour class and
+// a sweep is one pass per class, each followed by a cluster barrier.  A pass
+// reads and writes the single message buffer in place: nodes of a class are
+// not adjacent, so no slot is read and written by the same pass.  The
+// buffer starts from zero, and the means of a class are taken at its pass.
 #include "gabp_internal.h"
 #include "gabp_device.cuh"
 
@@ -100,10 +106,12 @@ __global__ void __launch_bounds__(kResBlock) resident64_kernel(ResidentView v) {
     mb = umax(mb, bits(fabs(bb[k])));
   }
   if (tid == 0) lrp[R] = S;
+  const bool colour = v.ncol > 0;
   for (int32_t s = tid; s < S; s += kResBlock) {
     a[s] = v.a64[s0 + s];
     dst[s] = v.dst[s0 + s];
     colp[s] = v.colp[s0 + s];
+    if (colour) m[0][s] = make_double2(0.0, 0.0);   // read before written by later classes
   }
   if (tid < 2) part[tid] = 0;
   __syncthreads();
@@ -141,55 +149,65 @@ __global__ void __launch_bounds__(kResBlock) resident64_kernel(ResidentView v) {
     if (!isfinite(rn) || rn > 1e30 * fmax(bnorm, DBL_MIN)) { status = GABP_ERR_DIVERGED; return true; }
     return false;
   };
+  const int passes = colour ? v.ncol : 1;
   for (int it = 0; it < v.max_iter; ++it) {
     const int cur = it & 1;
-    const bool first = it == 0;
+    // messages known to be zero: the first synchronous sweep (the colour
+    // schedule reads its zeroed buffer instead)
+    const bool zin = it == 0 && !colour;
     const bool write_x = ((it + 1) % v.check_every == 0) || it + 1 >= v.max_iter;   // a check
     const bool to_ring = ait > 0 && (write_x || (it + 1) % ait == 0);
     double *xw = xs[checks & 1];
     double *rw = ring[nw % 3];
     const double *rp1 = ring[(nw + 2) % 3], *rp2 = ring[(nw + 1) % 3];   // written 1 and 2 steps ago
-    const double2 *min = m[cur];
-    for (int k = tid; k < R; k += kResBlock) {
-      double sP = 0.0, sH = 0.0;
-      if (!first)
-        for (int32_t s = lrp[k]; s < lrp[k + 1]; ++s) {
-          sP += min[s].x;
-          sH += min[s].y;
-        }
-      const double TP = dg[k] + sP, Th = bb[k] + sH;
-      tp[k] = make_double2(TP, Th);
-      if (to_ring || write_x) {
-        const double xi = Th / TP;
-        if (to_ring) rw[k] = xi;
-        if (write_x) {
-          double y = xi;
-          if (ait > 0 && nw >= 2) {   // Delta^2 of the means of rounds t - 2s, t - s, t
-            const double c0 = rp2[k], c1 = rp1[k];
-            const double d1 = c1 - c0, den = (xi - c1) - d1;
-            const double scale = fmax(fmax(fabs(c0), fabs(c1)), fabs(xi));
-            if (fabs(den) > 64.0 * DBL_EPSILON * scale) y = c0 - d1 * d1 / den;
+    double2 *m_in = colour ? m[0] : m[cur];
+    double2 *m_out = colour ? m[0] : m[cur ^ 1];
+    for (int c = 0; c < passes; ++c) {
+      // this pass's rows: all of them, or those of colour class c
+      const int k0 = colour ? min(max(v.cb[c] - r0, 0), R) : 0;
+      const int k1 = colour ? min(max(v.cb[c + 1] - r0, 0), R) : R;
+      const double gam_c = (colour && v.damp_last && c + 1 < passes) ? 0.0 : gam;
+      for (int k = k0 + tid; k < k1; k += kResBlock) {
+        double sP = 0.0, sH = 0.0;
+        if (!zin)
+          for (int32_t s = lrp[k]; s < lrp[k + 1]; ++s) {
+            sP += m_in[s].x;
+            sH += m_in[s].y;
           }
-          xw[k] = y;
+        const double TP = dg[k] + sP, Th = bb[k] + sH;
+        tp[k] = make_double2(TP, Th);
+        if (to_ring || write_x) {
+          const double xi = Th / TP;
+          if (to_ring) rw[k] = xi;
+          if (write_x) {
+            double y = xi;
+            if (ait > 0 && nw >= 2) {   // Delta^2 of the means of rounds t - 2s, t - s, t
+              const double c0 = rp2[k], c1 = rp1[k];
+              const double d1 = c1 - c0, den = (xi - c1) - d1;
+              const double scale = fmax(fmax(fabs(c0), fabs(c1)), fabs(xi));
+              if (fabs(den) > 64.0 * DBL_EPSILON * scale) y = c0 - d1 * d1 / den;
+            }
+            xw[k] = y;
+          }
         }
       }
-    }
-    __syncthreads();
-    for (int32_t s = tid; s < S; s += kResBlock) {
-      const double2 t = tp[lrow[s]];
-      const double2 mi = first ? make_double2(0.0, 0.0) : min[s];
-      const double d = t.x - mi.x;   // P~_i - P_ji
-      brk |= zero_or_nonfinite(d);
-      const double as = a[s], inv = recip64(d);
-      const int32_t to = dst[s];
-      double eta = -as * (t.y - mi.y) * inv;
-      if (gam > 0.0) {
-        const double old = first ? 0.0 : cl.map_shared_rank(m[cur], to >> 24)[to & 0xFFFFFF].y;
-        eta = gam * old + (1.0 - gam) * eta;
+      __syncthreads();
+      for (int32_t s = lrp[k0] + tid; s < lrp[k1]; s += kResBlock) {
+        const double2 t = tp[lrow[s]];
+        const double2 mi = zin ? make_double2(0.0, 0.0) : m_in[s];
+        const double d = t.x - mi.x;   // P~_i - P_ji
+        brk |= zero_or_nonfinite(d);
+        const double as = a[s], inv = recip64(d);
+        const int32_t to = dst[s];
+        double eta = -as * (t.y - mi.y) * inv;
+        if (gam_c > 0.0) {
+          const double old = zin ? 0.0 : cl.map_shared_rank(m_in, to >> 24)[to & 0xFFFFFF].y;
+          eta = gam_c * old + (1.0 - gam_c) * eta;
+        }
+        cl.map_shared_rank(m_out, to >> 24)[to & 0xFFFFFF] = make_double2(-(as * as) * inv, eta);
       }
-      cl.map_shared_rank(m[cur ^ 1], to >> 24)[to & 0xFFFFFF] = make_double2(-(as * as) * inv, eta);
+      cl.sync();   // this pass's messages delivered everywhere (the last: round it + 1; x visible)
     }
-    cl.sync();   // round it + 1 delivered everywhere; x of this sweep visible
     if (to_ring) ++nw;
     if (pending >= 0) {
       const bool stop = decide(pending);

@@ -479,19 +479,25 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
                        int32_t *iters) {
   const bool mixed = h->opt.precision != GABP_PREC_FP64;
   const int mode = mixed ? CTL_MIXED : CTL_FP64;
-  if (!mixed && h->res.C > 0 && !h->opt.profile && h->g.nsys == 0 && !h->dense) {
-    bool ran = false;
-    const gabp_status s = resident_solve(h, b, x, tol, max_iter, iters, &ran);
-    if (ran) return s;
-  }
-  if (mixed) ensure32(h); else ensure64(h);
-  h->stats = gabp_stats{};
   double *x_out = x;
   if (h->g.ncol > 0) {   // colour schedule: solve in the renumbered order
     launch_permute(h->g.n, 1, h->stream, h->perm, b, h->bperm, false);
     b = h->bperm;
     x = h->xperm;
   }
+  if (!mixed && h->res.C > 0 && !h->opt.profile && h->g.nsys == 0 && !h->dense) {
+    bool ran = false;
+    const gabp_status s = resident_solve(h, b, x, tol, max_iter, iters, &ran);
+    if (ran) {
+      if (h->g.ncol > 0) {
+        launch_permute(h->g.n, 1, h->stream, h->perm, h->xperm, x_out, true);
+        CK(cudaStreamSynchronize(h->stream));
+      }
+      return s;
+    }
+  }
+  if (mixed) ensure32(h); else ensure64(h);
+  h->stats = gabp_stats{};
   init_ctl(h, mode, b, x, tol, max_iter, false);
   if (h->g.nsys > 0) {
     h->ctl_host->batched = 1;
@@ -782,7 +788,7 @@ bool build_resident(gabp_handle h, int C) {
 // parts fit.
 void setup_resident(gabp_handle h) {
   const Graph &g = h->g;
-  if (h->opt.small_form != 0 || h->g.ncol > 0 || g.E < 1 ||
+  if (h->opt.small_form != 0 || h->g.ncol > kResidentMaxColours || g.E < 1 ||
       g.E > static_cast<int64_t>(kResidentMaxCluster) * kResidentMaxSlots ||
       g.n > kResidentMaxCluster * kResidentMaxRows)
     return;
@@ -817,6 +823,10 @@ ResidentView resident_view(gabp_handle h, const double *b, double *x, double tol
   v.tol = tol;
   v.damping = h->opt.damping;
   v.out = r.out;
+  v.ncol = g.ncol;   // colour schedule: one pass per class (col_rows is empty without one)
+  v.damp_last = g.damp_last;
+  if (g.ncol > 0)
+    for (int c = 0; c <= g.ncol; ++c) v.cb[c] = g.col_rows[c];
   return v;
 }
 

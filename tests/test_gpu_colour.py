@@ -132,6 +132,34 @@ def test_colour_solves_need_fewer_sweeps(G, precision, name, make):
         assert sweeps[1] < sweeps[0], sweeps
 
 
+@pytest.mark.parametrize("name,make,damping,scope", [
+    ("poisson2d_32", lambda: W.poisson2d(32), 0.0, 0),
+    ("poisson3d_10", lambda: W.poisson3d(10), 0.0, 0),
+    ("er_3000", lambda: W.er_sdd(3000, 6, 1.1, 5), 0.3, 0),
+    ("poisson2d_24_damp_last", lambda: W.poisson2d(24), 0.3, 1)])
+def test_colour_resident_solve_matches_the_csr_path(G, name, make, damping, scope):
+    """Small FP64 systems under the colour schedule run in one cluster
+    launch (one pass and one cluster barrier per class); the per-sweep CSR
+    path (small_form = 1) runs the same schedule.  Both meet 1e-10, agree,
+    and stop within one check interval of each other."""
+    m = make()
+    b = W.uniform_rhs(m.n, 2)
+    bt = torch.tensor(b, device="cuda")
+    res = {}
+    for form in (0, 1):
+        s = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=0, schedule=1, small_form=form,
+                              damping=damping, damp_scope=scope, check_every=4)
+        xt, it = s.solve(bt, tol=1e-10, max_iter=100000)
+        res[form] = (xt.cpu().numpy(), it, s.stats())
+        s.close()
+    assert res[0][2]["kernel_launches"] == 1, res[0][2]   # the cluster kernel ran
+    for form in (0, 1):
+        x = res[form][0]
+        assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    assert _rel(res[0][0], res[1][0]) < 1e-8
+    assert abs(res[0][1] - res[1][1]) <= 4, (res[0][1], res[1][1])
+
+
 @pytest.mark.parametrize("name,make", [("poisson2d_40", lambda: W.poisson2d(40)),
                                        ("er_ragged_isolated", lambda: W.er_sdd(3001, 3, 1.05, 2))])
 def test_colour_multi_rhs_matches_synchronous(G, name, make):
