@@ -58,6 +58,11 @@ BYTES = {
     "full64": (44, 24),    # A 8 + (P,eta) in 16 + rev 4 + (P,eta) out 16 | diag 8 + b 8 + x out 8
     "residual": (20, 32),  # A 8 + col 4 + x[col] 8 | diag 8 + x 8 + b 8 + r 8
 }
+# The grid form (per-direction planes) has no reverse index to read.
+BYTES_GRID = {
+    "mean": (12, 12),      # c 4 + eta in 4 + eta out 4 | rhs 4 + 1/P 4 + d out 4
+    "full64": (40, 24),    # A 8 + (P,eta) in 16 + (P,eta) out 16 | diag 8 + b 8 + x out 8
+}
 
 
 # DRAM traffic of the dominant kernels from ncu captures (dram__bytes_read.sum
@@ -556,8 +561,12 @@ def run_poisson3d(args):
     for name, prec in (("mixed_fp32", gabp.PREC_MIXED_FP32), ("mixed_bf16", gabp.PREC_MIXED_BF16),
                        ("fp64", gabp.PREC_FP64)):
         t0 = time.perf_counter()
-        s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=prec, autotune=True,
-                                 schedule=args.schedule)
+        if args.form == "grid":
+            s = gabp.Solver.from_grid([p, p, p], m.row_ptr, m.col, m.val, precision=prec,
+                                      schedule=args.schedule)
+        else:
+            s = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=prec, autotune=True,
+                                     schedule=args.schedule)
         build_s = time.perf_counter() - t0
         ms, st, err = [], None, ""
         cap = args.fp64_max_iter if (prec == gabp.PREC_FP64 and args.fp64_max_iter) else args.max_iter
@@ -590,11 +599,14 @@ def run_poisson3d(args):
         if prec == gabp.PREC_FP64:
             per = 1e3 * sp["ms_full"] / max(1, sp["sweeps_full"])
             r["us_per_full_sweep"] = per
-            r["full_sweep_frac"] = (BYTES["full64"][0] * E + BYTES["full64"][1] * m.n) / (per * 1e-6) / 1e9 / hbm
+            bm = BYTES_GRID if args.form == "grid" else BYTES
+            r["full_sweep_frac"] = (bm["full64"][0] * E + bm["full64"][1] * m.n) / (per * 1e-6) / 1e9 / hbm
         else:
             if sp["sweeps_mean"]:
                 per = 1e3 * sp["ms_mean"] / sp["sweeps_mean"]
                 eb = 14 if prec == gabp.PREC_MIXED_BF16 else 16   # BF16: eta in/out 2 + 2
+                if args.form == "grid":
+                    eb -= 4                                        # no reverse index
                 r["us_per_mean_sweep"] = per
                 r["mean_sweep_frac"] = (eb * E + BYTES["mean"][1] * m.n) / (per * 1e-6) / 1e9 / hbm
             if sp["sweeps_full"]:
@@ -619,6 +631,7 @@ def run_poisson3d(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"3D Poisson 7-point {p}^3, b~U[-1,1], 1e-10 rel. residual",
                        "schedule": SCHEDULES[args.schedule],
+                       "form": "grid (per-direction planes, no index arrays)" if args.form == "grid" else "CSR tiles",
                        "n": m.n, "directed_edges": E, "max_iter": args.max_iter,
                        "generate_s": gen_s},
             "runs": res, "extrapolation": extrap,
@@ -749,6 +762,8 @@ def main():
                     help="poisson3d: separate sweep cap for the FP64 comparison (0 = --max-iter)")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="all workloads: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
+    ap.add_argument("--form", default="csr", choices=["csr", "grid"],
+                    help="poisson3d: general CSR handle, or the grid form (gabp_create_grid)")
     ap.add_argument("--damp-scope", type=int, default=0, choices=[0, 1],
                     help="detect with --schedule 1: 0 damp every message, 1 only those the last class sends")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")

@@ -254,6 +254,36 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
 gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *xhat_dev, double tol,
                                    int32_t max_iter, int32_t *iters);
 
+/*
+ * A handle for a matrix that couples only nearest neighbours of a box (the
+ * Laplacians of Section IX and any symmetric operator with the same
+ * pattern), kept in the grid form: no index arrays.  The nodes of the
+ * dims[0] x dims[1] x dims[2] box (ndim = 1, 2 or 3 entries of dims; dims[0]
+ * even and >= 2; x fastest) are split into the two colour classes of the
+ * box, (x + y + z) mod 2, and every message sits in a per-direction plane of
+ * its class, so a sweep reads and writes contiguous runs.
+ *
+ * Arguments: the CSR of A in host memory, rows in the box's natural order
+ * (i = x + dims[0] (y + dims[1] z)), the diagonal stored in every row and
+ * column indices strictly increasing; every off-diagonal entry must join
+ * nearest neighbours inside the box (a missing or zero entry is an absent
+ * edge).  The arrays are copied; the caller keeps ownership.  Options as
+ * gabp_create: schedule 0 runs the synchronous sweep of Alg. 2 (one launch
+ * per sweep), schedule 1 the serial schedule of Section III-C with the two
+ * classes in turn (red-black, one in-place launch per class), damp_scope 1
+ * limits damping to the second class.  b and x of gabp_solve stay in the
+ * natural order.  gabp_solve, gabp_solve_host, gabp_solve_multi (columns in
+ * turn) and gabp_run_rounds work as on a gabp_create handle;
+ * gabp_get_messages returns GABP_ERR_INVALID_ARG.
+ *
+ * Errors: GABP_ERR_INVALID_ARG (bad dims, an entry that is not a nearest
+ * neighbour, malformed CSR), GABP_ERR_NOT_SYMMETRIC, GABP_ERR_ZERO_DIAG,
+ * GABP_ERR_OOM, GABP_ERR_CUDA; the reason is in gabp_last_error(NULL).
+ */
+gabp_status gabp_create_grid(gabp_handle *out, int32_t ndim, const int32_t *dims, int64_t nnz,
+                             const int64_t *row_ptr_host, const int32_t *col_host,
+                             const double *val_host, const gabp_options *opt);
+
 /* Statistics of the last solve on the handle. */
 gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats);
 

@@ -309,6 +309,59 @@ int launch_refine_update(int32_t n, cudaStream_t st, Buffers B, Ctl *ctl);
 int launch_aitken(int32_t n, cudaStream_t st, Ctl *ctl, double *out);
 void prepare_dense_kernels(bool bf16);
 
+// ---- nearest-neighbour operators on a box in the grid form (gabp_grid.cu) ----
+// Nodes of a p0 x p1 x p2 box (p0 even; x fastest) are split into the two
+// colour classes of the box, c = (x + y + z) mod 2, and each class is kept as
+// a half grid: H = x / 2 + h0 (y + p1 z), h0 = p0 / 2; slot c Nh + H.  Per
+// class and direction d (0/1: +-x, 2/3: +-y, 4/5: +-z) one plane of Nh
+// entries, index (c D + d) Nh + H, holds A to that neighbour and the message
+// coming from it.  The neighbour of (c, H) in direction d is (1 - c, H +
+// off(d)) with off = s, s - 1, +-h0, +-h0 p1 and s = (c + y + z) mod 2: every
+// access is a contiguous run, no index arrays.
+struct GridView {
+  int32_t ndim, D;                 // axes, directions (2 ndim)
+  int32_t h0, p1, p2;              // half-row length, dims[1], dims[2]
+  int64_t Nh;                      // nodes per class
+  const double *a64, *diag64;      // [2 D Nh], [2 Nh]
+  const float *a32, *diag32;
+  int32_t pass;                    // -1: both classes (synchronous); c: colour pass over class c
+  int32_t in_place, no_control, no_damp;
+};
+
+struct Grid {
+  GridView v{};
+  double *a64 = nullptr, *diag64 = nullptr;   // owned device arrays
+  float *a32 = nullptr, *diag32 = nullptr;
+  int32_t dims[3] = {1, 1, 1};
+  bool colour = false, damp_last = false;     // red-black schedule; damping on class 1 only
+  bool have64 = false, have32 = false;
+  int64_t slots() const { return 2 * v.Nh; }
+  int64_t planes() const { return 2 * static_cast<int64_t>(v.D) * v.Nh; }
+  // the view of one launch: pass -1 (synchronous) or colour pass c
+  GridView pass_view(int c) const {
+    GridView w = v;
+    w.pass = c;
+    w.in_place = c >= 0;
+    w.no_control = c == 0;
+    w.no_damp = c == 0 && damp_last;
+    return w;
+  }
+};
+
+int launch_grid_full64(const GridView &v, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+int launch_grid_full32(const GridView &v, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                       bool bf16);
+int launch_grid_mean(const GridView &v, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
+                     bool bf16);
+int launch_grid_residual(const GridView &v, cudaStream_t st, double *r_out, Ctl *ctl,
+                         DevScalars *red, bool refine);
+// Host: checks that the CSR (natural order) couples only nearest neighbours of
+// the box `dims`, builds the planes and returns the slot -> natural row map.
+gabp_status build_grid(Grid &G, int32_t ndim, const int32_t *dims, int64_t nnz,
+                       const int64_t *row_ptr, const int32_t *col, const double *val,
+                       cudaStream_t st, std::vector<int32_t> &perm, std::string *msg);
+void free_grid(Grid &G);
+
 // ---- whole FP64 solves of small systems in one cluster launch (gabp_resident.cu) ----
 constexpr int kResidentMaxCluster = 16;   // CTAs of the cluster (16 needs the non-portable size)
 constexpr int kResidentMaxSlots = 3072;   // incoming-message slots per CTA
@@ -402,6 +455,7 @@ struct gabp_s {
   size_t capK = 0;                     // columns the multi buffers hold
   gabp::MultiCols cols{};              // device per-column arrays (capK each)
   gabp::Dense *dense = nullptr;        // Section VII batches in dense bipartite form
+  gabp::Grid *grid = nullptr;          // nearest-neighbour operators on a box, grid form
   gabp_tuning tuning{};                // launch shapes (chosen by the autotuner or default)
   gabp::Resident res{};                // small FP64 systems: one cluster launch per solve
   double *ring[3] = {};                // Aitken: the last three FP64 tentative means

@@ -136,9 +136,41 @@ void ensure_dense32(gabp_handle h) {
   d.have32 = true;
 }
 
+// Grid form: message planes (2 D Nh entries) and node slots (2 Nh).
+void ensure_grid64(gabp_handle h) {
+  Grid &G = *h->grid;
+  if (G.have64) return;
+  ensure(&h->buf.m64[0], G.planes());
+  ensure(&h->buf.m64[1], G.planes());
+  G.have64 = true;
+}
+
+void ensure_grid32(gabp_handle h) {
+  Grid &G = *h->grid;
+  if (G.have32) return;
+  Buffers &B = h->buf;
+  const size_t M = G.planes(), n = G.slots();
+  ensure(&B.m32[0], M); ensure(&B.m32[1], M);
+  const size_t eb = (M + kPad) * (is_bf16(h) ? sizeof(__nv_bfloat16) : sizeof(float));
+  for (int k = 0; k < 2; ++k) {
+    CK(cudaMalloc(&B.e[k], eb));
+    CK(cudaMemset(B.e[k], 0, eb));
+  }
+  ensure(&B.c32, M);
+  ensure(&B.invP32, n);
+  ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
+  ensure(&B.r64, n);
+  ensure(&B.rhs32, n);
+  G.have32 = true;
+}
+
+// Message entries of the handle's buffers (CSR slots, or grid planes).
+size_t message_entries(gabp_handle h) { return h->grid ? h->grid->planes() : h->g.E; }
+
 void ensure64(gabp_handle h) {
   ensure_common(h);
   if (h->dense) { ensure_dense64(h); return; }
+  if (h->grid) { ensure_grid64(h); return; }
   if (h->have64) return;
   ensure(&h->buf.m64[0], h->g.E);
   ensure(&h->buf.m64[1], h->g.E);
@@ -148,6 +180,7 @@ void ensure64(gabp_handle h) {
 void ensure32(gabp_handle h) {
   ensure_common(h);
   if (h->dense) { ensure_dense32(h); return; }
+  if (h->grid) { ensure_grid32(h); return; }
   if (h->have32) return;
   const size_t n = h->g.n, E = h->g.E;
   Buffers &B = h->buf;
@@ -221,6 +254,40 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     }
     return 0;
   }
+  if (h->grid) {
+    const Grid &G = *h->grid;
+    Buffers B = h->buf;
+    if (G.colour) {   // red-black: one in-place pass per class
+      B.m64[1] = B.m64[0];
+      B.m32[1] = B.m32[0];
+      B.e[1] = B.e[0];
+    }
+    auto passes = [&](auto launch) {
+      return G.colour ? launch(G.pass_view(0)) + launch(G.pass_view(1)) : launch(G.pass_view(-1));
+    };
+    switch (phase) {
+      case PH_FULL64:
+        return passes([&](const GridView &v) { return launch_grid_full64(v, st, B, h->ctl, h->red); });
+      case PH_CHECK64:   // (Aitken: the extrapolated means first)
+        return (h->opt.aitken > 0 ? launch_aitken(g.n, st, h->ctl, nullptr) : 0) +
+               launch_grid_residual(G.v, st, nullptr, h->ctl, h->red, false);
+      case PH_FULL32:
+        return passes([&](const GridView &v) {
+          return launch_grid_full32(v, st, B, h->ctl, h->red, is_bf16(h));
+        });
+      case PH_MEAN:
+        return passes([&](const GridView &v) {
+          return launch_grid_mean(v, st, B, h->ctl, h->red, is_bf16(h));
+        });
+      case PH_REFINE: {
+        const int k = launch_refine_update(g.n, st, h->buf, h->ctl) +
+                      launch_grid_residual(G.v, st, h->buf.r64, h->ctl, h->red, true);
+        if (G.colour) zero_messages(h, st, false);   // the next inner solve starts from zero
+        return k;
+      }
+    }
+    return 0;
+  }
   if (g.ncol > 0 &&
       (phase == PH_FULL64 || phase == PH_FULL32 || phase == PH_MEAN || phase == PH_MEANK)) {
     // colour schedule: one in-place pass per class (both parities alias one buffer)
@@ -264,7 +331,7 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
 // Colour schedule: the in-place passes read their message buffer from the
 // start of an inner solve on, so it must hold zeros then.
 void zero_messages(gabp_handle h, cudaStream_t st, bool full) {
-  const size_t E = h->g.E + kPad;
+  const size_t E = message_entries(h) + kPad;
   const Buffers &B = h->buf;
   if (full && B.m64[0]) CK(cudaMemsetAsync(B.m64[0], 0, sizeof(double2) * E, st));
   if (full && B.m32[0]) CK(cudaMemsetAsync(B.m32[0], 0, sizeof(float2) * E, st));
@@ -276,12 +343,18 @@ void zero_multi_messages(gabp_handle h, cudaStream_t st) {
   CK(cudaMemsetAsync(h->buf.eK[0], 0, sizeof(float) * h->g.E * h->graph_K, st));
 }
 
+// Launches of one message sweep: one, or one per colour class.
+int passes_per_sweep(gabp_handle h) {
+  if (h->grid) return h->grid->colour ? 2 : 1;
+  return std::max(1, h->g.ncol);
+}
+
 int launch_mode_init(gabp_handle h, cudaStream_t st, int mode) {
   if (mode == CTL_MULTI) {
     if (h->g.ncol > 0) zero_multi_messages(h, st);
     return launch_init_multi(h->g, st, h->buf, h->ctl, h->red, h->graph_K);
   }
-  if (h->g.ncol > 0) zero_messages(h, st, true);
+  if (h->g.ncol > 0 || (h->grid && h->grid->colour)) zero_messages(h, st, true);
   return launch_init(h->g, st, h->buf, h->ctl, h->red);
 }
 
@@ -446,7 +519,7 @@ void run_mode(gabp_handle h, int mode, int32_t max_iter) {
     CK(cudaStreamSynchronize(st));
     const Ctl &c = *h->ctl_host;
     const int per_check = (mode == CTL_MIXED || mode == CTL_MULTI) ? 2 : 1;
-    h->stats.kernel_launches += 1 + static_cast<int64_t>(c.sweeps) * std::max(1, h->g.ncol) +
+    h->stats.kernel_launches += 1 + static_cast<int64_t>(c.sweeps) * passes_per_sweep(h) +
                                 static_cast<int64_t>(c.checks) * per_check;
   } else {
     run(h, K_OTHER, [&] { return launch_mode_init(h, st, mode); });
@@ -480,7 +553,7 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
   const bool mixed = h->opt.precision != GABP_PREC_FP64;
   const int mode = mixed ? CTL_MIXED : CTL_FP64;
   double *x_out = x;
-  if (h->g.ncol > 0) {   // colour schedule: solve in the renumbered order
+  if (h->perm) {   // colour schedule or grid form: solve in the renumbered order
     launch_permute(h->g.n, 1, h->stream, h->perm, b, h->bperm, false);
     b = h->bperm;
     x = h->xperm;
@@ -489,7 +562,7 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
     bool ran = false;
     const gabp_status s = resident_solve(h, b, x, tol, max_iter, iters, &ran);
     if (ran) {
-      if (h->g.ncol > 0) {
+      if (h->perm) {
         launch_permute(h->g.n, 1, h->stream, h->perm, h->xperm, x_out, true);
         CK(cudaStreamSynchronize(h->stream));
       }
@@ -504,7 +577,7 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
     CK(cudaMemsetAsync(h->g.sys_bmax, 0, sizeof(unsigned long long) * h->g.nsys, h->stream));
   }
   run_mode(h, mode, max_iter);
-  if (h->g.ncol > 0) {
+  if (h->perm) {
     launch_permute(h->g.n, 1, h->stream, h->perm, h->xperm, x_out, true);
     CK(cudaStreamSynchronize(h->stream));
   }
@@ -619,6 +692,11 @@ void build_lsq_csr(int32_t nsys, const int32_t *K, const int32_t *N, const doubl
 }
 
 void release(gabp_handle h) {
+  if (h->grid) {
+    free_grid(*h->grid);
+    delete h->grid;
+    h->grid = nullptr;
+  }
   for (int m = 0; m < CTL_MODES; ++m) {
     if (h->exec[m]) cudaGraphExecDestroy(h->exec[m]);
     if (h->graph[m]) cudaGraphDestroy(h->graph[m]);
@@ -1343,6 +1421,48 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
   return GABP_OK;
 }
 
+gabp_status gabp_create_grid(gabp_handle *out, int32_t ndim, const int32_t *dims, int64_t nnz,
+                             const int64_t *row_ptr_host, const int32_t *col_host,
+                             const double *val_host, const gabp_options *opt) {
+  if (!out) return GABP_ERR_INVALID_ARG;
+  *out = nullptr;
+  gabp_handle h = nullptr;
+  gabp_status s = new_handle(opt, &h);
+  if (s != GABP_OK) return s;
+  s = guarded(h, [&] {
+    h->grid = new Grid;
+    std::vector<int32_t> perm;
+    std::string msg;
+    const gabp_status r = build_grid(*h->grid, ndim, dims, nnz, row_ptr_host, col_host, val_host,
+                                     h->stream, perm, &msg);
+    if (r != GABP_OK) {
+      h->last_error = msg;
+      return r;
+    }
+    Grid &G = *h->grid;
+    G.colour = h->opt.schedule == 1;
+    G.damp_last = h->opt.damp_scope == 1;
+    const int64_t n = G.slots();
+    h->g.n = static_cast<int32_t>(n);
+    h->g.E = nnz - n;   // directed off-diagonal edges (the diagonal is in every row)
+    h->user_nnz = nnz;
+    ensure(&h->perm, n);
+    ensure(&h->bperm, n);
+    ensure(&h->xperm, n);
+    CK(cudaMemcpyAsync(h->perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    fill_tuning(h);
+    return GABP_OK;
+  });
+  if (s != GABP_OK) {
+    g_create_error = h->last_error;
+    gabp_destroy(h);
+    return s;
+  }
+  *out = h;
+  return GABP_OK;
+}
+
 gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *xhat_dev, double tol,
                                    int32_t max_iter, int32_t *iters) {
   if (!h) return GABP_ERR_INVALID_ARG;
@@ -1408,8 +1528,8 @@ gabp_status gabp_solve_multi(gabp_handle h, const double *B_dev, double *X_dev, 
   if (!h) return GABP_ERR_INVALID_ARG;
   if (!B_dev || !X_dev || nrhs < 1 || !(tol >= 0.0) || !std::isfinite(tol) || max_iter < 1)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: invalid argument");
-  // dense Section VII batches solve the columns one after another
-  const bool shared_precisions = h->opt.precision != GABP_PREC_FP64 && !h->dense;
+  // dense Section VII batches and grid handles solve the columns one after another
+  const bool shared_precisions = h->opt.precision != GABP_PREC_FP64 && !h->dense && !h->grid;
   if (shared_precisions && nrhs > 256)
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_multi: at most 256 right-hand sides per call");
   if (shared_precisions)
@@ -1464,12 +1584,14 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
     cudaStream_t st = h->stream;
     ensure64(h);
     double *x_user = x_dev;
-    if (h->g.ncol > 0) {   // colour schedule: renumbered order, messages from zero
+    const bool in_place = h->g.ncol > 0 || (h->grid && h->grid->colour);
+    if (h->perm) {   // colour schedule or grid form: the renumbered order
       launch_permute(h->g.n, 1, st, h->perm, b_dev, h->bperm, false);
       b_dev = h->bperm;
       x_dev = h->xperm;
-      CK(cudaMemsetAsync(h->buf.m64[0], 0, sizeof(double2) * (h->g.E + kPad), st));
     }
+    if (in_place)    // one message buffer, read before it is written: from zero
+      CK(cudaMemsetAsync(h->buf.m64[0], 0, sizeof(double2) * (message_entries(h) + kPad), st));
     init_ctl(h, CTL_ROUNDS, b_dev, x_dev, 0.0, rounds, false);
     Ctl &c = *h->ctl_host;
     c.rounds_target = rounds;
@@ -1483,6 +1605,12 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
     for (int32_t t = 0; t <= rounds; ++t) {
       if (h->dense) {
         launch_dense_full64(*h->dense, st, h->buf, h->ctl, h->red);
+      } else if (h->grid && t < rounds) {
+        launch_phase(h, st, PH_FULL64);   // one round: both classes, or the two passes
+      } else if (h->grid) {
+        Buffers B = h->buf;               // the means of the last round
+        if (h->grid->colour) B.m64[1] = B.m64[0];
+        launch_grid_full64(h->grid->pass_view(-1), st, B, h->ctl, h->red);
       } else if (h->g.ncol > 0 && t < rounds) {
         launch_phase(h, st, PH_FULL64);   // one round: the colour passes
       } else if (h->g.ncol > 0) {
@@ -1494,7 +1622,7 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
       }
     }
     if (ait) launch_aitken(h->g.n, st, h->ctl, x_dev);
-    if (h->g.ncol > 0) launch_permute(h->g.n, 1, st, h->perm, h->xperm, x_user, true);
+    if (h->perm) launch_permute(h->g.n, 1, st, h->perm, h->xperm, x_user, true);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     DevScalars red{};
@@ -1511,6 +1639,9 @@ gabp_status gabp_get_messages(gabp_handle h, double *P_host, double *mu_host) {
   if (h->dense)
     return fail(h, GABP_ERR_INVALID_ARG,
                 "gabp_get_messages: a dense Section VII batch has no caller CSR to lay messages out on");
+  if (h->grid)
+    return fail(h, GABP_ERR_INVALID_ARG,
+                "gabp_get_messages: a grid handle keeps its messages per direction, not per CSR entry");
   return guarded(h, [&] {
     const Graph &g = h->g;
     std::memset(P_host, 0, sizeof(double) * h->user_nnz);

@@ -37,7 +37,7 @@ EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_str
             "gabp_run_rounds", "gabp_get_messages", "gabp_last_error", "gabp_status_string",
             "gabp_version", "gabp_create_batched", "gabp_create_lsq_batched",
             "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc", "gabp_get_tuning",
-            "gabp_set_profile")
+            "gabp_set_profile", "gabp_create_grid")
 
 
 class GabpOptions(ctypes.Structure):
@@ -123,6 +123,8 @@ def load(path: str = LIB_PATH):
         "gabp_create_lsq_batched": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int32, i32p, i32p, f64p,
                                                    f64p, ctypes.POINTER(GabpOptions)]),
         "gabp_solve_lsq_batched": (ctypes.c_int, [H, vp, vp, ctypes.c_double, ctypes.c_int32, i32p]),
+        "gabp_create_grid": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int32, i32p, ctypes.c_int64,
+                                            i64p, i32p, f64p, ctypes.POINTER(GabpOptions)]),
         "gabp_run_rounds_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp,
                                                    ctypes.c_int32, vp, vp]),
         "gabp_get_tuning": (ctypes.c_int, [H, ctypes.POINTER(GabpTuning)]),
@@ -205,6 +207,24 @@ def gabp_create_batched(sys_row_off, row_ptr, col, val, options: GabpOptions | N
                                  int(row_ptr[-1]), _ptr(row_ptr, ctypes.c_int64),
                                  _ptr(col, ctypes.c_int32), _ptr(val, ctypes.c_double),
                                  ctypes.byref(options))
+    _check(None, st)
+    return h
+
+
+def gabp_create_grid(dims, row_ptr, col, val, options: GabpOptions | None = None):
+    """Create a grid-form handle for a CSR (host arrays, natural order of the
+    box ``dims``, x fastest) that couples only nearest neighbours."""
+    lib = load()
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    if options is None:
+        options = gabp_default_options()
+    h = ctypes.c_void_p()
+    st = lib.gabp_create_grid(ctypes.byref(h), len(d), _ptr(d, ctypes.c_int32), int(row_ptr[-1]),
+                              _ptr(row_ptr, ctypes.c_int64), _ptr(col, ctypes.c_int32),
+                              _ptr(val, ctypes.c_double), ctypes.byref(options))
     _check(None, st)
     return h
 
@@ -321,6 +341,31 @@ def gabp_version() -> str:
     return load().gabp_version().decode()
 
 
+def _options(*, precision=PREC_FP64, residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0,
+             inner_tol=0.0, profile=False, damping=0.0, stream: int | None = None, autotune=False,
+             tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0, aitken=0,
+             schedule=0, damp_scope=0) -> GabpOptions:
+    o = gabp_default_options()
+    o.precision = precision
+    o.residual_kind = residual_kind
+    o.check_every = check_every
+    o.group_lanes = group_lanes
+    o.inner_tol = inner_tol
+    o.profile = 1 if profile else 0
+    o.damping = damping
+    o.stream = current_stream_handle() if stream is None else stream
+    o.autotune = 1 if autotune else 0
+    o.tile_slots = tile_slots
+    o.tile_rows = tile_rows
+    o.heavy_degree = heavy_degree
+    o.small_form = small_form
+    o.cluster_ctas = cluster_ctas
+    o.aitken = aitken
+    o.schedule = schedule
+    o.damp_scope = damp_scope
+    return o
+
+
 @dataclass
 class Solver:
     """Owning wrapper: ``Solver(csr, precision=...)`` then ``solve(b)``."""
@@ -334,25 +379,23 @@ class Solver:
                  profile=False, damping=0.0, stream: int | None = None, autotune=False,
                  tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0,
                  aitken=0, schedule=0, damp_scope=0):
-        o = gabp_default_options()
-        o.schedule = schedule
-        o.damp_scope = damp_scope
-        o.aitken = aitken
-        o.small_form = small_form
-        o.cluster_ctas = cluster_ctas
-        o.autotune = 1 if autotune else 0
-        o.tile_slots = tile_slots
-        o.tile_rows = tile_rows
-        o.heavy_degree = heavy_degree
-        o.precision = precision
-        o.residual_kind = residual_kind
-        o.check_every = check_every
-        o.group_lanes = group_lanes
-        o.inner_tol = inner_tol
-        o.profile = 1 if profile else 0
-        o.damping = damping
-        o.stream = current_stream_handle() if stream is None else stream
+        o = _options(precision=precision, residual_kind=residual_kind, check_every=check_every,
+                     group_lanes=group_lanes, inner_tol=inner_tol, profile=profile, damping=damping,
+                     stream=stream, autotune=autotune, tile_slots=tile_slots, tile_rows=tile_rows,
+                     heavy_degree=heavy_degree, small_form=small_form, cluster_ctas=cluster_ctas,
+                     aitken=aitken, schedule=schedule, damp_scope=damp_scope)
         h = gabp_create(row_ptr, col, val, rev, o)
+        return cls(h, len(row_ptr) - 1, int(row_ptr[-1]))
+
+    @classmethod
+    def from_grid(cls, dims, row_ptr, col, val, *, precision=PREC_FP64, residual_kind=RESIDUAL_REL,
+                  check_every=0, inner_tol=0.0, profile=False, damping=0.0,
+                  stream: int | None = None, aitken=0, schedule=0, damp_scope=0):
+        """Grid form (gabp_create_grid): ``dims`` of the box, CSR in its natural order."""
+        o = _options(precision=precision, residual_kind=residual_kind, check_every=check_every,
+                     inner_tol=inner_tol, profile=profile, damping=damping, stream=stream,
+                     aitken=aitken, schedule=schedule, damp_scope=damp_scope)
+        h = gabp_create_grid(dims, row_ptr, col, val, o)
         return cls(h, len(row_ptr) - 1, int(row_ptr[-1]))
 
     def solve(self, b, x=None, tol=1e-10, max_iter=10000):

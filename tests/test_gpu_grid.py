@@ -1,0 +1,161 @@
+"""GPU parity of the grid form (gabp_create_grid).
+
+A matrix that couples only nearest neighbours of a box is kept as two
+half grids (the box's colour classes) with one plane per direction.  FP64
+rounds of the synchronous schedule are compared with the oracle's Alg. 2 on
+the same CSR, and those of the red-black schedule with the oracle's serial
+schedule visiting class 0 ((x + y + z) even) before class 1, per round to
+1e-12; solves with the oracle's solution and with the CSR path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0810_1119_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts
+    pytest.skip("CUDA device required", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_0810_1119_gb300 import build_lib
+    build_lib.build()
+    from paper_0810_1119_gb300 import gabp
+    gabp.load()
+    return gabp
+
+
+def _rel(a, ref):
+    return float(np.abs(a - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def box_operator(dims, seed, laplacian=False, drop=0.0):
+    """Symmetric nearest-neighbour operator on the box (natural order, x
+    fastest): couplings -1 (Laplacian) or -(0.5 + U[0, 1)) with a fraction
+    `drop` left out; diagonal 2 ndim (Laplacian) or 1.1 sum |a| + 0.1."""
+    rng = np.random.default_rng(seed)
+    dims = list(dims)
+    n = int(np.prod(dims))
+    idx = np.arange(n).reshape(dims[::-1])          # [z][y][x]
+    rows, cols, vals = [], [], []
+    for axis in range(len(dims)):
+        ax = len(dims) - 1 - axis                    # numpy axis of this box axis
+        lo = np.take(idx, range(0, dims[axis] - 1), axis=ax).ravel()
+        hi = np.take(idx, range(1, dims[axis]), axis=ax).ravel()
+        w = -np.ones(lo.size) if laplacian else -(0.5 + rng.random(lo.size))
+        keep = rng.random(lo.size) >= drop
+        rows += [lo[keep], hi[keep]]
+        cols += [hi[keep], lo[keep]]
+        vals += [w[keep], w[keep]]
+    r, c, v = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    if laplacian:
+        diag = np.full(n, 2.0 * len(dims))
+    else:
+        diag = 1.1 * np.bincount(r, np.abs(v), minlength=n) + 0.1
+    d = np.arange(n)
+    return W.csr_from_coo(n, np.concatenate([r, d]), np.concatenate([c, d]), np.concatenate([v, diag]))
+
+
+def colour_of(dims):
+    n = int(np.prod(dims))
+    i = np.arange(n)
+    s = i % dims[0]
+    if len(dims) > 1:
+        s = s + (i // dims[0]) % dims[1]
+    if len(dims) > 2:
+        s = s + i // (dims[0] * dims[1])
+    return s % 2
+
+
+CASES = {
+    "1d_64": ([64], dict(seed=1)),
+    "2d_12x10_laplacian": ([12, 10], dict(seed=0, laplacian=True)),
+    "2d_34x31_dropped": ([34, 31], dict(seed=2, drop=0.1)),
+    "3d_6x5x4_dropped": ([6, 5, 4], dict(seed=3, drop=0.1)),
+    "3d_8x8x8_laplacian": ([8, 8, 8], dict(seed=0, laplacian=True)),
+}
+
+
+def _solver(G, dims, m, **kw):
+    return G.Solver.from_grid(dims, m.row_ptr, m.col, m.val, **kw)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("damping", [0.0, 0.4])
+def test_grid_rounds_match_oracle_synchronous(G, name, damping):
+    dims, kw = CASES[name]
+    m = box_operator(dims, **kw)
+    b = W.normal_rhs(m.n, 4)
+    s = _solver(G, dims, m, precision=0, damping=damping)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    for r in (0, 1, 2, 5, 9):
+        G.gabp_run_rounds(s.handle, bt, r, xt)
+        ref = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=r, damping=damping)
+        assert _rel(xt.cpu().numpy(), ref["x"]) <= 1e-12, r
+    s.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("damping,scope", [(0.0, 0), (0.4, 0), (0.4, 1)])
+def test_grid_rounds_match_oracle_red_black(G, name, damping, scope):
+    dims, kw = CASES[name]
+    m = box_operator(dims, **kw)
+    b = W.normal_rhs(m.n, 5)
+    c = colour_of(dims)
+    order = np.argsort(c, kind="stable")
+    s = _solver(G, dims, m, precision=0, schedule=1, damping=damping, damp_scope=scope)
+    bt = torch.tensor(b, device="cuda")
+    xt = torch.empty_like(bt)
+    for r in (0, 1, 2, 5, 9):
+        G.gabp_run_rounds(s.handle, bt, r, xt)
+        ref = oracle.gabp_serial(m.row_ptr, m.col, m.val, b, order=order, max_rounds=r,
+                                 damping=damping, damp_from=(c == 1) if scope else None)
+        assert _rel(xt.cpu().numpy(), ref["x"]) <= 1e-12, r
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("dims,kw", [([40, 40], dict(seed=0, laplacian=True)),
+                                     ([16, 16, 16], dict(seed=0, laplacian=True)),
+                                     ([60, 50], dict(seed=6, drop=0.05))])
+def test_grid_solves_match_the_csr_path(G, precision, dims, kw):
+    """Both schedules meet 1e-10 and agree with the CSR handle; red-black
+    needs fewer sweeps on the Laplacians."""
+    m = box_operator(dims, **kw)
+    b = W.uniform_rhs(m.n, 3)
+    bt = torch.tensor(b, device="cuda")
+    csr = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=precision, small_form=1)
+    x_csr = csr.solve(bt, tol=1e-10, max_iter=200000)[0].cpu().numpy()
+    csr.close()
+    sweeps = {}
+    for sched in (0, 1):
+        s = _solver(G, dims, m, precision=precision, schedule=sched)
+        xt, it = s.solve(bt, tol=1e-10, max_iter=200000)
+        x = xt.cpu().numpy()
+        assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+        assert _rel(x, x_csr) < 1e-8
+        sweeps[sched] = s.stats()["sweeps_total"]
+        s.close()
+    if kw.get("laplacian") and precision != 2:
+        assert sweeps[1] < sweeps[0], sweeps
+
+
+def test_grid_handle_rejects_message_export_and_solves_columns(G):
+    dims = [10, 8]
+    m = box_operator(dims, seed=2)
+    s = _solver(G, dims, m, precision=1)
+    with pytest.raises(G.GabpError):
+        G.gabp_get_messages(s.handle, m.nnz)
+    B = W.normal_rhs(m.n, 7, k=5)
+    Bt = torch.tensor(B, device="cuda")
+    X = torch.empty_like(Bt)
+    G.gabp_solve_multi(s.handle, Bt, X, 1e-10, 20000)
+    x = X.cpu().numpy()
+    for k in range(5):
+        assert oracle.residual_inf(m.row_ptr, m.col, m.val, B[:, k], x[:, k]) < 1e-10 * np.abs(B[:, k]).max()
+    s.close()

@@ -160,3 +160,34 @@ def test_damp_scope_is_validated(lib):
         with pytest.raises(G.GabpError) as ei:
             G.gabp_create(m.row_ptr, m.col, m.val, None, o)
         assert "damp_scope" in str(ei.value)
+
+
+def test_grid_create_validates_on_the_host(lib):
+    """gabp_create_grid accepts only a nearest-neighbour operator on the box
+    given, in natural order, with an even first dimension; every refusal is
+    a host check (no GPU needed)."""
+    from paper_0810_1119_gb300 import gabp as G
+    m = W.poisson2d(6)                                   # 6 x 6, natural order
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_grid([5, 6], m.row_ptr, m.col, m.val)   # odd first dimension (and 30 != 36 rows)
+    assert ei.value.name == "GABP_ERR_INVALID_ARG"
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_grid([4, 9], m.row_ptr, m.col, m.val)   # +-6 is no neighbour offset of a 4 x 9 box
+    assert "nearest neighbour" in str(ei.value)
+    A = np.zeros((8, 8))                                 # 4 x 2 box with a coupling that wraps a row
+    for i in range(8):
+        A[i, i] = 4.0
+    A[3, 4] = A[4, 3] = -1.0                             # (x=3, y=0) - (x=0, y=1): not adjacent
+    w = W.csr_from_dense(A)
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_grid([4, 2], w.row_ptr, w.col, w.val)
+    assert "nearest neighbour" in str(ei.value)
+    A[3, 4] = A[4, 3] = 0.0
+    A[0, 1], A[1, 0] = -1.0, -0.5                        # neighbours, but not symmetric
+    w = W.csr_from_dense(A)
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_grid([4, 2], w.row_ptr, w.col, w.val)
+    assert ei.value.name == "GABP_ERR_NOT_SYMMETRIC"
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_create_grid([6, 4], m.row_ptr, m.col, m.val)   # 24 rows expected, 36 given
+    assert ei.value.name == "GABP_ERR_INVALID_ARG"
