@@ -42,15 +42,18 @@ struct GNode {
   unsigned in_box;   // bit d: the neighbour in direction d exists
 };
 
+// The box holds fewer than 2^31 nodes, so the coordinates come from 32-bit
+// arithmetic (two 32-bit divisions per node; the class is a comparison).
 __device__ __forceinline__ bool node_of(const GridView &g, int64_t t, GNode &n) {
   const int64_t count = g.pass < 0 ? 2 * g.Nh : g.Nh;
   if (t >= count) return false;
   n.slot = g.pass < 0 ? t : g.pass * g.Nh + t;
-  n.c = static_cast<int>(n.slot / g.Nh);
+  n.c = n.slot >= g.Nh ? 1 : 0;
   n.H = n.slot - n.c * g.Nh;
-  const int64_t row = n.H / g.h0;
-  const int hx = static_cast<int>(n.H - row * g.h0);
-  const int y = static_cast<int>(row % g.p1), z = static_cast<int>(row / g.p1);
+  const uint32_t H = static_cast<uint32_t>(n.H), h0 = static_cast<uint32_t>(g.h0);
+  const uint32_t row = H / h0, z32 = row / static_cast<uint32_t>(g.p1);
+  const int hx = static_cast<int>(H - row * h0);
+  const int z = static_cast<int>(z32), y = static_cast<int>(row - z32 * static_cast<uint32_t>(g.p1));
   n.s = (n.c + y + z) & 1;
   const int x = 2 * hx + n.s, p0 = 2 * g.h0;
   unsigned m = 0;
@@ -257,28 +260,32 @@ grid_mean_kernel(GridView g, Buffers B, Ctl *ctl, DevScalars *red) {
   uint32_t mdd = 0, md = 0;
   GNode n;
   if (node_of(g, blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x, n)) {
-    float e[kMaxDir];
-    float sH = 0.f;
+    // every load of the node first (incoming messages, coefficients, node data)
+    float e[kMaxDir], cf[kMaxDir];
 #pragma unroll
     for (int d = 0; d < kMaxDir; ++d) {
-      e[d] = 0.f;
-      if (d >= g.D || !((n.in_box >> d) & 1u) || zin) continue;
-      e[d] = ld_e(ein + plane_in(g, n.c, d, n.H));
-      sH += e[d];
+      e[d] = cf[d] = 0.f;
+      if (d >= g.D || !((n.in_box >> d) & 1u)) continue;
+      const int64_t p = plane_in(g, n.c, d, n.H);
+      cf[d] = B.c32[p];
+      if (!zin) e[d] = ld_e(ein + p);
     }
     const float rhs = first ? static_cast<float>(B.r64[n.slot] * inv_rn) : B.rhs32[n.slot];
+    const float ip = B.invP32[n.slot];
+    float sH = 0.f;
+#pragma unroll
+    for (int d = 0; d < kMaxDir; ++d) sH += e[d];
     const float Th = rhs + sH;
     const float prev = first ? 0.f : mon_prev[n.slot].y;
-    const float di = Th * B.invP32[n.slot];
+    const float di = Th * ip;
     mon_out[n.slot] = make_float2(0.f, di);
     mdd = fmax_bits(mdd, di - prev);
     md = fmax_bits(md, di);
     if (first) B.rhs32[n.slot] = rhs;
 #pragma unroll
     for (int d = 0; d < kMaxDir; ++d) {
-      if (d >= g.D || !((n.in_box >> d) & 1u)) continue;
-      const float cc = B.c32[plane_in(g, n.c, d, n.H)];
-      if (cc == 0.f) continue;
+      const float cc = cf[d];
+      if (cc == 0.f) continue;   // out of the box, or no edge
       const int64_t q = plane_out(g, n, d);
       float eta = cc * (Th - e[d]);
       if (gam > 0.f) eta = gam * (zin ? 0.f : ld_e(ein + q)) + (1.f - gam) * eta;
