@@ -762,8 +762,8 @@ def main():
                     help="poisson3d: separate sweep cap for the FP64 comparison (0 = --max-iter)")
     ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
                     help="all workloads: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
-    ap.add_argument("--form", default="csr", choices=["csr", "grid"],
-                    help="poisson3d: general CSR handle, or the grid form (gabp_create_grid)")
+    ap.add_argument("--form", default="grid", choices=["csr", "grid"],
+                    help="poisson3d: the grid form (gabp_create_grid, default) or the general CSR handle")
     ap.add_argument("--damp-scope", type=int, default=0, choices=[0, 1],
                     help="detect with --schedule 1: 0 damp every message, 1 only those the last class sends")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")
