@@ -393,7 +393,7 @@ def run_multi(args):
     build_lib.build()
     from paper_0810_1119_gb300 import gabp
     from paper_0810_1119_gb300 import workloads as W
-    n, K = 2_000_000, 64
+    n, K = args.n, 64
     m = W.er_sdd(n, 10, 1.05, 0)
     E = m.n_directed_edges
     B = torch.tensor(W.normal_rhs(n, 5, k=K), device="cuda")
@@ -444,7 +444,7 @@ def run_multi(args):
             "value": updates / (t * 1e-3), "unit": "edge-rhs-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "multi-RHS: ER n=2e6 avg-degree 10 SDD (dominance 1.05), 64 RHS b~N(0,1), 1e-10 rel. residual per column",
+            "config": {"workload": f"multi-RHS: ER n={n:.0e} avg-degree 10 SDD (dominance 1.05), 64 RHS b~N(0,1), 1e-10 rel. residual per column",
                        "n": n, "directed_edges": E, "nrhs": K, "schedule": SCHEDULES[args.schedule]},
             "sweeps": {"precision": st["sweeps_full"], "mean_K_columns": st["sweeps_mean"],
                        "outer": st["outer_steps"]},
@@ -764,6 +764,7 @@ def main():
                     help="all workloads: 0 synchronous (Alg. 2), 1 colour-serial (Section III-C)")
     ap.add_argument("--form", default="grid", choices=["csr", "grid"],
                     help="poisson3d: the grid form (gabp_create_grid, default) or the general CSR handle")
+    ap.add_argument("--n", type=int, default=2_000_000, help="multi64: unknowns (smaller for profiling)")
     ap.add_argument("--damp-scope", type=int, default=0, choices=[0, 1],
                     help="detect with --schedule 1: 0 damp every message, 1 only those the last class sends")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")
