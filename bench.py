@@ -55,6 +55,10 @@ WORKLOAD = "ER n=1e6 avg-degree 8 SDD (dominance 1.1), b~N(0,1), solve to 1e-10 
 BYTES = {
     "mean": (16, 12),      # c 4 + eta in 4 + rev 4 + eta out 4 | rhs 4 + 1/P 4 + d out 4
     "full32": (24, 16),    # A 4 + (P,eta) in 8 + rev 4 + (P,eta) out 8 | diag 4 + rhs 4 + (P,d) out 8
+    # in-place form: A 4 + col 4 + (P,eta) in 8 + out 8 | diag 4 + rhs 4 + totals in 8 + out 8
+    # + monitors in 8 + out 8 (the gathered totals of the senders, an L2-resident n-entry
+    # table, are not counted)
+    "full32_inplace": (24, 40),
     "full64": (44, 24),    # A 8 + (P,eta) in 16 + rev 4 + (P,eta) out 16 | diag 8 + b 8 + x out 8
     "residual": (20, 32),  # A 8 + col 4 + x[col] 8 | diag 8 + x 8 + b 8 + r 8
 }
@@ -330,7 +334,8 @@ def run_gabp(args):
         }
         dom = max(kinds, key=lambda k: kinds[k][0])
         ms_k, n_k = kinds[dom]
-        per_edge, per_node = BYTES[dom]
+        lanes = mixed.tuning()["pull_lanes"]   # FP32 full sweep: 0 = scatter form
+        per_edge, per_node = BYTES["full32_inplace" if dom == "full32" and lanes > 0 else dom]
         bytes_launch = per_edge * E + per_node * m.n
         achieved = bytes_launch * n_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None
         kernel_names = {"mean": "mean_kernel<float> (FP32 mean-only sweep)",
@@ -338,6 +343,15 @@ def run_gabp(args):
                         "residual": "residual64_kernel (FP64 residual)"}
         fp64_ms = statistics.mean(ms_fp64)
         mixed_ms = tot_ms / args.steps
+        # the FP32 full sweep in the form the autotuner kept
+        fe, fn = BYTES["full32_inplace" if lanes > 0 else "full32"]
+        ms_f, n_f = kinds["full32"]
+        full_sweep = {"form": f"in place, {lanes} lanes per row" if lanes > 0 else "scatter",
+                      "us_per_launch": 1e3 * ms_f / max(n_f, 1),
+                      "bytes_per_launch": fe * E + fn * m.n,
+                      "hbm_frac": ((fe * E + fn * m.n) * n_f / (ms_f * 1e-3) / 1e9 / hbm) if ms_f > 0 else None}
+        if lanes > 0:
+            kernel_names["full32"] = "pull32_kernel (FP32 full sweep, in place)"
         line = {
             "metric": METRIC, "value": updates / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_ms,
@@ -365,6 +379,7 @@ def run_gabp(args):
                          "timing": "CUDA events around every kernel in a profiled pass "
                                    "of the same solves (host driver)"},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
+            "full_sweep": full_sweep,
             "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * m.n, "d2h_bytes_per_step": 8 * m.n,
                     "ms_per_step": 1e3 * e2e_s / args.steps},

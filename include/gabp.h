@@ -117,6 +117,14 @@ typedef struct {
                              1 = only those the last colour class sends (schedule = 1 only;
                              in the dense Section VII form: the z -> x^ messages, so the
                              x^ -> z ones are never stored).  The fixed point is the same. */
+  int32_t pull_lanes;     /* CSR form, FP32 full sweeps (mixed modes): -1 = scatter form (each
+                             row sends its messages to the receivers' slots); 2, 4, 8, 16 or 32 =
+                             in-place form with that many lanes per row (each slot recomputes the
+                             reverse message of the previous round from its own row's totals two
+                             rounds back and updates its incoming message; the only random
+                             access is a gather of the sender's node totals); 0 = automatic: the
+                             autotuner times both forms, else the scatter form.  The in-place
+                             form needs the synchronous schedule and no damping. */
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */
@@ -319,7 +327,7 @@ typedef struct {
   int32_t dense_rows_mean;  /* dense form: grid rows loaded ahead per warp, mean sweep */
   int32_t dense_rows_full;  /* dense form: the same, full sweeps */
   int32_t cluster_ctas;     /* small FP64 systems: CTAs of the resident cluster (0 = not used) */
-  int32_t reserved_i;
+  int32_t pull_lanes;       /* CSR form: lanes per row of the in-place FP32 full sweep (0 = scatter form) */
   double tune_ms;           /* host time spent tuning */
   double reserved[3];
 } gabp_tuning;

@@ -196,7 +196,9 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
       g.h_rev[s] = static_cast<int32_t>(slot_of[twin[e]]);
       g.h_user_pos[s] = e;
       a64[s] = val[e];
-      a32[s] = static_cast<float>(val[e]);
+      // the same FP32 value in both slots of a pair (the in-place FP32 sweep
+      // recomputes a message from the other slot's copy of A_ij)
+      a32[s] = static_cast<float>(0.5 * (val[e] + val[twin[e]]));
     }
   }
   // row pointers over slots

@@ -270,6 +270,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
         break;
       }
       c.par_mon ^= 1;
+      c.second = c.first;
       c.first = 0;
       c.sweeps++;
       c.k++;

@@ -93,6 +93,7 @@ struct Ctl {
   int phase;
   int par_m, par_e, par_mon;    // buffer parities: in = buf[par], out = buf[par ^ 1]
   int first;                    // first sweep of an inner solve: incoming messages are zero
+  int second;                   // the sweep after the first one (its round-t-2 messages are zero)
   int write_x;                  // FP64: this sweep writes the tentative means
   int frozen, pending_freeze;
   int k, stall, sweeps, sweeps_full, sweeps_mean, outer, checks, steps;
@@ -128,6 +129,7 @@ struct Buffers {
   float *c32;               // frozen coefficients c_ij (slot s of row i)
   float *invP32;            // frozen 1/P~_i
   float2 *mon32[2];         // (P~_i, d_i) of the last two sweeps
+  float2 *tot32[2];         // in-place FP32 full sweep: (P~_i, h~_i) of the last two rounds
   double *r64;              // FP64 residual
   float *rhs32;             // r_i / ||r|| of the current inner solve
   // multi right-hand sides (K columns, row-major n x K / E x K)
@@ -176,6 +178,8 @@ struct Graph {
   uint8_t *rord = nullptr;
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
+  int pull_lanes = 0;            // FP32 full sweep: 0 = scatter form, else lanes per row of the
+                                 // in-place form (synchronous schedule without damping)
   int tile_slots = 0, tile_rows = 0, heavy_degree = 0;   // row tiles of the FP32 sweeps
   // colour schedule: rows renumbered by colour class; class c holds rows
   // [col_rows[c], col_rows[c+1]) and tiles [col_tiles_*[c], col_tiles_*[c+1])

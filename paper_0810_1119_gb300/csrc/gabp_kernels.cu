@@ -73,6 +73,8 @@ __device__ __forceinline__ V seg_sum(V v, int key, bool &head) {
 // Storage type of the mean messages: FP32, or BF16 with FP32 arithmetic.
 __device__ __forceinline__ float ld_eta(const float *p) { return *p; }
 __device__ __forceinline__ float ld_eta(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void store_eta(float *p, float v) { *p = v; }
+__device__ __forceinline__ void store_eta(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 
 
 // ---------------------------------------------------------------------------
@@ -486,6 +488,135 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   block_max4(widen(mdd), widen(md), widen(mdP), widen(mP), &red->max_dx, &red->max_x,
              &red->max_dP, &red->max_P);
   last_block_control(ctl, red, g.no_control ? 0 : CK_SWEEP32);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 full sweep, in-place form (synchronous schedule, no damping).  The
+// message j -> i of round t depends on the reverse message i -> j of round
+// t - 1, and that one on the node totals of i at round t - 2 and on the
+// message j -> i of round t - 2 -- the value slot s of row i already holds.
+// So each slot recomputes the reverse message instead of receiving it:
+//     P_ij  = -A_ij^2 / (P~_i^(t-2) - P_ji^(t-2)),
+//     eta_ij = -A_ij (h~_i^(t-2) - eta_ji^(t-2)) / (P~_i^(t-2) - P_ji^(t-2)),
+//     P_ji  = -A_ij^2 / (P~_j^(t-1) - P_ij),
+//     eta_ji = -A_ij (h~_j^(t-1) - eta_ij) / (P~_j^(t-1) - P_ij)
+// (Alg. 2 applied twice, with the same expressions as the scatter form), and
+// overwrites slot s with the round-t message.  The round is exactly the
+// synchronous round of Section III-C; the only random access left is the
+// gather of the neighbour's totals (P~_j, h~_j)^(t-1) from an n-entry table,
+// where the scatter form stores every message at a random slot.
+// Buffers (par = par_m): m32[par ^ 1] holds round t - 2 and receives round t
+// in place; tot32[par] holds the totals of round t - 1 (gathered);
+// tot32[par ^ 1] holds this row's totals of round t - 2 and receives round
+// t (only the row's own lane group touches them).  Round 1 starts from zero
+// messages, so its reverse messages are zero and the totals of round 0 are
+// (A_jj, rhs_j); round 2 reads zero round-0 messages.
+// Freeze: c_ij = -A_ij / (P~_i - P_ji) from this round's totals and
+// messages, 1/P~_i, and the mean messages of round t + 1,
+// eta_ij = c_ij (h~_i - eta_ji), sent to the receivers' slots as the scatter
+// form's freeze sends them (once per solve), so that the next mean sweep
+// reports round t + 1.
+// G lanes per row; rows taken grid-stride by groups.
+// ---------------------------------------------------------------------------
+// One message of Alg. 2 from the sender's totals (Tx, Ty) and the reverse
+// message (mx, my): (-a^2 / (Tx - mx), -a (Ty - my) / (Tx - mx)).  Every step
+// is an explicitly rounded operation, so no contraction into a fused
+// multiply-add can make the copy a sender recomputes differ from the copy the
+// receiver stored.  The in-place form needs the two bit for bit: a difference
+// would travel back and forth along the edge with gain (A_ij^2 / (P_{i\j}
+// P_{j\i}))^2 per two rounds, which exceeds one on matrices that are not
+// walk-summable (measured: an indefinite tree of 300 nodes diverged).
+__device__ __forceinline__ float2 message32(float a, float Tx, float Ty, float mx, float my, bool &brk) {
+  const float d = __fsub_rn(Tx, mx);
+  brk |= !(d != 0.0f) || !isfinite(d);
+  const float inv = __fdiv_rn(1.0f, d);
+  return make_float2(__fmul_rn(-__fmul_rn(a, a), inv), __fmul_rn(__fmul_rn(-a, __fsub_rn(Ty, my)), inv));
+}
+
+template <class T, int G>
+__global__ void __launch_bounds__(kBlock)
+pull32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
+  const int pm = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
+  const bool first = ctl->first != 0;
+  const bool second = !first && ctl->second != 0;   // round-0 messages are zero
+  const bool freeze = ctl->pending_freeze != 0;
+  const double inv_rn = ctl->inv_rn;
+  float2 *__restrict__ msg = pm ? B.m32[0] : B.m32[1];
+  const float2 *__restrict__ tot_prev = pm ? B.tot32[1] : B.tot32[0];
+  float2 *__restrict__ tot_own = pm ? B.tot32[0] : B.tot32[1];
+  T *__restrict__ eta_out = static_cast<T *>((pe ? B.e[0] : B.e[1]));
+  const float2 *__restrict__ mon_prev = (pmon ? B.mon32[1] : B.mon32[0]);
+  float2 *__restrict__ mon_out = (pmon ? B.mon32[0] : B.mon32[1]);
+  const int gl = threadIdx.x % G;
+  uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;
+  bool brk = false;
+
+  // rows of the whole grid, G lanes each; every lane of a warp runs the
+  // same number of iterations (the group sums shuffle across the warp)
+  const int64_t groups = static_cast<int64_t>(gridDim.x) * (blockDim.x / G);
+  const int64_t grp0 = static_cast<int64_t>(blockIdx.x) * (blockDim.x / G) + threadIdx.x / G;
+  for (int64_t ib = grp0 - threadIdx.x % 32 / G; ib < g.n; ib += groups) {
+    const int64_t i = ib + threadIdx.x % 32 / G;
+    const bool valid = i < g.n;
+    int32_t rs = 0, re = 0;
+    float dgi = 0.f, rhs = 0.f, TP2 = 0.f, Th2 = 0.f;
+    if (valid) {
+      rs = g.rp[i];
+      re = g.rp[i + 1];
+      dgi = g.diag32[i];
+      rhs = first ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
+      if (second) { TP2 = dgi; Th2 = rhs; }
+      else if (!first) { const float2 t2 = tot_own[i]; TP2 = t2.x; Th2 = t2.y; }
+    }
+    float sP = 0.f, sH = 0.f;
+    for (int32_t s = rs + gl; s < re; s += G) {
+      const int32_t j = g.col[s];
+      const float a = g.a32[s];
+      float2 Tj;
+      if (first) Tj = make_float2(g.diag32[j], static_cast<float>(B.r64[j] * inv_rn));
+      else Tj = tot_prev[j];
+      // the reverse message i -> j of round t - 1 (zero in round 1), exactly
+      // as the receiver j computed and stored it, then the message j -> i
+      float2 r = make_float2(0.f, 0.f);
+      if (!first) {
+        const float2 m = second ? make_float2(0.f, 0.f) : msg[s];
+        r = message32(a, TP2, Th2, m.x, m.y, brk);
+      }
+      const float2 nw = message32(a, Tj.x, Tj.y, r.x, r.y, brk);
+      msg[s] = nw;
+      sP += nw.x;
+      sH += nw.y;
+    }
+    sP = group_sum<G>(sP);
+    sH = group_sum<G>(sH);
+    if (!valid) continue;
+    const float TP = dgi + sP, Th = rhs + sH;
+    if (gl == 0) {
+      tot_own[i] = make_float2(TP, Th);
+      const float2 prev = first ? make_float2(0.f, 0.f) : mon_prev[i];
+      const float di = Th / TP;
+      mon_out[i] = make_float2(TP, di);
+      mdd = fmax_bits(mdd, di - prev.y);
+      md = fmax_bits(md, di);
+      mdP = fmax_bits(mdP, TP - prev.x);
+      mP = fmax_bits(mP, TP);
+      if (freeze) B.invP32[i] = 1.0f / TP;
+      if (first) B.rhs32[i] = rhs;
+    }
+    if (freeze)
+      for (int32_t s = rs + gl; s < re; s += G) {
+        const float2 m = msg[s];      // written above by this thread
+        const float d = TP - m.x;
+        brk |= !(d != 0.0f) || !isfinite(d);
+        const float c = -g.a32[s] * (1.0f / d);
+        B.c32[s] = c;
+        store_eta(eta_out + g.rev[s], c * (Th - m.y));
+      }
+  }
+  if (brk) atomicOr(&red->breakdown, 1);
+  block_max4(widen(mdd), widen(md), widen(mdP), widen(mP), &red->max_dx, &red->max_x,
+             &red->max_dP, &red->max_P);
+  last_block_control(ctl, red, CK_SWEEP32);
 }
 
 // ---------------------------------------------------------------------------
@@ -1128,6 +1259,23 @@ void prepare_group() {
   resident_blocks(sweep64_kernel<G>, 2 * Layout64::bytes, kBlock);
 }
 
+// In-place FP32 full sweep: one wave of resident blocks, rows grid-stride.
+template <int G>
+void launch_pull(const GraphView &v, bool bf16, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
+  if (bf16)
+    launch_tiled(pull32_kernel<__nv_bfloat16, G>, 0, (v.n + kBlock / G - 1) / (kBlock / G), kBlock, st,
+                 v, B, ctl, red);
+  else
+    launch_tiled(pull32_kernel<float, G>, 0, (v.n + kBlock / G - 1) / (kBlock / G), kBlock, st, v, B,
+                 ctl, red);
+}
+
+template <int G>
+void prepare_pull() {
+  resident_blocks(pull32_kernel<float, G>, 0, kBlock);
+  resident_blocks(pull32_kernel<__nv_bfloat16, G>, 0, kBlock);
+}
+
 }  // namespace
 
 int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
@@ -1150,6 +1298,17 @@ int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScal
 
 int launch_sweep32(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                    bool bf16, const GraphView *view) {
+  if (g.pull_lanes > 0 && !view) {
+    const GraphView v = g.view();
+    switch (g.pull_lanes) {
+      case 2: launch_pull<2>(v, bf16, st, B, ctl, red); break;
+      case 4: launch_pull<4>(v, bf16, st, B, ctl, red); break;
+      case 8: launch_pull<8>(v, bf16, st, B, ctl, red); break;
+      case 16: launch_pull<16>(v, bf16, st, B, ctl, red); break;
+      default: launch_pull<32>(v, bf16, st, B, ctl, red); break;
+    }
+    return 1;
+  }
   const GraphView v = view ? *view : g.view();
   GABP_TS_DISPATCH(g, {
     const size_t smem = 2 * Layout32<TSZ>::bytes;
@@ -1264,6 +1423,11 @@ int launch_refine_multi(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, De
 // handle can launch (done at create time, before any graph is recorded).
 void prepare_kernels(int group, bool bf16) {
   num_sms();
+  prepare_pull<2>();
+  prepare_pull<4>();
+  prepare_pull<8>();
+  prepare_pull<16>();
+  prepare_pull<32>();
   switch (group) {
     case 2: prepare_group<2>(); break;
     case 4: prepare_group<4>(); break;

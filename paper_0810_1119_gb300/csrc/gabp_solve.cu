@@ -193,6 +193,7 @@ void ensure32(gabp_handle h) {
   ensure(&B.c32, E);
   ensure(&B.invP32, n);
   ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
+  ensure(&B.tot32[0], n); ensure(&B.tot32[1], n);
   ensure(&B.r64, n);
   ensure(&B.rhs32, n);
   h->have32 = true;
@@ -710,6 +711,7 @@ void release(gabp_handle h) {
   cudaFree(B.m64[0]); cudaFree(B.m64[1]);
   cudaFree(B.m32[0]); cudaFree(B.m32[1]); cudaFree(B.e[0]); cudaFree(B.e[1]);
   cudaFree(B.c32); cudaFree(B.invP32); cudaFree(B.mon32[0]); cudaFree(B.mon32[1]);
+  cudaFree(B.tot32[0]); cudaFree(B.tot32[1]);
   cudaFree(B.r64); cudaFree(B.rhs32);
   cudaFree(h->red); cudaFree(h->ctl);
   cudaFree(h->bbuf); cudaFree(h->xbuf);
@@ -992,6 +994,7 @@ void fill_tuning(gabp_handle h) {
   t.tile_rows = h->g.tile_rows;
   t.heavy_degree = h->g.heavy_degree;
   t.group_lanes = h->g.group;
+  t.pull_lanes = h->g.pull_lanes;
   const bool rows = h->dense && !h->dense->serial;   // the serial kernels take whole rows
   t.dense_rows_mean = rows ? h->dense->rows_mean : 0;
   t.dense_rows_full = rows ? h->dense->rows_full : 0;
@@ -1062,6 +1065,26 @@ void autotune(gabp_handle h) {
       }
     }
     CK(set_row_tiles(g, slots, rows, heavy, h->stream));
+    // form of the FP32 full sweep: scatter (on the tiles just chosen) or
+    // in place with 2..32 lanes per row (synchronous, undamped handles)
+    if (h->opt.pull_lanes == 0 && g.ncol == 0 && h->opt.damping == 0.0) {
+      g.pull_lanes = 0;
+      tuning_ctl(h);
+      float best_f = time_launches(h, 2, [&] { launch_sweep32(g, h->stream, h->buf, h->ctl, h->red, bf16); });
+      int pick = 0;
+      for (int G : {2, 4, 8, 16, 32}) {
+        g.pull_lanes = G;
+        // positive node totals of "earlier rounds" (bytes 0x3F: 0.75f), so
+        // that the timed rounds divide by ordinary numbers
+        CK(cudaMemsetAsync(h->buf.tot32[0], 0x3F, sizeof(float2) * g.n, h->stream));
+        CK(cudaMemsetAsync(h->buf.tot32[1], 0x3F, sizeof(float2) * g.n, h->stream));
+        tuning_ctl(h);
+        const float ms = time_launches(h, 2, [&] { launch_sweep32(g, h->stream, h->buf, h->ctl, h->red, bf16); });
+        ++T.candidates;
+        if (ms < best_f) { best_f = ms; pick = G; }
+      }
+      g.pull_lanes = pick;
+    }
   }
   if (!mixed && h->res.C > 0 && h->opt.cluster_ctas == 0) {
     // cluster size of the one-launch FP64 solve: 64 sweeps each, no early stop
@@ -1200,6 +1223,14 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
     g_create_error = "damp_scope must be 0, or 1 with schedule = 1";
     return GABP_ERR_INVALID_ARG;
   }
+  if (!(o.pull_lanes == -1 || o.pull_lanes == 0 || o.pull_lanes == 2 || o.pull_lanes == 4 ||
+        o.pull_lanes == 8 || o.pull_lanes == 16 || o.pull_lanes == 32) ||
+      (o.pull_lanes > 0 && (o.schedule != 0 || o.damping != 0.0))) {
+    delete h;
+    g_create_error = "pull_lanes must be -1, 0, 2, 4, 8, 16 or 32; the in-place form (> 0) needs "
+                     "schedule 0 and damping 0";
+    return GABP_ERR_INVALID_ARG;
+  }
   h->stream = static_cast<cudaStream_t>(h->opt.stream);
   *out = h;
   return GABP_OK;
@@ -1262,6 +1293,7 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
     });
   }
   if (s == GABP_OK) {
+    if (h->opt.pull_lanes > 0) h->g.pull_lanes = h->opt.pull_lanes;
     fill_tuning(h);
     if (h->opt.autotune) s = guarded(h, [&] { autotune(h); return GABP_OK; });
   }

@@ -162,6 +162,22 @@ def test_damp_scope_is_validated(lib):
         assert "damp_scope" in str(ei.value)
 
 
+def test_pull_lanes_is_validated(lib):
+    """The in-place FP32 full sweep takes 2..32 lanes per row (powers of two)
+    and needs the synchronous schedule without damping; refused on the host."""
+    from paper_0810_1119_gb300 import gabp as G
+    m = W.poisson2d(4)
+    for lanes, damping, schedule in ((3, 0.0, 0), (64, 0.0, 0), (-2, 0.0, 0), (1, 0.0, 0),
+                                     (8, 0.2, 0), (8, 0.0, 1)):
+        o = G.gabp_default_options()
+        o.precision = G.PREC_MIXED_FP32
+        o.pull_lanes, o.damping, o.schedule = lanes, damping, schedule
+        with pytest.raises(G.GabpError) as ei:
+            G.gabp_create(m.row_ptr, m.col, m.val, None, o)
+        assert ei.value.name == "GABP_ERR_INVALID_ARG"
+        assert "pull_lanes" in str(ei.value)
+
+
 def test_grid_create_validates_on_the_host(lib):
     """gabp_create_grid accepts only a nearest-neighbour operator on the box
     given, in natural order, with an even first dimension; every refusal is
