@@ -73,11 +73,13 @@ BYTES_GRID = {
 # + dram__bytes_write.sum per launch; ncu flushes caches between replays, so
 # these are cold-cache figures), valid only for the kernel sources they were
 # taken on: a changed source makes the figure null.  Commands and numbers:
-# profiles/mean_kernel_er1e6.md, profiles/dense_mean_kernel_detect1024.md and
-# profiles/dense_serial_detect1024.md.
+# profiles/mean_kernel_er1e6.md, profiles/pull32_kernel_er1e6.md,
+# profiles/dense_mean_kernel_detect1024.md and profiles/dense_serial_detect1024.md.
 TRAFFIC = {
-    "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "f7f18d076fe46b79",
-             "bytes_per_launch": 174.59e6},
+    "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "63b7797ba9709532",
+             "bytes_per_launch": 175.5e6},
+    "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "63b7797ba9709532",
+                       "bytes_per_launch": 201.25e6},
     "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "ef4785c46d22def4",
                    "bytes_per_pair": 23.05},
     "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "ef4785c46d22def4",
@@ -254,7 +256,7 @@ def run_gabp(args):
     # Launch shapes are picked by the library's autotuner at create time
     # (outside the timed region); the profiled pass reuses the same handle.
     mixed = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32,
-                                 autotune=True, schedule=args.schedule)
+                                 autotune=True, schedule=args.schedule, pull_lanes=args.pull_lanes)
     fp64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64, autotune=True,
                                 schedule=args.schedule)
     stream = torch.cuda.current_stream()
@@ -349,6 +351,7 @@ def run_gabp(args):
         full_sweep = {"form": f"in place, {lanes} lanes per row" if lanes > 0 else "scatter",
                       "us_per_launch": 1e3 * ms_f / max(n_f, 1),
                       "bytes_per_launch": fe * E + fn * m.n,
+                      "traffic": _traffic("full32_inplace") if lanes > 0 else None,
                       "hbm_frac": ((fe * E + fn * m.n) * n_f / (ms_f * 1e-3) / 1e9 / hbm) if ms_f > 0 else None}
         if lanes > 0:
             kernel_names["full32"] = "pull32_kernel (FP32 full sweep, in place)"
@@ -783,6 +786,9 @@ def main():
     ap.add_argument("--damp-scope", type=int, default=0, choices=[0, 1],
                     help="detect with --schedule 1: 0 damp every message, 1 only those the last class sends")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")
+    ap.add_argument("--pull-lanes", type=int, default=0, choices=[-1, 0, 2, 4, 8, 16, 32],
+                    help="er1e6: form of the FP32 full sweep: 0 = autotuned, -1 = scatter, "
+                         "2..32 = in place with that many lanes per row")
     ap.add_argument("--workload", default="er1e6",
                     choices=["er1e6", "multi64", "detect", "poisson32", "poisson3d"],
                     help="er1e6: the headline line; multi64 / detect / poisson32 / poisson3d: extra lines")
