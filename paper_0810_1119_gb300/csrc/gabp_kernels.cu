@@ -534,7 +534,7 @@ __device__ __forceinline__ float2 message32(float a, float Tx, float Ty, float m
 }
 
 template <class T, int G>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 6)
 pull32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const int pm = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
