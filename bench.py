@@ -76,10 +76,10 @@ BYTES_GRID = {
 # profiles/mean_kernel_er1e6.md, profiles/pull32_kernel_er1e6.md,
 # profiles/dense_mean_kernel_detect1024.md and profiles/dense_serial_detect1024.md.
 TRAFFIC = {
-    "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "63b7797ba9709532",
-             "bytes_per_launch": 175.5e6},
-    "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "63b7797ba9709532",
-                       "bytes_per_launch": 201.25e6},
+    "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "b04585fc006c2b3e",
+             "bytes_per_launch": 171.9e6},
+    "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "b04585fc006c2b3e",
+                       "bytes_per_launch": 202.3e6},
     "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "144478a72aeba38c",
                    "bytes_per_pair": 23.05},
     "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "144478a72aeba38c",
