@@ -115,6 +115,30 @@ def _workload(seed_rhs: int):
     return m, b
 
 
+def _scatter_floor_us(m, dev, reps=20):
+    """Device time of one torch index_copy_ that stores the E off-diagonal
+    four-byte values through the workload's reverse-edge permutation: the
+    random scatter a mean sweep makes, with nothing else (warm L2, int64
+    indices).  A reference for the mean sweep's floor, outside the timed
+    region; not the library's code."""
+    import torch
+    from paper_0810_1119_gb300 import workloads as W
+    rev = W.reverse_index(m)
+    r = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    idx = torch.tensor(rev[m.col != r], dtype=torch.int64, device=dev)
+    src = torch.rand(idx.numel(), device=dev)
+    dst = torch.zeros(m.nnz, device=dev)
+    for _ in range(3):
+        dst.index_copy_(0, idx, src)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        dst.index_copy_(0, idx, src)
+    z.record()
+    torch.cuda.synchronize()
+    return 1e3 * a.elapsed_time(z) / reps
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -345,6 +369,7 @@ def run_gabp(args):
                         "residual": "residual64_kernel (FP64 residual)"}
         fp64_ms = statistics.mean(ms_fp64)
         mixed_ms = tot_ms / args.steps
+        scatter_us = _scatter_floor_us(m, dev)
         # the FP32 full sweep in the form the autotuner kept
         fe, fn = BYTES["full32_inplace" if lanes > 0 else "full32"]
         ms_f, n_f = kinds["full32"]
@@ -379,6 +404,7 @@ def run_gabp(args):
                          "peak_source": peak_kind, "traffic": _traffic(dom),
                          "bytes_per_launch": bytes_launch, "launches": n_k,
                          "mean_launch_us": 1e3 * ms_k / max(n_k, 1),
+                         "random_scatter_us": scatter_us,
                          "timing": "CUDA events around every kernel in a profiled pass "
                                    "of the same solves (host driver)"},
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kinds.items()},
