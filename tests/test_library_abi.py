@@ -207,3 +207,32 @@ def test_grid_create_validates_on_the_host(lib):
     with pytest.raises(G.GabpError) as ei:
         G.gabp_create_grid([6, 4], m.row_ptr, m.col, m.val)   # 24 rows expected, 36 given
     assert ei.value.name == "GABP_ERR_INVALID_ARG"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets
+    of the C structures in include/gabp.h (compiled here with the host C
+    compiler), so options, statistics and tuning cross the ABI intact."""
+    import shutil
+    from paper_0810_1119_gb300 import gabp as G
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"gabp_options": G.GabpOptions, "gabp_stats": G.GabpStats, "gabp_tuning": G.GabpTuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gabp.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
