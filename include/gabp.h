@@ -125,6 +125,11 @@ typedef struct {
                              access is a gather of the sender's node totals); 0 = automatic: the
                              autotuner times both forms, else the scatter form.  The in-place
                              form needs the synchronous schedule and no damping. */
+  double pinv_shift;      /* gabp_create_lsq_batched, systems given psi_s = 0: their augmented
+                             matrix is built with Psi_0 = pinv_shift * (mean squared column norm
+                             of S_s) I and the solve iterates to S_s^+ y_s (see there); larger
+                             values make each augmented solve easier for GaBP and the iteration
+                             slower.  0 = 0.1 */
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */
@@ -247,7 +252,19 @@ gabp_status gabp_create_batched(gabp_handle *out, int32_t nsys, const int64_t *s
  * whose first K_s unknowns are x^_s = (S_s^T S_s + psi_s I)^{-1} S_s^T y_s
  * (the MMSE detector of Section VIII-B when psi_s is the noise variance).
  * The handle is a batched handle over the augmented systems (3 K_s rows
- * when N_s = 2 K_s).  Requires K_s, N_s >= 1 and psi_s > 0.
+ * when N_s = 2 K_s).  Requires K_s, N_s >= 1 and psi_s >= 0.
+ *
+ * psi_s = 0 asks for the Moore-Penrose solution x^_s = S_s^+ y_s, the case
+ * Section VII singles out.  GaBP cannot run on the augmented matrix with a
+ * zero Psi (every z node has a zero diagonal), so such a system is built with
+ * Psi_0 = pinv_shift * (mean squared column norm of S_s) I (option
+ * pinv_shift, 0 = 0.1), and gabp_solve_lsq_batched iterates
+ *     x^ <- x^ + (S^T S + Psi_0)^{-1} S^T (y - S x^),
+ * each step one augmented solve with right-hand side [0; y - S x^], until
+ * the normal equations hold: ||S_s^T (y_s - S_s x^_s)||_inf <=
+ * tol ||S_s^T y_s||_inf.  For S_s of full column rank that is S_s^+ y_s; each
+ * step multiplies the error along a singular direction of S_s (singular
+ * value sigma) by psi_0 / (sigma^2 + psi_0).
  */
 gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_t *K_host,
                                     const int32_t *N_host, const double *S_host,
@@ -258,6 +275,13 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
  * y_dev = the y_s concatenated (sum N_s FP64 device values), xhat_dev = the
  * x^_s concatenated (sum K_s values).  The stop rule (per system) is applied
  * to the augmented systems.  *iters as gabp_solve.
+ * If some system was given psi_s = 0, the solve runs the iteration described
+ * at gabp_create_lsq_batched; tol then also bounds the normal-equation
+ * residual of those systems.  *iters and the statistics sum the sweeps of
+ * all augmented solves, outer_steps counts them, and residual / rhs_norm
+ * are ||S^T (y - S x^)||_inf / ||S^T y||_inf of the system furthest from
+ * its rule.  GABP_ERR_NOT_CONVERGED after max_iter sweeps or 500 augmented
+ * solves; the status of a failed augmented solve otherwise.
  */
 gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *xhat_dev, double tol,
                                    int32_t max_iter, int32_t *iters);

@@ -14,6 +14,10 @@ Contents
 * ``residual_inf``  -- ||b - A x||_inf (Section II, residual definition).
 * ``augment_lsq``   -- the symmetric augmented system of Section VII
                        (``augment.py``).
+* ``pinv_solution``, ``iterated_tikhonov`` -- Section VII with Psi = 0: the
+                       Moore-Penrose solution, and the iteration that reaches
+                       it through augmented solves with Psi_0 > 0
+                       (``augment.py``).
 * ``gabp_serial``   -- the serial schedule of Section III-C over a given node
                        order (``greedy_colouring`` gives colour classes).
 * ``aitken``, ``gabp_aitken`` -- Aitken's Delta^2 extrapolation of the
@@ -33,7 +37,7 @@ import threading
 
 import numpy as np
 
-from .augment import augment_lsq  # noqa: F401
+from .augment import augment_lsq, iterated_tikhonov, pinv_solution  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gabp_oracle.c")

@@ -54,3 +54,29 @@ def augment_lsq(S, psi_diag, y):
     row_ptr = np.cumsum(row_ptr)
     rhs = np.concatenate([np.zeros(K), y])
     return row_ptr, cols, vals, rhs
+
+
+def pinv_solution(S, y):
+    """Section VII with Psi = 0: the Moore-Penrose solution x^ = S^+ y, which
+    the section states as the zero-noise case of its closed form.  Written as
+    the definition: the minimum-norm minimiser of ||y - S x||_2, through
+    LAPACK (numpy.linalg.lstsq)."""
+    S = np.asarray(S, dtype=np.float64)
+    return np.linalg.lstsq(S, np.asarray(y, dtype=np.float64), rcond=None)[0]
+
+
+def iterated_tikhonov(S, y, psi0, steps):
+    """The route the library takes to Psi = 0, where GaBP cannot run on the
+    augmented matrix (its z nodes would have a zero diagonal): from x^ = 0,
+    ``steps`` times x^ <- x^ + (S^T S + psi0 I)^{-1} S^T (y - S x^), each step
+    the Section VII closed form with Psi = psi0 I and right-hand side
+    y - S x^.  Returns the iterates x^_1 .. x^_steps (rows)."""
+    S = np.asarray(S, dtype=np.float64)
+    K = S.shape[1]
+    M = S.T @ S + psi0 * np.eye(K)
+    x = np.zeros(K)
+    out = []
+    for _ in range(steps):
+        x = x + np.linalg.solve(M, S.T @ (np.asarray(y, dtype=np.float64) - S @ x))
+        out.append(x.copy())
+    return np.array(out)

@@ -417,6 +417,21 @@ gabp_status build_graph(Graph &g, int64_t n, int64_t nnz, const int64_t *row_ptr
 gabp_status build_systems(Graph &g, int32_t nsys, const int64_t *sys_row_off,
                           const int64_t *row_ptr, const int32_t *col, cudaStream_t st,
                           std::string *msg);
+// Section VII systems with Psi = 0 (gabp_pinv.cu): u = offdiag(R~) v on the CSR
+// or the dense form, v = [x^; 0], [0; y - S x^] for flagged systems, x^ +=
+// (scaled) x^ part of an augmented solution, per-system max |u| over the x^ rows.
+int launch_csr_offdiag(const Graph &g, cudaStream_t st, const double *v, double *u);
+int launch_dense_offdiag(const Dense &d, cudaStream_t st, const double *v, double *u);
+int launch_pinv_embed(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row, const int64_t *aug_off,
+                      const int32_t *K, const int64_t *x_off, const double *xhat, double *v);
+int launch_pinv_rhs(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row, const int64_t *aug_off,
+                    const int32_t *K, const int64_t *y_off, const double *y, const double *u,
+                    const uint8_t *flag, double *rhs);
+int launch_pinv_update(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row, const int64_t *aug_off,
+                       const int32_t *K, const int64_t *x_off, const double *scale, const double *x_aug,
+                       double *xhat);
+int launch_pinv_sysmax(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row, const int64_t *aug_off,
+                       const int32_t *K, const double *u, unsigned long long *smax);
 int launch_lsq_rhs(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row,
                    const int64_t *aug_off, const int32_t *K, const int64_t *y_off, const double *y,
                    double *rhs);
@@ -455,6 +470,12 @@ struct gabp_s {
   int64_t *lsq_x_off = nullptr;        // device: offset of x^_s in the concatenated x^
   int64_t lsq_ny = 0, lsq_nx = 0;      // total lengths of y and x^
   double *lsq_rhs = nullptr, *lsq_x = nullptr;   // device: augmented rhs and solution
+  // systems given psi_s = 0 (the Moore-Penrose solution): iterated around the augmented solve
+  std::vector<uint8_t> lsq_pinv_host;  // per system: 1 = psi_s was 0
+  uint8_t *lsq_pinv = nullptr;         // device copy
+  double *lsq_inv_psi0 = nullptr;      // device: 1 / psi_0 of those systems, 0 for the others
+  double *lsq_u = nullptr, *lsq_v = nullptr;     // device: augmented work vectors
+  unsigned long long *lsq_gmax = nullptr;        // device: per-system max |S^T r| (bit patterns)
   int graph_K = 0;                     // K the CTL_MULTI graph was recorded for
   size_t capK = 0;                     // columns the multi buffers hold
   gabp::MultiCols cols{};              // device per-column arrays (capK each)

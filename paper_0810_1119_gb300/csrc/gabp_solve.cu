@@ -24,6 +24,7 @@
 #include "gabp_internal.h"
 
 #include <algorithm>
+#include <cfloat>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -587,6 +588,114 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
   return report(h, mixed ? "mixed solve" : "FP64 solve");
 }
 
+// Section VII systems given psi_s = 0 (the Moore-Penrose solution; the
+// reading and the kernels are in gabp_pinv.cu): iterated Tikhonov around the
+// augmented solve.  Step 0 solves every system with [0; y]; from then on
+// only the psi_s = 0 systems go on, with [S^T (y - S x^); 0] and the x^ part
+// scaled by 1 / psi_0 (the others get a zero right-hand side, so their
+// solutions stay as step 0 left them).  Ends when
+// every such system has ||S^T (y - S x^)||_inf <= tol ||S^T y||_inf, with
+// GABP_ERR_NOT_CONVERGED when the sweeps reach max_iter or the steps
+// kPinvSteps, or with the status of a failed augmented solve.  Statistics:
+// sweeps, checks and launches summed over the augmented solves; outer_steps =
+// their number; residual / rhs_norm = the largest ||S^T (y - S x^)||_inf /
+// ||S^T y||_inf of the psi_s = 0 systems.
+constexpr int kPinvSteps = 500;
+
+gabp_status lsq_pinv_solve(gabp_handle h, const double *y, double *xhat, double tol, int32_t max_iter,
+                           int32_t *iters) {
+  cudaStream_t st = h->stream;
+  const int64_t n = h->g.n;
+  const int32_t nsys = h->g.nsys;
+  const int32_t *sor = h->g.sys_of_row;
+  ensure(&h->lsq_u, n);
+  ensure(&h->lsq_v, n);
+  ensure(&h->lsq_gmax, nsys);
+  std::vector<unsigned long long> gbits(nsys);
+  auto offdiag = [&](const double *v, double *u) {
+    if (h->dense) launch_dense_offdiag(*h->dense, st, v, u);
+    else launch_csr_offdiag(h->g, st, v, u);
+  };
+  auto sysmax = [&](const double *u, std::vector<double> &out) {
+    CK(cudaMemsetAsync(h->lsq_gmax, 0, sizeof(unsigned long long) * nsys, st));
+    launch_pinv_sysmax(st, n, sor, h->lsq_aug_off, h->lsq_K, u, h->lsq_gmax);
+    CK(cudaMemcpyAsync(gbits.data(), h->lsq_gmax, sizeof(unsigned long long) * nsys,
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out.resize(nsys);
+    for (int32_t q = 0; q < nsys; ++q) out[q] = bits_to_double(gbits[q]);
+  };
+  // ||S^T y|| per system, and the first right-hand side [0; y]
+  launch_lsq_rhs(st, n, sor, h->lsq_aug_off, h->lsq_K, h->lsq_y_off, y, h->lsq_rhs);
+  offdiag(h->lsq_rhs, h->lsq_u);
+  std::vector<double> g0, g;
+  sysmax(h->lsq_u, g0);
+  CK(cudaMemsetAsync(xhat, 0, sizeof(double) * h->lsq_nx, st));
+  gabp_stats sum{};
+  int64_t launches = 4;
+  gabp_status status = GABP_ERR_NOT_CONVERGED;
+  std::string why = "lsq solve: " + std::to_string(kPinvSteps) + " augmented solves";
+  double worst = 0.0, worst_ref = 0.0;
+  int steps = 0;
+  while (steps < kPinvSteps && sum.sweeps_total < max_iter) {
+    int32_t it = 0;
+    const gabp_status s = solve_impl(h, h->lsq_rhs, h->lsq_x, tol, max_iter - sum.sweeps_total, &it);
+    ++steps;
+    sum.sweeps_total += h->stats.sweeps_total;
+    sum.sweeps_full += h->stats.sweeps_full;
+    sum.sweeps_mean += h->stats.sweeps_mean;
+    sum.residual_checks += h->stats.residual_checks;
+    launches += h->stats.kernel_launches;
+    if (s != GABP_OK) {
+      status = s;
+      why = h->last_error;
+      break;
+    }
+    // the first solve is x^ itself; a later one, from [g; 0], is psi_0 times the step
+    launch_pinv_update(st, n, sor, h->lsq_aug_off, h->lsq_K, h->lsq_x_off,
+                       steps == 1 ? nullptr : h->lsq_inv_psi0, h->lsq_x, xhat);
+    // g = S^T (y - S x^) of the psi_s = 0 systems (zero for the others): the
+    // stop rule's residual and, as [g; 0], the next right-hand side
+    launch_pinv_embed(st, n, sor, h->lsq_aug_off, h->lsq_K, h->lsq_x_off, xhat, h->lsq_v);
+    offdiag(h->lsq_v, h->lsq_u);
+    launch_pinv_rhs(st, n, sor, h->lsq_aug_off, h->lsq_K, h->lsq_y_off, y, h->lsq_u, h->lsq_pinv,
+                    h->lsq_v);
+    offdiag(h->lsq_v, h->lsq_rhs);
+    sysmax(h->lsq_rhs, g);
+    launches += 6;
+    bool done = true;
+    worst = worst_ref = 0.0;
+    for (int32_t q = 0; q < nsys; ++q) {
+      if (!h->lsq_pinv_host[q]) continue;
+      if (g0[q] > 0.0 && g[q] > tol * g0[q]) done = false;   // S^T y = 0: x^ = 0 from step 0
+      if (g0[q] > 0.0 && g[q] / g0[q] >= worst / std::max(worst_ref, DBL_MIN)) {
+        worst = g[q];
+        worst_ref = g0[q];
+      }
+    }
+    if (done) {
+      status = GABP_OK;
+      break;
+    }
+    why = "lsq solve: normal-equation residual " + std::to_string(worst) + " of " +
+          std::to_string(worst_ref) + " after " + std::to_string(steps) + " augmented solves";
+  }
+  sum.outer_steps = steps;
+  sum.status = status;
+  sum.residual = worst;
+  sum.rhs_norm = worst_ref;
+  sum.n = h->g.n;
+  sum.edges = h->g.E;
+  sum.kernel_launches = launches;
+  sum.ms_full = h->stats.ms_full;
+  sum.ms_mean = h->stats.ms_mean;
+  sum.ms_residual = h->stats.ms_residual;
+  sum.ms_other = h->stats.ms_other;
+  h->stats = sum;
+  if (iters) *iters = sum.sweeps_total;
+  return status == GABP_OK ? GABP_OK : fail(h, status, why);
+}
+
 void ensure_multi(gabp_handle h, int K) {
   if (h->capK >= static_cast<size_t>(K)) return;
   Buffers &B = h->buf;
@@ -718,6 +827,8 @@ void release(gabp_handle h) {
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   cudaFree(h->lsq_K); cudaFree(h->lsq_aug_off); cudaFree(h->lsq_y_off); cudaFree(h->lsq_x_off);
   cudaFree(h->lsq_rhs); cudaFree(h->lsq_x);
+  cudaFree(h->lsq_pinv); cudaFree(h->lsq_inv_psi0); cudaFree(h->lsq_u); cudaFree(h->lsq_v);
+  cudaFree(h->lsq_gmax);
   if (h->dense) {
     DenseView &v = h->dense->v;
     for (int k = 0; k < 2; ++k) {
@@ -1372,10 +1483,37 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
     return GABP_ERR_INVALID_ARG;
   }
   for (int32_t s = 0; s < nsys; ++s)
-    if (K_host[s] < 1 || N_host[s] < 1 || !(psi_host[s] > 0.0) || !std::isfinite(psi_host[s])) {
-      g_create_error = "gabp_create_lsq_batched: K_s, N_s >= 1 and psi_s > 0 required";
+    if (K_host[s] < 1 || N_host[s] < 1 || !(psi_host[s] >= 0.0) || !std::isfinite(psi_host[s])) {
+      g_create_error = "gabp_create_lsq_batched: K_s, N_s >= 1 and psi_s >= 0 required";
       return GABP_ERR_INVALID_ARG;
     }
+  const double shift = opt ? opt->pinv_shift : 0.0;
+  if (!(shift >= 0.0) || !std::isfinite(shift)) {
+    g_create_error = "gabp_create_lsq_batched: pinv_shift must be finite and >= 0";
+    return GABP_ERR_INVALID_ARG;
+  }
+  // psi_s = 0 (the Moore-Penrose solution): the augmented matrix is built with
+  // psi_0 = shift * (mean squared column norm of S_s) and the solve iterates
+  // around it; every other system keeps its psi_s
+  std::vector<double> psi_eff(psi_host, psi_host + nsys);
+  std::vector<uint8_t> pinv(nsys, 0);
+  bool any_pinv = false;
+  {
+    int64_t off = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+      const int64_t cnt = static_cast<int64_t>(K_host[s]) * N_host[s];
+      if (psi_host[s] == 0.0) {
+        double ss = 0.0;
+        for (int64_t p = 0; p < cnt; ++p) ss += S_host[off + p] * S_host[off + p];
+        const double col2 = ss / K_host[s];
+        psi_eff[s] = (shift > 0.0 ? shift : 0.1) * (col2 > 0.0 ? col2 : 1.0);
+        pinv[s] = 1;
+        any_pinv = true;
+      }
+      off += cnt;
+    }
+  }
+  psi_host = psi_eff.data();
   bool dense = !opt || opt->lsq_form == 0;
   for (int32_t s = 0; s < nsys && dense; ++s)
     dense = K_host[s] <= kDenseMaxK && N_host[s] <= kDenseMaxN;
@@ -1424,6 +1562,18 @@ gabp_status gabp_create_lsq_batched(gabp_handle *out, int32_t nsys, const int32_
     if (s != GABP_OK) return s;
   }
   s = guarded(h, [&] {
+    h->lsq_pinv_host = pinv;
+    if (any_pinv) {
+      std::vector<double> inv_psi0(nsys, 0.0);
+      for (int32_t q = 0; q < nsys; ++q)
+        if (pinv[q]) inv_psi0[q] = 1.0 / psi_eff[q];
+      ensure(&h->lsq_pinv, nsys);
+      ensure(&h->lsq_inv_psi0, nsys);
+      CK(cudaMemcpyAsync(h->lsq_pinv, pinv.data(), nsys, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->lsq_inv_psi0, inv_psi0.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
     std::vector<int64_t> y_off(nsys + 1, 0), x_off(nsys + 1, 0);
     for (int32_t k = 0; k < nsys; ++k) {
       y_off[k + 1] = y_off[k] + N_host[k];
@@ -1503,6 +1653,7 @@ gabp_status gabp_solve_lsq_batched(gabp_handle h, const double *y_dev, double *x
     return fail(h, GABP_ERR_INVALID_ARG, "gabp_solve_lsq_batched: invalid argument");
   return guarded(h, [&] {
     cudaStream_t st = h->stream;
+    if (h->lsq_pinv) return lsq_pinv_solve(h, y_dev, xhat_dev, tol, max_iter, iters);
     launch_lsq_rhs(st, h->g.n, h->g.sys_of_row, h->lsq_aug_off, h->lsq_K, h->lsq_y_off, y_dev,
                    h->lsq_rhs);
     const gabp_status s = solve_impl(h, h->lsq_rhs, h->lsq_x, tol, max_iter, iters);

@@ -50,7 +50,8 @@ class GabpOptions(ctypes.Structure):
                 ("heavy_degree", ctypes.c_int32), ("dense_rows", ctypes.c_int32),
                 ("small_form", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
                 ("aitken", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("damp_scope", ctypes.c_int32), ("pull_lanes", ctypes.c_int32)]
+                ("damp_scope", ctypes.c_int32), ("pull_lanes", ctypes.c_int32),
+                ("pinv_shift", ctypes.c_double)]
 
 
 class GabpStats(ctypes.Structure):
@@ -231,7 +232,8 @@ def gabp_create_grid(dims, row_ptr, col, val, options: GabpOptions | None = None
 
 def gabp_create_lsq_batched(S_list, psi, options: GabpOptions | None = None):
     """Create a least-squares batch (Section VII augmented systems) from a list
-    of dense S_s (N_s x K_s) and noise variances psi_s (scalar or list)."""
+    of dense S_s (N_s x K_s) and noise variances psi_s (scalar or list); psi_s
+    = 0 asks for the Moore-Penrose solution S_s^+ y_s."""
     lib = load()
     K = np.ascontiguousarray([S.shape[1] for S in S_list], dtype=np.int32)
     N = np.ascontiguousarray([S.shape[0] for S in S_list], dtype=np.int32)

@@ -107,11 +107,21 @@ def test_create_batched_rejects_coupled_systems(lib):
 
 
 def test_create_lsq_batched_rejects_bad_noise(lib):
+    """psi_s must be finite and >= 0 (0 asks for the Moore-Penrose solution),
+    pinv_shift finite and >= 0; refused on the host before any device work."""
     from paper_0810_1119_gb300 import gabp
     S = np.ones((4, 2)) / 2.0
-    with pytest.raises(gabp.GabpError) as ei:
-        gabp.gabp_create_lsq_batched([S], 0.0)
-    assert ei.value.name == "GABP_ERR_INVALID_ARG"
+    for psi in (-0.1, float("nan"), float("inf")):
+        with pytest.raises(gabp.GabpError) as ei:
+            gabp.gabp_create_lsq_batched([S], psi)
+        assert ei.value.name == "GABP_ERR_INVALID_ARG"
+        assert "psi_s >= 0" in str(ei.value)
+    for shift in (-1.0, float("nan")):
+        o = gabp.gabp_default_options()
+        o.pinv_shift = shift
+        with pytest.raises(gabp.GabpError) as ei:
+            gabp.gabp_create_lsq_batched([S], 0.0, o)
+        assert "pinv_shift" in str(ei.value)
 
 
 def test_launch_shape_options_are_validated():

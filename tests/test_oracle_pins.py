@@ -256,6 +256,68 @@ def test_augmented_system_closed_form(K):
 
 
 # --------------------------------------------------------------------------
+# Section VII with Psi = 0: the Moore-Penrose solution, and the iteration
+# that reaches it through augmented solves with Psi_0 > 0.
+# --------------------------------------------------------------------------
+def _rect(N, K, seed):
+    rng = np.random.default_rng(seed)
+    return rng.choice([-1.0, 1.0], size=(N, K)) / np.sqrt(N), rng.standard_normal(N)
+
+
+@pytest.mark.parametrize("N,K", [(8, 3), (40, 16), (64, 16)])
+def test_pinv_solution_meets_the_normal_equations(N, K):
+    S, y = _rect(N, K, N + K)
+    x = oracle.pinv_solution(S, y)
+    g = S.T @ (y - S @ x)                    # normal equations S^T (y - S x) = 0
+    assert np.abs(g).max() <= 1e-12 * np.abs(S.T @ y).max()
+    # full column rank: (S^T S)^{-1} S^T y, the formula the section prints
+    np.testing.assert_allclose(x, np.linalg.solve(S.T @ S, S.T @ y), rtol=1e-10, atol=1e-12)
+    # the zero-noise limit of the closed form (S^T S + psi I)^{-1} S^T y
+    for psi, tol in ((1e-6, 1e-4), (1e-9, 1e-7)):
+        closed = np.linalg.solve(S.T @ S + psi * np.eye(K), S.T @ y)
+        assert np.abs(closed - x).max() <= tol * np.abs(x).max()
+
+
+def test_pinv_solution_of_a_square_system_is_the_inverse():
+    """Section VII covers square nonsymmetric matrices too: S^+ = S^{-1}."""
+    rng = np.random.default_rng(5)
+    S = np.eye(6) + 0.3 * rng.standard_normal((6, 6))
+    y = rng.standard_normal(6)
+    np.testing.assert_allclose(oracle.pinv_solution(S, y), np.linalg.solve(S, y), rtol=1e-11)
+
+
+def test_pinv_solution_of_a_rank_deficient_system_has_minimum_norm():
+    """Two equal columns: every x with x_0 + x_1 fixed fits equally well; the
+    pseudoinverse takes the one of minimum norm, x_0 = x_1."""
+    rng = np.random.default_rng(6)
+    c, d = rng.standard_normal(7), rng.standard_normal(7)
+    S = np.stack([c, c, d], axis=1)
+    y = rng.standard_normal(7)
+    x = oracle.pinv_solution(S, y)
+    assert abs(x[0] - x[1]) <= 1e-12 * np.abs(x).max()
+    np.testing.assert_allclose(np.abs(S.T @ (y - S @ x)).max(), 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("psi0", [0.02, 0.1, 0.5])
+def test_iterated_tikhonov_reaches_the_pinv_at_the_predicted_rate(psi0):
+    """x^_k - S^+ y = (psi0 (S^T S + psi0 I)^{-1})^k (0 - S^+ y): the error
+    along each right singular vector shrinks by psi0 / (sigma^2 + psi0) per
+    step, so after k steps it is at most rho^k |S^+ y| with rho the largest
+    such factor, and the first step is the Section VII closed form."""
+    S, y = _rect(48, 16, 3)
+    xs = oracle.pinv_solution(S, y)
+    sig2 = np.linalg.svd(S, compute_uv=False) ** 2
+    rho = (psi0 / (sig2 + psi0)).max()
+    it = oracle.iterated_tikhonov(S, y, psi0, 30)
+    np.testing.assert_allclose(it[0], np.linalg.solve(S.T @ S + psi0 * np.eye(16), S.T @ y), rtol=1e-12)
+    for k in (1, 5, 10, 30):
+        err = np.linalg.norm(it[k - 1] - xs)
+        assert err <= rho ** k * np.linalg.norm(xs) * (1 + 1e-9) + 1e-13, (k, err)
+    # the bound is attained in the slowest direction, not just an upper bound
+    assert np.linalg.norm(it[9] - xs) >= 0.1 * rho ** 10 * np.abs(np.linalg.svd(S)[2][-1] @ xs)
+
+
+# --------------------------------------------------------------------------
 # Residual helper, input validation and breakdown.
 # --------------------------------------------------------------------------
 def test_residual_inf_matches_dense():
