@@ -70,3 +70,66 @@ def test_planted_mistake_is_caught(name, tmp_path):
     assert src.count(old) >= 1, f"mutation anchor for {name} not found"
     lib = oracle.compile_variant(src.replace(old, new, 1), str(tmp_path / f"{name}.so"))
     assert not _pins_hold(lib)
+
+
+# Section VII with Psi = 0 (oracle/augment.py): the same kind of plausible
+# mistakes planted in the Python source of pinv_solution / iterated_tikhonov,
+# and the facts test_oracle_pins.py pins them to (the normal equations, the
+# square inverse, the predicted contraction rate, the closed form as step 1).
+PINV_MUTANTS = {
+    "residual_sign": ("S.T @ (np.asarray(y, dtype=np.float64) - S @ x)",
+                      "S.T @ (np.asarray(y, dtype=np.float64) + S @ x)"),
+    "no_accumulation": ("x = x + np.linalg.solve(M, ", "x = np.linalg.solve(M, "),
+    "shift_on_the_wrong_gram": ("M = S.T @ S + psi0 * np.eye(K)",
+                                "M = S.T @ S[:K, :K].T + psi0 * np.eye(K)"),
+    "regularised_not_pinv": ("return np.linalg.lstsq(S, np.asarray(y, dtype=np.float64), rcond=None)[0]",
+                             "return np.linalg.solve(S.T @ S + 1e-3 * np.eye(S.shape[1]), S.T @ y)"),
+    "transposed_operand": ("return np.linalg.lstsq(S, np.asarray(y, dtype=np.float64), rcond=None)[0]",
+                           "return np.linalg.lstsq(S.T @ S, np.asarray(y, dtype=np.float64)[:S.shape[1]], rcond=None)[0]"),
+}
+
+
+def _pinv_namespace(src):
+    ns = {}
+    exec(compile(src, "augment_mutant.py", "exec"), ns)
+    return ns
+
+
+def _pinv_pins_hold(ns) -> bool:
+    try:
+        rng = np.random.default_rng(3)
+        S = rng.choice([-1.0, 1.0], size=(48, 16)) / np.sqrt(48)
+        y = rng.standard_normal(48)
+        x = ns["pinv_solution"](S, y)
+        if np.abs(S.T @ (y - S @ x)).max() > 1e-12 * np.abs(S.T @ y).max():
+            return False
+        Sq = np.eye(6) + 0.3 * rng.standard_normal((6, 6))
+        yq = rng.standard_normal(6)
+        if not np.allclose(ns["pinv_solution"](Sq, yq), np.linalg.solve(Sq, yq), rtol=1e-10):
+            return False
+        xs = np.linalg.solve(S.T @ S, S.T @ y)
+        psi0 = 0.1
+        rho = (psi0 / (np.linalg.svd(S, compute_uv=False) ** 2 + psi0)).max()
+        it = ns["iterated_tikhonov"](S, y, psi0, 20)
+        if not np.allclose(it[0], np.linalg.solve(S.T @ S + psi0 * np.eye(16), S.T @ y), rtol=1e-12):
+            return False
+        return all(np.linalg.norm(it[k - 1] - xs) <= rho ** k * np.linalg.norm(xs) * (1 + 1e-9) + 1e-13
+                   for k in (1, 5, 20))
+    except Exception:   # a mutant that does not even run is caught too
+        return False
+
+
+def test_pinv_pins_hold_for_the_oracle():
+    import inspect
+    from oracle import augment
+    assert _pinv_pins_hold(_pinv_namespace(inspect.getsource(augment)))
+
+
+@pytest.mark.parametrize("name", sorted(PINV_MUTANTS))
+def test_pinv_pins_catch_mutant(name):
+    import inspect
+    from oracle import augment
+    src = inspect.getsource(augment)
+    old, new = PINV_MUTANTS[name]
+    assert src.count(old) == 1, name
+    assert not _pinv_pins_hold(_pinv_namespace(src.replace(old, new)))
