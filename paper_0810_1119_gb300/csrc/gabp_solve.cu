@@ -597,7 +597,8 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
 // every such system has ||S^T (y - S x^)||_inf <= tol ||S^T y||_inf, with
 // GABP_ERR_NOT_CONVERGED when the sweeps reach max_iter or the steps
 // kPinvSteps, or with the status of a failed augmented solve.  Statistics:
-// sweeps, checks and launches summed over the augmented solves; outer_steps =
+// sweeps, checks, launches and profiled kernel times summed over the
+// augmented solves; outer_steps =
 // their number; residual / rhs_norm = the largest ||S^T (y - S x^)||_inf /
 // ||S^T y||_inf of the psi_s = 0 systems.
 constexpr int kPinvSteps = 500;
@@ -645,6 +646,10 @@ gabp_status lsq_pinv_solve(gabp_handle h, const double *y, double *xhat, double 
     sum.sweeps_full += h->stats.sweeps_full;
     sum.sweeps_mean += h->stats.sweeps_mean;
     sum.residual_checks += h->stats.residual_checks;
+    sum.ms_full += h->stats.ms_full;
+    sum.ms_mean += h->stats.ms_mean;
+    sum.ms_residual += h->stats.ms_residual;
+    sum.ms_other += h->stats.ms_other;
     launches += h->stats.kernel_launches;
     if (s != GABP_OK) {
       status = s;
@@ -687,10 +692,6 @@ gabp_status lsq_pinv_solve(gabp_handle h, const double *y, double *xhat, double 
   sum.n = h->g.n;
   sum.edges = h->g.E;
   sum.kernel_launches = launches;
-  sum.ms_full = h->stats.ms_full;
-  sum.ms_mean = h->stats.ms_mean;
-  sum.ms_residual = h->stats.ms_residual;
-  sum.ms_other = h->stats.ms_other;
   h->stats = sum;
   if (iters) *iters = sum.sweeps_total;
   return status == GABP_OK ? GABP_OK : fail(h, status, why);
