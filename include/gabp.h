@@ -130,6 +130,13 @@ typedef struct {
                              of S_s) I and the solve iterates to S_s^+ y_s (see there); larger
                              values make each augmented solve easier for GaBP and the iteration
                              slower.  0 = 0.1 */
+  int32_t naive;          /* 1 = FP64 sweeps by Algorithm 1, the naive form: every cavity sum
+                             P_{i\j} = A_ii + sum_{k != j} P_ki (and its information part) is
+                             added up over the other incoming messages directly, O(deg^2) per
+                             row, instead of node total minus reverse message (Algorithm 2).
+                             The same round without that cancellation, for cross-checks on
+                             small systems.  CSR handles, FP64, schedule 0, no damping;
+                             0 = Algorithm 2 */
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */

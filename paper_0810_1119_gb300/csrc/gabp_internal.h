@@ -178,6 +178,7 @@ struct Graph {
   uint8_t *rord = nullptr;
   int32_t ntiles_big = 0, ntiles_small = 0;
   int group = 8;                 // lanes per row in the sweep kernels
+  bool naive = false;            // FP64 sweep: Algorithm 1 (cavity sums taken directly)
   int pull_lanes = 0;            // FP32 full sweep: 0 = scatter form, else lanes per row of the
                                  // in-place form (synchronous schedule without damping)
   int tile_slots = 0, tile_rows = 0, heavy_degree = 0;   // row tiles of the FP32 sweeps

@@ -1216,7 +1216,7 @@ void autotune(gabp_handle h) {
     }
     if (!build_resident(h, pick)) free_resident(h->res);
   }
-  if (h->dense || mixed) {
+  if (h->dense || mixed || g.naive) {   // (Algorithm 1 has no lanes to tune)
   } else if (h->opt.group_lanes == 0) {
     ensure64(h);
     float best = 1e30f;
@@ -1335,6 +1335,12 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
     g_create_error = "damp_scope must be 0, or 1 with schedule = 1";
     return GABP_ERR_INVALID_ARG;
   }
+  if (!(o.naive == 0 || o.naive == 1) ||
+      (o.naive == 1 && (o.schedule != 0 || o.damping != 0.0 || o.precision != GABP_PREC_FP64))) {
+    delete h;
+    g_create_error = "naive must be 0 or 1; Algorithm 1 (naive = 1) needs FP64, schedule 0 and damping 0";
+    return GABP_ERR_INVALID_ARG;
+  }
   if (!(o.pull_lanes == -1 || o.pull_lanes == 0 || o.pull_lanes == 2 || o.pull_lanes == 4 ||
         o.pull_lanes == 8 || o.pull_lanes == 16 || o.pull_lanes == 32) ||
       (o.pull_lanes > 0 && (o.schedule != 0 || o.damping != 0.0))) {
@@ -1400,12 +1406,13 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
   });
   if (s == GABP_OK) {
     s = guarded(h, [&] {
-      if (h->opt.precision == GABP_PREC_FP64) setup_resident(h);
+      if (h->opt.precision == GABP_PREC_FP64 && !h->opt.naive) setup_resident(h);
       return GABP_OK;
     });
   }
   if (s == GABP_OK) {
     if (h->opt.pull_lanes > 0) h->g.pull_lanes = h->opt.pull_lanes;
+    h->g.naive = h->opt.naive == 1;
     fill_tuning(h);
     if (h->opt.autotune) s = guarded(h, [&] { autotune(h); return GABP_OK; });
   }

@@ -188,6 +188,20 @@ def test_pull_lanes_is_validated(lib):
         assert "pull_lanes" in str(ei.value)
 
 
+def test_naive_is_validated(lib):
+    """Algorithm 1 (naive = 1) needs FP64, the synchronous schedule and no
+    damping; refused on the host."""
+    from paper_0810_1119_gb300 import gabp as G
+    m = W.poisson2d(4)
+    for naive, prec, schedule, damping in ((2, 0, 0, 0.0), (-1, 0, 0, 0.0), (1, 1, 0, 0.0),
+                                          (1, 0, 1, 0.0), (1, 0, 0, 0.2)):
+        o = G.gabp_default_options()
+        o.naive, o.precision, o.schedule, o.damping = naive, prec, schedule, damping
+        with pytest.raises(G.GabpError) as ei:
+            G.gabp_create(m.row_ptr, m.col, m.val, None, o)
+        assert "naive" in str(ei.value)
+
+
 def test_grid_create_validates_on_the_host(lib):
     """gabp_create_grid accepts only a nearest-neighbour operator on the box
     given, in natural order, with an even first dimension; every refusal is
