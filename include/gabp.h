@@ -366,6 +366,21 @@ typedef struct {
 gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning);
 
 /*
+ * Diagnostics, no counterpart in the paper.  Every wait inside the library's
+ * kernels (the shared-memory staging of the sweeps) is bounded: after a fixed
+ * number of polls it gives up, the launch raises a flag, and the solve ends
+ * with GABP_ERR_TIMEOUT instead of hanging the device.  This call exercises
+ * that path on h's device and stream: one warp waits on a barrier that
+ * nothing ever completes, for `polls` polls (>= 1), then reports through the
+ * same controller.  Returns GABP_ERR_TIMEOUT when the path works (the handle
+ * stays usable); *seconds_per_poll (may be NULL) receives the measured
+ * duration of one unsatisfied poll, so the library's own limit (2^22 polls)
+ * can be turned into time on this device.  Allocates 8 bytes of device
+ * memory on first use.
+ */
+gabp_status gabp_check_wait_limit(gabp_handle h, int32_t polls, double *seconds_per_poll);
+
+/*
  * Instrumentation for parity tests.  Runs exactly `rounds` synchronous FP64
  * rounds of Alg. 2 from zero messages on b_dev and writes the tentative
  * means after the last round to x_dev (rounds = 0 gives x_i = b_i / A_ii).

@@ -422,6 +422,10 @@ gabp_status build_systems(Graph &g, int32_t nsys, const int64_t *sys_row_off,
 // or the dense form, v = [x^; 0], [0; y - S x^] for flagged systems, x^ +=
 // (scaled) x^ part of an augmented solution, per-system max |u| over the x^ rows.
 int launch_csr_offdiag(const Graph &g, cudaStream_t st, const double *v, double *u);
+// FP64 sweep by Algorithm 1, the naive form (gabp_naive.cu; option naive).
+int launch_naive64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
+// Diagnostics (gabp_selfcheck.cu): a bounded wait that runs out, reported as the sweeps report it.
+int launch_wait_limit(cudaStream_t st, Ctl *ctl, DevScalars *red, int32_t polls, unsigned long long *ns);
 int launch_dense_offdiag(const Dense &d, cudaStream_t st, const double *v, double *u);
 int launch_pinv_embed(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row, const int64_t *aug_off,
                       const int32_t *K, const int64_t *x_off, const double *xhat, double *v);
@@ -477,6 +481,7 @@ struct gabp_s {
   double *lsq_inv_psi0 = nullptr;      // device: 1 / psi_0 of those systems, 0 for the others
   double *lsq_u = nullptr, *lsq_v = nullptr;     // device: augmented work vectors
   unsigned long long *lsq_gmax = nullptr;        // device: per-system max |S^T r| (bit patterns)
+  unsigned long long *diag_ns = nullptr;         // device: duration of the wait-limit check
   int graph_K = 0;                     // K the CTL_MULTI graph was recorded for
   size_t capK = 0;                     // columns the multi buffers hold
   gabp::MultiCols cols{};              // device per-column arrays (capK each)

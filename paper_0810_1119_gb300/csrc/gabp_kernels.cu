@@ -303,67 +303,6 @@ sweep64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 round of Algorithm 1, the naive form (option naive): for every
-// directed edge i -> j the cavity sums
-//     P_{i\j} = A_ii + sum_{k in N(i)\j} P_ki,   h_{i\j} = b_i + sum_{k in N(i)\j} eta_ki
-// are added up over the other incoming messages directly, O(deg^2) per row,
-// instead of node total minus reverse message (Algorithm 2).  It is the same
-// round without that cancellation, so it cross-checks the broadcast kernels
-// on the same data.  One warp per row, lanes over the row's slots, each sum
-// in slot order; the tentative mean x_i = h~_i / P~_i uses every incoming
-// message.  Synchronous schedule, undamped.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBlock) naive64_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
-  const int par = ctl->par_m;
-  const bool first = ctl->first != 0;   // incoming messages are zero
-  bool write_x, write_msgs;
-  if (ctl->mode == CTL_ROUNDS) {
-    const bool infer_only = ctl->sweeps >= ctl->rounds_target;
-    write_x = infer_only || ctl->write_x != 0;
-    write_msgs = !infer_only;
-  } else {
-    write_x = ctl->write_x != 0;
-    write_msgs = true;
-  }
-  const double *__restrict__ b = ctl->b;
-  double *__restrict__ x = ctl->xw;
-  const double2 *__restrict__ min = (par ? B.m64[1] : B.m64[0]);
-  double2 *__restrict__ mout = (par ? B.m64[0] : B.m64[1]);
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
-  bool brk = false;
-  for (int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32; i < g.n;
-       i += warps) {
-    const int32_t rs = g.rp[i], re = g.rp[i + 1];
-    const double dgi = g.diag64[i], bi = b[i];
-    if (write_x && lane == 0) {
-      double P = dgi, H = bi;
-      if (!first)
-        for (int32_t t = rs; t < re; ++t) {
-          P += min[t].x;
-          H += min[t].y;
-        }
-      x[i] = H / P;
-    }
-    if (!write_msgs) continue;
-    for (int32_t s = rs + lane; s < re; s += 32) {
-      double P = dgi, H = bi;   // P_ii = A_ii and P_ii mu_ii = b_i
-      if (!first)
-        for (int32_t t = rs; t < re; ++t)
-          if (t != s) {
-            P += min[t].x;
-            H += min[t].y;
-          }
-      brk |= zero_or_nonfinite(P);
-      const double a = g.a64[s];
-      mout[g.rev[s]] = make_double2(-(a * a) / P, -a * H / P);
-    }
-  }
-  if (brk) atomicOr(&red->breakdown, 1);
-  last_block_control(ctl, red, CK_SWEEP64);
-}
-
-// ---------------------------------------------------------------------------
 // FP32 full sweep (mixed modes, precision phase).  Messages (P, eta) and
 // totals in FP32; rhs_i = r_i / ||r|| (scaled in FP64 by the first sweep of
 // an inner solve, then kept in FP32).  Records (P~_i, d_i = h~_i / P~_i) per
@@ -1346,12 +1285,6 @@ int launch_init(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars
 
 int launch_sweep64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                    const GraphView *view) {
-  if (g.naive && !view) {
-    const int64_t blocks = (static_cast<int64_t>(g.n) * 32 + kBlock - 1) / kBlock;
-    naive64_kernel<<<static_cast<int>(std::min<int64_t>(blocks, num_sms() * 8)), kBlock, 0, st>>>(
-        g.view(), B, ctl, red);
-    return 1;
-  }
   const GraphView v = view ? *view : g.view();
   switch (g.group) {
     case 2: launch64<2>(v, st, B, ctl, red); break;

@@ -309,7 +309,9 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     return k;
   }
   switch (phase) {
-    case PH_FULL64: return launch_sweep64(g, st, h->buf, h->ctl, h->red);
+    case PH_FULL64:
+      return g.naive ? launch_naive64(g, st, h->buf, h->ctl, h->red)
+                     : launch_sweep64(g, st, h->buf, h->ctl, h->red);
     case PH_CHECK64:
       return launch_check64(g, st, h->buf, h->ctl, h->red,
                             h->opt.aitken > 0 && h->opt.precision == GABP_PREC_FP64);
@@ -830,6 +832,7 @@ void release(gabp_handle h) {
   cudaFree(h->lsq_rhs); cudaFree(h->lsq_x);
   cudaFree(h->lsq_pinv); cudaFree(h->lsq_inv_psi0); cudaFree(h->lsq_u); cudaFree(h->lsq_v);
   cudaFree(h->lsq_gmax);
+  cudaFree(h->diag_ns);
   if (h->dense) {
     DenseView &v = h->dense->v;
     for (int k = 0; k < 2; ++k) {
@@ -1761,6 +1764,28 @@ gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning) {
   return GABP_OK;
 }
 
+gabp_status gabp_check_wait_limit(gabp_handle h, int32_t polls, double *seconds_per_poll) {
+  if (!h) return GABP_ERR_INVALID_ARG;
+  if (polls < 1) return fail(h, GABP_ERR_INVALID_ARG, "gabp_check_wait_limit: polls < 1");
+  return guarded(h, [&] {
+    cudaStream_t st = h->stream;
+    ensure_common(h);   // control block and reductions (a fresh handle has none yet)
+    ensure(&h->bbuf, h->g.n);
+    ensure(&h->diag_ns, 1);
+    init_ctl(h, CTL_FP64, h->bbuf, h->bbuf, 0.0, 1, false);
+    CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
+    launch_wait_limit(st, h->ctl, h->red, polls, h->diag_ns);
+    CK(cudaGetLastError());
+    unsigned long long ns = 0;
+    CK(cudaMemcpyAsync(&ns, h->diag_ns, sizeof(ns), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (seconds_per_poll) *seconds_per_poll = 1e-9 * static_cast<double>(ns) / polls;
+    return report(h, "wait-limit check");
+  });
+}
+
 gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats) {
   if (!h || !stats) return GABP_ERR_INVALID_ARG;
   *stats = h->stats;
@@ -1808,6 +1833,8 @@ gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, 
         Buffers B = h->buf;               // the means of the last round: one buffer
         B.m64[1] = B.m64[0];
         launch_sweep64(h->g, st, B, h->ctl, h->red);
+      } else if (h->g.naive) {
+        launch_naive64(h->g, st, h->buf, h->ctl, h->red);   // (the last pass only infers)
       } else {
         launch_sweep64(h->g, st, h->buf, h->ctl, h->red);   // (the last pass only infers)
       }

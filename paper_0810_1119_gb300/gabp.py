@@ -37,7 +37,7 @@ EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_str
             "gabp_run_rounds", "gabp_get_messages", "gabp_last_error", "gabp_status_string",
             "gabp_version", "gabp_create_batched", "gabp_create_lsq_batched",
             "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc", "gabp_get_tuning",
-            "gabp_set_profile", "gabp_create_grid")
+            "gabp_set_profile", "gabp_create_grid", "gabp_check_wait_limit")
 
 
 class GabpOptions(ctypes.Structure):
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH):
                                                    ctypes.c_int32, vp, vp]),
         "gabp_get_tuning": (ctypes.c_int, [H, ctypes.POINTER(GabpTuning)]),
         "gabp_set_profile": (ctypes.c_int, [H, ctypes.c_int32]),
+        "gabp_check_wait_limit": (ctypes.c_int, [H, ctypes.c_int32, f64p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -337,6 +338,15 @@ def gabp_run_rounds_noalloc(row_ptr, col, val, rev, b, rounds: int, x, stream: i
         _dev_ptr(b, "torch.float64"), int(rounds), _dev_ptr(x, "torch.float64", n),
         ctypes.c_void_p(current_stream_handle() if stream is None else stream))
     _check(None, st)
+
+
+def gabp_check_wait_limit(h, polls: int):
+    """Make one bounded device wait run out on purpose (see include/gabp.h).
+    Returns (status name, seconds per unsatisfied poll); the expected status
+    is GABP_ERR_TIMEOUT, and the handle stays usable."""
+    sp = ctypes.c_double(0.0)
+    st = load().gabp_check_wait_limit(h, int(polls), ctypes.byref(sp))
+    return STATUS_NAMES.get(st, str(st)), sp.value
 
 
 def gabp_version() -> str:
