@@ -375,8 +375,9 @@ gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning);
  * same controller.  Returns GABP_ERR_TIMEOUT when the path works (the handle
  * stays usable); *seconds_per_poll (may be NULL) receives the measured
  * duration of one unsatisfied poll, so the library's own limit (2^22 polls)
- * can be turned into time on this device.  Allocates 8 bytes of device
- * memory on first use.
+ * can be turned into time on this device.  On first use it allocates what
+ * a first solve would (the control block, the reductions, an n-entry FP64
+ * scratch vector) and 8 bytes more.
  */
 gabp_status gabp_check_wait_limit(gabp_handle h, int32_t polls, double *seconds_per_poll);
 
