@@ -569,7 +569,7 @@ def run_poisson32(args):
                              "sweeps": out["fp64_aitken2"]["stats"]["sweeps_total"],
                              "max_rel_err_vs_oracle": float(np.abs(out["fp64_aitken2"]["x"] - ref["x"]).max()
                                                             / np.abs(ref["x"]).max()),
-                             "note": "Aitken's Delta^2 on the means of rounds t-4, t-2, t (Section V)"},
+                             "note": "Aitken's Delta^2 on the means of rounds t-4, t-2, t (Section IV-A)"},
             "tuning": f["tuning"],
             "cpu_baseline": {"value": 1e3 * cpu_s, "unit": "ms", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": f"the full solve ({ref['rounds']} rounds)"}}

@@ -95,7 +95,7 @@ typedef struct {
                              0 = the whole solve in one cluster launch, 1 = always a launch
                              per sweep */
   int32_t cluster_ctas;   /* CTAs of that cluster (2, 4, 8 or 16); 0 = automatic */
-  int32_t aitken;         /* FP64 solves and gabp_run_rounds: Aitken's Delta^2 (Section V,
+  int32_t aitken;         /* FP64 solves and gabp_run_rounds: Aitken's Delta^2 (Section IV-A,
                              convergence acceleration) on the tentative means of rounds
                              t - 2s, t - s and t with stride s = aitken (1..64); the stop rule
                              and the returned x use the extrapolated means.  On grid

@@ -21,7 +21,7 @@ Contents
 * ``gabp_serial``   -- the serial schedule of Section III-C over a given node
                        order (``greedy_colouring`` gives colour classes).
 * ``aitken``, ``gabp_aitken`` -- Aitken's Delta^2 extrapolation of the
-                       tentative means (Section V, convergence acceleration),
+                       tentative means (Section IV-A, convergence acceleration),
                        applied per node to the means of rounds t - 2s, t - s
                        and t.
 
@@ -226,7 +226,7 @@ def set_num_threads(k: int) -> None:
 
 
 def aitken(x0, x1, x2):
-    """Aitken's Delta^2 per node (Section V, convergence acceleration):
+    """Aitken's Delta^2 per node (Section IV-A, convergence acceleration):
     y = x0 - (x1 - x0)^2 / (x2 - 2 x1 + x0) for three iterates of a sequence
     that converges linearly.  Where the second difference is not above the
     rounding level of the iterates (|x2 - 2 x1 + x0| <= 64 eps max|x_k|) the

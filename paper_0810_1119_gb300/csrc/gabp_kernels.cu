@@ -771,7 +771,7 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
 }
 
 // Aitken's Delta^2 per node on the last three tentative means in the ring
-// (Section V, convergence acceleration): y = x0 - (x1 - x0)^2 / (x2 - 2 x1
+// (Section IV-A, convergence acceleration): y = x0 - (x1 - x0)^2 / (x2 - 2 x1
 // + x0), or the latest mean x2 where the second difference is at rounding
 // level (|x2 - 2 x1 + x0| <= 64 eps max|x_k|) or fewer than three means exist.
 // out = nullptr: the solve's x (read from the control block, so a recorded

@@ -25,10 +25,11 @@ def _matrix(spec: str):
     return [[_num(t) for t in row.split()] for row in spec.split(";")]
 
 
-def toy_tree():
-    """dict: 'A','b','solution' (Fractions) and per-quantity lists over rounds."""
+def toy_tree(fname: str = "toy_tree.txt"):
+    """dict: 'A','b','solution' (Fractions) and per-quantity lists over rounds.
+    ``toy_tree_damped.txt`` (rounds 1 and 2 under damping) adds 'gamma'."""
     out = {}
-    for line in _lines("toy_tree.txt"):
+    for line in _lines(fname):
         key, rest = line.split(None, 1)
         if key == "matrix":
             out["A"] = _matrix(rest)

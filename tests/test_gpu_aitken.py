@@ -1,4 +1,4 @@
-"""GPU parity of Aitken's Delta^2 on the tentative means (Section V,
+"""GPU parity of Aitken's Delta^2 on the tentative means (Section IV-A,
 convergence acceleration), option `aitken` = stride s.
 
 * gabp_run_rounds with aitken = s returns the Delta^2 of the means of rounds

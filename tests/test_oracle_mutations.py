@@ -26,10 +26,44 @@ MUTANTS = {
     "marginal_divides_by_self_precision": ("    x[i] = hsum / Psum;\n    if (Pi) Pi[i] = Psum;",
                                            "    x[i] = hsum / Pii;\n    if (Pi) Pi[i] = Psum;"),
     "mean_message_sign": ("Mn[e] = (Pt * mut - Pji * muji) / Aij;", "Mn[e] = -(Pt * mut - Pji * muji) / Aij;"),
+    # the synchronous damping blend (reading of Section VI-D): weights swapped,
+    # and the blend applied to mu instead of to P mu
+    "damping_weights_swapped": ("const double eta = gamma * (Po[e] * Mo[e]) + (1.0 - gamma) * (Pn[e] * Mn[e]);",
+                                "const double eta = (1.0 - gamma) * (Po[e] * Mo[e]) + gamma * (Pn[e] * Mn[e]);"),
+    "damping_blends_mean": ("const double eta = gamma * (Po[e] * Mo[e]) + (1.0 - gamma) * (Pn[e] * Mn[e]);\n"
+                            "          Mn[e] = eta / Pn[e];",
+                            "Mn[e] = gamma * Mo[e] + (1.0 - gamma) * Mn[e];"),
 }
 
 
+def _damped_pins_hold(lib) -> bool:
+    """Rounds 1 and 2 of the damped toy tree against the hand derivation in
+    tests/golden/toy_tree_damped.txt."""
+    g = toy_tree("toy_tree_damped.txt")
+    A = np.array([[float(v) for v in row] for row in g["A"]])
+    m = W.csr_from_dense(A)
+    b = np.array([float(v) for v in g["rhs"]])
+    pos = {(i, int(m.col[e])): e for i in range(3) for e in range(m.row_ptr[i], m.row_ptr[i + 1])}
+    names = {"x": 0, "y": 1, "z": 2}
+    for t in (1, 2):
+        r = oracle.gabp(m.row_ptr, m.col, m.val, b, max_rounds=t, want_messages=True, lib=lib,
+                        damping=float(g["gamma"][0]))
+        for key, series in g.items():
+            kind, _, pair = key.partition("_")
+            if kind in ("P", "mu") and len(pair) == 2:
+                got = r["P" if kind == "P" else "mu"][pos[(names[pair[0]], names[pair[1]])]]
+            elif kind == "mu" and len(pair) == 1:
+                got = r["x"][names[pair]]
+            else:
+                continue
+            if abs(got - float(series[t - 1])) > 1e-12:
+                return False
+    return True
+
+
 def _pins_hold(lib) -> bool:
+    if not _damped_pins_hold(lib):
+        return False
     g = toy_tree()
     A = np.array([[float(v) for v in row] for row in g["A"]])
     m = W.csr_from_dense(A)

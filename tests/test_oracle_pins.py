@@ -358,6 +358,29 @@ def test_zero_damping_is_the_plain_rule():
         assert np.array_equal(a[key], c[key])
 
 
+def test_damped_toy_tree_rounds_match_the_hand_derivation():
+    """Rounds 1 and 2 of the synchronous damped rule on the Section VIII-A
+    tree, gamma = 1/4, against exact rationals worked out by hand
+    (tests/golden/toy_tree_damped.txt gives the derivation).  Round 1 fixes
+    which weight the new message gets; round 2, where P_xy changes from -4 to
+    1/2, fixes that the blend acts on P mu and not on mu."""
+    g = toy_tree("toy_tree_damped.txt")
+    gamma = float(g["gamma"][0])
+    m = _csr([[float(v) for v in row] for row in g["A"]])
+    b = np.array([float(v) for v in g["rhs"]])
+    for t in (1, 2):
+        r = _run(m, b, t, damping=gamma)
+        for key, series in g.items():
+            kind, _, pair = key.partition("_")
+            if kind in ("P", "mu") and len(pair) == 2:
+                e = _pos(m, TOY_NAMES[pair[0]], TOY_NAMES[pair[1]])
+                got = r["P" if kind == "P" else "mu"][e]
+                assert got == pytest.approx(float(series[t - 1]), rel=1e-14, abs=1e-14), (key, t)
+            elif kind == "mu" and len(pair) == 1:
+                got = r["x"][TOY_NAMES[pair]]
+                assert got == pytest.approx(float(series[t - 1]), rel=1e-14, abs=1e-14), (key, t)
+
+
 def test_damping_keeps_the_solution_and_rescues_divergence():
     # System 270 of this batch: plain synchronous GaBP diverges on its
     # augmented form (checked below), damped GaBP reaches the closed form.
@@ -377,7 +400,7 @@ def test_damping_keeps_the_solution_and_rescues_divergence():
 
 
 # ---------------------------------------------------------------------------
-# Aitken's Delta^2 (Section V, convergence acceleration)
+# Aitken's Delta^2 (Section IV-A, convergence acceleration)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("a", [0.5, -0.9, 0.99, -0.3])
 def test_aitken_is_exact_on_one_geometric_mode(a):
