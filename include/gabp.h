@@ -367,19 +367,21 @@ gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning);
 
 /*
  * Diagnostics, no counterpart in the paper.  Every wait inside the library's
- * kernels (the shared-memory staging of the sweeps) is bounded: after a fixed
- * number of polls it gives up, the launch raises a flag, and the solve ends
- * with GABP_ERR_TIMEOUT instead of hanging the device.  This call exercises
- * that path on h's device and stream: one warp waits on a barrier that
- * nothing ever completes, for `polls` polls (>= 1), then reports through the
- * same controller.  Returns GABP_ERR_TIMEOUT when the path works (the handle
- * stays usable); *seconds_per_poll (may be NULL) receives the measured
- * duration of one unsatisfied poll, so the library's own limit (2^22 polls)
- * can be turned into time on this device.  On first use it allocates what
- * a first solve would (the control block, the reductions, an n-entry FP64
- * scratch vector) and 8 bytes more.
+ * kernels (the shared-memory staging of the sweeps) is bounded in time:
+ * 100 ms of the GPU's global timer after its first unsatisfied poll it gives
+ * up, the launch raises a flag, and the solve ends with GABP_ERR_TIMEOUT
+ * instead of holding the device.  This call exercises that path on h's
+ * device and stream: one warp runs the sweeps' own bounded wait on a barrier
+ * that nothing ever completes (no copy is issued), for `limit_us`
+ * microseconds (1..100000; 0 = the library's limit of 100000), then reports
+ * through the same controller.  Returns GABP_ERR_TIMEOUT when the path works
+ * (the handle stays usable); GABP_ERR_INVALID_ARG for limit_us outside
+ * 0..100000.  *seconds_waited (may be NULL) receives the measured duration
+ * of the wait.  On first use it allocates what a first solve would (the
+ * control block, the reductions, an n-entry FP64 scratch vector) and 8 bytes
+ * more.
  */
-gabp_status gabp_check_wait_limit(gabp_handle h, int32_t polls, double *seconds_per_poll);
+gabp_status gabp_check_wait_limit(gabp_handle h, int32_t limit_us, double *seconds_waited);
 
 /*
  * Instrumentation for parity tests.  Runs exactly `rounds` synchronous FP64
@@ -400,9 +402,11 @@ gabp_status gabp_get_messages(gabp_handle h, double *P_host, double *mu_host);
 /*
  * gabp_run_rounds without any device allocation.  (The paper has no
  * counterpart: this is an interface for callers that cannot allocate device
- * memory when they call -- e.g. while another component records a CUDA
- * stream capture, or in applications that reserve all device memory up
- * front, or in loops that must never enter the allocator.)
+ * memory when they call -- applications that reserve all device memory up
+ * front, where a late cudaMalloc fails or is forbidden; code running inside
+ * an allocator or memory-pool callback, which cannot re-enter the
+ * allocator; loops that must never pay the device-wide synchronisation of
+ * cudaMalloc/cudaFree.)
  *
  * Runs exactly `rounds` synchronous FP64 rounds of Alg. 2 from zero messages
  * on a matrix the caller already holds in device memory and writes the
@@ -414,18 +418,27 @@ gabp_status gabp_get_messages(gabp_handle h, double *P_host, double *mu_host);
  *   rev_dev[nnz]: reverse-entry permutation, rev[e] = position of (j, i) for
  *     e = (i, j) (rev of a diagonal entry is itself);
  *   b_dev[n] in, x_dev[n] out; all FP64 / int device arrays owned by the
- *   caller; work is issued on `stream` (cudaStream_t, NULL = legacy default)
- *   and the call returns after synchronising it.
+ *   caller.
+ * Stream: work is issued on `stream` (cudaStream_t); NULL means the calling
+ * thread's per-thread default stream (cudaStreamPerThread), not the legacy
+ * default stream, which would synchronise implicitly with every blocking
+ * stream of the process.  The call ends by reading a status word into host
+ * memory and synchronising the stream, so the stream must not be capturing:
+ * a capturing stream is rejected with GABP_ERR_INVALID_ARG before any work
+ * is issued.
  * Working space: one fixed array of 2 x 2^18 message pairs (8 MiB) in the
  * library's static device memory, present on every GPU that loads the
  * library until the process exits.  nnz above 2^18 = 262144 is rejected
  * with GABP_ERR_INVALID_ARG (message via gabp_last_error(NULL)).  The call
  * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
- * The first call on each device looks up the array's device address; make
- * that first call before any stream capture.  All calls share the array and
- * it keeps the last call's contents (nothing in it needs to start at zero
- * except a status word the call clears itself); calls that overlap on the
- * GPU -- on different streams or host threads -- race on it.
+ * The array's device address is looked up on every call (a lookup
+ * allocates nothing); the first call on a device may load the library's
+ * module there, so make it before any stream capture on that device.  After
+ * a device reset the next call finds the array at its new address.  All
+ * calls share the array and it keeps the last call's contents (nothing in
+ * it needs to start at zero except a status word the call clears itself);
+ * calls that overlap on the GPU -- on different streams or host threads --
+ * race on it.
  * Errors: GABP_ERR_INVALID_ARG, GABP_ERR_BREAKDOWN, GABP_ERR_CUDA.
  */
 gabp_status gabp_run_rounds_noalloc(int64_t n, int64_t nnz, const int64_t *row_ptr_dev,

@@ -415,9 +415,10 @@ __device__ void last_block_control(Ctl *ctl, DevScalars *red, int kind) {
 
 // ---------------------------------------------------------------------------
 // Shared-memory staging with cp.async.bulk on an mbarrier.  Every wait is
-// bounded: after kWaitLimit polls it gives up and returns false.
+// bounded in time: once kWaitLimitNs (gabp_internal.h) of the GPU's global
+// timer have passed since its first unsatisfied poll it gives up and returns
+// false.
 // ---------------------------------------------------------------------------
-constexpr int kWaitLimit = 1 << 22;   // try_wait polls before giving up
 
 __host__ __device__ constexpr uint32_t r128(uint64_t b) {
   return static_cast<uint32_t>((b + 127) & ~uint64_t{127});
@@ -449,10 +450,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for phase `parity` of `bar` for at most `limit_ns` nanoseconds of
+// global time after the first unsatisfied poll (the timer is read only once
+// a poll has failed, so a wait whose copy has landed costs one poll).
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity,
+                                              unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_timer_ns();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if (global_timer_ns() - t0 >= limit_ns) return false;
+  }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, kWaitLimitNs);
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
                                          uint32_t bar) {

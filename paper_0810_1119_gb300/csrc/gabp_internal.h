@@ -425,7 +425,13 @@ int launch_csr_offdiag(const Graph &g, cudaStream_t st, const double *v, double 
 // FP64 sweep by Algorithm 1, the naive form (gabp_naive.cu; option naive).
 int launch_naive64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red);
 // Diagnostics (gabp_selfcheck.cu): a bounded wait that runs out, reported as the sweeps report it.
-int launch_wait_limit(cudaStream_t st, Ctl *ctl, DevScalars *red, int32_t polls, unsigned long long *ns);
+// Time limit of every bounded device wait (the sweeps' shared-memory
+// staging).  A copy that lands takes microseconds, so the limit only ever
+// ends a wait whose copy will not come, and it frees the SM within a tenth
+// of a second.
+constexpr unsigned long long kWaitLimitNs = 100ull * 1000 * 1000;   // 100 ms
+int launch_wait_limit(cudaStream_t st, Ctl *ctl, DevScalars *red, unsigned long long limit_ns,
+                      unsigned long long *ns);
 int launch_dense_offdiag(const Dense &d, cudaStream_t st, const double *v, double *u);
 int launch_pinv_embed(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row, const int64_t *aug_off,
                       const int32_t *K, const int64_t *x_off, const double *xhat, double *v);

@@ -73,8 +73,9 @@ __global__ void __launch_bounds__(kBlock) naive64_kernel(GraphView g, Buffers B,
 
 int launch_naive64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red) {
   // one warp per row, at most eight 256-thread blocks per SM in flight
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);   // the handle's device is current while it launches
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t blocks = (static_cast<int64_t>(g.n) * 32 + kBlock - 1) / kBlock;
   const int64_t cap = static_cast<int64_t>(std::max(sms, 1)) * 8;
   naive64_kernel<<<static_cast<int>(std::max<int64_t>(1, std::min(blocks, cap))), kBlock, 0, st>>>(

@@ -2,16 +2,17 @@
 // without any device allocation.
 //
 // Who needs this: callers that must not allocate device memory at the
-// moment they call us -- for example code that runs while another component
-// is recording a CUDA stream capture (an allocation there would break the
-// capture), applications that reserve all of their device memory up front
-// and treat a late allocation failure as fatal, and latency-critical loops
-// that must never enter the allocator.  Such callers already own their
-// inputs and outputs; what they cannot provide on demand is our working
-// space.  This entry point therefore keeps its working space (the two
-// message buffers of the parallel schedule) in one fixed, file-scope device
-// array that exists from the moment the library is loaded on a GPU until
-// the process exits.
+// moment they call us -- applications that reserve all of their device
+// memory up front (a serving process whose memory pool owns the whole GPU,
+// where a late cudaMalloc fails or must not happen), code that runs inside
+// an allocator or memory-pool callback and cannot re-enter the allocator,
+// and latency-critical loops where cudaMalloc/cudaFree would synchronise
+// the device.  Such callers already own their inputs and outputs; what they
+// cannot provide on demand is our working space.  This entry point
+// therefore keeps its working space (the two message buffers of the
+// parallel schedule) in one fixed, file-scope device array that exists from
+// the moment the library's module is loaded on a GPU until the process
+// exits (or the device is reset).
 //
 // The computation is the same as gabp_run_rounds: `rounds` synchronous
 // rounds of the broadcast form from zero messages, then the tentative means.
@@ -20,7 +21,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "../../include/gabp.h"
@@ -34,10 +34,6 @@ constexpr int64_t kNoAllocMaxEntries = int64_t{1} << 18;
 // (P, P mu) pairs, laid out per CSR entry, plus one breakdown flag word.
 // 2 * 2^18 * 16 B + 256 B = 8 MiB + 256 B per GPU that loads the library.
 static __device__ __align__(256) double2 g_noalloc_scratch[2 * kNoAllocMaxEntries + 16];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double2 *g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device
 
 // One round for row i (a thread per row).  Entry e = (i, j), j != i, holds
 // the message travelling INTO i from j in `in`; the message i -> j is written
@@ -95,25 +91,28 @@ extern "C" gabp_status gabp_run_rounds_noalloc(int64_t n, int64_t nnz, const int
     return fail(GABP_ERR_INVALID_ARG,
                 "gabp_run_rounds_noalloc: nnz = " + std::to_string(nnz) + " exceeds the fixed " +
                     "working space of " + std::to_string(kNoAllocMaxEntries) + " entries");
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
+  // NULL would be the legacy default stream, which synchronises implicitly
+  // with every blocking stream of the process (including one that another
+  // component may be capturing); the calling thread's per-thread default
+  // stream keeps the ordering with legacy-stream work without that.
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : cudaStreamPerThread;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(st, &cap);
   if (ce != cudaSuccess) return fail(GABP_ERR_CUDA, cudaGetErrorString(ce));
-  if (dev < 0 || dev >= kMaxDevices) return fail(GABP_ERR_CUDA, "device index out of range");
-  double2 *scratch = nullptr;
-  {
-    // First call on this device: look up the device address of the array
-    // (with this device current).  No memory is allocated.
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      void *p = nullptr;
-      ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (ce != cudaSuccess)
-        return fail(GABP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
-      g_scratch_ptr[dev] = static_cast<double2 *>(p);
-    }
-    scratch = g_scratch_ptr[dev];
-  }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(GABP_ERR_INVALID_ARG,
+                "gabp_run_rounds_noalloc: the stream is being captured; the call reads a status "
+                "word back to the host and synchronises its stream, so it cannot run there");
+  // Device address of the array on the current device.  Looked up on every
+  // call (no memory is allocated by the lookup): after a device reset the
+  // module is loaded again and the array may sit at a new address, so a
+  // cached pointer could go stale.  The first call on a device also loads
+  // the library's module there if it is not loaded yet.
+  void *p = nullptr;
+  ce = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (ce != cudaSuccess)
+    return fail(GABP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(ce));
+  double2 *scratch = static_cast<double2 *>(p);
   double2 *buf[2] = {scratch, scratch + kNoAllocMaxEntries};
   int *breakdown = reinterpret_cast<int *>(scratch + 2 * kNoAllocMaxEntries);
   // The flag is the only state that must start at zero; the message buffers

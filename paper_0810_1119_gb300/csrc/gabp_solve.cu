@@ -1764,9 +1764,15 @@ gabp_status gabp_get_tuning(gabp_handle h, gabp_tuning *tuning) {
   return GABP_OK;
 }
 
-gabp_status gabp_check_wait_limit(gabp_handle h, int32_t polls, double *seconds_per_poll) {
+gabp_status gabp_check_wait_limit(gabp_handle h, int32_t limit_us, double *seconds_waited) {
   if (!h) return GABP_ERR_INVALID_ARG;
-  if (polls < 1) return fail(h, GABP_ERR_INVALID_ARG, "gabp_check_wait_limit: polls < 1");
+  constexpr int64_t kMaxUs = static_cast<int64_t>(kWaitLimitNs / 1000);
+  if (limit_us < 0 || limit_us > kMaxUs)
+    return fail(h, GABP_ERR_INVALID_ARG,
+                "gabp_check_wait_limit: limit_us must be 0 (the library's limit) or 1.." +
+                    std::to_string(kMaxUs));
+  const unsigned long long limit_ns =
+      limit_us == 0 ? kWaitLimitNs : static_cast<unsigned long long>(limit_us) * 1000ull;
   return guarded(h, [&] {
     cudaStream_t st = h->stream;
     ensure_common(h);   // control block and reductions (a fresh handle has none yet)
@@ -1775,13 +1781,13 @@ gabp_status gabp_check_wait_limit(gabp_handle h, int32_t polls, double *seconds_
     init_ctl(h, CTL_FP64, h->bbuf, h->bbuf, 0.0, 1, false);
     CK(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->red, 0, sizeof(DevScalars), st));
-    launch_wait_limit(st, h->ctl, h->red, polls, h->diag_ns);
+    launch_wait_limit(st, h->ctl, h->red, limit_ns, h->diag_ns);
     CK(cudaGetLastError());
     unsigned long long ns = 0;
     CK(cudaMemcpyAsync(&ns, h->diag_ns, sizeof(ns), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (seconds_per_poll) *seconds_per_poll = 1e-9 * static_cast<double>(ns) / polls;
+    if (seconds_waited) *seconds_waited = 1e-9 * static_cast<double>(ns);
     return report(h, "wait-limit check");
   });
 }

@@ -340,13 +340,14 @@ def gabp_run_rounds_noalloc(row_ptr, col, val, rev, b, rounds: int, x, stream: i
     _check(None, st)
 
 
-def gabp_check_wait_limit(h, polls: int):
-    """Make one bounded device wait run out on purpose (see include/gabp.h).
-    Returns (status name, seconds per unsatisfied poll); the expected status
-    is GABP_ERR_TIMEOUT, and the handle stays usable."""
-    sp = ctypes.c_double(0.0)
-    st = load().gabp_check_wait_limit(h, int(polls), ctypes.byref(sp))
-    return STATUS_NAMES.get(st, str(st)), sp.value
+def gabp_check_wait_limit(h, limit_us: int = 0):
+    """Make the sweeps' bounded device wait run out on purpose (see
+    include/gabp.h): `limit_us` microseconds, 0 = the library's own limit.
+    Returns (status name, seconds waited); the expected status is
+    GABP_ERR_TIMEOUT, and the handle stays usable."""
+    sec = ctypes.c_double(0.0)
+    st = load().gabp_check_wait_limit(h, int(limit_us), ctypes.byref(sec))
+    return STATUS_NAMES.get(st, str(st)), sec.value
 
 
 def gabp_version() -> str:
