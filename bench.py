@@ -280,7 +280,8 @@ def run_gabp(args):
     # Launch shapes are picked by the library's autotuner at create time
     # (outside the timed region); the profiled pass reuses the same handle.
     mixed = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_MIXED_FP32,
-                                 autotune=True, schedule=args.schedule, pull_lanes=args.pull_lanes)
+                                 autotune=True, schedule=args.schedule, pull_lanes=args.pull_lanes,
+                                 mean_window=args.mean_window)
     fp64 = gabp.Solver.from_csr(m.row_ptr, m.col, m.val, precision=gabp.PREC_FP64, autotune=True,
                                 schedule=args.schedule)
     stream = torch.cuda.current_stream()
@@ -380,6 +381,10 @@ def run_gabp(args):
                       "hbm_frac": ((fe * E + fn * m.n) * n_f / (ms_f * 1e-3) / 1e9 / hbm) if ms_f > 0 else None}
         if lanes > 0:
             kernel_names["full32"] = "pull32_kernel (FP32 full sweep, in place)"
+        mwin = mixed.tuning()["mean_window"]
+        if mwin > 0:
+            kernel_names["mean"] = (f"mean_win_kernel<float> (FP32 mean-only sweep, window form, "
+                                    f"{mixed.tuning()['windows']} windows of about {mwin} slots)")
         line = {
             "metric": METRIC, "value": updates / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_ms,
@@ -829,6 +834,9 @@ def main():
     ap.add_argument("--pull-lanes", type=int, default=0, choices=[-1, 0, 2, 4, 8, 16, 32],
                     help="er1e6: form of the FP32 full sweep: 0 = autotuned, -1 = scatter, "
                          "2..32 = in place with that many lanes per row")
+    ap.add_argument("--mean-window", type=int, default=0,
+                    help="er1e6: form of the mean sweep: 0 = autotuned, -1 = tiles, "
+                         "256..65536 = windows of about that many slots")
     ap.add_argument("--workload", default="er1e6",
                     choices=["er1e6", "multi64", "detect", "poisson32", "poisson3d"],
                     help="er1e6: the headline line; multi64 / detect / poisson32 / poisson3d: extra lines")

@@ -137,6 +137,15 @@ typedef struct {
                              The same round without that cancellation, for cross-checks on
                              small systems.  CSR handles, FP64, schedule 0, no damping;
                              0 = Algorithm 2 */
+  int32_t mean_window;    /* CSR form, mean-only sweeps (mixed modes): -1 = tile form (each row
+                             sends its messages to the receivers' slots, a scattered store per
+                             edge); W in 256..65536 = window form with windows of about W
+                             slots: the rows are cut into windows of consecutive rows, each
+                             window's outgoing messages are kept sorted by destination, and a
+                             sweep moves them as contiguous runs through shared memory (no
+                             scattered access).  0 = automatic: with autotune the tuner times
+                             both forms and several window sizes, else the tile form.  The
+                             window form needs the synchronous schedule. */
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */
@@ -343,6 +352,10 @@ gabp_status gabp_set_profile(gabp_handle h, int32_t on);
  *     slot-parallel ("heavy") instead of thread-per-row (16, 32, 64, 128 or
  *     never), then the tile shape (slots x rows: 1024 x 256, 512 x 256,
  *     512 x 128, 256 x 64), scored by 4 mean sweeps + 1 full sweep;
+ *   CSR form, mixed precisions, synchronous schedule: the form of the FP32
+ *     full sweep (scatter, or in place with 2 .. 32 lanes per row), then the
+ *     form of the mean sweep (tiles, or windows of about E / (SMs x m)
+ *     slots, m = 3, 4, 6, 8), scored by mean sweeps alone;
  *   CSR form, FP64: lanes per row of the FP64 sweep (2 .. 32);
  *   dense Section VII form, mixed precisions: grid rows each warp loads
  *     ahead (1, 2 or 4) in the mean sweep and in the full sweep.
@@ -359,6 +372,9 @@ typedef struct {
   int32_t dense_rows_full;  /* dense form: the same, full sweeps */
   int32_t cluster_ctas;     /* small FP64 systems: CTAs of the resident cluster (0 = not used) */
   int32_t pull_lanes;       /* CSR form: lanes per row of the in-place FP32 full sweep (0 = scatter form) */
+  int32_t mean_window;      /* CSR form: target slots per window of the window-form mean sweep
+                               (0 = tile form) */
+  int32_t windows;          /* CSR form: windows of the window form (0 = tile form) */
   double tune_ms;           /* host time spent tuning */
   double reserved[3];
 } gabp_tuning;

@@ -257,11 +257,12 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
     case CK_MEAN: {
       if (kind == CK_SWEEP32) {
         c.sweeps_full++;
-        if (c.pending_freeze) { c.frozen = 1; c.pending_freeze = 0; c.par_e ^= 1; }
+        if (c.pending_freeze) { c.frozen = 1; c.pending_freeze = 0; c.par_e ^= 1; c.e_slots = 1; }
         else c.par_m ^= 1;
       } else {
         c.sweeps_mean++;
         c.par_e ^= 1;
+        c.e_slots = 0;
       }
       if (c.mode == CTL_PREC && c.frozen) {
         c.sweeps++;

@@ -115,6 +115,8 @@ struct Ctl {
   double *ring[3];
   double *xw;                   // where the next sweep that writes means writes them
   int check_now;                // the sweep just run is followed by a residual check
+  int e_slots;                  // the mean messages in e[par_e] are in the slot layout (written
+                                // by a freeze sweep); window handles read them so once
   int K;                        // CTL_MULTI: right-hand sides
   const double *Bm;             // CTL_MULTI: n x K right-hand sides (row-major)
   double *Xm;                   // CTL_MULTI: n x K solutions (row-major)
@@ -217,6 +219,49 @@ struct Graph {
     v.row1 = col_rows[c + 1];
     return v;
   }
+};
+
+// Window form of the mean-only sweep (gabp_window.cu).  Windows are ranges of
+// consecutive rows: win[w] = (first row, first slot), win[nwin] = (n, E).
+// Every window also owns a padded range [R0[w], R0[w+1]) (a multiple of 8
+// positions) of a second index space.  There the messages live in receive
+// order -- bins[.] holds at window J's range the messages bound for J,
+// grouped by source window -- and p2[R0[J] + k] = the window-local slot of
+// element k.  In the same space, the send order of window I: outmap[R0[I] +
+// q] = the window-local slot whose row sends the message of send position q
+// (positions sorted by destination slot), cq[R0[I] + q] = its coefficient.
+// sruns[r], r in [srun_ptr[I], srun_ptr[I+1]) = (first send position of the
+// run, window-local; its first receive position), one run per destination
+// window.  heavy_rows lists the rows of degree > 64.
+struct WinView {
+  const int2 *win;
+  const int32_t *R0;
+  const uint16_t *p2, *outmap;
+  const int32_t *srun_ptr;
+  const int2 *sruns;
+  const int32_t *heavy_ptr, *heavy_rows;
+  float *cq;
+  void *bins[2];                // receive-ordered messages (float or bf16), one per parity
+  int32_t nwin;
+  int32_t rcap;                 // most rows of a window
+  int32_t off_om, off_cq, off_slot, off_rows, off_srt;   // shared-memory layout (bytes)
+};
+
+struct Win {
+  int32_t nwin = 0, wcap = 0, runcap = 0, target = 0, rcap = 0;
+  int32_t off_om = 0, off_cq = 0, off_slot = 0, off_rows = 0, off_srt = 0;
+  int32_t blocks = 0, grid = 0;   // CTAs per SM; CTAs of a launch
+  int64_t nruns = 0;
+  size_t smem = 0;              // dynamic shared memory per CTA
+  int2 *win = nullptr;
+  int32_t *R0 = nullptr;
+  uint16_t *p2 = nullptr, *outmap = nullptr;
+  int32_t *srun_ptr = nullptr;
+  int2 *sruns = nullptr;
+  int32_t *heavy_ptr = nullptr, *heavy_rows = nullptr;
+  float *cq = nullptr;
+  void *bins[2] = {nullptr, nullptr};
+  WinView view() const;
 };
 
 // Kernel launchers (gabp_kernels.cu).  Each returns the number of kernels it
@@ -450,6 +495,12 @@ int launch_lsq_extract(cudaStream_t st, int64_t n_aug, const int32_t *sys_of_row
                        const int64_t *aug_off, const int32_t *K, const int64_t *x_off,
                        const double *x_aug, double *xhat);
 void free_graph(Graph &g);
+// Window form (gabp_window.cu): windows of about `target` slots.
+gabp_status build_windows(const Graph &g, int32_t target, bool bf16, Win &W, cudaStream_t st,
+                          std::string *msg);
+void free_windows(Win &W);
+int launch_mean_win(const Graph &g, const Win &W, cudaStream_t st, Buffers B, Ctl *ctl,
+                    DevScalars *red, bool bf16);
 cudaError_t set_row_tiles(Graph &g, int slots, int rows, int heavy_degree, cudaStream_t st);
 
 }  // namespace gabp
@@ -495,6 +546,7 @@ struct gabp_s {
   gabp::Grid *grid = nullptr;          // nearest-neighbour operators on a box, grid form
   gabp_tuning tuning{};                // launch shapes (chosen by the autotuner or default)
   gabp::Resident res{};                // small FP64 systems: one cluster launch per solve
+  gabp::Win win{};                     // window form of the mean sweep (nwin = 0: not in use)
   double *ring[3] = {};                // Aitken: the last three FP64 tentative means
   // colour schedule (Section III-C serial schedule by colour classes)
   int32_t *perm = nullptr;             // device: caller's row of renumbered row i

@@ -316,7 +316,9 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
       return launch_check64(g, st, h->buf, h->ctl, h->red,
                             h->opt.aitken > 0 && h->opt.precision == GABP_PREC_FP64);
     case PH_FULL32: return launch_sweep32(g, st, h->buf, h->ctl, h->red, is_bf16(h));
-    case PH_MEAN: return launch_mean(g, st, h->buf, h->ctl, h->red, is_bf16(h));
+    case PH_MEAN:
+      return h->win.nwin > 0 ? launch_mean_win(g, h->win, st, h->buf, h->ctl, h->red, is_bf16(h))
+                             : launch_mean(g, st, h->buf, h->ctl, h->red, is_bf16(h));
     case PH_REFINE: {
       const int k = launch_refine(g, st, h->buf, h->ctl, h->red);
       if (g.ncol > 0) zero_messages(h, st, false);   // the next inner solve starts from zero
@@ -819,6 +821,7 @@ void release(gabp_handle h) {
   cudaFree(h->cols.bnorm); cudaFree(h->cols.thr); cudaFree(h->cols.rn);
   cudaFree(h->cols.inv_rn); cudaFree(h->cols.bmax); cudaFree(h->cols.rmax);
   free_graph(h->g);
+  free_windows(h->win);
   Buffers &B = h->buf;
   cudaFree(B.m64[0]); cudaFree(B.m64[1]);
   cudaFree(B.m32[0]); cudaFree(B.m32[1]); cudaFree(B.e[0]); cudaFree(B.e[1]);
@@ -1067,6 +1070,13 @@ gabp_status resident_solve(gabp_handle h, const double *b, double *x, double tol
 }
 
 // ---- autotuner ----
+int64_t num_sms_host() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(sms, 1);
+}
+
 // Milliseconds per launch of `launch` (CUDA events on the handle's stream,
 // after one untimed launch).
 template <class F>
@@ -1110,6 +1120,8 @@ void fill_tuning(gabp_handle h) {
   t.heavy_degree = h->g.heavy_degree;
   t.group_lanes = h->g.group;
   t.pull_lanes = h->g.pull_lanes;
+  t.mean_window = h->win.nwin > 0 ? h->win.target : 0;
+  t.windows = h->win.nwin;
   const bool rows = h->dense && !h->dense->serial;   // the serial kernels take whole rows
   t.dense_rows_mean = rows ? h->dense->rows_mean : 0;
   t.dense_rows_full = rows ? h->dense->rows_full : 0;
@@ -1199,6 +1211,36 @@ void autotune(gabp_handle h) {
         if (ms < best_f) { best_f = ms; pick = G; }
       }
       g.pull_lanes = pick;
+    }
+    // form of the mean sweep: the tiles just chosen, or windows of about
+    // E / (SMs x m) slots (synchronous schedule)
+    if (h->opt.mean_window == 0 && g.ncol == 0 && g.E > 0) {
+      free_windows(h->win);
+      tuning_ctl(h);
+      float best_m = time_launches(h, 3, [&] { launch_mean(g, h->stream, h->buf, h->ctl, h->red, bf16); });
+      int32_t pick = 0;
+      const int64_t sms = num_sms_host();
+      std::vector<int32_t> targets;
+      for (int m : {3, 4, 6, 8}) {
+        const int64_t t = std::min<int64_t>(24000, std::max<int64_t>(256, (g.E + sms * m - 1) / (sms * m)));
+        if (std::find(targets.begin(), targets.end(), static_cast<int32_t>(t)) == targets.end())
+          targets.push_back(static_cast<int32_t>(t));
+      }
+      for (int32_t t : targets) {
+        std::string msg;
+        if (build_windows(g, t, bf16, h->win, h->stream, &msg) != GABP_OK) continue;
+        tuning_ctl(h);
+        const float ms = time_launches(h, 3, [&] {
+          launch_mean_win(g, h->win, h->stream, h->buf, h->ctl, h->red, bf16);
+        });
+        ++T.candidates;
+        if (ms < best_m) { best_m = ms; pick = t; }
+      }
+      free_windows(h->win);
+      if (pick > 0) {
+        std::string msg;
+        if (build_windows(g, pick, bf16, h->win, h->stream, &msg) != GABP_OK) free_windows(h->win);
+      }
     }
   }
   if (!mixed && h->res.C > 0 && h->opt.cluster_ctas == 0) {
@@ -1344,6 +1386,12 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
     g_create_error = "naive must be 0 or 1; Algorithm 1 (naive = 1) needs FP64, schedule 0 and damping 0";
     return GABP_ERR_INVALID_ARG;
   }
+  if (o.mean_window < -1 || (o.mean_window > 0 && (o.mean_window < 256 || o.mean_window > 65536)) ||
+      (o.mean_window > 0 && o.schedule != 0)) {
+    delete h;
+    g_create_error = "mean_window must be -1, 0 or 256..65536; the window form (> 0) needs schedule 0";
+    return GABP_ERR_INVALID_ARG;
+  }
   if (!(o.pull_lanes == -1 || o.pull_lanes == 0 || o.pull_lanes == 2 || o.pull_lanes == 4 ||
         o.pull_lanes == 8 || o.pull_lanes == 16 || o.pull_lanes == 32) ||
       (o.pull_lanes > 0 && (o.schedule != 0 || o.damping != 0.0))) {
@@ -1411,6 +1459,14 @@ gabp_status gabp_create(gabp_handle *out, int64_t n, int64_t nnz, const int64_t 
     s = guarded(h, [&] {
       if (h->opt.precision == GABP_PREC_FP64 && !h->opt.naive) setup_resident(h);
       return GABP_OK;
+    });
+  }
+  if (s == GABP_OK && h->opt.mean_window > 0 && h->opt.precision != GABP_PREC_FP64) {
+    s = guarded(h, [&] {
+      std::string msg;
+      const gabp_status r = build_windows(h->g, h->opt.mean_window, is_bf16(h), h->win, h->stream, &msg);
+      if (r != GABP_OK) h->last_error = msg;
+      return r;
     });
   }
   if (s == GABP_OK) {

@@ -51,7 +51,8 @@ class GabpOptions(ctypes.Structure):
                 ("small_form", ctypes.c_int32), ("cluster_ctas", ctypes.c_int32),
                 ("aitken", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("damp_scope", ctypes.c_int32), ("pull_lanes", ctypes.c_int32),
-                ("pinv_shift", ctypes.c_double), ("naive", ctypes.c_int32)]
+                ("pinv_shift", ctypes.c_double), ("naive", ctypes.c_int32),
+                ("mean_window", ctypes.c_int32)]
 
 
 class GabpStats(ctypes.Structure):
@@ -74,6 +75,7 @@ class GabpTuning(ctypes.Structure):
                 ("heavy_degree", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
                 ("dense_rows_mean", ctypes.c_int32), ("dense_rows_full", ctypes.c_int32),
                 ("cluster_ctas", ctypes.c_int32), ("pull_lanes", ctypes.c_int32),
+                ("mean_window", ctypes.c_int32), ("windows", ctypes.c_int32),
                 ("tune_ms", ctypes.c_double), ("reserved", ctypes.c_double * 3)]
 
     def as_dict(self):
@@ -357,7 +359,7 @@ def gabp_version() -> str:
 def _options(*, precision=PREC_FP64, residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0,
              inner_tol=0.0, profile=False, damping=0.0, stream: int | None = None, autotune=False,
              tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0, aitken=0,
-             schedule=0, damp_scope=0, pull_lanes=0, naive=0) -> GabpOptions:
+             schedule=0, damp_scope=0, pull_lanes=0, naive=0, mean_window=0) -> GabpOptions:
     o = gabp_default_options()
     o.precision = precision
     o.residual_kind = residual_kind
@@ -378,6 +380,7 @@ def _options(*, precision=PREC_FP64, residual_kind=RESIDUAL_REL, check_every=0, 
     o.damp_scope = damp_scope
     o.pull_lanes = pull_lanes
     o.naive = naive
+    o.mean_window = mean_window
     return o
 
 
@@ -393,13 +396,13 @@ class Solver:
                  residual_kind=RESIDUAL_REL, check_every=0, group_lanes=0, inner_tol=0.0,
                  profile=False, damping=0.0, stream: int | None = None, autotune=False,
                  tile_slots=0, tile_rows=0, heavy_degree=0, small_form=0, cluster_ctas=0,
-                 aitken=0, schedule=0, damp_scope=0, pull_lanes=0, naive=0):
+                 aitken=0, schedule=0, damp_scope=0, pull_lanes=0, naive=0, mean_window=0):
         o = _options(precision=precision, residual_kind=residual_kind, check_every=check_every,
                      group_lanes=group_lanes, inner_tol=inner_tol, profile=profile, damping=damping,
                      stream=stream, autotune=autotune, tile_slots=tile_slots, tile_rows=tile_rows,
                      heavy_degree=heavy_degree, small_form=small_form, cluster_ctas=cluster_ctas,
                      aitken=aitken, schedule=schedule, damp_scope=damp_scope, pull_lanes=pull_lanes,
-                     naive=naive)
+                     naive=naive, mean_window=mean_window)
         h = gabp_create(row_ptr, col, val, rev, o)
         return cls(h, len(row_ptr) - 1, int(row_ptr[-1]))
 

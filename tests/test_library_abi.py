@@ -188,6 +188,22 @@ def test_pull_lanes_is_validated(lib):
         assert "pull_lanes" in str(ei.value)
 
 
+def test_mean_window_is_validated(lib):
+    """The window form of the mean sweep takes windows of 256..65536 slots
+    (-1 = tile form, 0 = automatic) and needs the synchronous schedule;
+    refused on the host."""
+    from paper_0810_1119_gb300 import gabp as G
+    m = W.poisson2d(4)
+    for mw, schedule in ((-2, 0), (1, 0), (255, 0), (65537, 0), (1024, 1)):
+        o = G.gabp_default_options()
+        o.precision = G.PREC_MIXED_FP32
+        o.mean_window, o.schedule = mw, schedule
+        with pytest.raises(G.GabpError) as ei:
+            G.gabp_create(m.row_ptr, m.col, m.val, None, o)
+        assert ei.value.name == "GABP_ERR_INVALID_ARG"
+        assert "mean_window" in str(ei.value)
+
+
 def test_naive_is_validated(lib):
     """Algorithm 1 (naive = 1) needs FP64, the synchronous schedule and no
     damping; refused on the host."""
