@@ -244,12 +244,13 @@ struct WinView {
   void *bins[2];                // receive-ordered messages (float or bf16), one per parity
   int32_t nwin;
   int32_t rcap;                 // most rows of a window
-  int32_t off_om, off_cq, off_slot, off_rows, off_srt;   // shared-memory layout (bytes)
+  int32_t off_om, off_cq, off_slot, off_rows, off_srt, off_bits;   // shared-memory layout (bytes)
+  int32_t nbits;                // words of the run-start bitmap
 };
 
 struct Win {
   int32_t nwin = 0, wcap = 0, runcap = 0, target = 0, rcap = 0;
-  int32_t off_om = 0, off_cq = 0, off_slot = 0, off_rows = 0, off_srt = 0;
+  int32_t off_om = 0, off_cq = 0, off_slot = 0, off_rows = 0, off_srt = 0, off_bits = 0, nbits = 0;
   int32_t blocks = 0, grid = 0;   // CTAs per SM; CTAs of a launch
   int64_t nruns = 0;
   size_t smem = 0;              // dynamic shared memory per CTA

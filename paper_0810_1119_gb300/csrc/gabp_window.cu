@@ -112,11 +112,18 @@ __device__ __forceinline__ void issue_range(const int32_t *R0, const T *src, int
   if (bytes) bulk_g2s_hint(dst, src + r0, bytes, bar, pol);
 }
 
-template <class T>
-__global__ void __launch_bounds__(kWinBlock, 1)
-mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[2];   // [0]: receive stage, [1]: send streams
+// Input of a window sweep: none (the first sweep of an inner solve), the
+// slot layout (the sweep after a freeze), or the receive-ordered buffer.
+constexpr int kInZero = 0, kInSlots = 1, kInStaged = 2;
+
+// The sweep over this CTA's windows, specialised on its input, on whether it
+// copies c into send order and on damping (all three are the same for the
+// whole launch): the common case -- staged input, no copy, no damping --
+// keeps no dead branches in its inner loops.
+template <class T, int IN, bool REFRESH, bool DAMP>
+__device__ __forceinline__ void win_sweep(const GraphView &g, const WinView &w, const Buffers &B,
+                                          Ctl *ctl, DevScalars *red, unsigned char *smem,
+                                          uint64_t *bars) {
   T *recv = reinterpret_cast<T *>(smem);                                        // receive range
   uint16_t *om = reinterpret_cast<uint16_t *>(smem + w.off_om);                 // outmap
   float *cqs = reinterpret_cast<float *>(smem + w.off_cq);                      // cq
@@ -124,10 +131,11 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
   int32_t *rstart = reinterpret_cast<int32_t *>(smem + w.off_rows);             // row starts (+ end)
   float *rowv = reinterpret_cast<float *>(smem + w.off_rows + 4 * (w.rcap + 1)); // row sums, then h~
   int2 *srt = reinterpret_cast<int2 *>(smem + w.off_srt);                       // send runs + sentinel
+  uint32_t *rbits = reinterpret_cast<uint32_t *>(smem + w.off_bits);            // run starts (bitmap)
   const int pe = ctl->par_e, pmon = ctl->par_mon;
-  const bool zin = ctl->first != 0;        // incoming messages known to be zero
-  const bool slots_in = ctl->e_slots != 0; // input in the slot layout; refresh cq
-  const bool staged = !zin && !slots_in;   // input from the receive-ordered buffer
+  constexpr bool zin = IN == kInZero;        // incoming messages known to be zero
+  constexpr bool slots_in = REFRESH;         // c into send order (first sweep after a freeze)
+  constexpr bool staged = IN == kInStaged;   // input from the receive-ordered buffer
   const double inv_rn = ctl->inv_rn;
   // (the parity selects with ?: -- indexing a kernel parameter's array with a
   // runtime value would copy the parameter to local memory)
@@ -174,31 +182,36 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
     pend_s = j & 1;
     const int2 lo = w.win[wi], hi = w.win[wi + 1];
     const int32_t r0 = lo.x, s0 = lo.y, ns = hi.y - lo.y, nr = hi.x - lo.x;
-    // this thread's rows (at most kWinRowsPerThread): their data now, used in B
+    // this thread's rows (at most kWinRowsPerThread): their data now, used
+    // in B; the row starts go to shared memory after the scatter below, so
+    // that these loads overlap it
     float p_rhs[kWinRowsPerThread], p_invP[kWinRowsPerThread], p_prev[kWinRowsPerThread];
+    int32_t p_rp[kWinRowsPerThread];
 #pragma unroll
     for (int u = 0; u < kWinRowsPerThread; ++u) {
       const int32_t k = tid + u * NT;
       p_rhs[u] = 0.f;
       p_invP[u] = 0.f;
       p_prev[u] = 0.f;
+      p_rp[u] = 0;
       if (k < nr) {
         const int32_t i = r0 + k;
-        rstart[k] = g.rp[i] - s0;
+        p_rp[u] = g.rp[i];
         p_rhs[u] = zin ? static_cast<float>(B.r64[i] * inv_rn) : B.rhs32[i];
         p_invP[u] = B.invP32[i];
         p_prev[u] = zin ? 0.f : mon_prev[i].y;
       }
     }
-    if (tid == 0) rstart[nr] = ns;
+    const int32_t nsr = w.srun_ptr[wi + 1] - w.srun_ptr[wi];
     {
-      const int32_t sb = w.srun_ptr[wi], nsr = w.srun_ptr[wi + 1] - sb;
+      const int32_t sb = w.srun_ptr[wi];
       for (int32_t k = tid; k < nsr; k += NT) srt[k] = w.sruns[sb + k];
       if (tid == 0) srt[nsr] = make_int2(ns, 0);   // sentinel: runs end at ns
+      for (int32_t k = tid; k < w.nbits; k += NT) rbits[k] = 0u;
     }
 
     // ---- A: incoming messages into shared memory, slot order ----
-    if (slots_in && !zin) {
+    if (IN == kInSlots) {
       for (int32_t k = tid; k < ns; k += NT) slot[k] = ld_eta(eslot + s0 + k);
     } else if (staged) {
       const bool got = mbar_wait(bar_r, j & 1);
@@ -217,6 +230,12 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
         }
       }
     }
+#pragma unroll
+    for (int u = 0; u < kWinRowsPerThread; ++u) {
+      const int32_t k = tid + u * NT;
+      if (k < nr) rstart[k] = p_rp[u] - s0;
+    }
+    if (tid == 0) rstart[nr] = ns;
     __syncthreads();
     // the receive stage is free: the next window's range streams in during B and C
     if (staged && nx < w.nwin) {
@@ -227,10 +246,12 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
       pend_r = (j + 1) & 1;
     }
 
+    // run starts of the send order as a bitmap (read in C, after B's barrier)
+    for (int32_t k = tid; k < nsr; k += NT) atomicOr(&rbits[srt[k].x >> 5], 1u << (srt[k].x & 31));
     // ---- B: node totals, d_i, and h~_i - e for every incoming slot: a
     // thread per row (its data prefetched), the row's slots summed in slot
     // order; rows of degree > 64 first take their sum from a warp each ----
-    if (!zin) {
+    if constexpr (!zin) {
       for (int32_t hh = w.heavy_ptr[wi] + warp; hh < w.heavy_ptr[wi + 1]; hh += nwarp) {
         const int32_t k = w.heavy_rows[hh] - r0;
         const int32_t rs = rstart[k], re = rstart[k + 1];
@@ -246,12 +267,12 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
     for (int u = 0; u < kWinRowsPerThread; ++u) {
       const int32_t k = tid + u * NT;
       if (k < nr) {
-        const int32_t i = r0 + k;
-        const int32_t rs = rstart[k], re = rstart[k + 1];
+        const int32_t lr = k, i = r0 + k;
+        const int32_t rs = rstart[lr], re = rstart[lr + 1];
         const bool heavy = re - rs > kWinHeavy;
         float sH = 0.f;
-        if (!zin) {
-          if (heavy) sH = rowv[k];
+        if constexpr (!zin) {
+          if (heavy) sH = rowv[lr];
           else
             for (int32_t s = rs; s < re; ++s) sH += slot[s];
         }
@@ -260,9 +281,9 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
         mon_out[i] = make_float2(0.f, di);
         mdd = fmax_bits(mdd, di - p_prev[u]);
         md = fmax_bits(md, di);
-        if (zin) B.rhs32[i] = p_rhs[u];
-        if (heavy) rowv[k] = Th;
-        else if (zin)
+        if constexpr (zin) B.rhs32[i] = p_rhs[u];
+        if (heavy) rowv[lr] = Th;
+        else if constexpr (zin)
           for (int32_t s = rs; s < re; ++s) slot[s] = Th;
         else
           for (int32_t s = rs; s < re; ++s) slot[s] = Th - slot[s];
@@ -277,35 +298,68 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
       for (int32_t s = rs + lane; s < re; s += 32) slot[s] = zin ? Th : Th - slot[s];
     }
     if (w.heavy_ptr[wi + 1] > w.heavy_ptr[wi]) __syncthreads();
-    // ---- C: outgoing messages, a warp per send run ----
+    // ---- C: outgoing messages ----
     {
       const bool got = mbar_wait(bar_s, j & 1);
       if (__syncthreads_or(!got)) { failed = true; break; }
       pend_s = -1;
-      // a warp per run (one per destination window), lanes over its
-      // consecutive send positions: the destination is the run's first
-      // receive position plus the offset, and each store instruction writes
-      // one contiguous piece of the run
+      // each warp a contiguous range of send positions; the lanes take
+      // consecutive positions (so a store instruction writes a contiguous
+      // piece of a run), four rounds of 32 at a time.  A position's
+      // destination is its run's first receive position plus its offset in
+      // the run.
       const int32_t a = w.R0[wi];
-      const int32_t nsr = w.srun_ptr[wi + 1] - w.srun_ptr[wi];
-      for (int32_t r = warp; r < nsr; r += nwarp) {
-        const int2 e = srt[r];
-        const int32_t len = srt[r + 1].x - e.x;
-        for (int32_t t = lane; t < len; t += 32) {
-          const int32_t q = e.x + t, dst = e.y + t;
-          const int32_t sl = om[q];
-          float cc = cqs[q];
-          if (slots_in) {   // first sweep after a freeze: c into send order
-            cc = B.c32[s0 + sl];
-            w.cq[a + q] = cc;
+      const int32_t per = ((ns + nwarp - 1) / nwarp + 127) & ~127;
+      const int32_t qa = warp * per, qb = min(ns, qa + per);
+      // run holding the warp's first position; a lane's run is that one plus
+      // the run starts between the first position of its 32 and its own
+      int32_t rb = 0;
+      if (qa < qb) {
+        int32_t lo_r = 0, hi_r = nsr - 1;
+        while (lo_r < hi_r) {
+          const int32_t m = (lo_r + hi_r + 1) >> 1;
+          if (srt[m].x <= qa) lo_r = m; else hi_r = m - 1;
+        }
+        rb = lo_r;
+      }
+      const uint32_t below = ((2u << lane) - 1u) & ~1u;   // positions 1 .. lane of a word
+      for (int32_t q0 = qa; q0 < qb; q0 += 128) {
+        int32_t dst[4], sl[4];
+        float cc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t qw = q0 + 32 * u, q = qw + lane;
+          const uint32_t word = rbits[qw >> 5];
+          const int32_t rl = rb + __popc(word & below);
+          rb += __popc(word & ~1u) + static_cast<int32_t>(rbits[(qw >> 5) + 1] & 1u);
+          dst[u] = 0;
+          sl[u] = 0;
+          cc[u] = 0.f;
+          if (q < qb) {
+            const int2 e = srt[rl];
+            dst[u] = e.y + (q - e.x);
+            sl[u] = om[q];
+            cc[u] = cqs[q];
           }
-          float v = cc * slot[sl];
-          if (gam > 0.f) {
-            float o = 0.f;
-            if (!zin) o = slots_in ? ld_eta(eslot + g.rev[s0 + sl]) : ld_eta(bin_in + dst);
-            v = gam * o + (1.f - gam) * v;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t q = q0 + 32 * u + lane;
+          if (q < qb) {
+            float c = cc[u];
+            if constexpr (slots_in) {   // first sweep after a freeze: c into send order
+              c = B.c32[s0 + sl[u]];
+              w.cq[a + q] = c;
+            }
+            float v = c * slot[sl[u]];
+            if constexpr (DAMP) {
+              float o = 0.f;
+              if constexpr (IN == kInSlots) o = ld_eta(eslot + g.rev[s0 + sl[u]]);
+              else if constexpr (IN == kInStaged) o = ld_eta(bin_in + dst[u]);
+              v = gam * o + (1.f - gam) * v;
+            }
+            st_keep(bin_out + dst[u], v, pol_keep);
           }
-          st_keep(bin_out + dst, v, pol_keep);
         }
       }
     }
@@ -321,6 +375,29 @@ mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
   __syncthreads();
   block_max4(widen(mdd), widen(md), 0, 0, &red->max_dx, &red->max_x, nullptr, nullptr);
   last_block_control(ctl, red, CK_MEAN);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kWinBlock, 1)
+mean_win_kernel(GraphView g, WinView w, Buffers B, Ctl *ctl, DevScalars *red) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];   // [0]: receive stage, [1]: send streams
+  const bool zin = ctl->first != 0, slots = ctl->e_slots != 0, damp = ctl->damping > 0.0;
+  if (zin) {
+    if (slots) {
+      if (damp) win_sweep<T, kInZero, true, true>(g, w, B, ctl, red, smem, bars);
+      else win_sweep<T, kInZero, true, false>(g, w, B, ctl, red, smem, bars);
+    } else {
+      if (damp) win_sweep<T, kInZero, false, true>(g, w, B, ctl, red, smem, bars);
+      else win_sweep<T, kInZero, false, false>(g, w, B, ctl, red, smem, bars);
+    }
+  } else if (slots) {
+    if (damp) win_sweep<T, kInSlots, true, true>(g, w, B, ctl, red, smem, bars);
+    else win_sweep<T, kInSlots, true, false>(g, w, B, ctl, red, smem, bars);
+  } else {
+    if (damp) win_sweep<T, kInStaged, false, true>(g, w, B, ctl, red, smem, bars);
+    else win_sweep<T, kInStaged, false, false>(g, w, B, ctl, red, smem, bars);
+  }
 }
 
 constexpr int kWinMaxSmem = 225 * 1024;   // largest dynamic shared memory a handle may use
@@ -358,6 +435,8 @@ WinView Win::view() const {
   v.off_slot = off_slot;
   v.off_rows = off_rows;
   v.off_srt = off_srt;
+  v.off_bits = off_bits;
+  v.nbits = nbits;
   return v;
 }
 
@@ -365,7 +444,8 @@ void free_windows(Win &W) {
   for (void *p : {static_cast<void *>(W.win), static_cast<void *>(W.R0), static_cast<void *>(W.p2),
                   static_cast<void *>(W.outmap), static_cast<void *>(W.srun_ptr),
                   static_cast<void *>(W.sruns), static_cast<void *>(W.heavy_ptr),
-                  static_cast<void *>(W.heavy_rows), static_cast<void *>(W.cq), W.bins[0], W.bins[1]})
+                  static_cast<void *>(W.heavy_rows), static_cast<void *>(W.cq), W.bins[0],
+                  W.bins[1]})
     if (p) cudaFree(p);
   W = Win{};
 }
@@ -489,7 +569,9 @@ gabp_status build_windows(const Graph &g, int32_t target, bool bf16, Win &W, cud
   const size_t off_slot = off_cq + r128(static_cast<size_t>(ecap) * 4);
   const size_t off_rows = off_slot + r128(static_cast<size_t>(wcap) * 4);
   const size_t off_srt = off_rows + r128(static_cast<size_t>(2 * rowcap + 1) * 4);
-  const size_t smem = off_srt + sizeof(int2) * (static_cast<size_t>(runcap) + 1);
+  const size_t off_bits = off_srt + r128(sizeof(int2) * (static_cast<size_t>(runcap) + 1));
+  const int32_t nbits = (ecap + 31) / 32 + 8;   // the send loop reads a word past its last position
+  const size_t smem = off_bits + sizeof(uint32_t) * static_cast<size_t>(nbits);
   if (smem > static_cast<size_t>(kWinMaxSmem)) {
     *msg = "window form: a window does not fit shared memory";
     return GABP_ERR_INVALID_ARG;
@@ -530,6 +612,8 @@ gabp_status build_windows(const Graph &g, int32_t target, bool bf16, Win &W, cud
   W.off_slot = static_cast<int32_t>(off_slot);
   W.off_rows = static_cast<int32_t>(off_rows);
   W.off_srt = static_cast<int32_t>(off_srt);
+  W.off_bits = static_cast<int32_t>(off_bits);
+  W.nbits = nbits;
   W.smem = smem;
   W.blocks = bps;
   {
