@@ -72,9 +72,7 @@ BYTES_GRID = {
 # DRAM traffic of the dominant kernels from ncu captures (dram__bytes_read.sum
 # + dram__bytes_write.sum per launch; ncu flushes caches between replays, so
 # these are cold-cache figures), valid only for the kernel sources they were
-# taken on: a changed source makes the figure null.  Commands and numbers:
-# profiles/mean_kernel_er1e6.md, profiles/pull32_kernel_er1e6.md,
-# profiles/dense_mean_kernel_detect1024.md and profiles/dense_serial_detect1024.md.
+# taken on: a changed source makes the figure null.
 TRAFFIC = {
     "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "b04585fc006c2b3e",
              "bytes_per_launch": 171.9e6},
@@ -198,15 +196,44 @@ class ClockSampler:
 
 
 def _cpu_baseline(m, b, rounds: int):
+    """The oracle on the host cores: edge-updates/s over `rounds` fixed rounds
+    on all cores and over 2 rounds on one core, and the time to the 1e-10
+    relative residual on all cores (measured; on one core estimated from its
+    time per round, labelled as such)."""
     import oracle
+    E = m.n_directed_edges
+    cores = oracle.num_threads()
     t0 = time.perf_counter()
     r = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_FIXED, max_rounds=rounds)
     dt = time.perf_counter() - t0
-    E = m.n_directed_edges
-    return {"value": E * r["rounds"] / dt, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_FIXED, max_rounds=2)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    t0 = time.perf_counter()
+    rs = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=5000, tol=TOL)
+    dts = time.perf_counter() - t0
+    return {"value": E * r["rounds"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{r['rounds']} synchronous FP64 rounds (Alg. 2) of the n=1e6 ER system, "
-                      f"{dt:.2f} s"}
+                      f"{dt:.2f} s",
+            "single_thread": {"value": E * 2 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"2 rounds, {dt1:.2f} s"},
+            "time_to_1e-10_s": {"all_cores": dts, "rounds": rs["rounds"], "status": rs["status"],
+                                "single_thread_estimate": dt1 / 2 * rs["rounds"],
+                                "note": "all cores measured (a full oracle solve with its residual "
+                                        "check every round); one core = its time per round x rounds"}}
+
+
+def _emit(line, args):
+    """Print a workload's JSON line, or hand it back when the default run
+    collects it into its `configs` entry."""
+    if getattr(args, "collect", False):
+        return line
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def reduce_over_ranks(dist, times, counts, device):
@@ -250,6 +277,49 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _collect_configs(args):
+    """The other configurations of the workload list, each run the way its
+    own --workload run does it with 1-3 timed steps, and each with its error
+    against the oracle or the closed form: 2D Poisson 32x32 (FP64, absolute
+    1e-10), 64 right-hand sides on ER n=2e6, the 4096-system detection batch
+    (colour-serial, damping 0.2 on the z -> x^ messages), and 3D Poisson 256^3
+    in the grid form (red-black, mixed precision).  Clocks are sampled over
+    all of them."""
+    import copy
+    import torch
+    base = copy.copy(args)
+    base.collect = True
+    base.warmup = 1
+    jobs = (
+        ("poisson32", run_poisson32, {"steps": 3}),
+        ("multi64", run_multi, {"steps": 1, "n": 2_000_000, "oracle_check": True}),
+        ("detect", run_detect, {"steps": 2, "schedule": 1, "damp_scope": 1, "damping": 0.2,
+                                "psi_zero": False, "lsq_form": 0, "nsys": 4096}),
+        ("poisson3d_256_grid", run_poisson3d, {"steps": 1, "p": 256, "form": "grid", "schedule": 1,
+                                               "only": ("mixed_fp32",), "oracle_residual": True,
+                                               "max_iter": 400000}),
+    )
+    out = {}
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    for name, fn, kw in jobs:
+        a = copy.copy(base)
+        for k, v in kw.items():
+            setattr(a, k, v)
+        t0 = time.perf_counter()
+        try:
+            line = fn(a)
+            line.pop("tuning", None)
+            for r in line.get("runs", {}).values():
+                r.pop("tuning", None)
+            out[name] = line
+        except Exception as e:   # a failing configuration must not drop the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    out["clocks"] = sampler.stop()
+    return out
 
 
 def run_gabp(args):
@@ -421,8 +491,19 @@ def run_gabp(args):
             "clocks": clocks,
             "tuning": {"mixed": mixed.tuning(), "fp64": fp64.tuning()},
         }
+        if not args.no_cpu_baseline:
+            # the mixed solution against the oracle's FP64 solution to 1e-13
+            import oracle
+            ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=5000,
+                              tol=1e-13)
+            xg = xt.cpu().numpy()
+            line["max_rel_err_vs_oracle"] = float(np.abs(xg - ref["x"]).max() / np.abs(ref["x"]).max())
+            line["oracle_reference"] = {"rounds": ref["rounds"], "status": ref["status"],
+                                        "stop": "relative residual 1e-13"}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = _cpu_baseline(m, b, args.cpu_rounds)
+        if world == 1 and not args.no_configs:
+            line["configs"] = _collect_configs(args)
         print(json.dumps(line), flush=True)
     mixed.close()
     fp64.close()
@@ -489,6 +570,15 @@ def run_multi(args):
     z.record(stream)
     torch.cuda.synchronize()
     t64 = a.elapsed_time(z)
+    err_col0 = None
+    if getattr(args, "oracle_check", False):
+        # column 0 of the mixed solve against the oracle's FP64 solution to 1e-13
+        import oracle
+        gabp.gabp_solve_multi(s.handle, B, X, TOL, 5000)
+        x0 = X[:, 0].cpu().numpy()
+        ref = oracle.gabp(m.row_ptr, m.col, m.val, B[:, 0].cpu().numpy(), stop=oracle.STOP_RES_REL,
+                          max_rounds=5000, tol=1e-13)
+        err_col0 = float(np.abs(x0 - ref["x"]).max() / np.abs(ref["x"]).max())
     line = {"metric": "GaBP edge x RHS message updates/s (64 right-hand sides, mixed FP32 + FP64 refinement to 1e-10)",
             "value": updates / (t * 1e-3), "unit": "edge-rhs-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t, "higher_is_better": True,
@@ -500,13 +590,13 @@ def run_multi(args):
             "time_to_solution_ms": {"mixed_multi": t, "fp64_column_by_column": t64,
                                     "speedup_vs_fp64": t64 / t},
             "algorithmic_bytes_per_mean_sweep": bytes_meanK, "roofline": roof,
+            "max_rel_err_vs_oracle_column0": err_col0,
             "kernel_ms_per_step": {"mean_K": sp["ms_mean"], "precision": sp["ms_full"],
                                    "residual": sp["ms_residual"], "other": sp["ms_other"]},
             "tuning": s.tuning()}
-    print(json.dumps(line), flush=True)
     s.close()
     s64.close()
-    return 0
+    return _emit(line, args)
 
 
 def run_poisson32(args):
@@ -578,8 +668,7 @@ def run_poisson32(args):
             "tuning": f["tuning"],
             "cpu_baseline": {"value": 1e3 * cpu_s, "unit": "ms", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": f"the full solve ({ref['rounds']} rounds)"}}
-    print(json.dumps(line), flush=True)
-    return 0
+    return _emit(line, args)
 
 
 def run_poisson3d(args):
@@ -607,8 +696,11 @@ def run_poisson3d(args):
     stream = torch.cuda.current_stream()
     hbm, peak_src = _peaks()
     res = {}
+    only = getattr(args, "only", None)
     for name, prec in (("mixed_fp32", gabp.PREC_MIXED_FP32), ("mixed_bf16", gabp.PREC_MIXED_BF16),
                        ("fp64", gabp.PREC_FP64)):
+        if only and name not in only:
+            continue
         t0 = time.perf_counter()
         if args.form == "grid":
             s = gabp.Solver.from_grid([p, p, p], m.row_ptr, m.col, m.val, precision=prec,
@@ -637,6 +729,13 @@ def run_poisson3d(args):
              "sweeps_full": st["sweeps_full"], "sweeps_mean": st["sweeps_mean"],
              "outer": st["outer_steps"], "rel_residual": st["residual"] / st["rhs_norm"],
              "handle_build_s": build_s, "tuning": s.tuning()}
+        if getattr(args, "oracle_residual", False):
+            # the reached x checked by the oracle's own residual routine (the
+            # oracle cannot iterate this system to convergence in bench time)
+            import oracle
+            xr = xt.cpu().numpy()
+            r["rel_residual_by_oracle"] = (oracle.residual_inf(m.row_ptr, m.col, m.val, b, xr)
+                                           / float(np.abs(b).max()))
         # per-kernel times from a profiled pass capped at a few hundred sweeps
         gabp.gabp_set_profile(s.handle, True)
         try:
@@ -662,10 +761,10 @@ def run_poisson3d(args):
                 r["us_per_full_sweep"] = 1e3 * sp["ms_full"] / sp["sweeps_full"]
         res[name] = r
         s.close()
-    f64 = res["fp64"]
+    f64 = res.get("fp64")
     mixed = res["mixed_fp32"]
     extrap = None
-    if f64["status"] != "GABP_OK" and mixed["status"] == "GABP_OK":
+    if f64 is not None and f64["status"] != "GABP_OK" and mixed["status"] == "GABP_OK":
         # FP64 capped: its time to 1e-10 estimated from its measured time per
         # sweep and the FP64 / mixed sweep-count ratio measured at p = 64 and
         # 128 (0.77, 0.79)
@@ -685,8 +784,7 @@ def run_poisson3d(args):
                        "generate_s": gen_s},
             "runs": res, "extrapolation": extrap,
             "edge_updates_per_s_mixed": E * mixed["sweeps"] / (mixed["ms"] * 1e-3)}
-    print(json.dumps(line), flush=True)
-    return 0
+    return _emit(line, args)
 
 
 def run_detect(args):
@@ -805,8 +903,7 @@ def run_detect(args):
             "kernel_ms_per_step": {"mean": sp["ms_mean"], "full32": sp["ms_full"],
                                    "residual": sp["ms_residual"], "other": sp["ms_other"]},
             "tuning": tuning}
-    print(json.dumps(line), flush=True)
-    return 0
+    return _emit(line, args)
 
 
 def main():
@@ -819,6 +916,8 @@ def main():
     ap.add_argument("--cpu-rounds", type=int, default=10)
     ap.add_argument("--ref-rounds", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="er1e6: leave out the other configurations (configs entry of the line)")
     ap.add_argument("--p", type=int, default=128, help="poisson3d: grid side")
     ap.add_argument("--max-iter", type=int, default=200000, help="poisson3d: sweep cap per solve")
     ap.add_argument("--fp64-max-iter", type=int, default=0,
