@@ -930,6 +930,9 @@ def main():
     ap.add_argument("--damp-scope", type=int, default=0, choices=[0, 1],
                     help="detect with --schedule 1: 0 damp every message, 1 only those the last class sends")
     ap.add_argument("--skip-bf16", action="store_true", help="poisson3d: leave out the BF16 variant")
+    ap.add_argument("--runs", default="",
+                    help="poisson3d: comma list of the solves to run (mixed_fp32, mixed_bf16, fp64); "
+                         "default all")
     ap.add_argument("--pull-lanes", type=int, default=0, choices=[-1, 0, 2, 4, 8, 16, 32],
                     help="er1e6: form of the FP32 full sweep: 0 = autotuned, -1 = scatter, "
                          "2..32 = in place with that many lanes per row")
@@ -958,6 +961,8 @@ def main():
     if args.workload == "poisson32":
         return run_poisson32(args)
     if args.workload == "poisson3d":
+        if args.runs:
+            args.only = tuple(r.strip() for r in args.runs.split(",") if r.strip())
         return run_poisson3d(args)
     return run_gabp(args)
 

@@ -16,12 +16,14 @@
 // access is a coalesced run and a sweep streams the grid once.
 //
 // Work mapping: persistent CTAs of 8 warps claim whole systems, largest
-// first, from an atomic counter.  Inside a system, the K columns are cut into
-// chunks of 32 (one lane per column) and the 8 warps split into
-// (chunks, row groups); a warp walks the rows of its group, keeps the column
-// sums of its lanes in registers and adds each row's warp sum into the row
-// total in shared memory.  The node work of a round (totals, tentative means,
-// monitors) runs before the grid pass, from the sums the previous sweep left.
+// first, from an atomic counter.  Inside a system, a warp takes whole grid
+// rows (rows w, w + 8, ...), its lanes on the columns lane + 32 q (q < Q =
+// ceil(K / 32) rounded up to 1, 2, 4 or 8).  A row's sum is the warp's sum
+// and has one writer; each warp keeps the column sums of its lanes in
+// registers, and the warps' column sums are added in warp order.  No sum
+// depends on timing: the same input gives the same bits on every run.  The
+// node work of a round (totals, tentative means, monitors) runs before the
+// grid pass, from the sums the previous sweep left.
 #include "gabp_internal.h"
 #include "gabp_device.cuh"
 
@@ -122,25 +124,6 @@ __device__ __forceinline__ int32_t claim(Ctl *ctl, int32_t *slot) {
   if (threadIdx.x == 0) *slot = static_cast<int32_t>(atomicAdd(&ctl->work_next, 1u));
   __syncthreads();
   return *slot;
-}
-
-// Warp-to-work split of one system: chunk c of 32 columns and row group g.
-struct Split {
-  int kc, rg, c, g, r;
-  bool warp_on, lane_on;
-};
-__device__ __forceinline__ Split split_of(int K) {
-  Split s;
-  s.kc = (K + 31) >> 5;
-  const int kp = s.kc <= 1 ? 1 : s.kc <= 2 ? 2 : s.kc <= 4 ? 4 : 8;
-  const int w = threadIdx.x >> 5;
-  s.rg = kDenseWarps / kp;
-  s.c = w % kp;
-  s.g = w / kp;
-  s.r = s.c * 32 + (threadIdx.x & 31);
-  s.warp_on = s.c < s.kc;
-  s.lane_on = s.r < K;
-  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -297,18 +280,148 @@ struct MeanRound {
 // messages eta_ij = c (h~_i - eta_ji) are written (storage E) instead of full
 // messages.
 // ---------------------------------------------------------------------------
+// Columns each lane holds for a system of K columns: 1, 2, 4 or 8.
+template <class F>
+__device__ __forceinline__ void by_columns(int K, F &&f) {
+  const int kq = (K + 31) >> 5;
+  if (kq > 4) f(std::integral_constant<int, 8>{});
+  else if (kq > 2) f(std::integral_constant<int, 4>{});
+  else if (kq > 1) f(std::integral_constant<int, 2>{});
+  else f(std::integral_constant<int, 1>{});
+}
+
+// Grid rows each warp loads ahead: U (the tuned figure) when U rows of Q
+// columns a lane fit eight values, else 8 / Q.
+template <int U, int Q>
+constexpr int rows_ahead() {
+  return U * Q <= 8 ? U : (8 / Q > 0 ? 8 / Q : 1);
+}
+
+// One warp per grid row j (rows w, w + 8, ...), lanes on the columns lane +
+// 32 q (q < Q), as in the serial kernels.  The row sums (totals of z_j) have
+// one writer each and go straight to the round's sums; each warp keeps its
+// column sums (totals of x^_r) in registers, and they are added in warp
+// order through `part`, in two halves of four warps (so that the FP64 slices
+// fit shared memory) -- no atomics, the same bits on every run.
+template <class T, class E, int U, int Q>
+__device__ __forceinline__ void full_sync_rows(const DenseSys &sy, const T *__restrict__ Sg,
+                                               const FullIO<T> &io, float2 *__restrict__ C,
+                                               E *__restrict__ h_out, const T2<T> *tx,
+                                               const T2<T> *tz, T2<T> *part, T2<T> *ax,
+                                               FullRound<T> &R, bool &brk) {
+  using V = T2<T>;
+  constexpr bool kF64 = sizeof(T) == 8;
+  constexpr int UU = rows_ahead<U, Q>();
+  const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool first = R.first, freeze = R.freeze;
+  const T gam = R.gam;
+  V xr[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    xr[q] = r < K ? tx[r] : mk2<T>(T(1), T(0));
+  }
+  ColSum<T> cP[Q], cE[Q];
+  for (int j0 = w * UU; j0 < N; j0 += kDenseWarps * UU) {
+    T a[UU][Q];
+    Quad<T> m[UU][Q];
+#pragma unroll
+    for (int u = 0; u < UU; ++u)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = j0 + u, r = lane + 32 * q;
+        a[u][q] = T(0);
+        m[u][q] = Quad<T>{T(0), T(0), T(0), T(0)};
+        if (j < N && r < K) {
+          const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+          a[u][q] = __ldcs(Sg + p);
+          if (!first) m[u][q] = io.ld(p);
+        }
+      }
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+      const int j = j0 + u;
+      if (j >= N) break;   // the same for every lane of the warp
+      const V zj = tz[j];
+      T rz = T(0), re = T(0);
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        if (r >= K) continue;
+        const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+        const T av = a[u][q];
+        const Quad<T> &mm = m[u][q];
+        Quad<T> o{T(0), T(0), T(0), T(0)};
+        if (av != T(0)) {
+          const T dz = xr[q].x - mm.px;   // P~_r - P_{z_j -> x_r}: towards z_j
+          const T dx = zj.x - mm.pz;      // P~_j - P_{x_r -> z_j}: towards x_r
+          brk |= bad(dz) || bad(dx);
+          const T iz = rcp(dz), ix = rcp(dx);
+          if (!kF64 && freeze) {
+            const T cz = -av * iz, cx = -av * ix;
+            C[p] = make_float2(static_cast<float>(cz), static_cast<float>(cx));
+            o.ez = cz * (xr[q].y - mm.ex);
+            o.ex = cx * (zj.y - mm.ez);
+          } else {
+            o.pz = -(av * av) * iz;
+            o.px = -(av * av) * ix;
+            o.ez = -av * (xr[q].y - mm.ex) * iz;
+            o.ex = -av * (zj.y - mm.ez) * ix;
+          }
+          if (gam > T(0)) {   // blend the information with its previous value
+            o.ez = gam * mm.ez + (T(1) - gam) * o.ez;
+            o.ex = gam * mm.ex + (T(1) - gam) * o.ex;
+          }
+        } else if (!kF64 && freeze) {
+          C[p] = make_float2(0.f, 0.f);
+        }
+        if (!kF64 && freeze) {
+          st_h(h_out + p, make_float2(static_cast<float>(o.ez), static_cast<float>(o.ex)));
+        } else {
+          io.st(p, o);
+        }
+        rz += o.pz;
+        re += o.ez;
+        cP[q].add(o.px);
+        cE[q].add(o.ex);
+      }
+      rz = group_sum<32>(rz);
+      re = group_sum<32>(re);
+      if (lane == 0) R.put_sum(sy.node0 + K + j, mk2<T>(rz, re));
+    }
+  }
+  for (int half = 0; half < 2; ++half) {
+    if ((w >> 2) == half) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        if (r < K) part[(w & 3) * kDenseMaxK + r] = mk2<T>(cP[q].value(), cE[q].value());
+      }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += kDenseBlock) {
+      V s = half ? ax[k] : part[k];
+      for (int ww = half ? 0 : 1; ww < 4; ++ww) {
+        s.x += part[ww * kDenseMaxK + k].x;
+        s.y += part[ww * kDenseMaxK + k].y;
+      }
+      ax[k] = s;
+    }
+    __syncthreads();
+  }
+}
+
 template <class T, class E, int U>
 __global__ void __launch_bounds__(kDenseBlock)
 dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   using V = T2<T>;
   constexpr bool kF64 = sizeof(T) == 8;
   __shared__ V tx[kDenseMaxK], tz[kDenseMaxN];   // (P~, h~) of this round
-  __shared__ V ax[kDenseMaxK], az[kDenseMaxN];   // sums of the new messages
+  __shared__ V part[4 * kDenseMaxK];             // four warps' column sums at a time
+  __shared__ V ax[kDenseMaxK];                   // column sums of the new messages
   __shared__ int32_t cur;
   FullRound<T> R(d, B, ctl);
   const int par = ctl->par_m, pe = ctl->par_e;
-  const bool first = R.first, freeze = R.freeze;
-  const T gam = R.gam;
   const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
                                   : reinterpret_cast<const T *>(d.S32);
   FullIO<T> io;
@@ -324,7 +437,7 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   // freeze outputs: mean messages go to the other mean buffer
   E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
   bool brk = false;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
 
   for (;;) {
     const int32_t s = claim(ctl, &cur);
@@ -335,91 +448,17 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     for (int k = tid; k < K + N; k += kDenseBlock) {
       T rhs;
       const V t = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
-      if (k < K) { tx[k] = t; ax[k] = mk2<T>(T(0), T(0)); }
-      else { tz[k - K] = t; az[k - K] = mk2<T>(T(0), T(0)); }
+      if (k < K) tx[k] = t;
+      else tz[k - K] = t;
     }
     __syncthreads();
     if (!R.write_msgs) continue;
-    // ---- grid pass ----
-    const Split w = split_of(K);
-    if (w.warp_on) {
-      const V xr = w.lane_on ? tx[w.r] : mk2<T>(T(1), T(0));
-      ColSum<T> cP, cE;
-      const int64_t base = sy.pair0 + w.r;
-      auto one = [&](int j, T a, const Quad<T> &m) {
-        T rz = T(0), re = T(0);
-        if (w.lane_on) {
-          const int64_t p = base + static_cast<int64_t>(j) * K;
-          const V zj = tz[j];
-          Quad<T> q{T(0), T(0), T(0), T(0)};
-          if (a != T(0)) {
-            const T dz = xr.x - m.px;   // P~_r - P_{z_j -> x_r}: towards z_j
-            const T dx = zj.x - m.pz;   // P~_j - P_{x_r -> z_j}: towards x_r
-            brk |= bad(dz) || bad(dx);
-            const T iz = rcp(dz), ix = rcp(dx);
-            if (!kF64 && freeze) {
-              const T cz = -a * iz, cx = -a * ix;
-              d.C32[p] = make_float2(static_cast<float>(cz), static_cast<float>(cx));
-              q.ez = cz * (xr.y - m.ex);
-              q.ex = cx * (zj.y - m.ez);
-            } else {
-              q.pz = -(a * a) * iz;
-              q.px = -(a * a) * ix;
-              q.ez = -a * (xr.y - m.ex) * iz;
-              q.ex = -a * (zj.y - m.ez) * ix;
-            }
-            if (gam > T(0)) {   // blend the information with its previous value
-              q.ez = gam * m.ez + (T(1) - gam) * q.ez;
-              q.ex = gam * m.ex + (T(1) - gam) * q.ex;
-            }
-          } else if (!kF64 && freeze) {
-            d.C32[p] = make_float2(0.f, 0.f);
-          }
-          if (!kF64 && freeze) {
-            st_h(h_out + p, make_float2(static_cast<float>(q.ez), static_cast<float>(q.ex)));
-          } else {
-            io.st(p, q);
-          }
-          rz = q.pz;
-          re = q.ez;
-          cP.add(q.px);
-          cE.add(q.ex);
-        }
-        rz = group_sum<32>(rz);
-        re = group_sum<32>(re);
-        if (lane == 0) {
-          atomicAdd(&az[j].x, rz);
-          atomicAdd(&az[j].y, re);
-        }
-      };
-      // U rows of the group per step: all loads first, then the updates
-      for (int j0 = w.g; j0 < N; j0 += U * w.rg) {
-        T a[U];
-        Quad<T> m[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int j = j0 + u * w.rg;
-          a[u] = T(0);
-          m[u] = Quad<T>{T(0), T(0), T(0), T(0)};
-          if (w.lane_on && j < N) {
-            const int64_t p = base + static_cast<int64_t>(j) * K;
-            a[u] = __ldcs(Sg + p);
-            if (!first) m[u] = io.ld(p);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (j0 + u * w.rg < N) one(j0 + u * w.rg, a[u], m[u]);
-      }
-      if (w.lane_on) {
-        atomicAdd(&ax[w.r].x, cP.value());
-        atomicAdd(&ax[w.r].y, cE.value());
-      }
-    }
-    __syncthreads();
-    // ---- sums of the new round ----
-    for (int k = tid; k < K + N; k += kDenseBlock)
-      R.put_sum(sy.node0 + k, k < K ? ax[k] : az[k - K]);
+    // ---- grid pass (row sums of z written inside, column sums into ax) ----
+    by_columns(K, [&](auto q) {
+      full_sync_rows<T, E, U, decltype(q)::value>(sy, Sg, io, d.C32, h_out, tx, tz, part, ax, R,
+                                                  brk);
+    });
+    for (int k = tid; k < K; k += kDenseBlock) R.put_sum(sy.node0 + k, ax[k]);
   }
   R.finish(ctl, red, brk);
 }
@@ -428,21 +467,83 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
 // Mean-only sweep with frozen precisions (FP32 arithmetic; storage E = float2
 // or __nv_bfloat162 per grid position), synchronous schedule:
 //     eta_z' = c_z (h~_r - eta_x),   eta_x' = c_x (h~_j - eta_z).
+// Mapping and sums as in the full sweep: a warp per grid row, row sums with
+// one writer, column sums added in warp order.
 // ---------------------------------------------------------------------------
+template <class E, int U, int Q>
+__device__ __forceinline__ void mean_sync_rows(const DenseSys &sy, const float2 *__restrict__ C,
+                                               const E *__restrict__ h_in, E *__restrict__ h_out,
+                                               const float *tx, const float *tz, float *part,
+                                               MeanRound &R) {
+  constexpr int UU = rows_ahead<U, Q>();
+  const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool first = R.first;
+  const float gam = R.gam;
+  float hr[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    hr[q] = r < K ? tx[r] : 0.f;
+  }
+  ColSum<float> cE[Q];
+  for (int j0 = w * UU; j0 < N; j0 += kDenseWarps * UU) {
+    float2 c[UU][Q], hv[UU][Q];
+#pragma unroll
+    for (int u = 0; u < UU; ++u)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = j0 + u, r = lane + 32 * q;
+        c[u][q] = make_float2(0.f, 0.f);
+        hv[u][q] = c[u][q];
+        if (j < N && r < K) {
+          const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+          c[u][q] = __ldcs(C + p);
+          if (!first) hv[u][q] = ld_h(h_in + p);
+        }
+      }
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+      const int j = j0 + u;
+      if (j >= N) break;   // the same for every lane of the warp
+      const float tzj = tz[j];
+      float re = 0.f;
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int r = lane + 32 * q;
+        if (r >= K) continue;
+        const int64_t p = sy.pair0 + static_cast<int64_t>(j) * K + r;
+        float ez = c[u][q].x * (hr[q] - hv[u][q].y), ex = c[u][q].y * (tzj - hv[u][q].x);
+        if (gam > 0.f) {
+          ez = gam * hv[u][q].x + (1.f - gam) * ez;
+          ex = gam * hv[u][q].y + (1.f - gam) * ex;
+        }
+        st_h(h_out + p, make_float2(ez, ex));
+        re += ez;
+        cE[q].add(ex);
+      }
+      re = group_sum<32>(re);
+      if (lane == 0) R.sum_out[sy.node0 + K + j] = re;
+    }
+  }
+  // this warp's column sums to its own slice (added in warp order later)
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    if (r < K) part[w * kDenseMaxK + r] = cE[q].value();
+  }
+}
+
 template <class E, int U>
 __global__ void __launch_bounds__(kDenseBlock)
 dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
-  __shared__ float tx[kDenseMaxK], tz[kDenseMaxN];   // h~ of this round
-  __shared__ float ax[kDenseMaxK], az[kDenseMaxN];   // sums of the new messages
+  __shared__ float tx[kDenseMaxK], tz[kDenseMaxN];      // h~ of this round
+  __shared__ float part[kDenseWarps * kDenseMaxK];      // per-warp column sums
   __shared__ int32_t cur;
   MeanRound R(d, B, ctl);
   const int pe = ctl->par_e;
-  const bool first = R.first;
-  const float gam = R.gam;
   const E *__restrict__ h_in = static_cast<const E *>(pe ? d.H[1] : d.H[0]);
   E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
-  const float2 *__restrict__ C = d.C32;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x;
 
   for (;;) {
     const int32_t s = claim(ctl, &cur);
@@ -452,53 +553,19 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     for (int k = tid; k < K + N; k += kDenseBlock) {
       float rhs;
       const float Th = R.node(sy.node0 + k, B, &rhs);
-      if (k < K) { tx[k] = Th; ax[k] = 0.f; }
-      else { tz[k - K] = Th; az[k - K] = 0.f; }
+      if (k < K) tx[k] = Th;
+      else tz[k - K] = Th;
     }
     __syncthreads();
-    const Split w = split_of(K);
-    if (w.warp_on) {
-      const float hr = w.lane_on ? tx[w.r] : 0.f;
-      ColSum<float> cE;
-      const int64_t base = sy.pair0 + w.r;
-      auto one = [&](int j, float2 c, float2 h) {
-        float re = 0.f;
-        if (w.lane_on) {
-          const int64_t p = base + static_cast<int64_t>(j) * K;
-          float ez = c.x * (hr - h.y), ex = c.y * (tz[j] - h.x);
-          if (gam > 0.f) {
-            ez = gam * h.x + (1.f - gam) * ez;
-            ex = gam * h.y + (1.f - gam) * ex;
-          }
-          st_h(h_out + p, make_float2(ez, ex));
-          re = ez;
-          cE.add(ex);
-        }
-        re = group_sum<32>(re);
-        if (lane == 0) atomicAdd(&az[j], re);
-      };
-      for (int j0 = w.g; j0 < N; j0 += U * w.rg) {
-        float2 c[U], hv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int j = j0 + u * w.rg;
-          c[u] = make_float2(0.f, 0.f);
-          hv[u] = c[u];
-          if (w.lane_on && j < N) {
-            const int64_t p = base + static_cast<int64_t>(j) * K;
-            c[u] = __ldcs(C + p);
-            if (!first) hv[u] = ld_h(h_in + p);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (j0 + u * w.rg < N) one(j0 + u * w.rg, c[u], hv[u]);
-      }
-      if (w.lane_on) atomicAdd(&ax[w.r], cE.value());
-    }
+    by_columns(K, [&](auto q) {
+      mean_sync_rows<E, U, decltype(q)::value>(sy, d.C32, h_in, h_out, tx, tz, part, R);
+    });
     __syncthreads();
-    for (int k = tid; k < K + N; k += kDenseBlock)
-      R.sum_out[sy.node0 + k] = k < K ? ax[k] : az[k - K];
+    for (int k = tid; k < K; k += kDenseBlock) {
+      float sum = part[k];
+      for (int ww = 1; ww < kDenseWarps; ++ww) sum += part[ww * kDenseMaxK + k];
+      R.sum_out[sy.node0 + k] = sum;
+    }
   }
   R.finish(ctl, red);
 }
@@ -533,22 +600,13 @@ __device__ __forceinline__ float ld1(const __nv_bfloat16 *p) { return __bfloat16
 __device__ __forceinline__ void st1(float *p, float v) { __stcs(p, v); }
 __device__ __forceinline__ void st1(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
 
-// Columns each lane holds for a system of K columns: 1, 2, 4 or 8.
-template <class F>
-__device__ __forceinline__ void by_columns(int K, F &&f) {
-  const int kq = (K + 31) >> 5;
-  if (kq > 4) f(std::integral_constant<int, 8>{});
-  else if (kq > 2) f(std::integral_constant<int, 4>{});
-  else if (kq > 1) f(std::integral_constant<int, 2>{});
-  else f(std::integral_constant<int, 1>{});
-}
 
 template <class T, class E1, int Q>
 __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__restrict__ Sg,
                                                  T2<T> *__restrict__ mx, T2<T> *__restrict__ mz,
                                                  float2 *__restrict__ C, E1 *__restrict__ hx,
                                                  E1 *__restrict__ hz, const T2<T> *tx,
-                                                 const T *zr, T2<T> *ax, FullRound<T> &R,
+                                                 const T *zr, T2<T> *part, FullRound<T> &R,
                                                  bool &brk) {
   using V = T2<T>;
   constexpr bool kF64 = sizeof(T) == 8;
@@ -648,13 +706,11 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
       if (lane == 0) R.put_sum(sy.node0 + sy.K + j, mk2<T>(sP, sE));
     }
   }
+  // this warp's column sums to its own slice (added in warp order later)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int r = lane + 32 * q;
-    if (r < K) {
-      atomicAdd(&ax[r].x, cP[q].value());
-      atomicAdd(&ax[r].y, cE[q].value());
-    }
+    if (r < K) part[w * kDenseMaxK + r] = mk2<T>(cP[q].value(), cE[q].value());
   }
 }
 
@@ -665,7 +721,8 @@ dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   using V = T2<T>;
   using E1 = typename Half<E>::t;
   constexpr bool kF64 = sizeof(T) == 8;
-  __shared__ V tx[kDenseMaxK], ax[kDenseMaxK];   // totals of x^ / sums of the new Mx'
+  __shared__ V tx[kDenseMaxK];                   // totals of x^
+  __shared__ V part[kDenseWarps * kDenseMaxK];   // per-warp sums of the new Mx', by column
   __shared__ T zr[kDenseMaxN];                   // rhs of z
   __shared__ int32_t cur;
   FullRound<T> R(d, B, ctl);
@@ -692,17 +749,24 @@ dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     for (int k = tid; k < K + N; k += kDenseBlock) {
       T rhs;
       const V t = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
-      if (k < K) { tx[k] = t; ax[k] = mk2<T>(T(0), T(0)); }
+      if (k < K) tx[k] = t;
       else zr[k - K] = rhs;
     }
     __syncthreads();
     if (!R.write_msgs) continue;
     by_columns(K, [&](auto q) {
-      full_serial_rows<T, E1, decltype(q)::value>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, ax, R,
+      full_serial_rows<T, E1, decltype(q)::value>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R,
                                                   brk);
     });
     __syncthreads();
-    for (int k = tid; k < K; k += kDenseBlock) R.put_sum(sy.node0 + k, ax[k]);
+    for (int k = tid; k < K; k += kDenseBlock) {
+      V sum = part[k];
+      for (int ww = 1; ww < kDenseWarps; ++ww) {
+        sum.x += part[ww * kDenseMaxK + k].x;
+        sum.y += part[ww * kDenseMaxK + k].y;
+      }
+      R.put_sum(sy.node0 + k, sum);
+    }
   }
   R.finish(ctl, red, brk);
 }
@@ -710,7 +774,7 @@ dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
 template <class E1, int Q>
 __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float2 *__restrict__ C,
                                                  E1 *__restrict__ hx, E1 *__restrict__ hz,
-                                                 const float *tx, const float *zr, float *ax,
+                                                 const float *tx, const float *zr, float *part,
                                                  MeanRound &R) {
   constexpr int U = 8 / Q;
   const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -770,17 +834,19 @@ __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float
       if (lane == 0) R.sum_out[sy.node0 + sy.K + j] = sE;
     }
   }
+  // this warp's column sums to its own slice (added in warp order later)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int r = lane + 32 * q;
-    if (r < K) atomicAdd(&ax[r], cE[q].value());
+    if (r < K) part[w * kDenseMaxK + r] = cE[q].value();
   }
 }
 
 template <class E1>
 __global__ void __launch_bounds__(kDenseBlock)
 dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
-  __shared__ float tx[kDenseMaxK], ax[kDenseMaxK];   // h~ of x^ / sums of the new eta_x
+  __shared__ float tx[kDenseMaxK];                   // h~ of x^
+  __shared__ float part[kDenseWarps * kDenseMaxK];   // per-warp sums of the new eta_x, by column
   __shared__ float zr[kDenseMaxN];                   // rhs of z
   __shared__ int32_t cur;
   MeanRound R(d, B, ctl);
@@ -796,15 +862,19 @@ dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     for (int k = tid; k < K + N; k += kDenseBlock) {
       float rhs;
       const float Th = R.node(sy.node0 + k, B, &rhs);
-      if (k < K) { tx[k] = Th; ax[k] = 0.f; }
+      if (k < K) tx[k] = Th;
       else zr[k - K] = rhs;
     }
     __syncthreads();
     by_columns(K, [&](auto q) {
-      mean_serial_rows<E1, decltype(q)::value>(sy, d.C32, hx, hz, tx, zr, ax, R);
+      mean_serial_rows<E1, decltype(q)::value>(sy, d.C32, hx, hz, tx, zr, part, R);
     });
     __syncthreads();
-    for (int k = tid; k < K; k += kDenseBlock) R.sum_out[sy.node0 + k] = ax[k];
+    for (int k = tid; k < K; k += kDenseBlock) {
+      float sum = part[k];
+      for (int ww = 1; ww < kDenseWarps; ++ww) sum += part[ww * kDenseMaxK + k];
+      R.sum_out[sy.node0 + k] = sum;
+    }
   }
   R.finish(ctl, red);
 }

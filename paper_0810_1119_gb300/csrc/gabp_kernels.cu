@@ -330,6 +330,8 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ float2 tot[2][L::TR];   // heavy tiles: per-row sums, double-buffered
   __shared__ float2 nd[L::TR];       // heavy tiles: (A_ii, rhs_i) of the tile's rows
+  __shared__ int cont_key[L::TS / 32];      // heavy tiles: row continuing into chunk c (-1: none)
+  __shared__ float2 cont_sum[L::TS / 32];   //   and its partial sum over chunk c
   const int pm = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
   const bool zin = first && !g.in_place;   // incoming messages known to be zero
@@ -458,6 +460,10 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
     for (int32_t k = tid; k < nr; k += NT) nd[k] = make_float2(g.diag32[tb.r0 + k], rhs_at(tb.r0 + k));
+    // Sums in a fixed order: within a 32-slot chunk by the segmented
+    // shuffle sum; a row that starts in the chunk gets its total from that
+    // head alone, and the partial of a row continuing from earlier chunks
+    // is added afterwards by one thread, chunk by chunk.
     if (!zin) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
         const int32_t s = base + (tid & 31);
@@ -466,12 +472,23 @@ sweep32_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
         bool head;
         const float2 sum = seg_sum(v ? ms[s] : make_float2(0.f, 0.f), key, head);
         if (head && v) {
-          atomicAdd(&tc[key].x, sum.x);
-          atomicAdd(&tc[key].y, sum.y);
+          const bool cont = (s & 31) == 0 && s > 0 && lrow[s - 1] == key;
+          if (cont) { cont_key[s >> 5] = key; cont_sum[s >> 5] = sum; }
+          else tc[key] = sum;
         }
+        if ((tid & 31) == 0 && !(v && s > 0 && lrow[s - 1] == key)) cont_key[base >> 5] = -1;
       }
     }
     if (__syncthreads_or(!got)) return true;
+    if (!zin) {
+      if (tid == 0)
+        for (int32_t c = 1; 32 * c < ns; ++c)
+          if (cont_key[c] >= 0) {
+            tc[cont_key[c]].x += cont_sum[c].x;
+            tc[cont_key[c]].y += cont_sum[c].y;
+          }
+      __syncthreads();
+    }
     for (int32_t k = tid; k < nr; k += NT)
       node(tb.r0 + k, nd[k].x + tc[k].x, nd[k].y + tc[k].y, nd[k].y);
     for (int32_t s = tid; s < ns; s += NT) {
@@ -641,6 +658,8 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ __align__(8) uint64_t bars[2];
   __shared__ float tot[2][L::TR];    // heavy tiles: per-row sums, double-buffered
   __shared__ float rhs_s[L::TR];     // heavy tiles: rhs of the tile's rows
+  __shared__ int cont_key[L::TS / 32];     // heavy tiles: row continuing into chunk c (-1: none)
+  __shared__ float cont_sum[L::TS / 32];   //   and its partial sum over chunk c
   const int pe = ctl->par_e, pmon = ctl->par_mon;
   const bool first = ctl->first != 0;
   const bool zin = first && !g.in_place;   // incoming messages known to be zero
@@ -744,6 +763,8 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
     // heavy tile (a row of degree > kHeavyDegree): slot-parallel sums
     const uint16_t *lrow = Seg<uint16_t>::at(stage + L::lr, tb.s0);
     for (int32_t k = tid; k < nr; k += NT) rhs_s[k] = rhs_at(tb.r0 + k);
+    // Sums in a fixed order (as in sweep32_kernel): chunk-wise segmented
+    // sums, then the partials of rows continuing across chunks in chunk order.
     if (!zin) {
       for (int32_t base = tid & ~31; base < ns; base += NT) {
         const int32_t s = base + (tid & 31);
@@ -751,10 +772,21 @@ mean_kernel(GraphView g, Buffers B, Ctl *ctl, DevScalars *red) {
         const int key = v ? lrow[s] : kNoRow;
         bool head;
         const float sum = seg_sum(v ? ld_eta(es + s) : 0.f, key, head);
-        if (head && v) atomicAdd(&tc[key], sum);
+        if (head && v) {
+          const bool cont = (s & 31) == 0 && s > 0 && lrow[s - 1] == key;
+          if (cont) { cont_key[s >> 5] = key; cont_sum[s >> 5] = sum; }
+          else tc[key] = sum;
+        }
+        if ((tid & 31) == 0 && !(v && s > 0 && lrow[s - 1] == key)) cont_key[base >> 5] = -1;
       }
     }
     if (__syncthreads_or(!got)) return true;
+    if (!zin) {
+      if (tid == 0)
+        for (int32_t c = 1; 32 * c < ns; ++c)
+          if (cont_key[c] >= 0) tc[cont_key[c]] += cont_sum[c];
+      __syncthreads();
+    }
     for (int32_t k = tid; k < nr; k += NT) node(tb.r0 + k, rhs_s[k] + tc[k], rhs_s[k]);
     for (int32_t s = tid; s < ns; s += NT) {
       const int k = lrow[s];
