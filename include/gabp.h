@@ -146,6 +146,15 @@ typedef struct {
                              scattered access).  0 = automatic: with autotune the tuner times
                              both forms and several window sizes, else the tile form.  The
                              window form needs the synchronous schedule. */
+  int32_t batch_control;  /* gabp_create_lsq_batched in the dense form, mixed and FP64 solves:
+                             0 = per system: each system freezes its precisions, ends its
+                             inner solves and scales its refinement on its own numbers, and
+                             drops out of the sweeps, the refinement and the rules once it
+                             meets the stop rule -- so a system takes the same sweeps, and
+                             its x^ the same bits, in a batch as when it is solved alone;
+                             1 = one controller for the whole batch (its maxima decide the
+                             freeze and the end of each inner solve, and every system sweeps
+                             until the last one is done). */
 } gabp_options;
 
 /* Statistics of the last solve on a handle. */
@@ -167,7 +176,11 @@ typedef struct {
   double ms_mean;           /* mean-only sweeps */
   double ms_residual;       /* FP64 residual evaluations */
   double ms_other;          /* norms, scaling, refinement updates */
-  double reserved[2];
+  int64_t positions_swept;  /* dense Section VII batches: grid positions (edge pairs) that the
+                               solve's sweeps processed, summed over the sweeps (with per-system
+                               control a system that is done, or waits for the next refinement
+                               step, adds none); 0 for the other forms */
+  double reserved[1];
 } gabp_stats;
 
 /* Fills *opt with the defaults: FP64, relative residual, automatic check
@@ -334,6 +347,18 @@ gabp_status gabp_create_grid(gabp_handle *out, int32_t ndim, const int32_t *dims
 
 /* Statistics of the last solve on the handle. */
 gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats);
+
+/*
+ * Message sweeps each system of a batched handle took part in during its
+ * last solve, in the caller's order: sweeps_host[s] for s < nsys, nsys = the
+ * handle's number of systems (host memory, caller-owned).  With per-system
+ * control (gabp_options.batch_control 0 on a dense Section VII batch) these
+ * are the system's own sweeps; otherwise every system took part in every
+ * sweep and each entry is the solve's sweeps_total.  After a psi_s = 0
+ * (Moore-Penrose) solve they are those of its last augmented solve.
+ * GABP_ERR_INVALID_ARG for a handle that is not batched or a wrong nsys.
+ */
+gabp_status gabp_get_system_sweeps(gabp_handle h, int32_t *sweeps_host, int32_t nsys);
 
 /*
  * Turns per-kernel timing on (1) or off (0) for the handle's later solves,

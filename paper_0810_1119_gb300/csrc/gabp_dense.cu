@@ -150,7 +150,9 @@ struct FullRound {
   float *__restrict__ sumE_out;   // freeze: sums of the first mean messages
   const float2 *__restrict__ mon_prev;
   float2 *__restrict__ mon_out;
-  uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;
+  float2 *mon_keep;               // mon_prev's buffer (a system whose inner solve ends keeps d there)
+  uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;       // maxima over the CTA's systems
+  uint32_t smdd = 0, smd = 0, smdP = 0, smP = 0;   // maxima over the current system
 
   __device__ FullRound(const DenseView &d, const Buffers &B, const Ctl *ctl) {
     const int par = ctl->par_m, pe = ctl->par_e, pmon = ctl->par_mon;
@@ -180,6 +182,16 @@ struct FullRound {
     sumE_out = pe ? d.sumE[0] : d.sumE[1];
     mon_prev = pmon ? B.mon32[1] : B.mon32[0];
     mon_out = pmon ? B.mon32[0] : B.mon32[1];
+    mon_keep = pmon ? B.mon32[1] : B.mon32[0];
+  }
+
+  // The current system's maxima into the CTA's.
+  __device__ __forceinline__ void fold() {
+    mdd = max(mdd, smdd);
+    md = max(md, smd);
+    mdP = max(mdP, smdP);
+    mP = max(mP, smP);
+    smdd = smd = smdP = smP = 0;
   }
 
   // Totals (P~_i, h~_i) of node i; *rhs receives rhs_i.
@@ -197,10 +209,10 @@ struct FullRound {
       const float2 prev = first ? make_float2(0.f, 0.f) : mon_prev[i];
       const float di = Th / TP;
       mon_out[i] = make_float2(TP, di);
-      mdd = fmax_bits(mdd, di - prev.y);
-      md = fmax_bits(md, di);
-      mdP = fmax_bits(mdP, TP - prev.x);
-      mP = fmax_bits(mP, TP);
+      smdd = fmax_bits(smdd, di - prev.y);
+      smd = fmax_bits(smd, di);
+      smdP = fmax_bits(smdP, TP - prev.x);
+      smP = fmax_bits(smP, TP);
       if (freeze) B.invP32[i] = 1.0f / TP;
       if (first) B.rhs32[i] = r;
       *rhs = r;
@@ -237,7 +249,9 @@ struct MeanRound {
   float *__restrict__ sum_out;
   const float2 *__restrict__ mon_prev;
   float2 *__restrict__ mon_out;
-  uint32_t mdd = 0, md = 0;
+  float2 *mon_keep;               // mon_prev's buffer (a system whose inner solve ends keeps d there)
+  uint32_t mdd = 0, md = 0;       // maxima over the CTA's systems
+  uint32_t smdd = 0, smd = 0, smdP = 0, smP = 0;   // over the current system (no P~ here)
 
   __device__ MeanRound(const DenseView &d, const Buffers &B, const Ctl *ctl) {
     const int pe = ctl->par_e, pmon = ctl->par_mon;
@@ -249,6 +263,13 @@ struct MeanRound {
     sum_out = pe ? d.sumE[0] : d.sumE[1];
     mon_prev = pmon ? B.mon32[1] : B.mon32[0];
     mon_out = pmon ? B.mon32[0] : B.mon32[1];
+    mon_keep = pmon ? B.mon32[1] : B.mon32[0];
+  }
+
+  __device__ __forceinline__ void fold() {
+    mdd = max(mdd, smdd);
+    md = max(md, smd);
+    smdd = smd = 0;
   }
 
   // h~_i of node i; *rhs receives rhs_i.
@@ -258,8 +279,8 @@ struct MeanRound {
     const float prev = first ? 0.f : mon_prev[i].y;
     const float di = Th * B.invP32[i];
     mon_out[i] = make_float2(0.f, di);
-    mdd = fmax_bits(mdd, di - prev);
-    md = fmax_bits(md, di);
+    smdd = fmax_bits(smdd, di - prev);
+    smd = fmax_bits(smd, di);
     if (first) B.rhs32[i] = r;
     *rhs = r;
     return Th;
@@ -270,6 +291,268 @@ struct MeanRound {
     last_block_control(ctl, red, CK_MEAN);
   }
 };
+
+// ---------------------------------------------------------------------------
+// Per-system control (Ctl::retire = 1).  The CTA that claims a system applies
+// the controller's rules (gabp_device.cuh) to that system's own maxima: the
+// precision freeze of Section V after its full sweeps, the end of its inner
+// solve after the sweeps with frozen precisions.  When a system's inner
+// solve ends, the same CTA takes its refinement step at once (sys_refine:
+// x += rn_s d, its FP64 residual, its stop rule), and the first sweep of its
+// next inner solve comes with the next launch.  Systems that are done or
+// failed are passed over by every claim.  Every
+// rule reads only the system's own numbers, so a system takes the same
+// sweeps, and its solution the same bits, in a batch as when it is solved
+// alone.
+// ---------------------------------------------------------------------------
+struct SysShared {
+  SysCtl sc;                    // the claimed system's state (kept by thread 0)
+  int32_t s;                    // claimed index (largest-first order)
+  int32_t mode;                 // this sweep: 0 full, 1 freeze, 2 mean-only
+  int32_t flag;                 // 1: its inner solve ends here, 2: and the grid pass is skipped
+  union {                       // per-warp maxima (8-byte aligned for the 64-bit view)
+    uint32_t red[4][kDenseWarps];
+    unsigned long long red64[2][kDenseWarps];
+  };
+};
+static_assert(offsetof(SysShared, red64) % 8 == 0, "64-bit maxima must be 8-byte aligned");
+
+// Thread 0's counts over the systems its CTA handled, committed once per
+// launch (held in shared memory: only thread 0 touches them).
+struct Tally {
+  uint32_t frozen, done, failed, checks;
+  int32_t outer, fail_status;
+  unsigned long long positions, rmax, rrelmax;
+};
+
+__device__ __forceinline__ void tally_commit(Ctl *ctl, const Tally &t) {
+  if (threadIdx.x != 0) return;
+  if (t.positions) atomicAdd(&ctl->positions, t.positions);
+  if (t.frozen) atomicSub(&ctl->sys_unfrozen, static_cast<int>(t.frozen));
+  if (t.done) atomicAdd(&ctl->sys_done, static_cast<int>(t.done));
+  if (t.failed) atomicAdd(&ctl->sys_failed, static_cast<int>(t.failed));
+  if (t.checks) atomicAdd(&ctl->checks, static_cast<int>(t.checks));
+  if (t.outer) atomicMax(&ctl->outer, t.outer);
+  if (t.fail_status) atomicMax(&ctl->sys_fail_status, t.fail_status);
+  if (t.rmax) atomicMax(&ctl->sys_rmax, t.rmax);
+  if (t.rrelmax) atomicMax(&ctl->sys_rrelmax, t.rrelmax);
+}
+
+// Claims the next system and hands it to the whole CTA.  With per-system
+// control, systems that are not iterating (state != 0) are passed over and
+// thread 0 loads the claimed system's state into sh.sc; a system's first
+// sweep of the solve takes ||b_s||_inf as the scale of its first inner solve.
+__device__ __forceinline__ int32_t claim_sys(Ctl *ctl, const DenseView &d, bool on,
+                                             SysShared &sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t s;
+    for (;;) {
+      s = static_cast<int32_t>(atomicAdd(&ctl->work_next, 1u));
+      if (s >= d.nsys || !on) break;
+      const int32_t o = d.sys[s].orig;
+      if (d.sysctl[o].state == 0) {
+        sh.sc = d.sysctl[o];
+        if (sh.sc.sweeps == 0) sh.sc.rn = dv(d.sys_bmax[o]);
+        sh.mode = sh.sc.frozen;
+        break;
+      }
+    }
+    sh.s = s;
+  }
+  __syncthreads();
+  return sh.s;
+}
+
+__device__ __forceinline__ double sys_inv_rn(const SysShared &sh) {
+  const double rn = sh.sc.rn;
+  return rn > 0.0 ? 1.0 / rn : 0.0;
+}
+
+// The controller's rules for one system after the node work of a sweep of
+// the given mode, on the system's maxima (bit patterns of non-negative
+// floats): relative change of d, dd = max |d_i - d_i'| / max |d_i|, and on
+// full sweeps the same for P~.  Updates the history in sc and returns true
+// when the system's inner solve ends with this sweep.
+__device__ bool sys_rules(SysCtl &sc, const Ctl *ctl, int mode, uint32_t mdd, uint32_t md,
+                          uint32_t mdP, uint32_t mP) {
+  const int k = ++sc.k;
+  const double dd = static_cast<double>(__uint_as_float(mdd)) /
+                    fmax(static_cast<double>(__uint_as_float(md)), DBL_MIN);
+  if (mode == 0) {   // precision convergence: the freeze comes with the next sweep
+    const double dP = static_cast<double>(__uint_as_float(mdP)) /
+                      fmax(static_cast<double>(__uint_as_float(mP)), DBL_MIN);
+    const double rho = dP / (k == 1 ? INFINITY : sc.prev_dP);
+    const double errP = dP == 0.0 ? 0.0 : (rho < 1.0 ? dP * rho / (1.0 - rho) : INFINITY);
+    if (k >= 3 && (errP < 1e-6 || dP < 1e-7 || (rho >= 1.0 && dP < 1e-4))) sc.frozen = 1;
+    sc.prev_dP = dP;
+  }
+  const double rho_d = dd / (k == 1 ? INFINITY : sc.prev_dd);
+  const double err_d = dd == 0.0 ? 0.0 : (rho_d < 1.0 ? dd * rho_d / (1.0 - rho_d) : INFINITY);
+  sc.stall = rho_d >= 1.0 ? sc.stall + 1 : 0;
+  sc.prev_dd = dd;
+  if (k == 1 || dd < 0.9 * sc.best_dd) {
+    sc.best_dd = dd;
+    sc.since_best = 0;
+  } else {
+    sc.since_best++;
+  }
+  const bool plateau = ctl->plateau > 0 && sc.since_best >= ctl->plateau && dd < ctl->floor_dd;
+  return mode != 0 && k >= 3 &&
+         (err_d < ctl->inner_goal || (sc.stall >= 2 && dd < ctl->floor_dd) || plateau);
+}
+
+// After the node work of a system (every thread calls it): the system's
+// maxima over the CTA and the rules (thread 0).  Returns 0 when the system
+// goes on, 1 when its inner solve ends after this sweep's grid pass (a
+// freeze sweep still writes the frozen coefficients), 2 when it ends here
+// and the grid pass is skipped (a mean-only sweep; its sweep is then
+// counted).  The caller runs sys_refine in both cases.
+template <class Round>
+__device__ int sys_after_nodes(SysShared &sh, const Ctl *ctl, const DenseSys &sy, Round &R,
+                               int mode) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t v[4] = {R.smdd, R.smd, R.smdP, R.smP};
+  R.fold();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = __reduce_max_sync(0xffffffffu, v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sh.red[k][w] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      uint32_t m = 0;
+      for (int ww = 0; ww < kDenseWarps; ++ww) m = max(m, sh.red[k][ww]);
+      v[k] = m;
+    }
+    const bool end = sys_rules(sh.sc, ctl, mode, v[0], v[1], v[2], v[3]);
+    sh.flag = end ? (mode == 2 ? 2 : 1) : 0;
+    if (sh.flag == 2) sh.sc.sweeps++;
+  }
+  __syncthreads();
+  return sh.flag;
+}
+
+// The end of a system's sweep (thread 0): positions swept and, with
+// per-system control, its sweep count, a completed freeze and the write-back.
+__device__ __forceinline__ void sys_end(SysShared &sh, const DenseView &d, const DenseSys &sy,
+                                        bool on, int mode, Tally &t) {
+  if (threadIdx.x != 0) return;
+  t.positions += static_cast<unsigned long long>(sy.K) * sy.N;
+  if (!on) return;
+  if (mode == 1) {
+    sh.sc.frozen = 2;
+    t.frozen++;
+  }
+  sh.sc.sweeps++;
+  d.sysctl[sy.orig] = sh.sc;
+}
+
+// Doubles of shared memory sys_refine needs: x^ (K), z (N) and S x (N).
+constexpr int kRefineBuf = kDenseMaxK + 2 * kDenseMaxN;
+
+// The refinement step of a system whose inner solve ended in this sweep
+// (every thread of the CTA calls it; thread 0 holds the state in sh.sc).
+// With d the tentative means the sweep's node work left in `mon` and rn_s
+// the scale of the inner solve:
+//     x <- x + rn_s d,   r = b - R~ x   (FP64),
+// R~ x from S in FP64: S x with a warp per row, S^T z with a thread per
+// column summing the rows in order (fixed order: the same bits every run).
+// Then the system's stop rule: done when max |r| / ||b_s|| < tol (max |r| <
+// tol for the absolute rule); failed when r is not finite or exceeds 1e30
+// ||b_s||, or after eight refinement steps without a 10 % smaller stop
+// measure; otherwise r is kept as the right-hand side of its next inner
+// solve, whose scale is rn_s = max |r| (history reset, k = 0).
+__device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, const DenseSys &sy,
+                           const Buffers &B, const float2 *mon, double *buf, Tally &t) {
+  const int K = sy.K, N = sy.N, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  double *vx = buf, *vz = buf + K, *az = buf + K + N;
+  double *__restrict__ x = ctl->x;
+  const double *__restrict__ b = ctl->b;
+  const double *__restrict__ S = d.S64 + sy.pair0;
+  const double rn = sh.sc.rn;
+  for (int k = tid; k < K + N; k += kDenseBlock) {
+    const int64_t g = sy.node0 + k;
+    const double v = x[g] + static_cast<double>(mon[g].y) * rn;
+    x[g] = v;
+    if (k < K) vx[k] = v;
+    else vz[k - K] = v;
+  }
+  __syncthreads();
+  for (int j = w; j < N; j += kDenseWarps) {   // (S x)_j
+    double a = 0.0;
+#pragma unroll 2
+    for (int r = lane; r < K; r += 32) a += __ldcs(S + static_cast<int64_t>(j) * K + r) * vx[r];
+    a = group_sum<32>(a);
+    if (lane == 0) az[j] = a;
+  }
+  const double bs = dv(d.sys_bmax[sy.orig]);
+  unsigned long long smr = 0, smrel = 0;
+  auto residual = [&](int64_t g, double Ax) {
+    const double ri = b[g] - Ax;
+    B.r64[g] = ri;
+    smr = umax(smr, bits(fabs(ri)));
+    smrel = umax(smrel, bits(bs > 0.0 ? fabs(ri) / bs : (ri == 0.0 ? 0.0 : INFINITY)));
+  };
+  for (int r = tid; r < K; r += kDenseBlock) {   // x^ rows: x_r + (S^T z)_r
+    double c = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) c += S[static_cast<int64_t>(j) * K + r] * vz[j];
+    residual(sy.node0 + r, vx[r] + c);
+  }
+  __syncthreads();
+  for (int j = tid; j < N; j += kDenseBlock)   // z rows: (S x)_j - psi z_j
+    residual(sy.node0 + K + j, az[j] - sy.psi * vz[j]);
+  smr = warp_max(smr);
+  smrel = warp_max(smrel);
+  unsigned long long(*red)[kDenseWarps] = sh.red64;
+  if (lane == 0) {
+    red[0][w] = smr;
+    red[1][w] = smrel;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int ww = 1; ww < kDenseWarps; ++ww) {
+      smr = umax(smr, red[0][ww]);
+      smrel = umax(smrel, red[1][ww]);
+    }
+    SysCtl &sc = sh.sc;
+    const double rs = dv(smr), prog = ctl->rel ? dv(smrel) : rs;
+    sc.outer++;
+    t.checks++;
+    t.outer = max(t.outer, sc.outer);
+    int fail = 0;
+    if (prog < ctl->tol) {
+      sc.state = 2;
+      t.done++;
+    } else if (!isfinite(rs) || rs > 1e30 * fmax(bs, DBL_MIN)) {
+      fail = GABP_ERR_DIVERGED;
+    } else if (sc.outer == 1 || prog < 0.9 * sc.best_prog) {
+      sc.best_prog = prog;
+      sc.outer_stall = 0;
+    } else if (++sc.outer_stall >= 8) {
+      fail = GABP_ERR_NOT_CONVERGED;
+    }
+    if (fail) {
+      sc.state = 3;
+      t.failed++;
+      t.fail_status = max(t.fail_status, fail);
+    } else if (sc.state == 0) {   // its next inner solve
+      sc.k = 0;
+      sc.stall = 0;
+      sc.since_best = 0;
+      sc.rn = rs;
+    }
+    if (sc.state != 0) {
+      t.rmax = umax(t.rmax, smr);
+      t.rrelmax = umax(t.rrelmax, smrel);
+    }
+    d.sysctl[sy.orig] = sc;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Full sweep, T = double (FP64 solves and gabp_run_rounds) or float (mixed
@@ -297,8 +580,10 @@ constexpr int rows_ahead() {
   return U * Q <= 8 ? U : (8 / Q > 0 ? 8 / Q : 1);
 }
 
-// One warp per grid row j (rows w, w + 8, ...), lanes on the columns lane +
-// 32 q (q < Q), as in the serial kernels.  The row sums (totals of z_j) have
+// One warp per grid row j (rows w, w + 8, ...; the U rows it loads ahead are
+// j, j + 8, ..., so the rows each warp sums, and the bits of every sum, do
+// not depend on U), lanes on the columns lane + 32 q (q < Q), as in the
+// serial kernels.  The row sums (totals of z_j) have
 // one writer each and go straight to the round's sums; each warp keeps its
 // column sums (totals of x^_r) in registers, and they are added in warp
 // order through `part`, in two halves of four warps (so that the FP64 slices
@@ -322,14 +607,14 @@ __device__ __forceinline__ void full_sync_rows(const DenseSys &sy, const T *__re
     xr[q] = r < K ? tx[r] : mk2<T>(T(1), T(0));
   }
   ColSum<T> cP[Q], cE[Q];
-  for (int j0 = w * UU; j0 < N; j0 += kDenseWarps * UU) {
+  for (int j0 = w; j0 < N; j0 += kDenseWarps * UU) {
     T a[UU][Q];
     Quad<T> m[UU][Q];
 #pragma unroll
     for (int u = 0; u < UU; ++u)
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const int j = j0 + u, r = lane + 32 * q;
+        const int j = j0 + kDenseWarps * u, r = lane + 32 * q;
         a[u][q] = T(0);
         m[u][q] = Quad<T>{T(0), T(0), T(0), T(0)};
         if (j < N && r < K) {
@@ -340,7 +625,7 @@ __device__ __forceinline__ void full_sync_rows(const DenseSys &sy, const T *__re
       }
 #pragma unroll
     for (int u = 0; u < UU; ++u) {
-      const int j = j0 + u;
+      const int j = j0 + kDenseWarps * u;
       if (j >= N) break;   // the same for every lane of the warp
       const V zj = tz[j];
       T rz = T(0), re = T(0);
@@ -411,58 +696,6 @@ __device__ __forceinline__ void full_sync_rows(const DenseSys &sy, const T *__re
   }
 }
 
-template <class T, class E, int U>
-__global__ void __launch_bounds__(kDenseBlock)
-dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
-  using V = T2<T>;
-  constexpr bool kF64 = sizeof(T) == 8;
-  __shared__ V tx[kDenseMaxK], tz[kDenseMaxN];   // (P~, h~) of this round
-  __shared__ V part[4 * kDenseMaxK];             // four warps' column sums at a time
-  __shared__ V ax[kDenseMaxK];                   // column sums of the new messages
-  __shared__ int32_t cur;
-  FullRound<T> R(d, B, ctl);
-  const int par = ctl->par_m, pe = ctl->par_e;
-  const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
-                                  : reinterpret_cast<const T *>(d.S32);
-  FullIO<T> io;
-  if constexpr (kF64) {
-    io.inz = par ? d.Mz64[1] : d.Mz64[0];
-    io.inx = par ? d.Mx64[1] : d.Mx64[0];
-    io.outz = par ? d.Mz64[0] : d.Mz64[1];
-    io.outx = par ? d.Mx64[0] : d.Mx64[1];
-  } else {
-    io.in = par ? d.M32[1] : d.M32[0];
-    io.out = par ? d.M32[0] : d.M32[1];
-  }
-  // freeze outputs: mean messages go to the other mean buffer
-  E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
-  bool brk = false;
-  const int tid = threadIdx.x;
-
-  for (;;) {
-    const int32_t s = claim(ctl, &cur);
-    if (s >= d.nsys) break;
-    const DenseSys sy = d.sys[s];
-    const int K = sy.K, N = sy.N;
-    // ---- node work of the round ----
-    for (int k = tid; k < K + N; k += kDenseBlock) {
-      T rhs;
-      const V t = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
-      if (k < K) tx[k] = t;
-      else tz[k - K] = t;
-    }
-    __syncthreads();
-    if (!R.write_msgs) continue;
-    // ---- grid pass (row sums of z written inside, column sums into ax) ----
-    by_columns(K, [&](auto q) {
-      full_sync_rows<T, E, U, decltype(q)::value>(sy, Sg, io, d.C32, h_out, tx, tz, part, ax, R,
-                                                  brk);
-    });
-    for (int k = tid; k < K; k += kDenseBlock) R.put_sum(sy.node0 + k, ax[k]);
-  }
-  R.finish(ctl, red, brk);
-}
-
 // ---------------------------------------------------------------------------
 // Mean-only sweep with frozen precisions (FP32 arithmetic; storage E = float2
 // or __nv_bfloat162 per grid position), synchronous schedule:
@@ -486,13 +719,13 @@ __device__ __forceinline__ void mean_sync_rows(const DenseSys &sy, const float2 
     hr[q] = r < K ? tx[r] : 0.f;
   }
   ColSum<float> cE[Q];
-  for (int j0 = w * UU; j0 < N; j0 += kDenseWarps * UU) {
+  for (int j0 = w; j0 < N; j0 += kDenseWarps * UU) {
     float2 c[UU][Q], hv[UU][Q];
 #pragma unroll
     for (int u = 0; u < UU; ++u)
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
-        const int j = j0 + u, r = lane + 32 * q;
+        const int j = j0 + kDenseWarps * u, r = lane + 32 * q;
         c[u][q] = make_float2(0.f, 0.f);
         hv[u][q] = c[u][q];
         if (j < N && r < K) {
@@ -503,7 +736,7 @@ __device__ __forceinline__ void mean_sync_rows(const DenseSys &sy, const float2 
       }
 #pragma unroll
     for (int u = 0; u < UU; ++u) {
-      const int j = j0 + u;
+      const int j = j0 + kDenseWarps * u;
       if (j >= N) break;   // the same for every lane of the warp
       const float tzj = tz[j];
       float re = 0.f;
@@ -533,41 +766,153 @@ __device__ __forceinline__ void mean_sync_rows(const DenseSys &sy, const float2 
   }
 }
 
+// One system's mean-only round, synchronous schedule: node work (h~ of x^
+// into tx, of z into tz), the per-system rules, the grid pass and the column
+// sums.  Also the round of a system whose precisions are frozen inside a
+// sweep of the full phase (per-system control).
+template <class E, int U>
+__device__ __forceinline__ void mean_sync_system(const DenseView &d, const DenseSys &sy,
+                                                 const Buffers &B, Ctl *ctl, MeanRound &R,
+                                                 const E *__restrict__ h_in, E *__restrict__ h_out,
+                                                 float *tx, float *tz, float *part, double *rbuf,
+                                                 bool on, SysShared &sh, Tally &t) {
+  const int K = sy.K, N = sy.N, tid = threadIdx.x;
+  for (int k = tid; k < K + N; k += kDenseBlock) {
+    float rhs;
+    const float Th = R.node(sy.node0 + k, B, &rhs);
+    if (k < K) tx[k] = Th;
+    else tz[k - K] = Th;
+  }
+  if (on) {
+    if (sys_after_nodes(sh, ctl, sy, R, 2)) {   // its inner solve ends: no grid pass
+      sys_refine(sh, ctl, d, sy, B, R.mon_out, rbuf, t);
+      return;
+    }
+  } else {
+    R.fold();
+  }
+  __syncthreads();
+  by_columns(K, [&](auto q) {
+    mean_sync_rows<E, U, decltype(q)::value>(sy, d.C32, h_in, h_out, tx, tz, part, R);
+  });
+  __syncthreads();
+  for (int k = tid; k < K; k += kDenseBlock) {
+    float sum = part[k];
+    for (int ww = 1; ww < kDenseWarps; ++ww) sum += part[ww * kDenseMaxK + k];
+    R.sum_out[sy.node0 + k] = sum;
+  }
+  sys_end(sh, d, sy, on, 2, t);
+}
+
 template <class E, int U>
 __global__ void __launch_bounds__(kDenseBlock)
 dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ float tx[kDenseMaxK], tz[kDenseMaxN];      // h~ of this round
   __shared__ float part[kDenseWarps * kDenseMaxK];      // per-warp column sums
-  __shared__ int32_t cur;
+  __shared__ double rbuf[kRefineBuf];                   // refinement steps (per-system control)
+  __shared__ SysShared sh;
   MeanRound R(d, B, ctl);
+  const bool on = ctl->retire != 0;
   const int pe = ctl->par_e;
   const E *__restrict__ h_in = static_cast<const E *>(pe ? d.H[1] : d.H[0]);
   E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
+  __shared__ Tally t;   // thread 0's counts (kept out of the registers)
+  if (threadIdx.x == 0) t = Tally{};
+  for (;;) {
+    const int32_t s = claim_sys(ctl, d, on, sh);
+    if (s >= d.nsys) break;
+    if (on) {
+      R.inv_rn = sys_inv_rn(sh);
+      R.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
+    }
+    mean_sync_system<E, U>(d, d.sys[s], B, ctl, R, h_in, h_out, tx, tz, part, rbuf, on, sh, t);
+  }
+  tally_commit(ctl, t);
+  R.finish(ctl, red);
+}
+
+template <class T, class E, int U>
+__global__ void __launch_bounds__(kDenseBlock)
+dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
+  using V = T2<T>;
+  constexpr bool kF64 = sizeof(T) == 8;
+  __shared__ V tx[kDenseMaxK], tz[kDenseMaxN];   // (P~, h~) of this round
+  __shared__ V part[4 * kDenseMaxK];             // four warps' column sums at a time
+  __shared__ V ax[kDenseMaxK];                   // column sums of the new messages
+  __shared__ double rbuf[kF64 ? 1 : kRefineBuf];  // refinement steps (per-system control)
+  __shared__ SysShared sh;
+  FullRound<T> R(d, B, ctl);
+  const bool on = ctl->retire != 0;
+  const int par = ctl->par_m, pe = ctl->par_e;
+  const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
+                                  : reinterpret_cast<const T *>(d.S32);
+  FullIO<T> io;
+  if constexpr (kF64) {
+    io.inz = par ? d.Mz64[1] : d.Mz64[0];
+    io.inx = par ? d.Mx64[1] : d.Mx64[0];
+    io.outz = par ? d.Mz64[0] : d.Mz64[1];
+    io.outx = par ? d.Mx64[0] : d.Mx64[1];
+  } else {
+    io.in = par ? d.M32[1] : d.M32[0];
+    io.out = par ? d.M32[0] : d.M32[1];
+  }
+  // freeze outputs (and the mean-only rounds of frozen systems, per-system
+  // control): mean messages go to the other mean buffer
+  E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
+  const E *__restrict__ h_in = static_cast<const E *>(pe ? d.H[1] : d.H[0]);
+  MeanRound Rm(d, B, ctl);
+  bool brk = false;
+  __shared__ Tally t;   // thread 0's counts (kept out of the registers)
+  if (threadIdx.x == 0) t = Tally{};
   const int tid = threadIdx.x;
 
   for (;;) {
-    const int32_t s = claim(ctl, &cur);
+    const int32_t s = claim_sys(ctl, d, on, sh);
     if (s >= d.nsys) break;
     const DenseSys sy = d.sys[s];
     const int K = sy.K, N = sy.N;
+    int mode = R.freeze ? 1 : 0;
+    if constexpr (!kF64) {
+      if (on) {
+        mode = sh.mode;
+        R.freeze = mode == 1;
+        R.inv_rn = Rm.inv_rn = sys_inv_rn(sh);
+        R.first = Rm.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
+        if (mode == 2) {   // precisions frozen already: a mean-only round
+          mean_sync_system<E, U>(d, sy, B, ctl, Rm, h_in, h_out, reinterpret_cast<float *>(tx),
+                                 reinterpret_cast<float *>(tz), reinterpret_cast<float *>(part),
+                                 rbuf, on, sh, t);
+          continue;
+        }
+      }
+    }
+    // ---- node work of the round ----
     for (int k = tid; k < K + N; k += kDenseBlock) {
-      float rhs;
-      const float Th = R.node(sy.node0 + k, B, &rhs);
-      if (k < K) tx[k] = Th;
-      else tz[k - K] = Th;
+      T rhs;
+      const V tv = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
+      if (k < K) tx[k] = tv;
+      else tz[k - K] = tv;
     }
+    // (a full or freeze sweep never skips its grid pass: the freeze writes
+    // the frozen coefficients the next inner solve needs)
+    int end = 0;
+    if (!kF64 && on) end = sys_after_nodes(sh, ctl, sy, R, mode);
+    else R.fold();
     __syncthreads();
+    if (!R.write_msgs) continue;
+    // ---- grid pass (row sums of z written inside, column sums into ax) ----
     by_columns(K, [&](auto q) {
-      mean_sync_rows<E, U, decltype(q)::value>(sy, d.C32, h_in, h_out, tx, tz, part, R);
+      full_sync_rows<T, E, U, decltype(q)::value>(sy, Sg, io, d.C32, h_out, tx, tz, part, ax, R,
+                                                  brk);
     });
-    __syncthreads();
-    for (int k = tid; k < K; k += kDenseBlock) {
-      float sum = part[k];
-      for (int ww = 1; ww < kDenseWarps; ++ww) sum += part[ww * kDenseMaxK + k];
-      R.sum_out[sy.node0 + k] = sum;
-    }
+    for (int k = tid; k < K; k += kDenseBlock) R.put_sum(sy.node0 + k, ax[k]);
+    sys_end(sh, d, sy, on, mode, t);
+    if (end) sys_refine(sh, ctl, d, sy, B, R.mon_out, rbuf, t);
   }
-  R.finish(ctl, red);
+  tally_commit(ctl, t);
+  R.mdd = max(R.mdd, Rm.mdd);
+  R.md = max(R.md, Rm.md);
+  R.finish(ctl, red, brk);
 }
 
 // ---------------------------------------------------------------------------
@@ -714,63 +1059,6 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
   }
 }
 
-// FP32: three CTAs of 256 threads per SM (at most 85 registers a thread).
-template <class T, class E>
-__global__ void __launch_bounds__(kDenseBlock, sizeof(T) == 4 ? 3 : 1)
-dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
-  using V = T2<T>;
-  using E1 = typename Half<E>::t;
-  constexpr bool kF64 = sizeof(T) == 8;
-  __shared__ V tx[kDenseMaxK];                   // totals of x^
-  __shared__ V part[kDenseWarps * kDenseMaxK];   // per-warp sums of the new Mx', by column
-  __shared__ T zr[kDenseMaxN];                   // rhs of z
-  __shared__ int32_t cur;
-  FullRound<T> R(d, B, ctl);
-  const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
-                                  : reinterpret_cast<const T *>(d.S32);
-  V *mx, *mz;
-  if constexpr (kF64) {
-    mx = d.Mx64[0];
-    mz = d.Mz64[0];
-  } else {
-    mx = reinterpret_cast<float2 *>(d.M32[0]);
-    mz = mx + d.pairs;
-  }
-  E1 *hx = static_cast<E1 *>(d.H[0]);
-  E1 *hz = hx + d.pairs;
-  bool brk = false;
-  const int tid = threadIdx.x;
-
-  for (;;) {
-    const int32_t s = claim(ctl, &cur);
-    if (s >= d.nsys) break;
-    const DenseSys sy = d.sys[s];
-    const int K = sy.K, N = sy.N;
-    for (int k = tid; k < K + N; k += kDenseBlock) {
-      T rhs;
-      const V t = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
-      if (k < K) tx[k] = t;
-      else zr[k - K] = rhs;
-    }
-    __syncthreads();
-    if (!R.write_msgs) continue;
-    by_columns(K, [&](auto q) {
-      full_serial_rows<T, E1, decltype(q)::value>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R,
-                                                  brk);
-    });
-    __syncthreads();
-    for (int k = tid; k < K; k += kDenseBlock) {
-      V sum = part[k];
-      for (int ww = 1; ww < kDenseWarps; ++ww) {
-        sum.x += part[ww * kDenseMaxK + k].x;
-        sum.y += part[ww * kDenseMaxK + k].y;
-      }
-      R.put_sum(sy.node0 + k, sum);
-    }
-  }
-  R.finish(ctl, red, brk);
-}
-
 template <class E1, int Q>
 __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float2 *__restrict__ C,
                                                  E1 *__restrict__ hx, E1 *__restrict__ hz,
@@ -842,41 +1130,152 @@ __device__ __forceinline__ void mean_serial_rows(const DenseSys &sy, const float
   }
 }
 
+// One system's mean-only round, serial schedule (node work: h~ of x^ into
+// tx, rhs of z into zr), as mean_sync_system.
+template <class E1>
+__device__ __forceinline__ void mean_serial_system(const DenseView &d, const DenseSys &sy,
+                                                   const Buffers &B, Ctl *ctl, MeanRound &R,
+                                                   E1 *hx, E1 *hz, float *tx, float *zr,
+                                                   float *part, double *rbuf, bool on,
+                                                   SysShared &sh, Tally &t) {
+  const int K = sy.K, N = sy.N, tid = threadIdx.x;
+  for (int k = tid; k < K + N; k += kDenseBlock) {
+    float rhs;
+    const float Th = R.node(sy.node0 + k, B, &rhs);
+    if (k < K) tx[k] = Th;
+    else zr[k - K] = rhs;
+  }
+  if (on) {
+    if (sys_after_nodes(sh, ctl, sy, R, 2)) {   // its inner solve ends: no grid pass
+      sys_refine(sh, ctl, d, sy, B, R.mon_out, rbuf, t);
+      return;
+    }
+  } else {
+    R.fold();
+  }
+  __syncthreads();
+  by_columns(K, [&](auto q) {
+    mean_serial_rows<E1, decltype(q)::value>(sy, d.C32, hx, hz, tx, zr, part, R);
+  });
+  __syncthreads();
+  for (int k = tid; k < K; k += kDenseBlock) {
+    float sum = part[k];
+    for (int ww = 1; ww < kDenseWarps; ++ww) sum += part[ww * kDenseMaxK + k];
+    R.sum_out[sy.node0 + k] = sum;
+  }
+  sys_end(sh, d, sy, on, 2, t);
+}
+
 template <class E1>
 __global__ void __launch_bounds__(kDenseBlock)
 dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   __shared__ float tx[kDenseMaxK];                   // h~ of x^
   __shared__ float part[kDenseWarps * kDenseMaxK];   // per-warp sums of the new eta_x, by column
   __shared__ float zr[kDenseMaxN];                   // rhs of z
-  __shared__ int32_t cur;
+  __shared__ double rbuf[kRefineBuf];                // refinement steps (per-system control)
+  __shared__ SysShared sh;
   MeanRound R(d, B, ctl);
+  const bool on = ctl->retire != 0;
   E1 *hx = static_cast<E1 *>(d.H[0]);
   E1 *hz = hx + d.pairs;
+  __shared__ Tally t;   // thread 0's counts (kept out of the registers)
+  if (threadIdx.x == 0) t = Tally{};
+  for (;;) {
+    const int32_t s = claim_sys(ctl, d, on, sh);
+    if (s >= d.nsys) break;
+    if (on) {
+      R.inv_rn = sys_inv_rn(sh);
+      R.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
+    }
+    mean_serial_system<E1>(d, d.sys[s], B, ctl, R, hx, hz, tx, zr, part, rbuf, on, sh, t);
+  }
+  tally_commit(ctl, t);
+  R.finish(ctl, red);
+}
+
+// FP32: three CTAs of 256 threads per SM (at most 85 registers a thread).
+template <class T, class E>
+__global__ void __launch_bounds__(kDenseBlock, sizeof(T) == 4 ? 3 : 1)
+dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
+  using V = T2<T>;
+  using E1 = typename Half<E>::t;
+  constexpr bool kF64 = sizeof(T) == 8;
+  __shared__ V tx[kDenseMaxK];                   // totals of x^
+  __shared__ V part[kDenseWarps * kDenseMaxK];   // per-warp sums of the new Mx', by column
+  __shared__ T zr[kDenseMaxN];                   // rhs of z
+  __shared__ double rbuf[kF64 ? 1 : kRefineBuf];  // refinement steps (per-system control)
+  __shared__ SysShared sh;
+  FullRound<T> R(d, B, ctl);
+  const bool on = ctl->retire != 0;
+  const T *__restrict__ Sg = kF64 ? reinterpret_cast<const T *>(d.S64)
+                                  : reinterpret_cast<const T *>(d.S32);
+  V *mx, *mz;
+  if constexpr (kF64) {
+    mx = d.Mx64[0];
+    mz = d.Mz64[0];
+  } else {
+    mx = reinterpret_cast<float2 *>(d.M32[0]);
+    mz = mx + d.pairs;
+  }
+  E1 *hx = static_cast<E1 *>(d.H[0]);
+  E1 *hz = hx + d.pairs;
+  MeanRound Rm(d, B, ctl);
+  bool brk = false;
+  __shared__ Tally t;   // thread 0's counts (kept out of the registers)
+  if (threadIdx.x == 0) t = Tally{};
   const int tid = threadIdx.x;
 
   for (;;) {
-    const int32_t s = claim(ctl, &cur);
+    const int32_t s = claim_sys(ctl, d, on, sh);
     if (s >= d.nsys) break;
     const DenseSys sy = d.sys[s];
     const int K = sy.K, N = sy.N;
+    int mode = R.freeze ? 1 : 0;
+    if constexpr (!kF64) {
+      if (on) {
+        mode = sh.mode;
+        R.freeze = mode == 1;
+        R.inv_rn = Rm.inv_rn = sys_inv_rn(sh);
+        R.first = Rm.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
+        if (mode == 2) {   // precisions frozen already: a mean-only round
+          mean_serial_system<E1>(d, sy, B, ctl, Rm, hx, hz, reinterpret_cast<float *>(tx),
+                                 reinterpret_cast<float *>(zr), reinterpret_cast<float *>(part),
+                                 rbuf, on, sh, t);
+          continue;
+        }
+      }
+    }
     for (int k = tid; k < K + N; k += kDenseBlock) {
-      float rhs;
-      const float Th = R.node(sy.node0 + k, B, &rhs);
-      if (k < K) tx[k] = Th;
+      T rhs;
+      const V tv = R.node(sy.node0 + k, k < K ? T(1) : static_cast<T>(-sy.psi), B, &rhs);
+      if (k < K) tx[k] = tv;
       else zr[k - K] = rhs;
     }
+    int end = 0;   // (a full or freeze sweep never skips its grid pass)
+    if (!kF64 && on) end = sys_after_nodes(sh, ctl, sy, R, mode);
+    else R.fold();
     __syncthreads();
+    if (!R.write_msgs) continue;
     by_columns(K, [&](auto q) {
-      mean_serial_rows<E1, decltype(q)::value>(sy, d.C32, hx, hz, tx, zr, part, R);
+      full_serial_rows<T, E1, decltype(q)::value>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R,
+                                                  brk);
     });
     __syncthreads();
     for (int k = tid; k < K; k += kDenseBlock) {
-      float sum = part[k];
-      for (int ww = 1; ww < kDenseWarps; ++ww) sum += part[ww * kDenseMaxK + k];
-      R.sum_out[sy.node0 + k] = sum;
+      V sum = part[k];
+      for (int ww = 1; ww < kDenseWarps; ++ww) {
+        sum.x += part[ww * kDenseMaxK + k].x;
+        sum.y += part[ww * kDenseMaxK + k].y;
+      }
+      R.put_sum(sy.node0 + k, sum);
     }
+    sys_end(sh, d, sy, on, mode, t);
+    if (end) sys_refine(sh, ctl, d, sy, B, R.mon_out, rbuf, t);
   }
-  R.finish(ctl, red);
+  tally_commit(ctl, t);
+  R.mdd = max(R.mdd, Rm.mdd);
+  R.md = max(R.md, Rm.md);
+  R.finish(ctl, red, brk);
 }
 
 // ---------------------------------------------------------------------------
@@ -887,6 +1286,9 @@ dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
 // row (lanes on columns lane + 32 q, as in the serial sweeps): the row sum
 // has a single writer, and each warp's column sums go to its own slice of
 // `part`, added in warp order -- no atomics, the same result every run.
+// With per-system control (FP64 solves) the stop rule is applied to each
+// system here, and a system that meets it is done: later sweeps pass it over
+// and its x stays.
 // ---------------------------------------------------------------------------
 template <int Q>
 __device__ __forceinline__ void residual_rows(const DenseSys &sy, const double *__restrict__ S64,
@@ -938,11 +1340,17 @@ dense_residual_kernel(DenseView d, double *__restrict__ r_out, Ctl *ctl, DevScal
   __shared__ double vx[kDenseMaxK], vz[kDenseMaxN];   // x^ and z of the system
   __shared__ double az[kDenseMaxN];                   // sum_r S_jr x_r per row
   __shared__ double part[kDenseWarps * kDenseMaxK];   // per warp: sum_j S_jr z_j
+  __shared__ unsigned long long sred[2][kDenseWarps];
   __shared__ int32_t cur;
   const double *__restrict__ b = ctl->b;
   const double *__restrict__ x = ctl->x;
+  const bool on = ctl->retire != 0 && kind == CK_CHECK64;
+  const bool rel = ctl->rel != 0;
+  const double tol = ctl->tol;
   unsigned long long mr = 0, mrel = 0;
-  const int tid = threadIdx.x;
+  __shared__ Tally t;   // thread 0's counts (kept out of the registers)
+  if (threadIdx.x == 0) t = Tally{};
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   for (;;) {
     const int32_t s = claim(ctl, &cur);
     if (s >= d.nsys) break;
@@ -959,6 +1367,7 @@ dense_residual_kernel(DenseView d, double *__restrict__ r_out, Ctl *ctl, DevScal
     by_columns(K, [&](auto q) { residual_rows<decltype(q)::value>(sy, d.S64, vx, vz, az, part); });
     __syncthreads();
     const double bs = dv(d.sys_bmax[sy.orig]);
+    unsigned long long smr = 0, smrel = 0;
     for (int k = tid; k < K + N; k += kDenseBlock) {
       const int64_t i = sy.node0 + k;
       double Ax;
@@ -972,10 +1381,33 @@ dense_residual_kernel(DenseView d, double *__restrict__ r_out, Ctl *ctl, DevScal
       }
       const double ri = b[i] - Ax;
       if (r_out) r_out[i] = ri;
-      mr = umax(mr, bits(fabs(ri)));
-      mrel = umax(mrel, bits(bs > 0.0 ? fabs(ri) / bs : (ri == 0.0 ? 0.0 : INFINITY)));
+      smr = umax(smr, bits(fabs(ri)));
+      smrel = umax(smrel, bits(bs > 0.0 ? fabs(ri) / bs : (ri == 0.0 ? 0.0 : INFINITY)));
+    }
+    mr = umax(mr, smr);
+    mrel = umax(mrel, smrel);
+    if (on) {   // the system's own stop rule (thread 0)
+      smr = warp_max(smr);
+      smrel = warp_max(smrel);
+      if (lane == 0) {
+        sred[0][wid] = smr;
+        sred[1][wid] = smrel;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < kDenseWarps; ++w) {
+          smr = umax(smr, sred[0][w]);
+          smrel = umax(smrel, sred[1][w]);
+        }
+        SysCtl &sc = d.sysctl[sy.orig];
+        if (sc.state != 2 && (rel ? dv(smrel) < tol : dv(smr) < tol)) {
+          sc.state = 2;
+          t.done++;
+        }
+      }
     }
   }
+  tally_commit(ctl, t);
   block_max4(mr, mrel, 0, 0, &red->max_r, &red->max_rrel, nullptr, nullptr);
   last_block_control(ctl, red, kind);
 }

@@ -255,7 +255,13 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
     }
     case CK_SWEEP32:
     case CK_MEAN: {
-      if (kind == CK_SWEEP32) {
+      if (kind == CK_SWEEP32 && c.retire) {
+        // per-system control: the sweep moved the full messages of unfrozen
+        // systems and the mean messages of frozen (and freezing) ones
+        c.sweeps_full++;
+        c.par_m ^= 1;
+        c.par_e ^= 1;
+      } else if (kind == CK_SWEEP32) {
         c.sweeps_full++;
         if (c.pending_freeze) { c.frozen = 1; c.pending_freeze = 0; c.par_e ^= 1; c.e_slots = 1; }
         else c.par_m ^= 1;
@@ -281,6 +287,22 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (r->breakdown) { finish(c, GABP_ERR_BREAKDOWN); break; }
       const double dd = mdx / fmax(mx, DBL_MIN);
       if (!isfinite(dd)) { finish(c, GABP_ERR_DIVERGED); break; }
+      if (c.retire) {
+        // per-system control: the sweep applied every rule to each system and
+        // ran the refinement steps; the solve ends when every system is done
+        // or failed, or at max_iter sweeps
+        volatile Ctl *vc = &c;
+        const int finished = vc->sys_done + vc->sys_failed;
+        if (finished >= c.nsys || c.sweeps >= c.max_iter) {
+          c.residual = dv(vc->sys_rmax);
+          if (finished < c.nsys) finish(c, GABP_ERR_NOT_CONVERGED);
+          else finish(c, vc->sys_failed ? vc->sys_fail_status : GABP_OK);
+          break;
+        }
+        c.frozen = vc->sys_unfrozen == 0;
+        c.phase = c.frozen ? PH_MEAN : PH_FULL32;
+        break;
+      }
       if (kind == CK_SWEEP32 && !c.frozen && !c.pending_freeze) {
         // Precision convergence: relative change of the node precisions,
         // remaining error extrapolated with the observed contraction rate.

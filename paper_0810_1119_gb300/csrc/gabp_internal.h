@@ -117,6 +117,16 @@ struct Ctl {
   int check_now;                // the sweep just run is followed by a residual check
   int e_slots;                  // the mean messages in e[par_e] are in the slot layout (written
                                 // by a freeze sweep); window handles read them so once
+  // Section VII batches in dense form with per-system control (retire = 1),
+  // kept by the kernels' atomics: systems whose precisions are not frozen
+  // yet, systems done and failed, the largest failure status, and the
+  // largest final |r| and |r| / ||b_s|| over the systems that finished.
+  // Also the grid positions swept (every dense solve).
+  int retire;
+  int nsys;
+  int sys_unfrozen, sys_done, sys_failed, sys_fail_status;
+  unsigned long long sys_rmax, sys_rrelmax;
+  unsigned long long positions;
   int K;                        // CTL_MULTI: right-hand sides
   const double *Bm;             // CTL_MULTI: n x K right-hand sides (row-major)
   double *Xm;                   // CTL_MULTI: n x K solutions (row-major)
@@ -309,6 +319,34 @@ struct DenseSys {
   double psi;
 };
 
+// Per-system state of a batched solve with per-system control (device, one
+// per system, caller's order).  Every rule the controller applies to a whole
+// solve -- the precision freeze, the end of an inner solve, the scale of the
+// refinement, the stop rule, the stall of the refinement -- is applied to
+// each system on its own numbers, and each system refines as soon as its own
+// inner solve ends:
+//   state   0 = iterating, 2 = done (met the stop rule), 3 = failed
+//           (diverged, or eight refinement steps without a 10 % smaller
+//           stop measure);
+//   frozen  0 = full sweeps, 1 = its next sweep freezes the precisions,
+//           2 = mean-only sweeps;
+//   rn      the scale ||r_s||_inf of its current inner solve (the first inner
+//           solve uses ||b_s||_inf);
+//   k, prev_dd, best_dd, since_best, stall, prev_dP: the inner solve's sweep
+//           count (k = 0: its next sweep is the first of an inner solve) and
+//           the history of the relative changes of d and P~;
+//   outer, best_prog, outer_stall: refinement steps, the smallest stop
+//           measure after one, and steps since it last shrank by 10 %.
+struct SysCtl {
+  double rn;
+  double prev_dd, best_dd, prev_dP;
+  double best_prog;
+  int32_t k, stall, since_best;
+  int32_t state, frozen;
+  int32_t sweeps;               // message sweeps of this system in the solve
+  int32_t outer, outer_stall;
+};
+
 constexpr int kDenseMaxK = 256;    // largest K_s (and N_s) the dense kernels take
 constexpr int kDenseMaxN = 1024;
 
@@ -336,6 +374,7 @@ struct DenseView {
   float *sumE[2];
   const int32_t *sys_of_row;
   unsigned long long *sys_bmax;
+  SysCtl *sysctl;               // per-system control state (used when Ctl::retire = 1)
 };
 
 struct Dense {

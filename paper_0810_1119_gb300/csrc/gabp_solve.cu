@@ -493,6 +493,7 @@ void finish_stats(gabp_handle h) {
   S.rhs_norm = c.bnorm;
   S.n = h->g.n;
   S.edges = h->g.E;
+  S.positions_swept = h->dense ? static_cast<int64_t>(c.positions) : 0;
 }
 
 // Runs one control mode whose control block has been filled in the pinned
@@ -525,8 +526,12 @@ void run_mode(gabp_handle h, int mode, int32_t max_iter) {
     CK(cudaStreamSynchronize(st));
     const Ctl &c = *h->ctl_host;
     const int per_check = (mode == CTL_MIXED || mode == CTL_MULTI) ? 2 : 1;
-    h->stats.kernel_launches += 1 + static_cast<int64_t>(c.sweeps) * passes_per_sweep(h) +
-                                static_cast<int64_t>(c.checks) * per_check;
+    if (c.retire)   // per-system control: refinement steps run inside the sweeps
+      h->stats.kernel_launches += 1 + static_cast<int64_t>(c.sweeps) +
+                                  (mode == CTL_FP64 ? static_cast<int64_t>(c.checks) : 0);
+    else
+      h->stats.kernel_launches += 1 + static_cast<int64_t>(c.sweeps) * passes_per_sweep(h) +
+                                  static_cast<int64_t>(c.checks) * per_check;
   } else {
     run(h, K_OTHER, [&] { return launch_mode_init(h, st, mode); });
     const int64_t cap = 4 * static_cast<int64_t>(max_iter) + 128;
@@ -581,6 +586,12 @@ gabp_status solve_impl(gabp_handle h, const double *b, double *x, double tol, in
   if (h->g.nsys > 0) {
     h->ctl_host->batched = 1;
     CK(cudaMemsetAsync(h->g.sys_bmax, 0, sizeof(unsigned long long) * h->g.nsys, h->stream));
+  }
+  if (h->dense && h->opt.batch_control == 0) {   // per-system control
+    Ctl &c = *h->ctl_host;
+    c.retire = 1;
+    c.nsys = c.sys_unfrozen = h->dense->nsys;
+    CK(cudaMemsetAsync(h->dense->v.sysctl, 0, sizeof(SysCtl) * h->dense->nsys, h->stream));
   }
   run_mode(h, mode, max_iter);
   if (h->perm) {
@@ -846,6 +857,7 @@ void release(gabp_handle h) {
     cudaFree(const_cast<float *>(v.S32));
     cudaFree(const_cast<double *>(v.S64));
     cudaFree(h->dense->sys);
+    cudaFree(v.sysctl);
     delete h->dense;
     h->dense = nullptr;
   }
@@ -906,6 +918,8 @@ void build_dense(gabp_handle h, int32_t nsys, const int32_t *K, const int32_t *N
   CK(cudaMemsetAsync(g.sys_bmax, 0, sizeof(unsigned long long) * nsys, st));
   CK(cudaMalloc(reinterpret_cast<void **>(&d->sys), sizeof(DenseSys) * nsys));
   CK(cudaMemcpyAsync(d->sys, sys.data(), sizeof(DenseSys) * nsys, cudaMemcpyHostToDevice, st));
+  CK(cudaMalloc(reinterpret_cast<void **>(&d->v.sysctl), sizeof(SysCtl) * nsys));
+  CK(cudaMemsetAsync(d->v.sysctl, 0, sizeof(SysCtl) * nsys, st));
   float *S32d = nullptr;
   double *S64d = nullptr;
   ensure(&S32d, pairs);
@@ -1386,6 +1400,11 @@ gabp_status new_handle(const gabp_options *opt, gabp_handle *out) {
     g_create_error = "naive must be 0 or 1; Algorithm 1 (naive = 1) needs FP64, schedule 0 and damping 0";
     return GABP_ERR_INVALID_ARG;
   }
+  if (o.batch_control < 0 || o.batch_control > 1) {
+    delete h;
+    g_create_error = "batch_control must be 0 (per system) or 1 (whole batch)";
+    return GABP_ERR_INVALID_ARG;
+  }
   if (o.mean_window < -1 || (o.mean_window > 0 && (o.mean_window < 256 || o.mean_window > 65536)) ||
       (o.mean_window > 0 && o.schedule != 0)) {
     delete h;
@@ -1852,6 +1871,25 @@ gabp_status gabp_get_stats(gabp_handle h, gabp_stats *stats) {
   if (!h || !stats) return GABP_ERR_INVALID_ARG;
   *stats = h->stats;
   return GABP_OK;
+}
+
+gabp_status gabp_get_system_sweeps(gabp_handle h, int32_t *sweeps_host, int32_t nsys) {
+  if (!h) return GABP_ERR_INVALID_ARG;
+  if (!sweeps_host || h->g.nsys <= 0 || nsys != h->g.nsys)
+    return fail(h, GABP_ERR_INVALID_ARG,
+                "gabp_get_system_sweeps: not a batched handle, or nsys is not its number of systems");
+  return guarded(h, [&] {
+    if (h->dense && h->ctl_host->retire) {
+      std::vector<SysCtl> sc(nsys);
+      CK(cudaMemcpyAsync(sc.data(), h->dense->v.sysctl, sizeof(SysCtl) * nsys,
+                         cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (int32_t s = 0; s < nsys; ++s) sweeps_host[s] = sc[s].sweeps;
+    } else {
+      for (int32_t s = 0; s < nsys; ++s) sweeps_host[s] = h->stats.sweeps_total;
+    }
+    return GABP_OK;
+  });
 }
 
 gabp_status gabp_run_rounds(gabp_handle h, const double *b_dev, int32_t rounds, double *x_dev) {

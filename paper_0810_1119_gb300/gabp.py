@@ -37,7 +37,8 @@ EXPORTED = ("gabp_default_options", "gabp_create", "gabp_destroy", "gabp_set_str
             "gabp_run_rounds", "gabp_get_messages", "gabp_last_error", "gabp_status_string",
             "gabp_version", "gabp_create_batched", "gabp_create_lsq_batched",
             "gabp_solve_lsq_batched", "gabp_run_rounds_noalloc", "gabp_get_tuning",
-            "gabp_set_profile", "gabp_create_grid", "gabp_check_wait_limit")
+            "gabp_set_profile", "gabp_create_grid", "gabp_check_wait_limit",
+            "gabp_get_system_sweeps")
 
 
 class GabpOptions(ctypes.Structure):
@@ -52,7 +53,7 @@ class GabpOptions(ctypes.Structure):
                 ("aitken", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("damp_scope", ctypes.c_int32), ("pull_lanes", ctypes.c_int32),
                 ("pinv_shift", ctypes.c_double), ("naive", ctypes.c_int32),
-                ("mean_window", ctypes.c_int32)]
+                ("mean_window", ctypes.c_int32), ("batch_control", ctypes.c_int32)]
 
 
 class GabpStats(ctypes.Structure):
@@ -63,7 +64,8 @@ class GabpStats(ctypes.Structure):
                 ("n", ctypes.c_int64), ("edges", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_full", ctypes.c_double),
                 ("ms_mean", ctypes.c_double), ("ms_residual", ctypes.c_double),
-                ("ms_other", ctypes.c_double), ("reserved", ctypes.c_double * 2)]
+                ("ms_other", ctypes.c_double), ("positions_swept", ctypes.c_int64),
+                ("reserved", ctypes.c_double * 1)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -116,6 +118,7 @@ def load(path: str = LIB_PATH):
         "gabp_solve_multi": (ctypes.c_int, [H, vp, vp, ctypes.c_int32, ctypes.c_double,
                                             ctypes.c_int32, i32p]),
         "gabp_get_stats": (ctypes.c_int, [H, ctypes.POINTER(GabpStats)]),
+        "gabp_get_system_sweeps": (ctypes.c_int, [H, i32p, ctypes.c_int32]),
         "gabp_run_rounds": (ctypes.c_int, [H, vp, ctypes.c_int32, vp]),
         "gabp_get_messages": (ctypes.c_int, [H, f64p, f64p]),
         "gabp_last_error": (ctypes.c_char_p, [H]),
@@ -305,6 +308,14 @@ def gabp_get_stats(h) -> dict:
     s = GabpStats()
     _check(h, load().gabp_get_stats(h, ctypes.byref(s)))
     return s.as_dict()
+
+
+def gabp_get_system_sweeps(h, nsys: int) -> np.ndarray:
+    """Message sweeps each system of a batched handle took part in during the
+    last solve (caller's order)."""
+    out = np.zeros(nsys, dtype=np.int32)
+    _check(h, load().gabp_get_system_sweeps(h, _ptr(out, ctypes.c_int32), int(nsys)))
+    return out
 
 
 def gabp_set_profile(h, on: bool):

@@ -204,6 +204,23 @@ def test_mean_window_is_validated(lib):
         assert "mean_window" in str(ei.value)
 
 
+def test_batch_control_is_validated(lib):
+    """batch_control is 0 (per system) or 1 (whole batch); refused on the host,
+    and gabp_get_system_sweeps refuses a handle that is not batched."""
+    from paper_0810_1119_gb300 import gabp as G
+    m = W.poisson2d(4)
+    for bc in (-1, 2):
+        o = G.gabp_default_options()
+        o.batch_control = bc
+        with pytest.raises(G.GabpError) as ei:
+            G.gabp_create(m.row_ptr, m.col, m.val, None, o)
+        assert ei.value.name == "GABP_ERR_INVALID_ARG"
+        assert "batch_control" in str(ei.value)
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_get_system_sweeps(None, 1)
+    assert ei.value.name == "GABP_ERR_INVALID_ARG"
+
+
 def test_naive_is_validated(lib):
     """Algorithm 1 (naive = 1) needs FP64, the synchronous schedule and no
     damping; refused on the host."""
