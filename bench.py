@@ -476,7 +476,8 @@ def run_gabp(args):
             "roofline": {"bound": "hbm", "kernel": kernel_names[dom],
                          "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None,
-                         "peak_source": peak_kind, "traffic": _traffic(dom),
+                         "peak_source": peak_kind,
+                         "traffic": _traffic("mean_win" if (dom == "mean" and mwin > 0) else dom),
                          "bytes_per_launch": bytes_launch, "launches": n_k,
                          "mean_launch_us": 1e3 * ms_k / max(n_k, 1),
                          "random_scatter_us": scatter_us,

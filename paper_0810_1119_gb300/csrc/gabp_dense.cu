@@ -51,7 +51,16 @@ __device__ __forceinline__ T2<T> mk2(T a, T b) {
   return v;
 }
 
-__device__ __forceinline__ float rcp(float d) { return 1.0f / d; }
+// FP32 1/d: the hardware approximation (rcp.approx, within about one unit in
+// the last place; denominators are node precisions, never subnormal).  The
+// FP32 messages only drive the inner solves; the FP64 refinement removes any
+// error of that size.  The IEEE division sequence cost a third of the full
+// sweep's instructions.
+__device__ __forceinline__ float rcp(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
 __device__ __forceinline__ double rcp(double d) { return recip64(d); }
 
 __device__ __forceinline__ bool bad(float d) { return !(d != 0.0f) || !isfinite(d); }
@@ -97,25 +106,16 @@ __device__ __forceinline__ void st_h(__nv_bfloat162 *p, float2 v) {
   __stcs(p, __float22bfloat162_rn(v));
 }
 
-// Column sums run down up to 1024 rows in one lane.  In FP32 they are
-// compensated (Kahan): a plain running sum carries a rounding floor near
-// 1e-5 relative on 512-term columns, which the precision iteration turns into
-// a two-sweep cycle of that size; compensated, the floor is the rounding of
-// the messages themselves (about 2e-7).  FP64 sums need no compensation.
+// A lane's running column sum.  With a warp per grid row it runs down only
+// the rows of its warp, N / 8 <= 64 terms, and the eight warps' sums are
+// added in warp order: the rounding floor stays near 1e-6 relative in FP32,
+// below the precision rule's 1e-4 cycle threshold, so no compensation is
+// carried (a compensated sum cost four adds a term).
 template <class T>
 struct ColSum {
-  T s = T(0), c = T(0);
-  __device__ __forceinline__ void add(T v) {
-    if constexpr (sizeof(T) == 8) {
-      s += v;
-    } else {
-      const T y = v - c;
-      const T t = s + y;
-      c = (t - s) - y;
-      s = t;
-    }
-  }
-  __device__ __forceinline__ T value() const { return s - c; }
+  T s = T(0);
+  __device__ __forceinline__ void add(T v) { s += v; }
+  __device__ __forceinline__ T value() const { return s; }
 };
 
 // Claims the next system (thread 0) and hands its index to the whole CTA.
@@ -292,6 +292,16 @@ struct MeanRound {
   }
 };
 
+// Columns each lane holds for a system of K columns: 1, 2, 4 or 8.
+template <class F>
+__device__ __forceinline__ void by_columns(int K, F &&f) {
+  const int kq = (K + 31) >> 5;
+  if (kq > 4) f(std::integral_constant<int, 8>{});
+  else if (kq > 2) f(std::integral_constant<int, 4>{});
+  else if (kq > 1) f(std::integral_constant<int, 2>{});
+  else f(std::integral_constant<int, 1>{});
+}
+
 // ---------------------------------------------------------------------------
 // Per-system control (Ctl::retire = 1).  The CTA that claims a system applies
 // the controller's rules (gabp_device.cuh) to that system's own maxima: the
@@ -451,16 +461,52 @@ __device__ __forceinline__ void sys_end(SysShared &sh, const DenseView &d, const
   d.sysctl[sy.orig] = sh.sc;
 }
 
-// Doubles of shared memory sys_refine needs: x^ (K), z (N) and S x (N).
-constexpr int kRefineBuf = kDenseMaxK + 2 * kDenseMaxN;
+// Doubles of shared memory sys_refine needs: x^ (K), z (N), S x (N) and the
+// warps' partial sums of S^T z (kDenseWarps x K).
+constexpr int kRefineBuf = kDenseMaxK + 2 * kDenseMaxN + kDenseWarps * kDenseMaxK;
+
+// One pass over S (FP64) for R~ x: a warp per grid row j (rows w, w + 8,
+// ...), lanes on the columns lane + 32 q; (S x)_j is the warp's sum, and each
+// warp's partial column sums of S^T z go to its own slice of `part` (added
+// in warp order by the caller).  x^ is read from shared memory, so only the
+// column sums live in registers.
+template <int Q>
+__device__ __forceinline__ void refine_rows(const DenseSys &sy, const double *__restrict__ S,
+                                            const double *vx, const double *vz, double *az,
+                                            double *part) {
+  const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double col[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) col[q] = 0.0;
+  for (int j = w; j < N; j += kDenseWarps) {
+    const double zj = vz[j];
+    double row = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int r = lane + 32 * q;
+      if (r < K) {
+        const double a = __ldcs(S + static_cast<int64_t>(j) * K + r);
+        row += a * vx[r];
+        col[q] += a * zj;
+      }
+    }
+    row = group_sum<32>(row);
+    if (lane == 0) az[j] = row;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int r = lane + 32 * q;
+    if (r < K) part[w * kDenseMaxK + r] = col[q];
+  }
+}
 
 // The refinement step of a system whose inner solve ended in this sweep
 // (every thread of the CTA calls it; thread 0 holds the state in sh.sc).
 // With d the tentative means the sweep's node work left in `mon` and rn_s
 // the scale of the inner solve:
 //     x <- x + rn_s d,   r = b - R~ x   (FP64),
-// R~ x from S in FP64: S x with a warp per row, S^T z with a thread per
-// column summing the rows in order (fixed order: the same bits every run).
+// R~ x from S in FP64 in one pass (refine_rows; fixed order: the same bits
+// every run).
 // Then the system's stop rule: done when max |r| / ||b_s|| < tol (max |r| <
 // tol for the absolute rule); failed when r is not finite or exceeds 1e30
 // ||b_s||, or after eight refinement steps without a 10 % smaller stop
@@ -469,7 +515,7 @@ constexpr int kRefineBuf = kDenseMaxK + 2 * kDenseMaxN;
 __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, const DenseSys &sy,
                            const Buffers &B, const float2 *mon, double *buf, Tally &t) {
   const int K = sy.K, N = sy.N, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  double *vx = buf, *vz = buf + K, *az = buf + K + N;
+  double *vx = buf, *vz = buf + K, *az = buf + K + N, *part = buf + K + 2 * N;
   double *__restrict__ x = ctl->x;
   const double *__restrict__ b = ctl->b;
   const double *__restrict__ S = d.S64 + sy.pair0;
@@ -481,14 +527,11 @@ __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, co
     if (k < K) vx[k] = v;
     else vz[k - K] = v;
   }
+  for (int k = tid; k < kDenseWarps * K; k += kDenseBlock)
+    part[(k / K) * kDenseMaxK + k % K] = 0.0;   // warps without rows leave theirs at zero
   __syncthreads();
-  for (int j = w; j < N; j += kDenseWarps) {   // (S x)_j
-    double a = 0.0;
-#pragma unroll 2
-    for (int r = lane; r < K; r += 32) a += __ldcs(S + static_cast<int64_t>(j) * K + r) * vx[r];
-    a = group_sum<32>(a);
-    if (lane == 0) az[j] = a;
-  }
+  by_columns(K, [&](auto q) { refine_rows<decltype(q)::value>(sy, S, vx, vz, az, part); });
+  __syncthreads();
   const double bs = dv(d.sys_bmax[sy.orig]);
   unsigned long long smr = 0, smrel = 0;
   auto residual = [&](int64_t g, double Ax) {
@@ -499,11 +542,10 @@ __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, co
   };
   for (int r = tid; r < K; r += kDenseBlock) {   // x^ rows: x_r + (S^T z)_r
     double c = 0.0;
-#pragma unroll 4
-    for (int j = 0; j < N; ++j) c += S[static_cast<int64_t>(j) * K + r] * vz[j];
+#pragma unroll
+    for (int ww = 0; ww < kDenseWarps; ++ww) c += part[ww * kDenseMaxK + r];
     residual(sy.node0 + r, vx[r] + c);
   }
-  __syncthreads();
   for (int j = tid; j < N; j += kDenseBlock)   // z rows: (S x)_j - psi z_j
     residual(sy.node0 + K + j, az[j] - sy.psi * vz[j]);
   smr = warp_max(smr);
@@ -563,15 +605,6 @@ __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, co
 // messages eta_ij = c (h~_i - eta_ji) are written (storage E) instead of full
 // messages.
 // ---------------------------------------------------------------------------
-// Columns each lane holds for a system of K columns: 1, 2, 4 or 8.
-template <class F>
-__device__ __forceinline__ void by_columns(int K, F &&f) {
-  const int kq = (K + 31) >> 5;
-  if (kq > 4) f(std::integral_constant<int, 8>{});
-  else if (kq > 2) f(std::integral_constant<int, 4>{});
-  else if (kq > 1) f(std::integral_constant<int, 2>{});
-  else f(std::integral_constant<int, 1>{});
-}
 
 // Grid rows each warp loads ahead: U (the tuned figure) when U rows of Q
 // columns a lane fit eight values, else 8 / Q.
