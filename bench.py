@@ -728,6 +728,7 @@ def run_poisson3d(args):
             st = s.stats()
         r = {"ms": statistics.mean(ms), "status": err or "GABP_OK", "sweeps": st["sweeps_total"],
              "sweeps_full": st["sweeps_full"], "sweeps_mean": st["sweeps_mean"],
+             "sweeps_mean_fp32_after_ladder": st["sweeps_wide"],
              "outer": st["outer_steps"], "rel_residual": st["residual"] / st["rhs_norm"],
              "handle_build_s": build_s, "tuning": s.tuning()}
         if getattr(args, "oracle_residual", False):

@@ -58,7 +58,13 @@ typedef enum {
 typedef enum {
   GABP_PREC_FP64 = 0,        /* plain FP64 messages, every sweep updates P and mu */
   GABP_PREC_MIXED_FP32 = 1,  /* FP32 messages inside FP64 residual refinement */
-  GABP_PREC_MIXED_BF16 = 2   /* as MIXED_FP32 with BF16 storage of the mean messages */
+  GABP_PREC_MIXED_BF16 = 2   /* as MIXED_FP32 with BF16 storage of the mean messages, climbing
+                                a precision ladder: the first refinement step that fails to
+                                shrink the residual by 10 % (BF16 messages hold about three
+                                digits, which ill-conditioned systems can need more than)
+                                switches the later inner solves to FP32 storage of the mean
+                                messages (per system in a dense batch under per-system
+                                control); the handle holds both buffers */
 } gabp_precision;
 
 typedef enum {
@@ -180,7 +186,10 @@ typedef struct {
                                solve's sweeps processed, summed over the sweeps (with per-system
                                control a system that is done, or waits for the next refinement
                                step, adds none); 0 for the other forms */
-  double reserved[1];
+  int32_t sweeps_wide;      /* MIXED_BF16: mean-only sweeps that stored FP32 mean messages
+                               after the precision ladder climbed (dense batch under
+                               per-system control: sweeps in which some system had climbed) */
+  int32_t reserved_i;
 } gabp_stats;
 
 /* Fills *opt with the defaults: FP64, relative residual, automatic check

@@ -51,16 +51,7 @@ __device__ __forceinline__ T2<T> mk2(T a, T b) {
   return v;
 }
 
-// FP32 1/d: the hardware approximation (rcp.approx, within about one unit in
-// the last place; denominators are node precisions, never subnormal).  The
-// FP32 messages only drive the inner solves; the FP64 refinement removes any
-// error of that size.  The IEEE division sequence cost a third of the full
-// sweep's instructions.
-__device__ __forceinline__ float rcp(float d) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
-  return r;
-}
+__device__ __forceinline__ float rcp(float d) { return rcp32(d); }
 __device__ __forceinline__ double rcp(double d) { return recip64(d); }
 
 __device__ __forceinline__ bool bad(float d) { return !(d != 0.0f) || !isfinite(d); }
@@ -330,7 +321,7 @@ static_assert(offsetof(SysShared, red64) % 8 == 0, "64-bit maxima must be 8-byte
 // Thread 0's counts over the systems its CTA handled, committed once per
 // launch (held in shared memory: only thread 0 touches them).
 struct Tally {
-  uint32_t frozen, done, failed, checks;
+  uint32_t frozen, done, failed, checks, wide_seen;
   int32_t outer, fail_status;
   unsigned long long positions, rmax, rrelmax;
 };
@@ -344,6 +335,7 @@ __device__ __forceinline__ void tally_commit(Ctl *ctl, const Tally &t) {
   if (t.checks) atomicAdd(&ctl->checks, static_cast<int>(t.checks));
   if (t.outer) atomicMax(&ctl->outer, t.outer);
   if (t.fail_status) atomicMax(&ctl->sys_fail_status, t.fail_status);
+  if (t.wide_seen) atomicOr(&ctl->wide_now, 1);
   if (t.rmax) atomicMax(&ctl->sys_rmax, t.rmax);
   if (t.rrelmax) atomicMax(&ctl->sys_rrelmax, t.rrelmax);
 }
@@ -407,9 +399,12 @@ __device__ bool sys_rules(SysCtl &sc, const Ctl *ctl, int mode, uint32_t mdd, ui
   } else {
     sc.since_best++;
   }
-  const bool plateau = ctl->plateau > 0 && sc.since_best >= ctl->plateau && dd < ctl->floor_dd;
+  // (a system whose ladder climbed takes the FP32 storage's rule)
+  const double floor_dd = sc.wide ? ctl->floor_dd_wide : ctl->floor_dd;
+  const int plateau_n = sc.wide ? 0 : ctl->plateau;
+  const bool plateau = plateau_n > 0 && sc.since_best >= plateau_n && dd < floor_dd;
   return mode != 0 && k >= 3 &&
-         (err_d < ctl->inner_goal || (sc.stall >= 2 && dd < ctl->floor_dd) || plateau);
+         (err_d < ctl->inner_goal || (sc.stall >= 2 && dd < floor_dd) || plateau);
 }
 
 // After the node work of a system (every thread calls it): the system's
@@ -510,8 +505,10 @@ __device__ __forceinline__ void refine_rows(const DenseSys &sy, const double *__
 // Then the system's stop rule: done when max |r| / ||b_s|| < tol (max |r| <
 // tol for the absolute rule); failed when r is not finite or exceeds 1e30
 // ||b_s||, or after eight refinement steps without a 10 % smaller stop
-// measure; otherwise r is kept as the right-hand side of its next inner
-// solve, whose scale is rn_s = max |r| (history reset, k = 0).
+// measure (a BF16 handle's system first climbs the precision ladder at its
+// first such step: its later inner solves store FP32 mean messages, with a
+// fresh stall budget); otherwise r is kept as the right-hand side of its
+// next inner solve, whose scale is rn_s = max |r| (history reset, k = 0).
 __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, const DenseSys &sy,
                            const Buffers &B, const float2 *mon, double *buf, Tally &t) {
   const int K = sy.K, N = sy.N, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -574,6 +571,9 @@ __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, co
       fail = GABP_ERR_DIVERGED;
     } else if (sc.outer == 1 || prog < 0.9 * sc.best_prog) {
       sc.best_prog = prog;
+      sc.outer_stall = 0;
+    } else if (ctl->ladder && !sc.wide) {   // BF16 storage: climb to FP32 at the first stall
+      sc.wide = 1;
       sc.outer_stall = 0;
     } else if (++sc.outer_stall >= 8) {
       fail = GABP_ERR_NOT_CONVERGED;
@@ -849,6 +849,9 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   const int pe = ctl->par_e;
   const E *__restrict__ h_in = static_cast<const E *>(pe ? d.H[1] : d.H[0]);
   E *__restrict__ h_out = static_cast<E *>(pe ? d.H[0] : d.H[1]);
+  // (systems whose precision ladder climbed: FP32 mean messages)
+  const float2 *__restrict__ w_in = static_cast<const float2 *>(pe ? d.H32[1] : d.H32[0]);
+  float2 *__restrict__ w_out = static_cast<float2 *>(pe ? d.H32[0] : d.H32[1]);
   __shared__ Tally t;   // thread 0's counts (kept out of the registers)
   if (threadIdx.x == 0) t = Tally{};
   for (;;) {
@@ -857,6 +860,14 @@ dense_mean_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     if (on) {
       R.inv_rn = sys_inv_rn(sh);
       R.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
+      if constexpr (!std::is_same_v<E, float2>) {
+        if (sh.sc.wide) {
+          if (threadIdx.x == 0) t.wide_seen = 1;
+          mean_sync_system<float2, U>(d, d.sys[s], B, ctl, R, w_in, w_out, tx, tz, part, rbuf, on,
+                                      sh, t);
+          continue;
+        }
+      }
     }
     mean_sync_system<E, U>(d, d.sys[s], B, ctl, R, h_in, h_out, tx, tz, part, rbuf, on, sh, t);
   }
@@ -912,9 +923,18 @@ dense_full_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
         R.inv_rn = Rm.inv_rn = sys_inv_rn(sh);
         R.first = Rm.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
         if (mode == 2) {   // precisions frozen already: a mean-only round
-          mean_sync_system<E, U>(d, sy, B, ctl, Rm, h_in, h_out, reinterpret_cast<float *>(tx),
-                                 reinterpret_cast<float *>(tz), reinterpret_cast<float *>(part),
-                                 rbuf, on, sh, t);
+          float *ftx = reinterpret_cast<float *>(tx), *ftz = reinterpret_cast<float *>(tz);
+          float *fpart = reinterpret_cast<float *>(part);
+          if constexpr (!std::is_same_v<E, float2>) {
+            if (sh.sc.wide) {   // its precision ladder climbed: FP32 mean messages
+              if (threadIdx.x == 0) t.wide_seen = 1;
+              mean_sync_system<float2, U>(
+                  d, sy, B, ctl, Rm, static_cast<const float2 *>(pe ? d.H32[1] : d.H32[0]),
+                  static_cast<float2 *>(pe ? d.H32[0] : d.H32[1]), ftx, ftz, fpart, rbuf, on, sh, t);
+              continue;
+            }
+          }
+          mean_sync_system<E, U>(d, sy, B, ctl, Rm, h_in, h_out, ftx, ftz, fpart, rbuf, on, sh, t);
           continue;
         }
       }
@@ -1211,6 +1231,8 @@ dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
   const bool on = ctl->retire != 0;
   E1 *hx = static_cast<E1 *>(d.H[0]);
   E1 *hz = hx + d.pairs;
+  float *wx = static_cast<float *>(d.H32[0]);   // (systems whose ladder climbed: FP32 planes)
+  float *wz = wx + d.pairs;
   __shared__ Tally t;   // thread 0's counts (kept out of the registers)
   if (threadIdx.x == 0) t = Tally{};
   for (;;) {
@@ -1219,6 +1241,13 @@ dense_mean_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     if (on) {
       R.inv_rn = sys_inv_rn(sh);
       R.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
+      if constexpr (!std::is_same_v<E1, float>) {
+        if (sh.sc.wide) {
+          if (threadIdx.x == 0) t.wide_seen = 1;
+          mean_serial_system<float>(d, d.sys[s], B, ctl, R, wx, wz, tx, zr, part, rbuf, on, sh, t);
+          continue;
+        }
+      }
     }
     mean_serial_system<E1>(d, d.sys[s], B, ctl, R, hx, hz, tx, zr, part, rbuf, on, sh, t);
   }
@@ -1271,9 +1300,18 @@ dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
         R.inv_rn = Rm.inv_rn = sys_inv_rn(sh);
         R.first = Rm.first = sh.sc.k == 0;   // the first sweep of the system's inner solve
         if (mode == 2) {   // precisions frozen already: a mean-only round
-          mean_serial_system<E1>(d, sy, B, ctl, Rm, hx, hz, reinterpret_cast<float *>(tx),
-                                 reinterpret_cast<float *>(zr), reinterpret_cast<float *>(part),
-                                 rbuf, on, sh, t);
+          float *ftx = reinterpret_cast<float *>(tx), *fzr = reinterpret_cast<float *>(zr);
+          float *fpart = reinterpret_cast<float *>(part);
+          if constexpr (!std::is_same_v<E1, float>) {
+            if (sh.sc.wide) {   // its precision ladder climbed: FP32 mean messages
+              if (threadIdx.x == 0) t.wide_seen = 1;
+              float *wx = static_cast<float *>(d.H32[0]);
+              mean_serial_system<float>(d, sy, B, ctl, Rm, wx, wx + d.pairs, ftx, fzr, fpart, rbuf,
+                                        on, sh, t);
+              continue;
+            }
+          }
+          mean_serial_system<E1>(d, sy, B, ctl, Rm, hx, hz, ftx, fzr, fpart, rbuf, on, sh, t);
           continue;
         }
       }
@@ -1543,24 +1581,26 @@ int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *c
 // Caches the occupancy of every dense kernel (done at create time, before
 // any graph is recorded).
 void prepare_dense_kernels(bool bf16) {
+  // (a BF16 handle also runs the FP32-storage mean kernels once its
+  // precision ladder climbs)
   dense_grid(dense_full_kernel<double, float2, 2>, 1);
   dense_grid(dense_full_serial_kernel<double, float2>, 1);
   dense_grid(dense_residual_kernel, 1);
+  dense_grid(dense_mean_serial_kernel<float>, 1);
   if (bf16) {
     dense_grid(dense_full_serial_kernel<float, __nv_bfloat162>, 1);
     dense_grid(dense_mean_serial_kernel<__nv_bfloat16>, 1);
   } else {
     dense_grid(dense_full_serial_kernel<float, float2>, 1);
-    dense_grid(dense_mean_serial_kernel<float>, 1);
   }
   for (int u : {1, 2, 4}) {
     GABP_ROWS_DISPATCH(u, {
+      dense_grid(dense_mean_kernel<float2, UR>, 1);
       if (bf16) {
         dense_grid(dense_full_kernel<float, __nv_bfloat162, UR>, 1);
         dense_grid(dense_mean_kernel<__nv_bfloat162, UR>, 1);
       } else {
         dense_grid(dense_full_kernel<float, float2, UR>, 1);
-        dense_grid(dense_mean_kernel<float2, UR>, 1);
       }
     });
   }

@@ -101,6 +101,19 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
+// FP32 1/d of a cavity precision (the dense Section VII full sweeps): the
+// hardware approximation (rcp.approx, within about one unit in the last
+// place; precisions are never subnormal).  FP32 messages only drive the inner
+// solves of the FP64 refinement, which removes errors of that size; there the
+// IEEE division sequence was a third of a full sweep's instructions.  The CSR
+// and grid sweeps keep the IEEE division: on an indefinite tree the in-place
+// CSR form needed 60 % more sweeps with the approximation.
+__device__ __forceinline__ float rcp32(float d) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  return r;
+}
+
 // 1/d in FP64: an FP32 reciprocal seed (relative error e0 < 2^-22), then the
 // cubic Newton-Raphson step y (1 + e + e^2) with e = 1 - d y, whose error is
 // e0^3 < 2^-66 before rounding.  For |d| outside [2^-99, 2^99) (where the
@@ -224,14 +237,26 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       if (kind == CK_CHECK64) { c.phase = PH_FULL64; break; }
       // Refinement that stopped paying: eight outer steps without a 10 %
       // smaller residual (inner solves no more accurate than their storage
-      // allows, e.g. BF16 messages on an ill-conditioned system).  Slow but
-      // real progress -- a batch whose slowest system gains a little per
-      // step -- keeps going.
+      // allows).  Slow but real progress -- a batch whose slowest system
+      // gains a little per step -- keeps going.  BF16 storage climbs the
+      // precision ladder at its first such step: from then on the inner
+      // solves store FP32 mean messages (each starts from zero messages, so
+      // nothing is converted), with a fresh stall budget.
       {
         // progress in the measure the stop rule uses (batches: worst relative)
         const double prog = (c.batched && c.rel) ? rrel : rn;
-        if (c.outer_stall < 0 || prog < 0.9 * c.best_rn) { c.best_rn = prog; c.outer_stall = 0; }
-        else if (++c.outer_stall >= 8) { finish(c, GABP_ERR_NOT_CONVERGED); break; }
+        if (c.outer_stall < 0 || prog < 0.9 * c.best_rn) {
+          c.best_rn = prog;
+          c.outer_stall = 0;
+        } else if (c.ladder && !c.wide) {
+          c.wide = 1;
+          c.outer_stall = 0;
+          c.floor_dd = c.floor_dd_wide;
+          c.plateau = 0;
+        } else if (++c.outer_stall >= 8) {
+          finish(c, GABP_ERR_NOT_CONVERGED);
+          break;
+        }
       }
       // next refinement step: solve A d = r / ||r|| from zero mean messages.
       // One system: the inner solve only has to shrink the residual by the
@@ -250,7 +275,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       c.since_best = 0;
       c.prev_dP = INFINITY;
       c.first = 1;
-      c.phase = c.frozen ? PH_MEAN : PH_FULL32;
+      c.phase = c.frozen ? (c.wide ? PH_MEANW : PH_MEAN) : PH_FULL32;
       break;
     }
     case CK_SWEEP32:
@@ -267,8 +292,16 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
         else c.par_m ^= 1;
       } else {
         c.sweeps_mean++;
+        c.sweeps_wide += c.wide;
         c.par_e ^= 1;
         c.e_slots = 0;
+      }
+      if (c.retire) {   // per-system control: a sweep in which some system stored FP32
+        volatile Ctl *vc = &c;
+        if (vc->wide_now) {
+          c.sweeps_wide++;
+          c.wide_now = 0;
+        }
       }
       if (c.mode == CTL_PREC && c.frozen) {
         c.sweeps++;
@@ -326,7 +359,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       const bool inner_done = c.frozen && c.k >= 3 &&
                               (err_d < c.inner_goal || (c.stall >= 2 && dd < c.floor_dd) || plateau);
       if (inner_done || c.sweeps >= c.max_iter) c.phase = PH_REFINE;
-      else c.phase = c.frozen ? PH_MEAN : PH_FULL32;
+      else c.phase = c.frozen ? (c.wide ? PH_MEANW : PH_MEAN) : PH_FULL32;
       break;
     }
     case CK_INITK: {

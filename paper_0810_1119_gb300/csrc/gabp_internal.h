@@ -58,7 +58,8 @@ enum Phase : int {
   PH_REFINE = 4,    // x += ||r|| d, r = b - A x
   PH_MEANK = 5,     // mean-only sweep of K right-hand sides at once
   PH_REFINEK = 6,   // X += ||r_k|| D, R = B - A X for K columns
-  PH_COUNT = 7,
+  PH_MEANW = 7,     // mean-only sweep in FP32 storage once a BF16 handle's ladder climbed
+  PH_COUNT = 8,
   PH_DONE = 15
 };
 
@@ -102,6 +103,14 @@ struct Ctl {
   int since_best;               // sweeps since best_dd last shrank by 10 %
   int plateau;                  // > 0: an inner solve also ends after this many such sweeps
   double floor_dd;              // relative change below which a stall ends an inner solve
+  // BF16 mean storage, precision ladder (ladder = 1): after the first
+  // refinement step that fails to shrink the residual by 10 %, the inner
+  // solves store their mean messages in FP32 (wide = 1), with the FP32
+  // storage's inner rule (floor_dd_wide, no plateau).  sweeps_wide counts the
+  // mean-only sweeps that ran with FP32 storage; wide_now is set by a dense
+  // sweep in which some system (per-system control) stored FP32 messages.
+  int ladder, wide, sweeps_wide, wide_now;
+  double floor_dd_wide;
   double best_rn;               // smallest FP64 residual of the refinement so far
   int outer_stall;              // refinement steps since best_rn last halved
   double bnorm, thr, rn, inv_rn, residual;
@@ -138,6 +147,7 @@ struct Buffers {
   double2 *m64[2];
   float2 *m32[2];
   void *e[2];               // mean messages: float or bf16 (per precision mode)
+  void *e32[2];             // BF16 handles: FP32 mean messages once the ladder climbs
   float *c32;               // frozen coefficients c_ij (slot s of row i)
   float *invP32;            // frozen 1/P~_i
   float2 *mon32[2];         // (P~_i, d_i) of the last two sweeps
@@ -336,7 +346,9 @@ struct DenseSys {
 //           count (k = 0: its next sweep is the first of an inner solve) and
 //           the history of the relative changes of d and P~;
 //   outer, best_prog, outer_stall: refinement steps, the smallest stop
-//           measure after one, and steps since it last shrank by 10 %.
+//           measure after one, and steps since it last shrank by 10 %;
+//   wide    BF16 handles: the system's ladder climbed (its first stalled
+//           refinement step), and its inner solves store FP32 mean messages.
 struct SysCtl {
   double rn;
   double prev_dd, best_dd, prev_dP;
@@ -345,6 +357,8 @@ struct SysCtl {
   int32_t state, frozen;
   int32_t sweeps;               // message sweeps of this system in the solve
   int32_t outer, outer_stall;
+  int32_t wide;                 // BF16 handles: its inner solves store FP32 mean messages
+  int32_t pad;
 };
 
 constexpr int kDenseMaxK = 256;    // largest K_s (and N_s) the dense kernels take
@@ -369,6 +383,7 @@ struct DenseView {
   double2 *Mz64[2], *Mx64[2];
   float2 *C32;
   void *H[2];                   // float2 or __nv_bfloat162 (eta_z, eta_x)
+  void *H32[2];                 // BF16 handles: FP32 mean messages after the ladder climbs
   float2 *sum32[2];
   double2 *sum64[2];
   float *sumE[2];

@@ -127,6 +127,11 @@ void ensure_dense32(gabp_handle h) {
     ensure(&v.M32[k], d.pairs);
     CK(cudaMalloc(&v.H[k], hb));
     CK(cudaMemset(v.H[k], 0, hb));
+    if (is_bf16(h)) {   // FP32 mean messages for the precision ladder
+      const size_t wb = (d.pairs + kPad) * sizeof(float2);
+      CK(cudaMalloc(&v.H32[k], wb));
+      CK(cudaMemset(v.H32[k], 0, wb));
+    }
   }
   ensure(&v.C32, d.pairs);
   const size_t n = h->g.n;
@@ -156,6 +161,10 @@ void ensure_grid32(gabp_handle h) {
   for (int k = 0; k < 2; ++k) {
     CK(cudaMalloc(&B.e[k], eb));
     CK(cudaMemset(B.e[k], 0, eb));
+    if (is_bf16(h)) {   // FP32 mean messages for the precision ladder
+      CK(cudaMalloc(&B.e32[k], (M + kPad) * sizeof(float)));
+      CK(cudaMemset(B.e32[k], 0, (M + kPad) * sizeof(float)));
+    }
   }
   ensure(&B.c32, M);
   ensure(&B.invP32, n);
@@ -191,6 +200,12 @@ void ensure32(gabp_handle h) {
   CK(cudaMalloc(&B.e[1], eb));
   CK(cudaMemset(B.e[0], 0, eb));
   CK(cudaMemset(B.e[1], 0, eb));
+  if (is_bf16(h)) {   // FP32 mean messages for the precision ladder
+    for (int k = 0; k < 2; ++k) {
+      CK(cudaMalloc(&B.e32[k], (E + kPad) * sizeof(float)));
+      CK(cudaMemset(B.e32[k], 0, (E + kPad) * sizeof(float)));
+    }
+  }
   ensure(&B.c32, E);
   ensure(&B.invP32, n);
   ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
@@ -250,6 +265,12 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
       case PH_CHECK64: return launch_dense_residual(d, st, nullptr, h->ctl, h->red, false);
       case PH_FULL32: return launch_dense_full32(d, st, h->buf, h->ctl, h->red, is_bf16(h));
       case PH_MEAN: return launch_dense_mean(d, st, h->buf, h->ctl, h->red, is_bf16(h));
+      case PH_MEANW: {   // FP32 mean messages after the ladder climbed (one controller)
+        Dense w = d;
+        w.v.H[0] = d.v.H32[0];
+        w.v.H[1] = d.v.H32[1];
+        return launch_dense_mean(w, st, h->buf, h->ctl, h->red, false);
+      }
       case PH_REFINE:
         return launch_refine_update(g.n, st, h->buf, h->ctl) +
                launch_dense_residual(d, st, h->buf.r64, h->ctl, h->red, true);
@@ -281,6 +302,14 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
         return passes([&](const GridView &v) {
           return launch_grid_mean(v, st, B, h->ctl, h->red, is_bf16(h));
         });
+      case PH_MEANW: {   // FP32 mean messages after the ladder climbed
+        Buffers W = B;
+        W.e[0] = B.e32[0];
+        W.e[1] = G.colour ? B.e32[0] : B.e32[1];
+        return passes([&](const GridView &v) {
+          return launch_grid_mean(v, st, W, h->ctl, h->red, false);
+        });
+      }
       case PH_REFINE: {
         const int k = launch_refine_update(g.n, st, h->buf, h->ctl) +
                       launch_grid_residual(G.v, st, h->buf.r64, h->ctl, h->red, true);
@@ -290,8 +319,8 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     }
     return 0;
   }
-  if (g.ncol > 0 &&
-      (phase == PH_FULL64 || phase == PH_FULL32 || phase == PH_MEAN || phase == PH_MEANK)) {
+  if (g.ncol > 0 && (phase == PH_FULL64 || phase == PH_FULL32 || phase == PH_MEAN ||
+                    phase == PH_MEANK || phase == PH_MEANW)) {
     // colour schedule: one in-place pass per class (both parities alias one buffer)
     Buffers B = h->buf;
     B.m64[1] = B.m64[0];
@@ -304,6 +333,11 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
       if (phase == PH_FULL64) k += launch_sweep64(g, st, B, h->ctl, h->red, &v);
       else if (phase == PH_FULL32) k += launch_sweep32(g, st, B, h->ctl, h->red, is_bf16(h), &v);
       else if (phase == PH_MEAN) k += launch_mean(g, st, B, h->ctl, h->red, is_bf16(h), &v);
+      else if (phase == PH_MEANW) {   // FP32 mean messages after the ladder climbed
+        Buffers W = B;
+        W.e[0] = W.e[1] = B.e32[0];
+        k += launch_mean(g, st, W, h->ctl, h->red, false, &v);
+      }
       else k += launch_mean_multi(g, st, B, h->ctl, h->red, h->graph_K, &v);
     }
     return k;
@@ -319,6 +353,12 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     case PH_MEAN:
       return h->win.nwin > 0 ? launch_mean_win(g, h->win, st, h->buf, h->ctl, h->red, is_bf16(h))
                              : launch_mean(g, st, h->buf, h->ctl, h->red, is_bf16(h));
+    case PH_MEANW: {   // FP32 mean messages after the ladder climbed (tile form)
+      Buffers W = h->buf;
+      W.e[0] = W.e32[0];
+      W.e[1] = W.e32[1];
+      return launch_mean(g, st, W, h->ctl, h->red, false);
+    }
     case PH_REFINE: {
       const int k = launch_refine(g, st, h->buf, h->ctl, h->red);
       if (g.ncol > 0) zero_messages(h, st, false);   // the next inner solve starts from zero
@@ -342,6 +382,7 @@ void zero_messages(gabp_handle h, cudaStream_t st, bool full) {
   if (full && B.m64[0]) CK(cudaMemsetAsync(B.m64[0], 0, sizeof(double2) * E, st));
   if (full && B.m32[0]) CK(cudaMemsetAsync(B.m32[0], 0, sizeof(float2) * E, st));
   if (B.e[0]) CK(cudaMemsetAsync(B.e[0], 0, (is_bf16(h) ? 2 : 4) * E, st));
+  if (B.e32[0]) CK(cudaMemsetAsync(B.e32[0], 0, 4 * E, st));
 }
 
 // The K-column mean messages of the multi right-hand-side solve (colour schedule).
@@ -364,10 +405,17 @@ int launch_mode_init(gabp_handle h, cudaStream_t st, int mode) {
   return launch_init(h->g, st, h->buf, h->ctl, h->red);
 }
 
+// The FP32-storage mean phase of the precision ladder: BF16 handles whose
+// ladder is climbed by the controller (every form but a dense batch under
+// per-system control, whose systems climb inside the sweeps).
+bool ladder_phase(gabp_handle h) {
+  return is_bf16(h) && !(h->dense && h->opt.batch_control == 0);
+}
+
 bool phase_used(int mode, int p) {
   switch (mode) {
     case CTL_FP64: return p == PH_FULL64 || p == PH_CHECK64;
-    case CTL_MIXED: return p == PH_FULL32 || p == PH_MEAN || p == PH_REFINE;
+    case CTL_MIXED: return p == PH_FULL32 || p == PH_MEAN || p == PH_REFINE || p == PH_MEANW;
     case CTL_PREC: return p == PH_FULL32;
     case CTL_MULTI: return p == PH_MEANK || p == PH_REFINEK;
   }
@@ -377,7 +425,7 @@ bool phase_used(int mode, int p) {
 int phase_kind(int phase) {
   switch (phase) {
     case PH_FULL64: case PH_FULL32: return K_FULL;
-    case PH_MEAN: case PH_MEANK: return K_MEAN;
+    case PH_MEAN: case PH_MEANK: case PH_MEANW: return K_MEAN;
     case PH_CHECK64: case PH_REFINE: case PH_REFINEK: return K_RES;
   }
   return K_OTHER;
@@ -420,7 +468,7 @@ void build_solve_graph(gabp_handle h, int mode) {
   CK(cudaGraphAddNode(&snode, body, nullptr, nullptr, 0, &sp));
   for (int p = 0; p < PH_COUNT; ++p) {
     cudaGraph_t pb = sp.conditional.phGraph_out[p];
-    if (!phase_used(mode, p)) {
+    if (!phase_used(mode, p) || (p == PH_MEANW && !ladder_phase(h))) {
       cudaGraphNode_t e;
       CK(cudaGraphAddEmptyNode(&e, pb, nullptr, 0));
       continue;
@@ -476,6 +524,9 @@ void init_ctl(gabp_handle h, int mode, const double *b, double *x, double tol, i
   // near 1e-2 relative change, where the refinement takes over
   c.floor_dd = is_bf16(h) ? 3e-2 : 1e-4;
   c.plateau = is_bf16(h) ? 16 : 0;
+  // BF16 storage climbs to FP32 at the first stalled refinement step
+  c.ladder = is_bf16(h) && mode == CTL_MIXED;
+  c.floor_dd_wide = 1e-4;
   c.prev_dP = std::numeric_limits<double>::infinity();
   c.status = GABP_ERR_NOT_CONVERGED;
 }
@@ -494,6 +545,7 @@ void finish_stats(gabp_handle h) {
   S.n = h->g.n;
   S.edges = h->g.E;
   S.positions_swept = h->dense ? static_cast<int64_t>(c.positions) : 0;
+  S.sweeps_wide = c.sweeps_wide;
 }
 
 // Runs one control mode whose control block has been filled in the pinned
@@ -836,6 +888,7 @@ void release(gabp_handle h) {
   Buffers &B = h->buf;
   cudaFree(B.m64[0]); cudaFree(B.m64[1]);
   cudaFree(B.m32[0]); cudaFree(B.m32[1]); cudaFree(B.e[0]); cudaFree(B.e[1]);
+  cudaFree(B.e32[0]); cudaFree(B.e32[1]);
   cudaFree(B.c32); cudaFree(B.invP32); cudaFree(B.mon32[0]); cudaFree(B.mon32[1]);
   cudaFree(B.tot32[0]); cudaFree(B.tot32[1]);
   cudaFree(B.r64); cudaFree(B.rhs32);
@@ -851,6 +904,7 @@ void release(gabp_handle h) {
     DenseView &v = h->dense->v;
     for (int k = 0; k < 2; ++k) {
       cudaFree(v.M32[k]); cudaFree(v.Mz64[k]); cudaFree(v.Mx64[k]); cudaFree(v.H[k]);
+      cudaFree(v.H32[k]);
       cudaFree(v.sum32[k]); cudaFree(v.sum64[k]); cudaFree(v.sumE[k]);
     }
     cudaFree(v.C32);

@@ -163,20 +163,31 @@ def test_oversized_system_takes_the_csr_path(G):
     G.gabp_destroy(h)
 
 
-def test_bf16_refinement_that_stalls_stops_early(G):
-    """BF16 mean messages on the 10 dB batch: the solve either reaches 1e-10
-    or stops once eight refinement steps in a row fail to shrink the FP64
-    residual by 10 % -- long before the sweep budget.  Damped (gamma 0.3):
-    undamped, one system of this batch does not converge at all, and the
-    erratic residuals of its inner solves can beat the best by 10 % by
-    chance, which is not the stall this test is about."""
+@pytest.mark.parametrize("batch_control", [0, 1])
+def test_bf16_refinement_converges_on_the_10db_batch(G, batch_control):
+    """BF16 mean messages on the 10 dB batch: every system meets 1e-10 and
+    its closed form to 1e-8 (per system, and under one controller for the
+    whole batch).  Where a refinement step fails to shrink a residual by
+    10 %, the precision ladder switches the later inner solves to FP32
+    storage; the count of such sweeps stays below the mean sweeps.  Damped
+    (gamma 0.3): undamped, one system of this batch does not converge."""
     systems = W.detection_batch(40, 16, 130, 10.0, seed=2)
-    h = _handle(G, [(d.S, d.sigma2, d.y) for d in systems], precision=2, damping=0.3)
+    o = G.gabp_default_options()
+    o.precision = 2
+    o.damping = 0.3
+    o.batch_control = batch_control
+    o.stream = G.current_stream_handle()
+    h = G.gabp_create_lsq_batched([d.S for d in systems], [d.sigma2 for d in systems], o)
     y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
     xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
-    try:
-        G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 20000)
-    except G.GabpError as e:
-        assert e.name == "GABP_ERR_NOT_CONVERGED"
-        assert G.gabp_get_stats(h)["sweeps_total"] < 5000
+    G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 20000)
+    st = G.gabp_get_stats(h)
     G.gabp_destroy(h)
+    assert st["status"] == 0
+    got, off = xh.cpu().numpy(), 0
+    for d in systems:
+        A, bb = d.dense_system()
+        closed = np.linalg.solve(A, bb)
+        assert np.abs(got[off:off + d.K] - closed).max() <= 1e-8 * np.abs(closed).max()
+        off += d.K
+    assert st["sweeps_wide"] <= st["sweeps_mean"], st

@@ -145,6 +145,71 @@ def test_grid_solves_match_the_csr_path(G, precision, dims, kw):
         assert sweeps[1] < sweeps[0], sweeps
 
 
+@pytest.fixture(scope="module")
+def poisson32():
+    """3-D Poisson 32^3 (7-point Laplacian), a uniform right-hand side and the
+    oracle's FP64 solution to 1e-13."""
+    dims = [32, 32, 32]
+    m = box_operator(dims, seed=0, laplacian=True)
+    b = W.uniform_rhs(m.n, 5)
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=200000,
+                      tol=1e-13)["x"]
+    return dims, m, b, ref
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_bf16_poisson3d_climbs_the_ladder_to_1e10(G, poisson32, schedule):
+    """BF16 mean storage on 3-D Poisson 32^3 meets 1e-10 and the oracle's
+    solution to 1e-8.  (Here every refinement step still shrinks the
+    residual by 10 %, so the precision ladder need not climb; the climb is
+    tested on a system where BF16 storage stalls.)"""
+    dims, m, b, ref = poisson32
+    s = _solver(G, dims, m, precision=2, schedule=schedule)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=200000)
+    x = xt.cpu().numpy()
+    st = s.stats()
+    s.close()
+    assert st["status"] == 0
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    assert _rel(x, ref) < 1e-8
+    assert st["sweeps_wide"] < st["sweeps_mean"], st
+
+
+def test_bf16_ladder_on_the_csr_path(G, poisson32):
+    """The same ladder on the general CSR handle (tile form of the mean sweep)."""
+    dims, m, b, ref = poisson32
+    s = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=G.PREC_MIXED_BF16)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=200000)
+    x = xt.cpu().numpy()
+    st = s.stats()
+    s.close()
+    assert st["status"] == 0
+    assert _rel(x, ref) < 1e-8
+    assert st["sweeps_wide"] < st["sweeps_mean"], st
+
+
+@pytest.mark.parametrize("dims,schedule", [([64, 64], 0), ([100, 100], 1)])
+def test_bf16_ladder_climbs_where_bf16_storage_stalls(G, dims, schedule):
+    """2-D Laplacians on which BF16 mean storage stalls: a refinement step
+    fails to shrink the residual by 10 %, the handle climbs to FP32 storage
+    for the later inner solves, and the solve meets 1e-10 and the oracle's
+    FP64 solution to 1e-8 (without the ladder it would end NOT_CONVERGED
+    after eight such steps)."""
+    m = box_operator(dims, seed=0, laplacian=True)
+    b = W.uniform_rhs(m.n, 5)
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=400000,
+                      tol=1e-13)["x"]
+    s = _solver(G, dims, m, precision=2, schedule=schedule)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=400000)
+    x = xt.cpu().numpy()
+    st = s.stats()
+    s.close()
+    assert st["status"] == 0
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    assert _rel(x, ref) < 1e-8
+    assert 0 < st["sweeps_wide"] < st["sweeps_mean"], st
+
+
 def test_grid_handle_rejects_message_export_and_solves_columns(G):
     dims = [10, 8]
     m = box_operator(dims, seed=2)
