@@ -76,12 +76,14 @@ BYTES_GRID = {
 TRAFFIC = {
     "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "b04585fc006c2b3e",
              "bytes_per_launch": 171.9e6},
-    "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "b04585fc006c2b3e",
-                       "bytes_per_launch": 202.3e6},
-    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "144478a72aeba38c",
-                   "bytes_per_pair": 23.05},
-    "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "144478a72aeba38c",
-                          "bytes_per_pair": 15.17},
+    "mean_win": {"sources": ("gabp_window.cu", "gabp_device.cuh"), "sha": "bf81306419150e08",
+                 "bytes_per_launch": 122.97e6},
+    "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "19d4d4b12b5ae513",
+                       "bytes_per_launch": 203.5e6},
+    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "0946f7edfb188213",
+                   "bytes_per_pair": 23.15},
+    "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "0946f7edfb188213",
+                          "bytes_per_pair": 15.16},
 }
 
 
