@@ -999,7 +999,7 @@ __device__ __forceinline__ void st1(float *p, float v) { __stcs(p, v); }
 __device__ __forceinline__ void st1(__nv_bfloat16 *p, float v) { __stcs(p, __float2bfloat16_rn(v)); }
 
 
-template <class T, class E1, int Q>
+template <class T, class E1, int Q, bool FZ, bool FI>
 __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__restrict__ Sg,
                                                  T2<T> *__restrict__ mx, T2<T> *__restrict__ mz,
                                                  float2 *__restrict__ C, E1 *__restrict__ hx,
@@ -1011,7 +1011,7 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
   constexpr int U = 8 / Q;   // rows in flight per warp step: U Q loads per lane and array
   const int K = sy.K, N = sy.N, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // damp_x: blend the z -> x^ messages; damp_z: the x^ -> z ones as well
-  const bool first = R.first, freeze = !kF64 && R.freeze;
+  constexpr bool first = FI, freeze = !kF64 && FZ;
   const bool damp_x = R.gam > T(0), damp_z = damp_x && R.damp_all;
   const T gam = R.gam;
   const T aii = static_cast<T>(-sy.psi);
@@ -1049,7 +1049,6 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
         if (av != T(0)) {
           const V xr = tx[r];
           const T dz = xr.x - m[u][q].x;   // P~_r - P_{z_j -> x_r}
-          brk |= bad(dz);
           const T iz = rcp(dz);
           pz[q] = -(av * av) * iz;
           if (freeze) {
@@ -1068,6 +1067,9 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
       }
       sP = group_sum<32>(sP);
       sE = group_sum<32>(sE);
+      // breakdown (a zero or non-finite P~_r - P_{z_j -> x_r} in the row) shows
+      // as a non-finite row sum; the z_j -> x^_r messages' in the column sums
+      brk |= !isfinite(sP) || !isfinite(sE);
       const T TPz = aii + sP, Thz = zr[j] + sE;
       // z_j -> x^_r
 #pragma unroll
@@ -1079,7 +1081,6 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
         T px = T(0), ex = T(0), cx = T(0);
         if (av != T(0)) {
           const T dx = TPz - pz[q];   // P~_j - P_{x_r -> z_j}
-          brk |= bad(dx);
           const T ix = rcp(dx);
           px = -(av * av) * ix;
           if (freeze) {
@@ -1104,6 +1105,8 @@ __device__ __forceinline__ void full_serial_rows(const DenseSys &sy, const T *__
       if (lane == 0) R.put_sum(sy.node0 + sy.K + j, mk2<T>(sP, sE));
     }
   }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) brk |= !isfinite(cP[q].value()) || !isfinite(cE[q].value());
   // this warp's column sums to its own slice (added in warp order later)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -1328,8 +1331,17 @@ dense_full_serial_kernel(DenseView d, Buffers B, Ctl *ctl, DevScalars *red) {
     __syncthreads();
     if (!R.write_msgs) continue;
     by_columns(K, [&](auto q) {
-      full_serial_rows<T, E1, decltype(q)::value>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R,
-                                                  brk);
+      // (the sweep's kind as template flags: the common full sweep carries
+      // neither the freeze's stores nor the first round's zero messages)
+      constexpr int QQ = decltype(q)::value;
+      if (R.freeze && R.first)
+        full_serial_rows<T, E1, QQ, true, true>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R, brk);
+      else if (R.freeze)
+        full_serial_rows<T, E1, QQ, true, false>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R, brk);
+      else if (R.first)
+        full_serial_rows<T, E1, QQ, false, true>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R, brk);
+      else
+        full_serial_rows<T, E1, QQ, false, false>(sy, Sg, mx, mz, d.C32, hx, hz, tx, zr, part, R, brk);
     });
     __syncthreads();
     for (int k = tid; k < K; k += kDenseBlock) {

@@ -191,3 +191,27 @@ def test_bf16_refinement_converges_on_the_10db_batch(G, batch_control):
         assert np.abs(got[off:off + d.K] - closed).max() <= 1e-8 * np.abs(closed).max()
         off += d.K
     assert st["sweeps_wide"] <= st["sweeps_mean"], st
+
+
+@pytest.mark.parametrize("precision,schedule", [(0, 1), (1, 1), (2, 1), (1, 0)])
+def test_dense_breakdown_is_reported(G, precision, schedule):
+    """S = I with psi = 1e-40: in the first round the z node's cavity
+    precision P~_j - P_{x_r -> z_j} = (-psi - 1) - (-1) is zero in FP64 and
+    FP32 (the serial kernels see it as a non-finite row or column sum), and
+    the solve ends with GABP_ERR_BREAKDOWN instead of returning garbage.  The
+    synchronous FP32 round meets -psi as a subnormal instead; its infinite
+    message ends the solve too (breakdown or divergence)."""
+    o = G.gabp_default_options()
+    o.precision = precision
+    o.schedule = schedule
+    o.stream = G.current_stream_handle()
+    h = G.gabp_create_lsq_batched([np.eye(4)], [1e-40], o)
+    y = torch.ones(4, dtype=torch.float64, device="cuda")
+    xh = torch.empty(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 1000)
+    G.gabp_destroy(h)
+    if schedule == 1:
+        assert ei.value.name == "GABP_ERR_BREAKDOWN"
+    else:
+        assert ei.value.name in ("GABP_ERR_BREAKDOWN", "GABP_ERR_DIVERGED")
