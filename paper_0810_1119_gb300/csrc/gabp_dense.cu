@@ -355,7 +355,10 @@ __device__ __forceinline__ int32_t claim_sys(Ctl *ctl, const DenseView &d, bool 
       const int32_t o = d.sys[s].orig;
       if (d.sysctl[o].state == 0) {
         sh.sc = d.sysctl[o];
-        if (sh.sc.sweeps == 0) sh.sc.rn = dv(d.sys_bmax[o]);
+        if (sh.sc.sweeps == 0) {   // the first inner solve of the solve
+          sh.sc.rn = dv(d.sys_bmax[o]);
+          sh.sc.goal = ctl->inner_tol;
+        }
         sh.mode = sh.sc.frozen;
         break;
       }
@@ -404,7 +407,7 @@ __device__ bool sys_rules(SysCtl &sc, const Ctl *ctl, int mode, uint32_t mdd, ui
   const int plateau_n = sc.wide ? 0 : ctl->plateau;
   const bool plateau = plateau_n > 0 && sc.since_best >= plateau_n && dd < floor_dd;
   return mode != 0 && k >= 3 &&
-         (err_d < ctl->inner_goal || (sc.stall >= 2 && dd < floor_dd) || plateau);
+         (err_d < sc.goal || (sc.stall >= 2 && dd < floor_dd) || plateau);
 }
 
 // After the node work of a system (every thread calls it): the system's
@@ -508,7 +511,8 @@ __device__ __forceinline__ void refine_rows(const DenseSys &sy, const double *__
 // measure (a BF16 handle's system first climbs the precision ladder at its
 // first such step: its later inner solves store FP32 mean messages, with a
 // fresh stall budget); otherwise r is kept as the right-hand side of its
-// next inner solve, whose scale is rn_s = max |r| (history reset, k = 0).
+// next inner solve, whose scale is rn_s = max |r| (history reset, k = 0) and
+// whose goal is what the system's stop rule still needs.
 __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, const DenseSys &sy,
                            const Buffers &B, const float2 *mon, double *buf, Tally &t) {
   const int K = sy.K, N = sy.N, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -587,6 +591,9 @@ __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, co
       sc.stall = 0;
       sc.since_best = 0;
       sc.rn = rs;
+      // the next inner solve only has to shrink the residual by the factor
+      // the stop rule still needs (0.3 margin), never more than inner_tol
+      sc.goal = fmax(ctl->inner_tol, 0.3 * ctl->tol / fmax(prog, DBL_MIN));
     }
     if (sc.state != 0) {
       t.rmax = umax(t.rmax, smr);

@@ -345,6 +345,10 @@ struct DenseSys {
 //   k, prev_dd, best_dd, since_best, stall, prev_dP: the inner solve's sweep
 //           count (k = 0: its next sweep is the first of an inner solve) and
 //           the history of the relative changes of d and P~;
+//   goal    the accuracy asked of its current inner solve: inner_tol at
+//           first, then max(inner_tol, 0.3 tol / its stop measure), so that
+//           an inner solve shrinks the residual only by the factor the
+//           system's own stop rule still needs;
 //   outer, best_prog, outer_stall: refinement steps, the smallest stop
 //           measure after one, and steps since it last shrank by 10 %;
 //   wide    BF16 handles: the system's ladder climbed (its first stalled
@@ -353,6 +357,7 @@ struct SysCtl {
   double rn;
   double prev_dd, best_dd, prev_dP;
   double best_prog;
+  double goal;                  // accuracy asked of its current inner solve
   int32_t k, stall, since_best;
   int32_t state, frozen;
   int32_t sweeps;               // message sweeps of this system in the solve
