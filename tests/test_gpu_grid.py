@@ -210,6 +210,30 @@ def test_bf16_ladder_climbs_where_bf16_storage_stalls(G, dims, schedule):
     assert 0 < st["sweeps_wide"] < st["sweeps_mean"], st
 
 
+@pytest.mark.parametrize("dims,kw", [([64, 64], dict(mean_window=-1)),
+                                     ([64, 64], dict(mean_window=1024)),
+                                     ([100, 100], dict(schedule=1))])
+def test_bf16_ladder_climbs_on_the_csr_forms(G, dims, kw):
+    """The same climb on a CSR handle of a 2-D Laplacian: from the tile form
+    or the window form of the BF16 mean sweep to the FP32 tile form (64 x 64),
+    and in the colour schedule (100 x 100: one in-place FP32 buffer after the
+    climb; at 64 x 64 that schedule converges in BF16 without climbing).  The
+    solve meets 1e-10 and the oracle's solution to 1e-8."""
+    m = box_operator(dims, seed=0, laplacian=True)
+    b = W.uniform_rhs(m.n, 5)
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=400000,
+                      tol=1e-13)["x"]
+    s = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=G.PREC_MIXED_BF16, **kw)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=400000)
+    x = xt.cpu().numpy()
+    st = s.stats()
+    s.close()
+    assert st["status"] == 0
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    assert _rel(x, ref) < 1e-8
+    assert 0 < st["sweeps_wide"] < st["sweeps_mean"], st
+
+
 def test_grid_handle_rejects_message_export_and_solves_columns(G):
     dims = [10, 8]
     m = box_operator(dims, seed=2)
