@@ -568,12 +568,13 @@ __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, co
     t.checks++;
     t.outer = max(t.outer, sc.outer);
     int fail = 0;
+    const bool progressed = sc.outer == 1 || prog < 0.9 * sc.best_prog;
     if (prog < ctl->tol) {
       sc.state = 2;
       t.done++;
     } else if (!isfinite(rs) || rs > 1e30 * fmax(bs, DBL_MIN)) {
       fail = GABP_ERR_DIVERGED;
-    } else if (sc.outer == 1 || prog < 0.9 * sc.best_prog) {
+    } else if (progressed) {
       sc.best_prog = prog;
       sc.outer_stall = 0;
     } else if (ctl->ladder && !sc.wide) {   // BF16 storage: climb to FP32 at the first stall
@@ -592,8 +593,11 @@ __device__ void sys_refine(SysShared &sh, const Ctl *ctl, const DenseView &d, co
       sc.since_best = 0;
       sc.rn = rs;
       // the next inner solve only has to shrink the residual by the factor
-      // the stop rule still needs (0.3 margin), never more than inner_tol
-      sc.goal = fmax(ctl->inner_tol, 0.3 * ctl->tol / fmax(prog, DBL_MIN));
+      // the stop rule still needs (0.3 margin; at most 1e-2, never tighter
+      // than inner_tol); after a step that did not shrink the stop measure
+      // by 10 % it takes inner_tol again
+      sc.goal = progressed ? fmin(1e-2, fmax(ctl->inner_tol, 0.3 * ctl->tol / fmax(prog, DBL_MIN)))
+                           : ctl->inner_tol;
     }
     if (sc.state != 0) {
       t.rmax = umax(t.rmax, smr);

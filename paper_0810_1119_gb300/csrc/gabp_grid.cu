@@ -23,8 +23,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 namespace gabp {
@@ -42,8 +44,14 @@ struct GNode {
   unsigned in_box;   // bit d: the neighbour in direction d exists
 };
 
+// n / d for n < 2^31 from the view's multiplier and shift.
+__device__ __forceinline__ uint32_t div_by(uint32_t n, uint64_t m, int s) {
+  return static_cast<uint32_t>((static_cast<uint64_t>(n) * m) >> s);
+}
+
 // The box holds fewer than 2^31 nodes, so the coordinates come from 32-bit
-// arithmetic (two 32-bit divisions per node; the class is a comparison).
+// arithmetic: the two divisions per node are multiplications by the
+// precomputed reciprocals (the class is a comparison).
 __device__ __forceinline__ bool node_of(const GridView &g, int64_t t, GNode &n) {
   const int64_t count = g.pass < 0 ? 2 * g.Nh : g.Nh;
   if (t >= count) return false;
@@ -51,7 +59,7 @@ __device__ __forceinline__ bool node_of(const GridView &g, int64_t t, GNode &n) 
   n.c = n.slot >= g.Nh ? 1 : 0;
   n.H = n.slot - n.c * g.Nh;
   const uint32_t H = static_cast<uint32_t>(n.H), h0 = static_cast<uint32_t>(g.h0);
-  const uint32_t row = H / h0, z32 = row / static_cast<uint32_t>(g.p1);
+  const uint32_t row = div_by(H, g.m_h0, g.s_h0), z32 = div_by(row, g.m_p1, g.s_p1);
   const int hx = static_cast<int>(H - row * h0);
   const int z = static_cast<int>(z32), y = static_cast<int>(row - z32 * static_cast<uint32_t>(g.p1));
   n.s = (n.c + y + z) & 1;
@@ -96,6 +104,26 @@ __device__ __forceinline__ int64_t slot_of(const GridView &g, const GNode &n, in
 
 int64_t grid_blocks(int64_t count) {
   return std::max<int64_t>(1, (count + kGridBlock - 1) / kGridBlock);
+}
+
+// CTAs of a kernel resident on the device, cached per kernel (primed at
+// create time, before any graph is recorded): the grid-stride launches take
+// at most this many.
+std::mutex g_res_mu;
+std::unordered_map<const void *, int64_t> g_res_blocks;
+
+template <class Kern>
+int64_t resident_grid_blocks(Kern kernel) {
+  std::lock_guard<std::mutex> lk(g_res_mu);
+  auto it = g_res_blocks.find(reinterpret_cast<const void *>(kernel));
+  if (it != g_res_blocks.end()) return it->second;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kGridBlock, 0);
+  const int64_t r = static_cast<int64_t>(std::max(sms, 1)) * std::max(per_sm, 1);
+  g_res_blocks[reinterpret_cast<const void *>(kernel)] = r;
+  return r;
 }
 int64_t launch_count(const GridView &v) { return v.pass < 0 ? 2 * v.Nh : v.Nh; }
 
@@ -259,7 +287,10 @@ grid_mean_kernel(GridView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const float gam = g.no_damp ? 0.f : static_cast<float>(ctl->damping);
   uint32_t mdd = 0, md = 0;
   GNode n;
-  if (node_of(g, blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x, n)) {
+  // nodes grid-stride (the grid is at most the resident CTAs), so that every
+  // block reduces its monitors once
+  for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; node_of(g, t, n);
+       t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     // every load of the node first (incoming messages, coefficients, node data)
     float e[kMaxDir], cf[kMaxDir];
 #pragma unroll
@@ -337,8 +368,13 @@ int launch_grid_full32(const GridView &v, cudaStream_t st, Buffers B, Ctl *ctl, 
 
 int launch_grid_mean(const GridView &v, cudaStream_t st, Buffers B, Ctl *ctl, DevScalars *red,
                      bool bf16) {
-  if (bf16) grid_mean_kernel<__nv_bfloat16><<<grid_blocks(launch_count(v)), kGridBlock, 0, st>>>(v, B, ctl, red);
-  else grid_mean_kernel<float><<<grid_blocks(launch_count(v)), kGridBlock, 0, st>>>(v, B, ctl, red);
+  if (bf16) {
+    auto k = grid_mean_kernel<__nv_bfloat16>;
+    k<<<std::min<int64_t>(grid_blocks(launch_count(v)), resident_grid_blocks(k)), kGridBlock, 0, st>>>(v, B, ctl, red);
+  } else {
+    auto k = grid_mean_kernel<float>;
+    k<<<std::min<int64_t>(grid_blocks(launch_count(v)), resident_grid_blocks(k)), kGridBlock, 0, st>>>(v, B, ctl, red);
+  }
   return 1;
 }
 
@@ -474,6 +510,19 @@ gabp_status build_grid(Grid &G, int32_t ndim, const int32_t *dims, int64_t nnz,
   v.h0 = static_cast<int32_t>(h0);
   v.p1 = static_cast<int32_t>(p[1]);
   v.p2 = static_cast<int32_t>(p[2]);
+  // multiplier and shift for n / d, 0 <= n < 2^31: with l = ceil(log2 d) and
+  // m = ceil(2^(31 + l) / d), m d - 2^(31 + l) < d <= 2^l, which makes
+  // floor(n m / 2^(31 + l)) = floor(n / d) (Granlund and Montgomery, Thm 4.2)
+  auto magic = [](uint64_t d, uint64_t *m, int32_t *s) {
+    int l = 0;
+    while ((uint64_t{1} << l) < d) ++l;
+    *s = 31 + l;
+    *m = ((uint64_t{1} << (31 + l)) + d - 1) / d;
+  };
+  magic(static_cast<uint64_t>(h0), &v.m_h0, &v.s_h0);
+  magic(static_cast<uint64_t>(p[1]), &v.m_p1, &v.s_p1);
+  resident_grid_blocks(grid_mean_kernel<float>);
+  resident_grid_blocks(grid_mean_kernel<__nv_bfloat16>);
   v.Nh = Nh;
   v.a64 = G.a64;
   v.diag64 = G.diag64;

@@ -346,9 +346,10 @@ struct DenseSys {
 //           count (k = 0: its next sweep is the first of an inner solve) and
 //           the history of the relative changes of d and P~;
 //   goal    the accuracy asked of its current inner solve: inner_tol at
-//           first, then max(inner_tol, 0.3 tol / its stop measure), so that
-//           an inner solve shrinks the residual only by the factor the
-//           system's own stop rule still needs;
+//           first, then min(1e-2, max(inner_tol, 0.3 tol / its stop
+//           measure)), so that an inner solve shrinks the residual only by
+//           the factor the system's own stop rule still needs (inner_tol
+//           again after a step without a 10 % gain);
 //   outer, best_prog, outer_stall: refinement steps, the smallest stop
 //           measure after one, and steps since it last shrank by 10 %;
 //   wide    BF16 handles: the system's ladder climbed (its first stalled
@@ -431,6 +432,10 @@ void prepare_dense_kernels(bool bf16);
 struct GridView {
   int32_t ndim, D;                 // axes, directions (2 ndim)
   int32_t h0, p1, p2;              // half-row length, dims[1], dims[2]
+  // n / h0 and n / p1 for n < 2^31 as (n * m) >> s (division by an invariant
+  // integer through multiplication, Granlund and Montgomery 1994)
+  uint64_t m_h0, m_p1;
+  int32_t s_h0, s_p1;
   int64_t Nh;                      // nodes per class
   const double *a64, *diag64;      // [2 D Nh], [2 Nh]
   const float *a32, *diag32;
