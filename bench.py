@@ -874,8 +874,12 @@ def run_detect(args):
     h1, t1, _ = timed(1, max(1, min(args.steps, 3)), 1)
     st1 = gabp.gabp_get_stats(h1)
     gabp.gabp_set_profile(h1, True)
-    gabp.gabp_solve_lsq_batched(h1, y, xh, TOL, max_iter)
-    sp = gabp.gabp_get_stats(h1)
+    sp = None
+    for _ in range(2):   # events around host-driven launches absorb host delays: keep the faster pass
+        gabp.gabp_solve_lsq_batched(h1, y, xh, TOL, max_iter)
+        s2 = gabp.gabp_get_stats(h1)
+        if sp is None or s2["ms_mean"] < sp["ms_mean"]:
+            sp = s2
     gabp.gabp_destroy(h1)
     hbm, peak_src = _peaks()
     pairs = E // 2
