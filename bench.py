@@ -80,9 +80,9 @@ TRAFFIC = {
                  "bytes_per_launch": 122.97e6},
     "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "19d4d4b12b5ae513",
                        "bytes_per_launch": 203.5e6},
-    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "c0e5a00402fb5cac",
+    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "80b831a3cc8ac8ef",
                    "bytes_per_pair": 23.15},
-    "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "c0e5a00402fb5cac",
+    "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "80b831a3cc8ac8ef",
                           "bytes_per_pair": 15.16},
 }
 

@@ -141,7 +141,6 @@ struct FullRound {
   float *__restrict__ sumE_out;   // freeze: sums of the first mean messages
   const float2 *__restrict__ mon_prev;
   float2 *__restrict__ mon_out;
-  float2 *mon_keep;               // mon_prev's buffer (a system whose inner solve ends keeps d there)
   uint32_t mdd = 0, md = 0, mdP = 0, mP = 0;       // maxima over the CTA's systems
   uint32_t smdd = 0, smd = 0, smdP = 0, smP = 0;   // maxima over the current system
 
@@ -173,7 +172,6 @@ struct FullRound {
     sumE_out = pe ? d.sumE[0] : d.sumE[1];
     mon_prev = pmon ? B.mon32[1] : B.mon32[0];
     mon_out = pmon ? B.mon32[0] : B.mon32[1];
-    mon_keep = pmon ? B.mon32[1] : B.mon32[0];
   }
 
   // The current system's maxima into the CTA's.
@@ -240,7 +238,6 @@ struct MeanRound {
   float *__restrict__ sum_out;
   const float2 *__restrict__ mon_prev;
   float2 *__restrict__ mon_out;
-  float2 *mon_keep;               // mon_prev's buffer (a system whose inner solve ends keeps d there)
   uint32_t mdd = 0, md = 0;       // maxima over the CTA's systems
   uint32_t smdd = 0, smd = 0, smdP = 0, smP = 0;   // over the current system (no P~ here)
 
@@ -254,7 +251,6 @@ struct MeanRound {
     sum_out = pe ? d.sumE[0] : d.sumE[1];
     mon_prev = pmon ? B.mon32[1] : B.mon32[0];
     mon_out = pmon ? B.mon32[0] : B.mon32[1];
-    mon_keep = pmon ? B.mon32[1] : B.mon32[0];
   }
 
   __device__ __forceinline__ void fold() {

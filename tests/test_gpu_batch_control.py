@@ -152,3 +152,27 @@ def test_host_driven_solve_matches_the_graph(G):
     assert np.array_equal(xg, xp)
     assert np.array_equal(swg, swp)
     assert stg["positions_swept"] == stp["positions_swept"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_max_iter_ends_the_batch_cleanly(G, precision):
+    """A sweep budget below what the slowest systems need: the solve ends
+    GABP_ERR_NOT_CONVERGED at max_iter sweeps, the handle stays usable, and
+    a full solve on it afterwards meets every closed form."""
+    systems = _mixed_batch()
+    o = _opts(G, precision, 0, 0)
+    h = G.gabp_create_lsq_batched([d.S for d in systems], [d.sigma2 for d in systems], o)
+    y = torch.tensor(np.concatenate([d.y for d in systems]), device="cuda")
+    xh = torch.empty(sum(d.K for d in systems), dtype=torch.float64, device="cuda")
+    with pytest.raises(G.GabpError) as ei:
+        G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 12)
+    assert ei.value.name == "GABP_ERR_NOT_CONVERGED"
+    st = G.gabp_get_stats(h)
+    assert st["sweeps_total"] == 12
+    assert np.all(G.gabp_get_system_sweeps(h, len(systems)) <= 12)
+    G.gabp_solve_lsq_batched(h, y, xh, 1e-10, 50000)
+    for d, xs in zip(systems, _split(xh.cpu().numpy(), systems)):
+        A, b = d.dense_system()
+        closed = np.linalg.solve(A, b)
+        assert np.abs(xs - closed).max() <= 1e-8 * np.abs(closed).max()
+    G.gabp_destroy(h)
