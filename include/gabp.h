@@ -154,10 +154,11 @@ typedef struct {
                              window form needs the synchronous schedule. */
   int32_t batch_control;  /* gabp_create_lsq_batched in the dense form, mixed and FP64 solves:
                              0 = per system: each system freezes its precisions, ends its
-                             inner solves and scales its refinement on its own numbers, and
-                             drops out of the sweeps, the refinement and the rules once it
-                             meets the stop rule -- so a system takes the same sweeps, and
-                             its x^ the same bits, in a batch as when it is solved alone;
+                             inner solves (asking only the accuracy its own stop rule still
+                             needs) and takes its refinement step on its own numbers, inside
+                             the sweep that ends the inner solve, and drops out of the sweeps
+                             once it meets the stop rule -- so a system takes the same sweeps,
+                             and its x^ the same bits, in a batch as when it is solved alone;
                              1 = one controller for the whole batch (its maxima decide the
                              freeze and the end of each inner solve, and every system sweeps
                              until the last one is done). */
@@ -184,8 +185,9 @@ typedef struct {
   double ms_other;          /* norms, scaling, refinement updates */
   int64_t positions_swept;  /* dense Section VII batches: grid positions (edge pairs) that the
                                solve's sweeps processed, summed over the sweeps (with per-system
-                               control a system that is done, or waits for the next refinement
-                               step, adds none); 0 for the other forms */
+                               control a system that is done adds none, and the sweep that ends
+                               a system's inner solve skips its grid pass); 0 for the other
+                               forms */
   int32_t sweeps_wide;      /* MIXED_BF16: mean-only sweeps that stored FP32 mean messages
                                after the precision ladder climbed (dense batch under
                                per-system control: sweeps in which some system had climbed) */
