@@ -167,3 +167,60 @@ def test_pinv_pins_catch_mutant(name):
     old, new = PINV_MUTANTS[name]
     assert src.count(old) == 1, name
     assert not _pinv_pins_hold(_pinv_namespace(src.replace(old, new)))
+
+
+# Steffensen's iteration in residual form (oracle.steffensen_residual): the
+# same kind of mistakes planted in its Python source, checked against the
+# facts test_oracle_pins.py pins it to (the LAPACK solution of 2D Poisson,
+# at least 1000 x below plain refinement with the same rounds, and one-step
+# exactness on a chain).
+STEFFENSEN_MUTANTS = {
+    "update_sign": ("x = x + y", "x = x - y"),
+    "correction_replaces_x": ("x = x + y", "x = y"),
+    "residual_sign": ("r = b - A @ x", "r = A @ x - b"),
+    "no_extrapolation": ("y = aitken(*ds)", "y = ds[-1]"),
+    "oldest_iterate": ("y = aitken(*ds)", "y = ds[0]"),
+}
+
+
+def _steffensen_pins_hold(fn) -> bool:
+    try:
+        m = W.poisson2d(10)
+        b = W.uniform_rhs(m.n, 0)
+        A = np.zeros((m.n, m.n))
+        for i in range(m.n):
+            A[i, m.col[m.row_ptr[i]:m.row_ptr[i + 1]]] = m.val[m.row_ptr[i]:m.row_ptr[i + 1]]
+        ref = np.linalg.solve(A, b)
+        xs, hs = fn(m.row_ptr, m.col, m.val, b, inner_rounds=32, spacing=2, outer_steps=6)
+        _, hp = fn(m.row_ptr, m.col, m.val, b, inner_rounds=32, spacing=0, outer_steps=6)
+        if not (np.abs(xs - ref).max() <= 1e-11 * np.abs(ref).max() and hs[-1] <= 1e-3 * hp[-1]):
+            return False
+        rng = np.random.default_rng(9)
+        n = 12
+        off = -(0.2 + rng.random(n - 1))
+        T = np.diag(2.5 + rng.random(n)) + np.diag(off, 1) + np.diag(off, -1)
+        bt = rng.standard_normal(n)
+        mt = W.csr_from_dense(T)
+        x, _ = fn(mt.row_ptr, mt.col, mt.val, bt, inner_rounds=n + 1, spacing=1, outer_steps=1)
+        return np.abs(x - np.linalg.solve(T, bt)).max() <= 1e-13 * np.abs(x).max()
+    except Exception:   # a mutant that does not even run is caught too
+        return False
+
+
+def _steffensen_variant(src):
+    ns = dict(oracle.__dict__)
+    exec(compile(src, "steffensen_mutant.py", "exec"), ns)
+    return ns["steffensen_residual"]
+
+
+def test_steffensen_pins_hold_for_the_oracle():
+    assert _steffensen_pins_hold(oracle.steffensen_residual)
+
+
+@pytest.mark.parametrize("name", sorted(STEFFENSEN_MUTANTS))
+def test_steffensen_pins_catch_mutant(name):
+    import inspect
+    src = inspect.getsource(oracle.steffensen_residual)
+    old, new = STEFFENSEN_MUTANTS[name]
+    assert src.count(old) == 1, name
+    assert not _steffensen_pins_hold(_steffensen_variant(src.replace(old, new)))
