@@ -107,7 +107,18 @@ typedef struct {
                              and the returned x use the extrapolated means.  On grid
                              (bipartite) graphs the synchronous schedule's error flips sign
                              every round: s = 2 accelerates there, s = 1 does not.
-                             0 = off (dense Section VII handles: always off) */
+                             Mixed solves with one right-hand side on CSR and grid handles
+                             (any aitken > 0): each inner solve's means d are recorded every
+                             2^j sweeps (j = 6..12) and the refinement step uses d
+                             extrapolated by Delta^2 from the widest spacing s with 6 s <=
+                             the inner solve's sweeps (no extrapolation after an
+                             extrapolated step that failed to shrink the residual by 10 %);
+                             the next inner solve then restarts GaBP from the extrapolated
+                             solution (Steffensen's iteration, Section IV-A, in residual
+                             form).  It holds 21 FP32 values per node; on CSR handles one
+                             small extra launch follows every mean sweep.
+                             0 = off (dense Section VII handles and multi right-hand-side
+                             solves: always off) */
   int32_t schedule;       /* 0 = synchronous (the parallel schedule of Section III-C, two message
                              buffers); 1 = colour-serial: rows are coloured greedily in the
                              caller's order (no two neighbours share a colour) and every sweep
@@ -191,7 +202,8 @@ typedef struct {
   int32_t sweeps_wide;      /* MIXED_BF16: mean-only sweeps that stored FP32 mean messages
                                after the precision ladder climbed (dense batch under
                                per-system control: sweeps in which some system had climbed) */
-  int32_t reserved_i;
+  int32_t aitken_steps;     /* mixed solves with aitken > 0: refinement steps that used
+                               the extrapolated means */
 } gabp_stats;
 
 /* Fills *opt with the defaults: FP64, relative residual, automatic check

@@ -160,6 +160,14 @@ __device__ bool diverged(double rn, double bnorm) {
   return !isfinite(rn) || rn > 1e30 * fmax(bnorm, DBL_MIN);
 }
 
+// Phase of the next mean-only sweep, number c.k + 1 of the inner solve: FP32
+// storage once the ladder climbed, and the Aitken records after sweeps 64,
+// 128, ... where a kernel of their own takes them (CSR handles).
+__device__ __forceinline__ int mean_phase(const Ctl &c) {
+  const bool rec = c.ait_rec && ((c.k + 1) & ((1 << kAitMinLevel) - 1)) == 0;
+  return c.wide ? (rec ? PH_MEANWR : PH_MEANW) : (rec ? PH_MEANR : PH_MEAN);
+}
+
 // Reductions are read through volatile loads (they were committed by other
 // blocks' atomics) and zeroed once consumed.
 __device__ void control(Ctl &c, DevScalars *red, int kind) {
@@ -258,6 +266,12 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
           break;
         }
       }
+      // Aitken on the mixed inner solves: after an extrapolated step that
+      // did not shrink the residual by 10 %, the next step goes without
+      if (c.ait_mixed) {
+        c.ait_ok = !c.ait_use || rn < 0.9 * c.rn;
+        c.ait_use = 0;
+      }
       // next refinement step: solve A d = r / ||r|| from zero mean messages.
       // One system: the inner solve only has to shrink the residual by the
       // factor the stop rule still needs (0.3 margin), never more than
@@ -275,7 +289,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       c.since_best = 0;
       c.prev_dP = INFINITY;
       c.first = 1;
-      c.phase = c.frozen ? (c.wide ? PH_MEANW : PH_MEAN) : PH_FULL32;
+      c.phase = c.frozen ? mean_phase(c) : PH_FULL32;
       break;
     }
     case CK_SWEEP32:
@@ -358,8 +372,25 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       const bool plateau = c.plateau > 0 && c.since_best >= c.plateau && dd < c.floor_dd;
       const bool inner_done = c.frozen && c.k >= 3 &&
                               (err_d < c.inner_goal || (c.stall >= 2 && dd < c.floor_dd) || plateau);
-      if (inner_done || c.sweeps >= c.max_iter) c.phase = PH_REFINE;
-      else c.phase = c.frozen ? (c.wide ? PH_MEANW : PH_MEAN) : PH_FULL32;
+      if (inner_done || c.sweeps >= c.max_iter) {
+        c.phase = PH_REFINE;
+        if (c.ait_mixed) {
+          // Aitken on the inner solve's means: the widest record spacing s
+          // with 6 s <= k (three records, the oldest past the first sixth)
+          int sel = -1;
+          for (int j = kAitLevels - 1; j >= 0; --j) {
+            const int s = 1 << (kAitMinLevel + j);
+            if (6 * s <= c.k) { sel = j; break; }
+          }
+          c.ait_level = sel;
+          c.ait_m = sel >= 0 ? c.k >> (kAitMinLevel + sel) : 0;
+          c.ait_use = sel >= 0 && c.ait_ok;
+          c.ait_steps += c.ait_use;
+          c.ait_md = mx;
+        }
+      } else {
+        c.phase = c.frozen ? mean_phase(c) : PH_FULL32;
+      }
       break;
     }
     case CK_INITK: {

@@ -285,6 +285,11 @@ grid_mean_kernel(GridView g, Buffers B, Ctl *ctl, DevScalars *red) {
   const float2 *__restrict__ mon_prev = pmon ? B.mon32[1] : B.mon32[0];
   float2 *__restrict__ mon_out = pmon ? B.mon32[0] : B.mon32[1];
   const float gam = g.no_damp ? 0.f : static_cast<float>(ctl->damping);
+  // Aitken on the inner solves (mixed solves with aitken > 0): this sweep is
+  // number kk of its inner solve; at multiples of 2^j it records d in slot
+  // (kk >> j) mod 3 of level j
+  const int kk = ctl->k + 1;
+  const bool rec = ctl->ait_mixed != 0 && (kk & ((1 << kAitMinLevel) - 1)) == 0;
   uint32_t mdd = 0, md = 0;
   GNode n;
   // nodes grid-stride (the grid is at most the resident CTAs), so that every
@@ -313,6 +318,15 @@ grid_mean_kernel(GridView g, Buffers B, Ctl *ctl, DevScalars *red) {
     mdd = fmax_bits(mdd, di - prev);
     md = fmax_bits(md, di);
     if (first) B.rhs32[n.slot] = rhs;
+    if (rec) {
+      const int64_t slots = 2 * g.Nh;
+#pragma unroll 1
+      for (int j = 0; j < kAitLevels; ++j) {
+        const int lvl = kAitMinLevel + j;
+        if (kk & ((1 << lvl) - 1)) break;   // not a multiple of 2^lvl: nor of the wider ones
+        B.ait32[(static_cast<int64_t>(j) * 3 + (kk >> lvl) % 3) * slots + n.slot] = di;
+      }
+    }
 #pragma unroll
     for (int d = 0; d < kMaxDir; ++d) {
       const float cc = cf[d];

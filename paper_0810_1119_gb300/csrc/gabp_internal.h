@@ -59,7 +59,9 @@ enum Phase : int {
   PH_MEANK = 5,     // mean-only sweep of K right-hand sides at once
   PH_REFINEK = 6,   // X += ||r_k|| D, R = B - A X for K columns
   PH_MEANW = 7,     // mean-only sweep in FP32 storage once a BF16 handle's ladder climbed
-  PH_COUNT = 8,
+  PH_MEANR = 8,     // PH_MEAN, then the Aitken records of the sweep (CSR handles)
+  PH_MEANWR = 9,    // PH_MEANW, then the Aitken records of the sweep (CSR handles)
+  PH_COUNT = 10,
   PH_DONE = 15
 };
 
@@ -111,6 +113,18 @@ struct Ctl {
   // sweep in which some system (per-system control) stored FP32 messages.
   int ladder, wide, sweeps_wide, wide_now;
   double floor_dd_wide;
+  // Mixed solves with Aitken (ait_mixed = 1; grid and CSR handles, one
+  // right-hand side): the mean sweeps record d every 2^j sweeps
+  // (j = kAitMinLevel ...) of an inner solve, the last three records per
+  // level; at the end of an inner solve of k sweeps the controller picks the
+  // widest spacing s with 6 s <= k (level ait_level, m = k / s records), and
+  // the refinement update extrapolates the last three (ait_use) unless the
+  // last extrapolated step failed to shrink the residual by 10 % (ait_ok = 0).
+  // ait_md: max |d| of the last sweep.
+  // ait_rec: the records are taken by a kernel of their own (CSR handles),
+  // so the controller picks PH_MEANR / PH_MEANWR for sweeps 64, 128, ...
+  int ait_mixed, ait_rec, ait_use, ait_level, ait_m, ait_ok, ait_steps;
+  double ait_md;
   double best_rn;               // smallest FP64 residual of the refinement so far
   int outer_stall;              // refinement steps since best_rn last halved
   double bnorm, thr, rn, inv_rn, residual;
@@ -148,6 +162,7 @@ struct Buffers {
   float2 *m32[2];
   void *e[2];               // mean messages: float or bf16 (per precision mode)
   void *e32[2];             // BF16 handles: FP32 mean messages once the ladder climbs
+  float *ait32;             // mixed solves with Aitken: kAitLevels x 3 records of d (n each)
   float *c32;               // frozen coefficients c_ij (slot s of row i)
   float *invP32;            // frozen 1/P~_i
   float2 *mon32[2];         // (P~_i, d_i) of the last two sweeps
@@ -367,6 +382,10 @@ struct SysCtl {
   int32_t pad;
 };
 
+// Aitken records of the mixed grid solves: spacings 2^6 ... 2^12 sweeps.
+constexpr int kAitMinLevel = 6;
+constexpr int kAitLevels = 7;
+
 constexpr int kDenseMaxK = 256;    // largest K_s (and N_s) the dense kernels take
 constexpr int kDenseMaxN = 1024;
 
@@ -417,6 +436,7 @@ int launch_dense_mean(const Dense &d, cudaStream_t st, Buffers B, Ctl *ctl, DevS
 int launch_dense_residual(const Dense &d, cudaStream_t st, double *r_out, Ctl *ctl,
                           DevScalars *red, bool refine);
 int launch_refine_update(int32_t n, cudaStream_t st, Buffers B, Ctl *ctl);
+int launch_ait_record(int32_t n, cudaStream_t st, Buffers B, const Ctl *ctl);
 int launch_aitken(int32_t n, cudaStream_t st, Ctl *ctl, double *out);
 void prepare_dense_kernels(bool bf16);
 

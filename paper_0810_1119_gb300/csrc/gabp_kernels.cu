@@ -830,14 +830,59 @@ __global__ void __launch_bounds__(kBlock) aitken_kernel(int32_t n, const Ctl *ct
   }
 }
 
-// x_i += ||r|| d_i (FP64), d_i from the latest monitor.
+// x_i += ||r|| d_i (FP64), d_i from the latest monitor.  With Aitken on a
+// mixed grid solve (ait_use), d_i is extrapolated from the inner solve's last
+// three records y0, y1, y2 at spacing 2^level (Section IV-A):
+//     d_i = y2 - (y2 - y1)^2 / (y2 - 2 y1 + y0),
+// except where the second difference is at FP32 rounding level
+// (|y2 - 2 y1 + y0| <= 64 eps max |d|), which keeps the latest d_i.
+// Records of an inner solve's means for Aitken on mixed solves (CSR forms;
+// the grid mean sweep records its own).  The controller runs the mean sweeps
+// 64, 128, ... of an inner solve as phases that add this kernel behind the
+// sweep and its control step, so ctl->k counts the sweep and par_mon names
+// the monitor buffer it wrote.  Each node's mean d_i goes to the ring of
+// every spacing 2^j (j = 6..12) that divides k, at slot (k / 2^j) mod 3.
+__global__ void __launch_bounds__(kBlock) ait_record_kernel(int32_t n, Buffers B, const Ctl *ctl) {
+  const int k = ctl->k;
+  if (!ctl->ait_mixed || k <= 0 || (k & ((1 << kAitMinLevel) - 1)) != 0) return;
+  const float2 *__restrict__ mon = ctl->par_mon ? B.mon32[1] : B.mon32[0];
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float d = mon[i].y;
+    for (int j = 0; j < kAitLevels; ++j) {
+      const int lvl = kAitMinLevel + j;
+      if (k & ((1 << lvl) - 1)) break;
+      B.ait32[(static_cast<int64_t>(j) * 3 + (k >> lvl) % 3) * n + i] = d;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) refine_update_kernel(int32_t n, Buffers B, Ctl *ctl) {
   double *x = ctl->x;
   const double rn = ctl->rn;
   const float2 *mon = (ctl->par_mon ? B.mon32[1] : B.mon32[0]);
+  const bool ait = ctl->ait_use != 0;
+  const float *R = nullptr;
+  int64_t o0 = 0, o1 = 0, o2 = 0;
+  double floor_d2 = 0.0;
+  if (ait) {
+    const int m = ctl->ait_m;
+    R = B.ait32 + static_cast<int64_t>(ctl->ait_level) * 3 * n;
+    o2 = static_cast<int64_t>(m % 3) * n;
+    o1 = static_cast<int64_t>((m - 1) % 3) * n;
+    o0 = static_cast<int64_t>((m - 2) % 3) * n;
+    floor_d2 = 64.0 * FLT_EPSILON * ctl->ait_md;
+  }
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-    x[i] += static_cast<double>(mon[i].y) * rn;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double di = static_cast<double>(mon[i].y);
+    if (ait) {
+      const double y0 = R[o0 + i], y1 = R[o1 + i], y2 = R[o2 + i];
+      const double d2 = y2 - 2.0 * y1 + y0;
+      if (fabs(d2) > floor_d2) di = y2 - (y2 - y1) * (y2 - y1) / d2;
+    }
+    x[i] += di * rn;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1401,6 +1446,11 @@ int launch_check64(const Graph &g, cudaStream_t st, Buffers B, Ctl *ctl, DevScal
 
 int launch_aitken(int32_t n, cudaStream_t st, Ctl *ctl, double *out) {
   aitken_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, ctl, out);
+  return 1;
+}
+
+int launch_ait_record(int32_t n, cudaStream_t st, Buffers B, const Ctl *ctl) {
+  ait_record_kernel<<<flat_grid(n), kBlock, 0, st>>>(n, B, ctl);
   return 1;
 }
 

@@ -167,6 +167,7 @@ void ensure_grid32(gabp_handle h) {
     }
   }
   ensure(&B.c32, M);
+  if (h->opt.aitken > 0) ensure(&B.ait32, static_cast<size_t>(kAitLevels) * 3 * n);
   ensure(&B.invP32, n);
   ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
   ensure(&B.r64, n);
@@ -207,6 +208,7 @@ void ensure32(gabp_handle h) {
     }
   }
   ensure(&B.c32, E);
+  if (h->opt.aitken > 0) ensure(&B.ait32, static_cast<size_t>(kAitLevels) * 3 * n);
   ensure(&B.invP32, n);
   ensure(&B.mon32[0], n); ensure(&B.mon32[1], n);
   ensure(&B.tot32[0], n); ensure(&B.tot32[1], n);
@@ -319,6 +321,9 @@ int launch_phase(gabp_handle h, cudaStream_t st, int phase) {
     }
     return 0;
   }
+  if (phase == PH_MEANR || phase == PH_MEANWR)   // the sweep, then its Aitken records
+    return launch_phase(h, st, phase == PH_MEANR ? PH_MEAN : PH_MEANW) +
+           launch_ait_record(g.n, st, h->buf, h->ctl);
   if (g.ncol > 0 && (phase == PH_FULL64 || phase == PH_FULL32 || phase == PH_MEAN ||
                     phase == PH_MEANK || phase == PH_MEANW)) {
     // colour schedule: one in-place pass per class (both parities alias one buffer)
@@ -412,10 +417,19 @@ bool ladder_phase(gabp_handle h) {
   return is_bf16(h) && !(h->dense && h->opt.batch_control == 0);
 }
 
+// The mean phases followed by the Aitken records: CSR handles of mixed
+// solves with aitken > 0 (grid mean sweeps take their records themselves;
+// dense handles have none).
+bool ait_record_phase(gabp_handle h) {
+  return !h->dense && !h->grid && h->buf.ait32 != nullptr;
+}
+
 bool phase_used(int mode, int p) {
   switch (mode) {
     case CTL_FP64: return p == PH_FULL64 || p == PH_CHECK64;
-    case CTL_MIXED: return p == PH_FULL32 || p == PH_MEAN || p == PH_REFINE || p == PH_MEANW;
+    case CTL_MIXED:
+      return p == PH_FULL32 || p == PH_MEAN || p == PH_REFINE || p == PH_MEANW || p == PH_MEANR ||
+             p == PH_MEANWR;
     case CTL_PREC: return p == PH_FULL32;
     case CTL_MULTI: return p == PH_MEANK || p == PH_REFINEK;
   }
@@ -425,7 +439,7 @@ bool phase_used(int mode, int p) {
 int phase_kind(int phase) {
   switch (phase) {
     case PH_FULL64: case PH_FULL32: return K_FULL;
-    case PH_MEAN: case PH_MEANK: case PH_MEANW: return K_MEAN;
+    case PH_MEAN: case PH_MEANK: case PH_MEANW: case PH_MEANR: case PH_MEANWR: return K_MEAN;
     case PH_CHECK64: case PH_REFINE: case PH_REFINEK: return K_RES;
   }
   return K_OTHER;
@@ -468,7 +482,8 @@ void build_solve_graph(gabp_handle h, int mode) {
   CK(cudaGraphAddNode(&snode, body, nullptr, nullptr, 0, &sp));
   for (int p = 0; p < PH_COUNT; ++p) {
     cudaGraph_t pb = sp.conditional.phGraph_out[p];
-    if (!phase_used(mode, p) || (p == PH_MEANW && !ladder_phase(h))) {
+    if (!phase_used(mode, p) || ((p == PH_MEANW || p == PH_MEANWR) && !ladder_phase(h)) ||
+        ((p == PH_MEANR || p == PH_MEANWR) && !ait_record_phase(h))) {
       cudaGraphNode_t e;
       CK(cudaGraphAddEmptyNode(&e, pb, nullptr, 0));
       continue;
@@ -527,6 +542,10 @@ void init_ctl(gabp_handle h, int mode, const double *b, double *x, double tol, i
   // BF16 storage climbs to FP32 at the first stalled refinement step
   c.ladder = is_bf16(h) && mode == CTL_MIXED;
   c.floor_dd_wide = 1e-4;
+  // Aitken on the inner solves of mixed grid solves
+  c.ait_mixed = mode == CTL_MIXED && h->opt.aitken > 0 && h->buf.ait32 != nullptr;
+  c.ait_rec = c.ait_mixed && ait_record_phase(h);
+  c.ait_ok = 1;
   c.prev_dP = std::numeric_limits<double>::infinity();
   c.status = GABP_ERR_NOT_CONVERGED;
 }
@@ -546,6 +565,7 @@ void finish_stats(gabp_handle h) {
   S.edges = h->g.E;
   S.positions_swept = h->dense ? static_cast<int64_t>(c.positions) : 0;
   S.sweeps_wide = c.sweeps_wide;
+  S.aitken_steps = c.ait_steps;
 }
 
 // Runs one control mode whose control block has been filled in the pinned
@@ -889,6 +909,7 @@ void release(gabp_handle h) {
   cudaFree(B.m64[0]); cudaFree(B.m64[1]);
   cudaFree(B.m32[0]); cudaFree(B.m32[1]); cudaFree(B.e[0]); cudaFree(B.e[1]);
   cudaFree(B.e32[0]); cudaFree(B.e32[1]);
+  cudaFree(B.ait32);
   cudaFree(B.c32); cudaFree(B.invP32); cudaFree(B.mon32[0]); cudaFree(B.mon32[1]);
   cudaFree(B.tot32[0]); cudaFree(B.tot32[1]);
   cudaFree(B.r64); cudaFree(B.rhs32);

@@ -65,7 +65,7 @@ class GabpStats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("ms_full", ctypes.c_double),
                 ("ms_mean", ctypes.c_double), ("ms_residual", ctypes.c_double),
                 ("ms_other", ctypes.c_double), ("positions_swept", ctypes.c_int64),
-                ("sweeps_wide", ctypes.c_int32), ("reserved_i", ctypes.c_int32)]
+                ("sweeps_wide", ctypes.c_int32), ("aitken_steps", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
