@@ -266,6 +266,33 @@ def test_aitken_on_mixed_inner_solves_csr_poisson3d_32(G, poisson32, kw):
     assert _rel(x, ref) < 1e-8
 
 
+@pytest.mark.parametrize("form", ["grid", "csr"])
+def test_aitken_with_the_bf16_ladder(G, form):
+    """BF16 mean storage with Aitken on the inner solves on the 2-D
+    Laplacian 64 x 64, where the ladder climbs to FP32 storage: the sweeps
+    after the climb take their records too (on the CSR handle through the
+    FP32-storage record phase), and the solve meets 1e-10 and the oracle's
+    solution to 1e-8 with extrapolated steps taken."""
+    dims = [64, 64]
+    m = box_operator(dims, seed=0, laplacian=True)
+    b = W.uniform_rhs(m.n, 5)
+    ref = oracle.gabp(m.row_ptr, m.col, m.val, b, stop=oracle.STOP_RES_REL, max_rounds=400000,
+                      tol=1e-13)["x"]
+    if form == "grid":
+        s = _solver(G, dims, m, precision=G.PREC_MIXED_BF16, aitken=2)
+    else:
+        s = G.Solver.from_csr(m.row_ptr, m.col, m.val, precision=G.PREC_MIXED_BF16, mean_window=-1,
+                              aitken=2)
+    xt, _ = s.solve(torch.tensor(b, device="cuda"), tol=1e-10, max_iter=400000)
+    x = xt.cpu().numpy()
+    st = s.stats()
+    s.close()
+    assert st["status"] == 0
+    assert oracle.residual_inf(m.row_ptr, m.col, m.val, b, x) < 1e-10 * np.abs(b).max()
+    assert _rel(x, ref) < 1e-8
+    assert st["sweeps_wide"] > 0 and st["aitken_steps"] > 0, st
+
+
 @pytest.mark.parametrize("form,schedule", [("grid", 1), ("csr", 0)])
 def test_aitken_on_mixed_inner_solves_saves_sweeps_poisson3d_64(G, form, schedule):
     """3-D Poisson 64^3 (grid handle, red-black; CSR handle, synchronous):
