@@ -76,13 +76,13 @@ BYTES_GRID = {
 TRAFFIC = {
     "mean": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "b04585fc006c2b3e",
              "bytes_per_launch": 171.9e6},
-    "mean_win": {"sources": ("gabp_window.cu", "gabp_device.cuh"), "sha": "0d6fa0b610bf05c9",
+    "mean_win": {"sources": ("gabp_window.cu", "gabp_device.cuh"), "sha": "b584bc04817140ca",
                  "bytes_per_launch": 121.1e6},
-    "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "ad7a6594e4d267a5",
-                       "bytes_per_launch": 203.4e6},
-    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "7c7a265e86d6a78a",
+    "full32_inplace": {"sources": ("gabp_kernels.cu", "gabp_device.cuh"), "sha": "fe67705660b1de65",
+                       "bytes_per_launch": 203.5e6},
+    "dense_mean": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "60dde3d85b4a733b",
                    "bytes_per_pair": 23.14},
-    "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "7c7a265e86d6a78a",
+    "dense_mean_serial": {"sources": ("gabp_dense.cu", "gabp_device.cuh"), "sha": "60dde3d85b4a733b",
                           "bytes_per_pair": 15.16},
 }
 

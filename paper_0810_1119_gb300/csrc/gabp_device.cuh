@@ -283,6 +283,7 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
       c.inv_rn = 1.0 / rn;
       c.inner_goal = c.batched ? c.inner_tol : fmax(c.inner_tol, 0.3 * c.thr / fmax(rn, DBL_MIN));
       c.k = 0;
+      c.ait_k0 = 0;
       c.stall = 0;
       c.prev_dd = INFINITY;
       c.best_dd = INFINITY;
@@ -302,7 +303,13 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
         c.par_e ^= 1;
       } else if (kind == CK_SWEEP32) {
         c.sweeps_full++;
-        if (c.pending_freeze) { c.frozen = 1; c.pending_freeze = 0; c.par_e ^= 1; c.e_slots = 1; }
+        if (c.pending_freeze) {
+          c.frozen = 1;
+          c.pending_freeze = 0;
+          c.par_e ^= 1;
+          c.e_slots = 1;
+          c.ait_k0 = c.k + 1;   // this full sweep's number: the records start after it
+        }
         else c.par_m ^= 1;
       } else {
         c.sweeps_mean++;
@@ -376,11 +383,12 @@ __device__ void control(Ctl &c, DevScalars *red, int kind) {
         c.phase = PH_REFINE;
         if (c.ait_mixed) {
           // Aitken on the inner solve's means: the widest record spacing s
-          // with 6 s <= k (three records, the oldest past the first sixth)
+          // with 6 s <= k whose three latest records were all taken by mean
+          // sweeps (after the freeze sweep ait_k0 of the first inner solve)
           int sel = -1;
           for (int j = kAitLevels - 1; j >= 0; --j) {
             const int s = 1 << (kAitMinLevel + j);
-            if (6 * s <= c.k) { sel = j; break; }
+            if (6 * s <= c.k && ((c.k >> (kAitMinLevel + j)) - 2) * s > c.ait_k0) { sel = j; break; }
           }
           c.ait_level = sel;
           c.ait_m = sel >= 0 ? c.k >> (kAitMinLevel + sel) : 0;

@@ -117,13 +117,16 @@ struct Ctl {
   // right-hand side): the mean sweeps record d every 2^j sweeps
   // (j = kAitMinLevel ...) of an inner solve, the last three records per
   // level; at the end of an inner solve of k sweeps the controller picks the
-  // widest spacing s with 6 s <= k (level ait_level, m = k / s records), and
+  // widest spacing s with 6 s <= k whose last three records come after sweep
+  // ait_k0 (level ait_level, m = k / s records), and
   // the refinement update extrapolates the last three (ait_use) unless the
   // last extrapolated step failed to shrink the residual by 10 % (ait_ok = 0).
   // ait_md: max |d| of the last sweep.
   // ait_rec: the records are taken by a kernel of their own (CSR handles),
   // so the controller picks PH_MEANR / PH_MEANWR for sweeps 64, 128, ...
-  int ait_mixed, ait_rec, ait_use, ait_level, ait_m, ait_ok, ait_steps;
+  // ait_k0: the number of the freeze sweep within the first inner solve
+  // (full sweeps take no records; later inner solves have none).
+  int ait_mixed, ait_rec, ait_use, ait_level, ait_m, ait_ok, ait_steps, ait_k0;
   double ait_md;
   double best_rn;               // smallest FP64 residual of the refinement so far
   int outer_stall;              // refinement steps since best_rn last halved
