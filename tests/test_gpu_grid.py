@@ -5,7 +5,11 @@ half grids (the box's colour classes) with one plane per direction.  FP64
 rounds of the synchronous schedule are compared with the oracle's Alg. 2 on
 the same CSR, and those of the red-black schedule with the oracle's serial
 schedule visiting class 0 ((x + y + z) even) before class 1, per round to
-1e-12; solves with the oracle's solution and with the CSR path.
+1e-12; solves with the oracle's solution and with the CSR path.  Also the
+BF16 precision ladder and Aitken's Delta^2 on the inner solves of mixed
+solves (Steffensen's iteration in residual form), on grid and CSR handles of
+box operators: solutions against the oracle's, sweeps against the plain
+solve.
 """
 import numpy as np
 import pytest
